@@ -1,0 +1,436 @@
+"""FP64 CPU oracle for the pressure step of the low-Mach two-phase solver of
+Dalla Barba, Scapin, Rosti, Picano and Brandt, "An interface capturing method
+for liquid-gas flows at low-Mach number" (arXiv:2005.11806).
+
+TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  It shares no code
+with the CUDA path: it imports numpy/scipy only, and nothing from the product
+package.  It is deliberately plain and slow: numpy array expressions, numpy's
+FFT and dense/sparse library solves as single steps, no fusion, no blocking.
+
+Discretisation (Sec. 3, "Numerical methodology": a Cartesian marker-and-cell
+grid, velocities on faces, scalar fields at cell centres):
+
+* arrays are ``[nz][ny][nx]``, x fastest;
+* ``u[k, j, i]`` lives on the x-face at ``i - 1/2`` (periodic in x),
+  ``v[k, j, i]`` on the y-face at ``j - 1/2`` (periodic in y),
+  ``w[k, j, i]`` (shape ``[nz + 1][ny][nx]``) on the z-face ``k``; faces 0 and
+  nz are the no-penetration walls;
+* z may be stretched: ``zf`` holds the nz + 1 face coordinates, the cell
+  centre is the midpoint of its faces, ``dzf[k]`` is the width of cell k and
+  ``dzc[k]`` the distance between the centres that share the z-face k.
+
+Readings of points the paper leaves open (each one listed in the design doc):
+
+* the density on a face is the arithmetic mean of its two cells, so the
+  centred form of ``u . grad(rho)`` used by Method III is
+  ``D(rho_f u) - rho_c D u``;
+* the pressure satisfies homogeneous Neumann conditions at the z walls and is
+  periodic in x and y; it is fixed to zero volume-weighted mean;
+* the divergence target ``S`` (Eq. 34) is made compatible with the closed box
+  by removing its volume-weighted mean;
+* Algorithm 1 is read as: iteration s uses ``u^s`` (``u^0 = u*``) to produce
+  ``p^{s+1}`` and ``u^{s+1}``; it stops on the relative L2 norm of
+  ``D u^{s+1} - S_c`` (the paper's L1 sum is reported too).
+
+Pins (tests/test_oracle_pins.py): the single-mode closed form, dense LU
+solves of systems assembled entry by entry, exact-linear-field identities of
+D and G, the projection invariants, the constant-density reduction and the
+agreement of Algorithm 1 with the direct sparse solve.  ``adjoint_*`` is
+pinned by central finite differences of ``projection_direct`` and by the
+dot-product identity.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+__all__ = [
+    "Grid", "mixture_density", "divergence", "gradient", "face_density",
+    "volume_mean", "laplacian", "solve_constant", "method3", "projection_direct",
+    "correct_velocity", "adjoint_direct", "adjoint_method3",
+]
+
+
+class Grid:
+    """MAC grid: nx x ny cells of uniform width in x and y, nz cells in z with
+    face coordinates ``zf`` (length nz + 1, increasing).  Sec. 3 uses uniform
+    spacing; a stretched ``zf`` is allowed."""
+
+    def __init__(self, nx, ny, nz, lx, ly, zf):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.lx, self.ly = float(lx), float(ly)
+        zf = np.asarray(zf, dtype=np.float64)
+        if zf.shape != (self.nz + 1,) or np.any(np.diff(zf) <= 0):
+            raise ValueError("zf must hold nz + 1 increasing face coordinates")
+        self.zf = zf
+        self.dx = self.lx / self.nx
+        self.dy = self.ly / self.ny
+        self.dzf = zf[1:] - zf[:-1]                     # width of cell k
+        self.zc = 0.5 * (zf[1:] + zf[:-1])              # centre of cell k
+        self.dzc = np.zeros(self.nz + 1)                # centre distance across z-face k
+        self.dzc[1:-1] = self.zc[1:] - self.zc[:-1]
+        self.lz = zf[-1] - zf[0]
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def cell_volume(self):
+        """Delta V of every cell, broadcastable to the cell shape."""
+        return (self.dx * self.dy * self.dzf)[:, None, None]
+
+
+def mixture_density(phi, rho_g, rho_l):
+    """Eq. 22 with the indicator H replaced by the cell volume fraction Phi:
+    rho = rho_g Phi + rho_l (1 - Phi)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    return rho_g * phi + rho_l * (1.0 - phi)
+
+
+def divergence(g, u, v, w):
+    """Discrete divergence D: faces -> cell centres (Sec. 3, MAC grid)."""
+    return ((np.roll(u, -1, axis=2) - u) / g.dx
+            + (np.roll(v, -1, axis=1) - v) / g.dy
+            + (w[1:] - w[:-1]) / g.dzf[:, None, None])
+
+
+def gradient(g, p):
+    """Discrete gradient G: cell centres -> faces.  The wall z-faces carry a
+    zero gradient (homogeneous Neumann pressure at no-penetration walls)."""
+    gx = (p - np.roll(p, 1, axis=2)) / g.dx
+    gy = (p - np.roll(p, 1, axis=1)) / g.dy
+    gz = np.zeros((g.nz + 1, g.ny, g.nx))
+    gz[1:-1] = (p[1:] - p[:-1]) / g.dzc[1:-1, None, None]
+    return gx, gy, gz
+
+
+def face_density(g, rho):
+    """Density on the faces: arithmetic mean of the two cells sharing the face.
+    The wall z-faces take the value of their only cell (it never enters: both
+    G p and the velocity vanish there)."""
+    rx = 0.5 * (rho + np.roll(rho, 1, axis=2))
+    ry = 0.5 * (rho + np.roll(rho, 1, axis=1))
+    rz = np.empty((g.nz + 1, g.ny, g.nx))
+    rz[1:-1] = 0.5 * (rho[1:] + rho[:-1])
+    rz[0] = rho[0]
+    rz[-1] = rho[-1]
+    return rx, ry, rz
+
+
+def volume_mean(g, f):
+    """Volume-weighted mean of a cell field."""
+    dv = g.cell_volume()
+    return float(np.sum(f * dv) / (np.sum(dv) * g.nx * g.ny))
+
+
+def laplacian(g, p):
+    """L = D G, the compact 7-point operator."""
+    return divergence(g, *gradient(g, p))
+
+
+def _z_coefficients(g):
+    """Sub- and super-diagonal of the z part of L in one column:
+    (L_z p)_k = a_k p_{k-1} - (a_k + c_k) p_k + c_k p_{k+1}, with no flux
+    through the walls."""
+    a = np.zeros(g.nz)
+    c = np.zeros(g.nz)
+    a[1:] = 1.0 / (g.dzc[1:-1] * g.dzf[1:])
+    c[:-1] = 1.0 / (g.dzc[1:-1] * g.dzf[:-1])
+    return a, c
+
+
+def solve_constant(g, f):
+    """Constant-coefficient pressure solve by the eigenexpansion method
+    (Sec. 3.3.1: homogeneous pressure boundary conditions, solved exactly).
+
+    Returns the zero-mean p with ``D G p = f - <f>_V``.  Steps: real DFT in x,
+    complex DFT in y (numpy's FFT), one tridiagonal system per (kx, ky) along
+    z with the eigenvalues of the periodic second difference on its diagonal
+    (Thomas algorithm), the singular (0, 0) column by a bordered dense solve
+    that fixes its zero weighted mean, then the inverse DFTs.
+    """
+    nx, ny, nz = g.nx, g.ny, g.nz
+    fc = f - volume_mean(g, f)
+    fh = np.fft.rfft2(fc, axes=(1, 2))                  # [nz, ny, nx//2 + 1]
+    kx = np.arange(nx // 2 + 1)
+    ky = np.arange(ny)
+    lam = (-4.0 / g.dx ** 2 * np.sin(np.pi * kx / nx) ** 2)[None, :] \
+        + (-4.0 / g.dy ** 2 * np.sin(np.pi * ky / ny) ** 2)[:, None]
+    a, c = _z_coefficients(g)
+    lam_safe = lam.copy()
+    lam_safe[0, 0] = -1.0                               # replaced below
+    # Thomas algorithm, vectorised over all (kx, ky) columns.
+    dprime = np.empty((nz,) + lam.shape)
+    y = np.empty_like(fh)
+    dprime[0] = -(a[0] + c[0]) + lam_safe
+    y[0] = fh[0]
+    for k in range(1, nz):
+        m = a[k] / dprime[k - 1]
+        dprime[k] = (-(a[k] + c[k]) + lam_safe) - m * c[k - 1]
+        y[k] = fh[k] - m * y[k - 1]
+    ph = np.empty_like(fh)
+    ph[nz - 1] = y[nz - 1] / dprime[nz - 1]
+    for k in range(nz - 2, -1, -1):
+        ph[k] = (y[k] - c[k] * ph[k + 1]) / dprime[k]
+    # (kx, ky) = (0, 0): L_z x + mu 1 = f, sum_k dzf_k x_k = 0.
+    lz = np.zeros((nz + 1, nz + 1))
+    for k in range(nz):
+        lz[k, k] = -(a[k] + c[k])
+        if k > 0:
+            lz[k, k - 1] = a[k]
+        if k < nz - 1:
+            lz[k, k + 1] = c[k]
+        lz[k, nz] = 1.0
+        lz[nz, k] = g.dzf[k]
+    rhs = np.zeros(nz + 1, dtype=np.complex128)
+    rhs[:nz] = fh[:, 0, 0]
+    ph[:, 0, 0] = np.linalg.solve(lz, rhs)[:nz]
+    p = np.fft.irfft2(ph, s=(ny, nx), axes=(1, 2))
+    return p - volume_mean(g, p)
+
+
+def correct_velocity(g, us, vs, ws, rho, p, dt):
+    """Correction step, Eq. (eqn:corr): u = u* - (dt / rho_f) G p."""
+    rx, ry, rz = face_density(g, rho)
+    gx, gy, gz = gradient(g, p)
+    return us - dt * gx / rx, vs - dt * gy / ry, ws - dt * gz / rz
+
+
+def method3(g, us, vs, ws, rho, S, dt, rtol=1e-13, maxit=1000):
+    """Method III, Algorithm 1 (Sec. 3.3.1), in the paper's order.
+
+    The two loop-invariant terms of Eq. (eqn:new_poisson), D(rho u*) and
+    rho D u^{n+1} with D u^{n+1} = S_c, are formed once before the loop, as
+    the paper notes.  Each pass builds the right-hand side with the current
+    ``u^s . grad(rho)`` (centred: ``D(rho_f u^s) - rho_c D u^s``), solves the
+    constant-coefficient equation, applies the correction step and evaluates
+    the residual ``D u^{s+1} - S_c``.
+
+    Returns ``(p, u, v, w, info)`` with ``info`` holding the iteration count,
+    the relative L2 residual history and the paper's L1 sum.
+    """
+    Sc = S - volume_mean(g, S)
+    rx, ry, rz = face_density(g, rho)
+    pre = divergence(g, rx * us, ry * vs, rz * ws) - rho * Sc
+    res0 = np.linalg.norm((divergence(g, us, vs, ws) - Sc).ravel())
+    u, v, w = us, vs, ws
+    p = np.zeros(g.shape)
+    hist = []
+    eps_l1 = float(np.sum(np.abs(divergence(g, us, vs, ws) - Sc)))
+    if res0 == 0.0:
+        return p, u, v, w, {"iters": 0, "res_hist": [], "res_l1_sum": eps_l1,
+                            "res0": 0.0, "mean_S_removed": volume_mean(g, S)}
+    s = 0
+    while s < maxit:
+        conv = divergence(g, rx * u, ry * v, rz * w) - rho * divergence(g, u, v, w)
+        rhs = (pre - conv) / dt
+        p = solve_constant(g, rhs)
+        u, v, w = correct_velocity(g, us, vs, ws, rho, p, dt)
+        d = divergence(g, u, v, w) - Sc
+        eps_l1 = float(np.sum(np.abs(d)))
+        hist.append(float(np.linalg.norm(d.ravel()) / res0))
+        s += 1
+        if hist[-1] <= rtol:
+            break
+    info = {"iters": s, "res_hist": hist, "res_l1_sum": eps_l1, "res0": float(res0),
+            "mean_S_removed": volume_mean(g, S)}
+    return p, u, v, w, info
+
+
+# ---------------------------------------------------------------------------
+# Direct solve of the variable-coefficient equation (small grids)
+# ---------------------------------------------------------------------------
+
+def _index(g):
+    return np.arange(g.nx * g.ny * g.nz).reshape(g.shape)
+
+
+def _sparse_operators(g):
+    """Sparse D (cells x faces) and G (faces x cells).  Face unknowns are
+    ordered [u (nz*ny*nx), v (nz*ny*nx), w (nz+1)*ny*nx]."""
+    nx, ny, nz = g.nx, g.ny, g.nz
+    nc = nx * ny * nz
+    cid = _index(g)
+    nu = nc
+    nw = (nz + 1) * ny * nx
+    fid_u = cid
+    fid_v = nu + cid
+    fid_w = 2 * nu + np.arange(nw).reshape(nz + 1, ny, nx)
+    rows, cols, vals = [], [], []
+
+    def add(r, cidx, val):
+        rows.append(r.ravel()); cols.append(cidx.ravel())
+        vals.append(np.broadcast_to(val, r.shape).ravel())
+
+    # D: (u_{i+1} - u_i)/dx + (v_{j+1} - v_j)/dy + (w_{k+1} - w_k)/dzf_k
+    add(cid, np.roll(fid_u, -1, axis=2), 1.0 / g.dx)
+    add(cid, fid_u, -1.0 / g.dx)
+    add(cid, np.roll(fid_v, -1, axis=1), 1.0 / g.dy)
+    add(cid, fid_v, -1.0 / g.dy)
+    inv_dzf = np.broadcast_to((1.0 / g.dzf)[:, None, None], g.shape)
+    add(cid, fid_w[1:], inv_dzf)
+    add(cid, fid_w[:-1], -inv_dzf)
+    D = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(nc, 2 * nu + nw))
+    rows, cols, vals = [], [], []
+    # G: x-face i: (p_i - p_{i-1})/dx; y likewise; interior z-face k:
+    # (p_k - p_{k-1})/dzc_k; wall z-faces: no rows (zero gradient).
+    add(fid_u, cid, 1.0 / g.dx)
+    add(fid_u, np.roll(cid, 1, axis=2), -1.0 / g.dx)
+    add(fid_v, cid, 1.0 / g.dy)
+    add(fid_v, np.roll(cid, 1, axis=1), -1.0 / g.dy)
+    inv_dzc = np.broadcast_to((1.0 / g.dzc[1:-1])[:, None, None], (nz - 1, ny, nx))
+    add(fid_w[1:-1], cid[1:], inv_dzc)
+    add(fid_w[1:-1], cid[:-1], -inv_dzc)
+    G = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(2 * nu + nw, nc))
+    return D, G
+
+
+def _face_vector(u, v, w):
+    return np.concatenate([u.ravel(), v.ravel(), w.ravel()])
+
+
+def _split_faces(g, x):
+    nc = g.nx * g.ny * g.nz
+    return (x[:nc].reshape(g.shape), x[nc:2 * nc].reshape(g.shape),
+            x[2 * nc:].reshape(g.nz + 1, g.ny, g.nx))
+
+
+def _beta_vector(g, rho):
+    rx, ry, rz = face_density(g, rho)
+    return 1.0 / _face_vector(rx, ry, rz)
+
+
+def _bordered_solve(g, A, rhs):
+    """Solve A p = rhs - mu (mu a scalar) with sum dV p = 0.  A has the
+    constant vector as null vector; mu takes up any incompatible part."""
+    n = A.shape[0]
+    dv = np.broadcast_to(g.cell_volume(), g.shape).ravel()
+    K = sp.bmat([[A, sp.csr_matrix(np.ones((n, 1)))],
+                 [sp.csr_matrix(dv[None, :]), None]], format="csc")
+    sol = spla.spsolve(K, np.concatenate([rhs, [0.0]]))
+    return sol[:n]
+
+
+def projection_direct(g, us, vs, ws, rho, S, dt):
+    """The plain definition the projection reaches: the zero-mean p with
+    D(rho_f^{-1} G p) = (D u* - S_c)/dt (Eq. lap_p with the target
+    divergence S_c), and u^{n+1} = u* - dt rho_f^{-1} G p (Eq. corr).
+    Sparse direct solve; for grids up to about 24^3."""
+    D, G = _sparse_operators(g)
+    beta = _beta_vector(g, rho)
+    A = (D @ sp.diags(beta) @ G).tocsr()
+    Sc = S - volume_mean(g, S)
+    rhs = (D @ _face_vector(us, vs, ws) - Sc.ravel()) / dt
+    p = _bordered_solve(g, A, rhs)
+    un = _face_vector(us, vs, ws) - dt * beta * (G @ p)
+    u, v, w = _split_faces(g, un)
+    return p.reshape(g.shape), u, v, w
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of the converged projection
+# ---------------------------------------------------------------------------
+#
+# With beta = 1/rho_f (face-wise), B = diag(beta), A = D B G and the
+# gauge-fixed solve of A p = (D u* - S_c)/dt, the projection is
+#     u^{n+1} = u* - dt B G p.
+# For an upstream gradient g = dL/du^{n+1} (wall z-faces excluded: they are
+# not unknowns, w = 0 there), implicit differentiation gives
+#     g_u*   = g - D^T lambda,        A^T lambda = G^T B g,  sum(lambda) = 0,
+#     g_beta = -dt (G p) * g_u*       (face-wise),
+#     g_rho  = sum over the faces of a cell of g_beta * (-beta^2 / 2)
+# (beta_f = 2/(rho_a + rho_b) on interior faces; wall faces do not depend on
+# rho).  rho_c's role as the scaling inside Algorithm 1 does not change the
+# fixed point, so it contributes nothing.
+
+
+def _zero_walls(gw):
+    gw = np.array(gw, dtype=np.float64, copy=True)
+    gw[0] = 0.0
+    gw[-1] = 0.0
+    return gw
+
+
+def _bordered_solve_transposed(g, A, rhs):
+    """Solve A^T x = rhs with sum(x) = 0.  A^T has the volume vector as null
+    vector and the constant vector as left null vector, so a compatible rhs
+    has zero plain sum; the bordering scalar takes up round-off."""
+    n = A.shape[0]
+    dv = np.broadcast_to(g.cell_volume(), g.shape).ravel()
+    K = sp.bmat([[A.T.tocsr(), sp.csr_matrix(dv[:, None])],
+                 [sp.csr_matrix(np.ones((1, n))), None]], format="csc")
+    sol = spla.spsolve(K, np.concatenate([rhs, [0.0]]))
+    return sol[:n]
+
+
+def _beta_to_rho(g, beta, gbeta):
+    """Pull a face gradient w.r.t. beta_f = 2/(rho_a + rho_b) back to the
+    cells: d beta_f / d rho = -beta_f^2 / 2 for both cells of the face."""
+    bu, bv, bw = _split_faces(g, beta)
+    gu, gv, gw = _split_faces(g, gbeta)
+    tu = -0.5 * bu ** 2 * gu
+    tv = -0.5 * bv ** 2 * gv
+    tw = -0.5 * bw ** 2 * gw
+    tw[0] = 0.0
+    tw[-1] = 0.0
+    # x-face i touches cells i-1 and i; y likewise; z-face k touches k-1, k.
+    out = tu + np.roll(tu, -1, axis=2) + tv + np.roll(tv, -1, axis=1)
+    return out + tw[:-1] + tw[1:]
+
+
+def adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv, gw):
+    """Gradients of L(u^{n+1}) w.r.t. u* and rho_c by implicit
+    differentiation of the plain definition (``projection_direct``), with
+    literal sparse transposes.  Small grids only.  Returns
+    ``(g_us, g_vs, g_ws, g_rho)``; wall entries of ``g_ws`` are zero."""
+    D, G = _sparse_operators(g)
+    beta = _beta_vector(g, rho)
+    A = (D @ sp.diags(beta) @ G).tocsr()
+    Sc = S - volume_mean(g, S)
+    rhs = (D @ _face_vector(us, vs, ws) - Sc.ravel()) / dt
+    p = _bordered_solve(g, A, rhs)
+    gvec = _face_vector(gu, gv, _zero_walls(gw))
+    lam = _bordered_solve_transposed(g, A, G.T @ (beta * gvec))
+    gus = gvec - D.T @ lam
+    u, v, w = _split_faces(g, gus)
+    w = _zero_walls(w)
+    gus = _face_vector(u, v, w)
+    grho = _beta_to_rho(g, beta, -dt * (G @ p) * gus)
+    return u, v, w, grho
+
+
+def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=1000):
+    """The same gradients for any grid size, with Algorithm 1 as the solver.
+
+    With W_c = diag(dzf) on cells and W_f = diag(dzf of the layer) on x/y
+    faces, diag(dzc) on z faces, the discrete operators satisfy
+    D^T = -W_f G W_c^{-1} and G^T = -W_c D W_f^{-1}; hence
+    A^T = W_c A W_c^{-1}, and lambda = W_c mu with
+        A mu = -D(B W_f^{-1} g),
+    which is the projection equation with u* = -dt B W_f^{-1} g and S = 0.
+    Then g_u* = g + W_f G mu (the gauge of mu does not matter).
+    ``p`` is the converged pressure of the forward projection.
+    """
+    gw = _zero_walls(gw)
+    rx, ry, rz = face_density(g, rho)
+    wlay = g.dzf[:, None, None]
+    wz = np.ones(g.nz + 1)
+    wz[1:-1] = g.dzc[1:-1]
+    wz = wz[:, None, None]
+    ya, yb, yc = gu / (rx * wlay), gv / (ry * wlay), gw / (rz * wz)
+    zero = np.zeros(g.shape)
+    mu, _, _, _, info_adj = method3(g, -dt * ya, -dt * yb, -dt * yc, rho, zero, dt,
+                                    rtol=rtol, maxit=maxit)
+    gx, gy, gz = gradient(g, mu)
+    gus, gvs, gws = gu + wlay * gx, gv + wlay * gy, gw + wz * gz
+    gws = _zero_walls(gws)
+    p, _, _, _, info_fwd = method3(g, us, vs, ws, rho, S, dt, rtol=rtol, maxit=maxit)
+    px, py, pz = gradient(g, p)
+    gbeta = _face_vector(-dt * px * gus, -dt * py * gvs, -dt * pz * gws)
+    beta = 1.0 / _face_vector(rx, ry, rz)
+    grho = _beta_to_rho(g, beta, gbeta)
+    return gus, gvs, gws, grho, {"fwd": info_fwd, "adj": info_adj}

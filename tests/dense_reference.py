@@ -1,0 +1,83 @@
+"""Entry-by-entry assembly of the discrete operators with plain Python loops,
+written directly from the stencil definitions (Sec. 3 MAC grid), for dense
+LU pins on tiny grids.  Independent of the oracle's array code."""
+import numpy as np
+
+
+def metrics(nz, zf):
+    dzf = [zf[k + 1] - zf[k] for k in range(nz)]
+    zc = [0.5 * (zf[k + 1] + zf[k]) for k in range(nz)]
+    return dzf, zc
+
+
+def assemble_variable(nx, ny, nz, lx, ly, zf, rho):
+    """Matrix of p -> D(beta G p) with beta = 2/(rho_a + rho_b) on each face,
+    zero flux through the z walls, periodic x and y.  rho=None means beta=1."""
+    dx, dy = lx / nx, ly / ny
+    dzf, zc = metrics(nz, zf)
+    n = nx * ny * nz
+
+    def idx(i, j, k):
+        return (k * ny + (j % ny)) * nx + (i % nx)
+
+    def beta(c1, c2):
+        if rho is None:
+            return 1.0
+        return 2.0 / (rho[c1] + rho[c2])
+
+    A = np.zeros((n, n))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                r = idx(i, j, k)
+                cell = (k, j, i)
+                # x faces: right face between (i, i+1), left face between (i-1, i)
+                for di in (+1, -1):
+                    nb = (k, j, (i + di) % nx)
+                    b = beta(cell, nb) / (dx * dx)
+                    A[r, idx(i + di, j, k)] += b
+                    A[r, r] -= b
+                for dj in (+1, -1):
+                    nb = (k, (j + dj) % ny, i)
+                    b = beta(cell, nb) / (dy * dy)
+                    A[r, idx(i, j + dj, k)] += b
+                    A[r, r] -= b
+                for dk in (+1, -1):
+                    kk = k + dk
+                    if kk < 0 or kk >= nz:
+                        continue  # wall: no flux
+                    nb = (kk, j, i)
+                    dist = abs(zc[kk] - zc[k])
+                    b = beta(cell, nb) / (dist * dzf[k])
+                    A[r, idx(i, j, kk)] += b
+                    A[r, r] -= b
+    return A
+
+
+def bordered_solve(A, rhs, weights):
+    """Solve A x + mu 1 = rhs with weights . x = 0 (dense LU)."""
+    n = A.shape[0]
+    K = np.zeros((n + 1, n + 1))
+    K[:n, :n] = A
+    K[:n, n] = 1.0
+    K[n, :n] = weights
+    sol = np.linalg.solve(K, np.concatenate([rhs, [0.0]]))
+    return sol[:n]
+
+
+def cell_weights(nx, ny, nz, zf):
+    dzf, _ = metrics(nz, zf)
+    return np.repeat(np.array(dzf), nx * ny)
+
+
+def divergence_loops(nx, ny, nz, lx, ly, zf, u, v, w):
+    dx, dy = lx / nx, ly / ny
+    dzf, _ = metrics(nz, zf)
+    out = np.zeros((nz, ny, nx))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                out[k, j, i] = ((u[k, j, (i + 1) % nx] - u[k, j, i]) / dx
+                                + (v[k, (j + 1) % ny, i] - v[k, j, i]) / dy
+                                + (w[k + 1, j, i] - w[k, j, i]) / dzf[k])
+    return out

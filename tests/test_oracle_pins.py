@@ -1,0 +1,285 @@
+"""Pins of the CPU oracle against what the mathematics fixes (no GPU).
+
+Each test names the plausible mistake it would catch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.pressure_oracle as orc
+from paper_2005_11806_gb300 import workloads as wl
+from tests import dense_reference as dr
+
+
+def _grid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, beta=None):
+    zf = wl.uniform_zfaces(nz, lz) if beta is None else wl.tanh_zfaces(nz, lz, beta)
+    return orc.Grid(nx, ny, nz, lx, ly, zf)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+# --- constant-coefficient solve -------------------------------------------
+
+@pytest.mark.parametrize("dims,mode,phase", [
+    ((32, 32, 32), (3, 5, 2), (0.0, 0.0)),
+    ((24, 20, 16), (3, 2, 1), (0.3, -1.1)),
+    ((17, 12, 9), (4, 5, 7), (0.7, 0.2)),      # odd nx, Nyquist-free
+])
+def test_single_mode_closed_form(dims, mode, phase):
+    """Discrete eigenmode: L f = lambda f exactly, so p = f / lambda.  Catches
+    wrong modified wavenumbers, a swapped axis, a wrong Neumann end row or a
+    wrong DFT sign/normalisation."""
+    nx, ny, nz = dims
+    lx, ly, lz = 1.0, 1.5, 0.7
+    g = _grid(nx, ny, nz, lx, ly, lz)
+    a, b, c = mode
+    i = np.arange(nx)[None, None, :]
+    j = np.arange(ny)[None, :, None]
+    k = np.arange(nz)[:, None, None]
+    f = (np.cos(2 * np.pi * a * i / nx + phase[0]) * np.cos(2 * np.pi * b * j / ny + phase[1])
+         * np.cos(np.pi * c * (k + 0.5) / nz))
+    dx, dy, dz = lx / nx, ly / ny, lz / nz
+    lam = -(4 / dx ** 2 * math.sin(math.pi * a / nx) ** 2 + 4 / dy ** 2 * math.sin(math.pi * b / ny) ** 2
+            + 4 / dz ** 2 * math.sin(math.pi * c / (2 * nz)) ** 2)
+    p = orc.solve_constant(g, f)
+    assert _rel(p, f / lam) < 1e-12
+    assert _rel(orc.laplacian(g, f), lam * f) < 1e-12
+
+
+@pytest.mark.parametrize("dims,beta", [((8, 8, 8), None), ((8, 8, 8), 1.5), ((6, 5, 7), 2.0)])
+def test_constant_solve_vs_dense_lu(dims, beta):
+    """Dense LU of the 7-point matrix assembled entry by entry; catches any
+    error in the z coefficients on stretched grids and in the zero-mode gauge."""
+    nx, ny, nz = dims
+    lx, ly, lz = 1.0, 0.8, 1.3
+    g = _grid(nx, ny, nz, lx, ly, lz, beta)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal(g.shape)
+    A = dr.assemble_variable(nx, ny, nz, lx, ly, g.zf, None)
+    wts = dr.cell_weights(nx, ny, nz, g.zf)
+    fc = f.ravel() - np.dot(wts, f.ravel()) / wts.sum()
+    p_lu = dr.bordered_solve(A, fc, wts).reshape(g.shape)
+    p = orc.solve_constant(g, f)
+    assert _rel(p, p_lu) < 1e-12
+    # residual of the 7-point equation, evaluated with the assembled matrix
+    assert np.linalg.norm(A @ p.ravel() - fc) / np.linalg.norm(fc) < 1e-12
+
+
+def test_operator_identities_stretched():
+    """Linear fields: D of w = z_face is exactly 1, G of p = z_centre is
+    exactly 1 on interior z faces and 0 on the walls; G of a constant is 0.
+    Catches dzf/dzc mix-ups and an off-by-one face index."""
+    g = _grid(6, 5, 9, beta=1.5)
+    zero = np.zeros(g.shape)
+    w = np.broadcast_to(g.zf[:, None, None], (g.nz + 1, g.ny, g.nx)).copy()
+    assert np.allclose(orc.divergence(g, zero, zero, w), 1.0, rtol=0, atol=1e-12)
+    p = np.broadcast_to(g.zc[:, None, None], g.shape).copy()
+    gx, gy, gz = orc.gradient(g, p)
+    assert np.allclose(gz[1:-1], 1.0, atol=1e-12) and np.all(gz[0] == 0) and np.all(gz[-1] == 0)
+    assert np.allclose(gx, 0) and np.allclose(gy, 0)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(g.shape)
+    v = rng.standard_normal(g.shape)
+    w = rng.standard_normal((g.nz + 1, g.ny, g.nx))
+    ref = dr.divergence_loops(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, u, v, w)
+    assert np.allclose(orc.divergence(g, u, v, w), ref, rtol=0, atol=1e-10)
+
+
+def test_summation_by_parts_weights():
+    """sum_f W_f (G p) y = -sum_c W_c p (D y) for y with no wall flux: the
+    weighted transpose relation D^T = -W_f G W_c^{-1} used by the adjoint."""
+    g = _grid(5, 6, 7, beta=2.0)
+    rng = np.random.default_rng(11)
+    p = rng.standard_normal(g.shape)
+    yu, yv = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    yw = rng.standard_normal((g.nz + 1, g.ny, g.nx))
+    yw[0] = yw[-1] = 0
+    gx, gy, gz = orc.gradient(g, p)
+    wl_ = g.dzf[:, None, None]
+    wz = np.ones(g.nz + 1); wz[1:-1] = g.dzc[1:-1]
+    lhs = np.sum(wl_ * gx * yu) + np.sum(wl_ * gy * yv) + np.sum(wz[:, None, None] * gz * yw)
+    rhs = -np.sum(wl_ * p * orc.divergence(g, yu, yv, yw))
+    assert abs(lhs - rhs) < 1e-10 * abs(rhs)
+
+
+# --- variable-density projection ------------------------------------------
+
+def _small_case(nx, ny, nz, beta=None, ratio=1000.0, seed=5, S_on=True, lz=1.0):
+    g = _grid(nx, ny, nz, 1.0, ny / nx, lz, beta)
+    rng = np.random.default_rng(seed)
+    phi = np.zeros(g.shape)
+    # a blob of gas plus one interface layer
+    phi[nz // 4:nz // 2 + 1, ny // 4:ny // 2 + 1, nx // 3:2 * nx // 3 + 1] = 1.0
+    phi[nz // 2 + 1, ny // 4:ny // 2, nx // 3:2 * nx // 3] = 0.4
+    rho = orc.mixture_density(phi, 1.0, ratio)
+    us, vs, ws = (rng.standard_normal(g.shape) * 0.1, rng.standard_normal(g.shape) * 0.1,
+                  rng.standard_normal((nz + 1, ny, nx)) * 0.1)
+    ws[0] = ws[-1] = 0
+    S = wl.gas_source(phi) if S_on else np.zeros(g.shape)
+    return g, us, vs, ws, rho, S
+
+
+def test_mixture_density_endpoints():
+    assert np.allclose(orc.mixture_density(np.array([0.0, 1.0, 0.25]), 1.2, 1000.0),
+                       [1000.0, 1.2, 0.25 * 1.2 + 0.75 * 1000.0])
+
+
+@pytest.mark.parametrize("beta", [None, 1.5])
+def test_projection_direct_vs_dense(beta):
+    """Plain definition (sparse) vs a dense LU of D(beta G) assembled entry by
+    entry with arithmetic face densities; catches a harmonic/other face
+    average, a missing 1/dt or a wrong correction sign."""
+    g, us, vs, ws, rho, S = _small_case(5, 4, 6, beta)
+    dt = 1e-3
+    p, u, v, w = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    A = dr.assemble_variable(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, rho)
+    wts = dr.cell_weights(g.nx, g.ny, g.nz, g.zf)
+    Sc = S.ravel() - np.dot(wts, S.ravel()) / wts.sum()
+    div = dr.divergence_loops(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, us, vs, ws).ravel()
+    p_lu = dr.bordered_solve(A, (div - Sc) / dt, wts).reshape(g.shape)
+    assert _rel(p, p_lu) < 1e-11
+    # the corrected field meets the divergence target exactly
+    dnew = dr.divergence_loops(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, u, v, w).ravel()
+    assert np.max(np.abs(dnew - Sc)) < 1e-11 * np.max(np.abs(div))
+
+
+@pytest.mark.parametrize("beta,ratio", [(None, 1000.0), (1.5, 1000.0), (None, 10.0)])
+def test_method3_reaches_direct_solution(beta, ratio):
+    """Algorithm 1 converges to the plain definition (its fixed point is the
+    discrete Eq. lap_p exactly, as the paper states for Method III)."""
+    g, us, vs, ws, rho, S = _small_case(12, 10, 14, beta, ratio)
+    dt = 1e-3
+    p, u, v, w, info = orc.method3(g, us, vs, ws, rho, S, dt, rtol=1e-13)
+    assert info["res_hist"][-1] <= 1e-13
+    pd, ud, vd, wd = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    assert _rel(p, pd) < 1e-10
+    for a, b in ((u, ud), (v, vd), (w, wd)):
+        assert _rel(a, b) < 1e-11
+
+
+def test_projection_invariants():
+    """D u^{n+1} = S_c, sum S_c dV = 0, idempotence and rho_f-weighted
+    orthogonality of the correction (S = 0)."""
+    g, us, vs, ws, rho, S = _small_case(16, 16, 16, 1.5, 1000.0)
+    dt = 1e-3
+    p, u, v, w, info = orc.method3(g, us, vs, ws, rho, S, dt, rtol=1e-13)
+    Sc = S - orc.volume_mean(g, S)
+    assert abs(np.sum(Sc * g.cell_volume())) < 1e-15 * np.sum(np.abs(S))
+    d0 = orc.divergence(g, us, vs, ws)
+    assert np.max(np.abs(orc.divergence(g, u, v, w) - Sc)) < 1e-12 * np.max(np.abs(d0))
+    # S = 0: orthogonality and idempotence
+    zero = np.zeros(g.shape)
+    p1, u1, v1, w1, _ = orc.method3(g, us, vs, ws, rho, zero, dt, rtol=1e-13)
+    rx, ry, rz = orc.face_density(g, rho)
+    wl_ = g.dzf[:, None, None]
+    wz = np.ones(g.nz + 1); wz[1:-1] = g.dzc[1:-1]
+    dot = (np.sum(wl_ * rx * (us - u1) * u1) + np.sum(wl_ * ry * (vs - v1) * v1)
+           + np.sum(wz[:, None, None] * rz * (ws - w1) * w1))
+    scale = np.sum(wl_ * rx * u1 * u1) + np.sum(wl_ * ry * v1 * v1)
+    assert abs(dot) < 1e-11 * scale
+    # u1 already meets the constraint to round-off: projecting it again
+    # (a few passes) leaves it unchanged and gives a vanishing pressure.
+    p2, u2, v2, w2, info2 = orc.method3(g, u1, v1, w1, rho, zero, dt, rtol=1e-10, maxit=3)
+    assert _rel(u2, u1) < 1e-12
+    assert np.max(np.abs(p2)) < 1e-10 * np.max(np.abs(p1))
+
+
+def test_constant_density_one_iteration():
+    """rho = const: Method III's right-hand side is exact after one pass and
+    equals the constant-coefficient projection with p scaled by rho."""
+    g = _grid(16, 12, 10, beta=1.5)
+    rng = np.random.default_rng(2)
+    us, vs = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    ws = rng.standard_normal((g.nz + 1, g.ny, g.nx)); ws[0] = ws[-1] = 0
+    rho = np.full(g.shape, 3.0)
+    S = np.zeros(g.shape)
+    dt = 1e-3
+    p, u, v, wv, info = orc.method3(g, us, vs, ws, rho, S, dt, rtol=1e-12)
+    assert info["iters"] == 1
+    pc = orc.solve_constant(g, orc.divergence(g, us, vs, ws) / dt) * 3.0
+    assert _rel(p, pc) < 1e-12
+
+
+# --- adjoint --------------------------------------------------------------
+
+def _loss(g, us, vs, ws, rho, S, dt, tgt):
+    _, u, v, w = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    return float(np.sum((u - tgt[0]) ** 2) + np.sum((v - tgt[1]) ** 2)
+                 + np.sum((w[1:-1] - tgt[2][1:-1]) ** 2))
+
+
+def test_adjoint_central_differences():
+    """adjoint_direct vs central differences of the projection (eps = 1e-6
+    relative), on entries of u*, v*, w* and rho."""
+    g, us, vs, ws, rho, S = _small_case(5, 4, 6, 2.0, 100.0, seed=9, lz=0.5)
+    dt = 1e-3
+    rng = np.random.default_rng(21)
+    tgt = (rng.standard_normal(g.shape) * 0.1, rng.standard_normal(g.shape) * 0.1,
+           rng.standard_normal((g.nz + 1, g.ny, g.nx)) * 0.1)
+    _, u, v, w = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    gu, gv, gw = 2 * (u - tgt[0]), 2 * (v - tgt[1]), 2 * (w - tgt[2])
+    gus, gvs, gws, grho = orc.adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv, gw)
+    checks = [("u", (1, 2, 3)), ("v", (4, 1, 0)), ("w", (3, 2, 2)), ("rho", (2, 1, 2)),
+              ("rho", (1, 1, 1)), ("rho", (3, 3, 4))]
+    for name, idx in checks:
+        arrs = {"u": us, "v": vs, "w": ws, "rho": rho}
+        base = arrs[name]
+        h = 1e-6 * max(1.0, abs(base[idx]))
+        plus = base.copy(); plus[idx] += h
+        minus = base.copy(); minus[idx] -= h
+        args_p = dict(us=us, vs=vs, ws=ws, rho=rho); args_m = dict(args_p)
+        key = {"u": "us", "v": "vs", "w": "ws", "rho": "rho"}[name]
+        args_p[key] = plus; args_m[key] = minus
+        fd = (_loss(g, args_p["us"], args_p["vs"], args_p["ws"], args_p["rho"], S, dt, tgt)
+              - _loss(g, args_m["us"], args_m["vs"], args_m["ws"], args_m["rho"], S, dt, tgt)) / (2 * h)
+        an = {"u": gus, "v": gvs, "w": gws, "rho": grho}[name][idx]
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * np.max(np.abs(gus))), (name, idx, fd, an)
+
+
+def test_adjoint_dot_product_and_method3():
+    """<P d, g> = <d, P^T g> for the velocity part, and the Algorithm-1 form
+    of the adjoint (weighted transposes) equals the literal sparse one."""
+    g, us, vs, ws, rho, S = _small_case(8, 6, 10, 2.0, 100.0, seed=4, lz=0.5)
+    dt = 1e-3
+    rng = np.random.default_rng(8)
+    gu, gv = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    gw = rng.standard_normal((g.nz + 1, g.ny, g.nx)); gw[0] = gw[-1] = 0
+    du, dv = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    dw = rng.standard_normal((g.nz + 1, g.ny, g.nx)); dw[0] = dw[-1] = 0
+    zero = np.zeros(g.shape)
+    _, pu, pv, pw = orc.projection_direct(g, du, dv, dw, rho, zero, dt)
+    a1, a2, a3, grho = orc.adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv, gw)
+    lhs = np.sum(pu * gu) + np.sum(pv * gv) + np.sum(pw * gw)
+    rhs = np.sum(du * a1) + np.sum(dv * a2) + np.sum(dw * a3)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    b1, b2, b3, brho, _ = orc.adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13)
+    for x, y in ((b1, a1), (b2, a2), (b3, a3), (brho, grho)):
+        assert _rel(x, y) < 1e-9
+
+
+# --- planted mistakes: the pins above must catch them ---------------------
+
+def test_planted_harmonic_face_density_is_caught(monkeypatch):
+    orig = orc.face_density
+
+    def planted(g, rho):
+        rx = 2.0 / (1.0 / rho + 1.0 / np.roll(rho, 1, axis=2))
+        _, ry, rz = orig(g, rho)
+        return rx, ry, rz
+    monkeypatch.setattr(orc, "face_density", planted)
+    with pytest.raises(AssertionError):
+        test_projection_direct_vs_dense(None)
+
+
+def test_planted_gradient_sign_is_caught(monkeypatch):
+    orig = orc.gradient
+
+    def planted(g, p):
+        gx, gy, gz = orig(g, p)
+        return gx, gy, -gz
+    monkeypatch.setattr(orc, "gradient", planted)
+    with pytest.raises(AssertionError):
+        test_single_mode_closed_form((24, 20, 16), (3, 2, 1), (0.3, -1.1))
