@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark of the Method III pressure projection (Algorithm 1 of
+arXiv:2005.11806) on one GB300 per rank.
+
+Workload: 512^3 cells over [0, 2 pi]^3 (x, y periodic; z walls, tanh
+stretching beta = 1.5), 200 seeded gas bubbles of radius 0.05-0.12 at density
+ratio 1000:1, predicted velocity N(0, 0.1), gas divergence source from the
+thermodynamic-pressure rate 1e-2.  One step = mixture density from the volume
+fraction + one pressure_correct to relative residual <= 1e-10 (FP64
+residual), starting from p = 0.  Metric: Gpts/s = cells / step time / 1e9.
+
+Every field is larger than L2 (1.07 GB each), so no flush is needed between
+steps.  Under torchrun every rank solves its own copy (replicas; weak
+scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x FP64 FMA/clk x 2 flop x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--bubbles", type=int, default=200)
+    ap.add_argument("--ratio", type=float, default=1000.0)
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--maxit", type=int, default=50000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--compare-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2005_11806_gb300 import workloads as wl
+    return wl.bubbles_case(n=args.n, nbubbles=args.bubbles, seed=1003, beta=1.5,
+                           rho_g=1.0, rho_l=args.ratio)
+
+
+def config_dict(args, w):
+    return {"workload": f"{w.name}; Method III to rel. residual <= {args.rtol:g}",
+            "grid": [w.nx, w.ny, w.nz], "domain": "[0,2pi]^3, tanh(1.5) z",
+            "bubbles": args.bubbles, "density_ratio": args.ratio, "rtol": args.rtol,
+            "precision": args.precision, "l2": "inputs larger than L2 (1.07 GB per field)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, device_index):
+        self.fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(self.fd)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device_index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)}
+
+
+def algorithmic(kernel, w, precision):
+    """Algorithmic bytes and FP64 flops of one launch of each kernel (see
+    the design doc, 'Kernels and rooflines')."""
+    npts = w.nx * w.ny * w.nz
+    nsp = (w.nx // 2 + 1) * w.ny * w.nz
+    cs = 16 if precision == "fp64" else 8
+    if kernel == "resid_fftx":
+        # reads b, rho, p, cx, cy, cz (FP64); writes the half spectrum
+        return {"bytes": 48 * npts + cs * nsp, "fp64_flops": 24 * npts}
+    if kernel in ("ffty_fwd", "ffty_inv"):
+        return {"bytes": 2 * cs * nsp, "fp64_flops": 0}
+    if kernel == "tridiag_z":
+        return {"bytes": (2 * cs + 8) * nsp, "fp64_flops": 14 * nsp}
+    if kernel == "fftx_inv_update":
+        return {"bytes": cs * nsp + 16 * npts, "fp64_flops": 2 * npts}
+    return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2005_11806_gb300 import pressure as pp
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    t0 = time.time()
+    w = workload(args)
+    gen_s = time.time() - t0
+    npts = w.nx * w.ny * w.nz
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    us, vs, ws, phi, S = T(w.us), T(w.vs), T(w.ws), T(w.phi), T(w.S)
+    rho = torch.empty(w.shape, dtype=torch.float64, device=dev)
+    p = torch.empty_like(rho); u = torch.empty_like(rho); v = torch.empty_like(rho)
+    wo = torch.empty((w.nz + 1, w.ny, w.nx), dtype=torch.float64, device=dev)
+    lz = float(w.zf[-1] - w.zf[0])
+
+    def make_plan(prec):
+        return pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, lz, zfaces=w.zf, precision=prec)
+
+    def step(plan):
+        pp.pressure_mixture_density(plan.handle, phi, w.rho_g, w.rho_l, rho)
+        return pp.pressure_correct(plan.handle, us, vs, ws, rho, S, w.dt, p, u, v, wo,
+                                   rtol=args.rtol, maxit=args.maxit, allow_not_converged=True)
+
+    def timed(plan, steps, warmup, profile):
+        for _ in range(warmup):
+            step(plan)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        pp.pressure_profile_enable(plan.handle, profile)
+        sampler = ClockSampler(local_rank)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = [step(plan) for _ in range(steps)]
+        e1.record()
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        kern, launches = pp.pressure_profile_read(plan.handle)
+        pp.pressure_profile_enable(plan.handle, False)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, kern, launches, clocks
+
+    plan = make_plan(args.precision)
+    ms, infos, kern, launches, clocks = timed(plan, args.steps, args.warmup, True)
+    info = infos[-1]
+    value = world * npts / (ms / 1e3) / 1e9
+
+    # dominant kernel and its roofline (live CUDA-event durations)
+    dom = max(kern.items(), key=lambda kv: kv[1][1])
+    name, (nl, tot_ms) = dom
+    avg_s = tot_ms / nl / 1e3
+    alg = algorithmic(name, w, args.precision) or {"bytes": 0, "fp64_flops": 0}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    t_hbm = alg["bytes"] / (hbm_peak * 1e9)
+    t_alu = alg["fp64_flops"] / (FP64_PEAK_TFLOPS * 1e12)
+    if t_alu > t_hbm:
+        achieved = alg["fp64_flops"] / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s (FP64)", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": None, "kernel": name, "avg_launch_ms": round(avg_s * 1e3, 4),
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz"}
+    else:
+        achieved = alg["bytes"] / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": name,
+                "avg_launch_ms": round(avg_s * 1e3, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    kernels = {k: {"launches": n, "total_ms": round(t, 3), "avg_ms": round(t / n, 4),
+                   "share": round(t / sum(x[1] for x in kern.values()), 4)} for k, (n, t) in kern.items()}
+
+    out = {"metric": "pressure-solve Gpts/s, 512^3: mixed-prec vs FP64 at rel. residual <=1e-10",
+           "value": round(value, 5), "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+           "config": config_dict(args, w),
+           "iterations": info["iters"], "res_final": info["res_final"], "status": info["status"],
+           "per_iteration_gpts": round(world * npts * info["iters"] / (ms / 1e3) / 1e9, 4),
+           "gpu_launches": int(launches), "roofline": roof, "kernels": kernels, "clocks": clocks,
+           "input_gen_s": round(gen_s, 1)}
+
+    # FP64 comparison leg (same input, same tolerance)
+    if not args.no_compare and args.precision == "mixed":
+        plan.close()
+        plan64 = make_plan("fp64")
+        ms64, infos64, kern64, _, clocks64 = timed(plan64, args.compare_steps, 1, True)
+        out["fp64"] = {"value": round(world * npts / (ms64 / 1e3) / 1e9, 5), "ms_per_step": round(ms64, 3),
+                       "iterations": infos64[-1]["iters"], "res_final": infos64[-1]["res_final"],
+                       "steps": args.compare_steps, "warmup": 1, "clocks": clocks64,
+                       "kernels": {k: {"launches": n, "total_ms": round(t, 3)} for k, (n, t) in kern64.items()}}
+        out["speedup_mixed_vs_fp64"] = round(ms64 / ms, 3)
+        plan64.close()
+        plan = make_plan(args.precision)
+
+    # end to end through the C ABI with host (pinned) buffers
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        h = {k: pin(getattr(w, k)) for k in ("us", "vs", "ws", "phi", "S")}
+        hrho = torch.empty(w.shape, dtype=torch.float64).pin_memory()
+        hp = torch.empty_like(hrho).pin_memory(); hu = torch.empty_like(hrho).pin_memory()
+        hv = torch.empty_like(hrho).pin_memory()
+        hw = torch.empty((w.nz + 1, w.ny, w.nx), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            pp.pressure_mixture_density(plan.handle, h["phi"], w.rho_g, w.rho_l, hrho)
+            return pp.pressure_correct(plan.handle, h["us"], h["vs"], h["ws"], hrho, h["S"], w.dt, hp, hu,
+                                       hv, hw, rtol=args.rtol, maxit=args.maxit, allow_not_converged=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        es = time.perf_counter() - t
+        nc, nw = npts * 8, (w.nz + 1) * w.ny * w.nx * 8
+        out["e2e"] = {"value": round(world * npts / es / 1e9, 5), "unit": "Gpts/s",
+                      "h2d_bytes_per_step": 5 * nc + nw, "d2h_bytes_per_step": 4 * nc + nw,
+                      "steps": 1, "warmup": 1}
+    plan.close()
+    return out, w
+
+
+def cpu_baseline(w, iters, passes=1):
+    """The oracle as it stands, timed on this host: `passes` Method III
+    passes on the full workload, scaled to one projection of `iters` passes."""
+    import numpy as np
+
+    import oracle.pressure_oracle as orc
+    rho = orc.mixture_density(w.phi, w.rho_g, w.rho_l)
+    g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf)
+    c0 = time.process_time()
+    t0 = time.perf_counter()
+    orc.method3(g, w.us, w.vs, w.ws, rho, w.S, w.dt, rtol=0.0, maxit=passes)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    npts = w.nx * w.ny * w.nz
+    per_pass = wall / passes
+    return {"value": npts / (per_pass * max(iters, 1)) / 1e9, "unit": "Gpts/s",
+            "cores": max(1, int(round(cpu / wall))), "kind": "oracle",
+            "sample": f"{passes} of {iters} Method III passes of the same 512^3 workload "
+                      f"({per_pass:.1f} s per pass), scaled to the full projection",
+            "host_threads_available": os.cpu_count(), "seconds_per_pass": round(per_pass, 2)}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w = workload(args)
+        iters = int(os.environ.get("PP_REF_ITERS", "0")) or REF_ITERS_DEFAULT
+        samples = []
+        for _ in range(args.warmup + args.steps):
+            samples.append(cpu_baseline(w, iters))
+        vals = [s["value"] for s in samples[args.warmup:]]
+        v = statistics.median(vals)
+        cb = dict(samples[-1])
+        cb["value"] = v
+        print(json.dumps({"impl": "reference", "metric": "pressure-solve Gpts/s, 512^3: mixed-prec vs FP64 "
+                          "at rel. residual <=1e-10", "value": v, "unit": "Gpts/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                          "ms_per_step": 1e3 * w.nx * w.ny * w.nz / (v * 1e9), "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": config_dict(args, w), "cpu_baseline": cb,
+                          "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out, w = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, out["iterations"])
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# Method III passes the benchmark workload needs in FP64 (measured on the GPU
+# path, whose iterates equal the oracle's); used to scale the oracle's
+# per-pass time in the reference arm.
+REF_ITERS_DEFAULT = 1
+
+if __name__ == "__main__":
+    sys.exit(main())

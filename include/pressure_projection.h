@@ -1,0 +1,148 @@
+/*
+ * pressure_projection.h -- C ABI of the GB300 pressure-projection library.
+ *
+ * The library solves the implicit pressure equation of the low-Mach
+ * two-phase solver of Dalla Barba, Scapin, Rosti, Picano and Brandt,
+ * "An interface capturing method for liquid-gas flows at low-Mach number"
+ * (arXiv:2005.11806), Sec. 3.3 "Flow solver":
+ *
+ *   D(rho_f^{-1} G p) = (D u* - S_c) / dt             (Eq. lap_p)
+ *   u^{n+1} = u* - dt rho_f^{-1} G p                 (Eq. corr)
+ *
+ * with Method III (Sec. 3.3.1, Eq. new_poisson, Algorithm 1): a
+ * constant-coefficient recast solved iteratively, each pass calling the
+ * eigenexpansion (FFT in x and y, tridiagonal in z) Poisson solver.
+ *
+ * Grid (Sec. 3): marker-and-cell, x and y periodic with uniform spacing,
+ * z bounded by no-penetration walls (homogeneous Neumann pressure), uniform
+ * or stretched.  Arrays are contiguous, x fastest:
+ *   cell fields  (p, rho, S, phi)  [nz][ny][nx]
+ *   u            [nz][ny][nx]      u[k][j][i] on the x-face at i - 1/2
+ *   v            [nz][ny][nx]      v[k][j][i] on the y-face at j - 1/2
+ *   w            [nz+1][ny][nx]    w[k][j][i] on the z-face k (0 and nz: walls)
+ * The face density is the arithmetic mean of the two adjacent cells.  The
+ * divergence target S is made compatible with the closed box by removing its
+ * volume-weighted mean (S_c = S - <S>_V); p is returned with zero
+ * volume-weighted mean.
+ *
+ * Pointers: every field pointer may be a device pointer or a host pointer
+ * (pageable or pinned); the library tells them apart with
+ * cudaPointerGetAttributes.  Host pointers are staged through device buffers
+ * owned by the plan (allocated on the first call that needs them) with
+ * copies on the plan's stream.  The caller owns every field buffer.
+ * Errors: every call returns a pp_status and never aborts; on error the
+ * output buffers are unspecified.  Plans are not thread-safe; calls on one
+ * plan are serialised on its stream.
+ */
+#ifndef PRESSURE_PROJECTION_H
+#define PRESSURE_PROJECTION_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PP_OK = 0,
+    PP_ERR_INVALID_ARG = 1,   /* bad pointer, size, tolerance or dt */
+    PP_ERR_UNSUPPORTED = 2,   /* grid size with a prime factor > 5, bad bc */
+    PP_ERR_NOT_CONVERGED = 3, /* maxit reached before the tolerance */
+    PP_ERR_NUMERIC = 4,       /* NaN/Inf in the residual */
+    PP_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    PP_ERR_OOM = 6            /* device allocation failed */
+} pp_status;
+
+typedef enum { PP_BC_PERIODIC = 0, PP_BC_WALL = 1 } pp_bc;
+
+typedef enum {
+    PP_FP64 = 0,       /* every step in FP64 */
+    PP_MIXED_FP32 = 1  /* x/y transforms in FP32; residual, z solve and p in FP64 */
+} pp_precision;
+
+typedef struct {
+    int nx, ny, nz;        /* cells; nx, ny have prime factors in {2,3,5}; nx even */
+    double lx, ly, lz;     /* domain lengths */
+    const double* zfaces;  /* host, nz+1 increasing face coordinates, or NULL (uniform) */
+    int bc[3];             /* must be {PP_BC_PERIODIC, PP_BC_PERIODIC, PP_BC_WALL} */
+} pp_grid;
+
+typedef struct {
+    int iters;             /* constant-coefficient solves performed (Algorithm 1's s) */
+    double res0;           /* ||D u* - S_c||_2 */
+    double res_final;      /* ||D u^{n+1} - S_c||_2 / res0 at exit */
+    double res_l1_sum;     /* Algorithm 1's epsilon: sum over cells of |D u^{n+1} - S_c| */
+    double mean_S_removed; /* <S>_V */
+    int status;            /* pp_status of the iteration */
+} pp_info;
+
+typedef struct pp_plan_s* pp_plan;
+
+/* Create a plan for one grid: eigenvalues, twiddles, z coefficients and the
+ * inverse Thomas pivots are computed once; every workspace of the solves is
+ * allocated here.  stream is a cudaStream_t (NULL = legacy default stream).
+ * Follows Sec. 3 (grid) and Sec. 3.3.1 (homogeneous pressure BCs). */
+pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* stream,
+                               pp_plan* out);
+
+pp_status pressure_plan_destroy(pp_plan plan);
+
+/* Constant-coefficient solve by the eigenexpansion method (Sec. 3.3.1):
+ * the zero-mean p with D G p = f - <f>_V.  f, p: cell fields. */
+pp_status pressure_solve(pp_plan plan, const double* f, double* p, pp_info* info);
+
+/* Eq. 22 with H replaced by the volume fraction Phi:
+ * rho = rho_g phi + rho_l (1 - phi).  phi, rho: cell fields. */
+pp_status pressure_mixture_density(pp_plan plan, const double* phi, double rho_g, double rho_l,
+                                   double* rho);
+
+/* Method III projection (Algorithm 1, Sec. 3.3.1; Eqs. new_poisson, corr).
+ * In: us, vs, ws (u*, faces; ws wall planes are taken as zero), rho (cell
+ * density, > 0), S (divergence target, Eq. 34; may be NULL for zero), dt > 0,
+ * p (cell field; used as the initial iterate when warm_start != 0).
+ * Out: p (zero mean), u, v, w (u^{n+1}; w wall planes written as zero).
+ * Stops when ||D u^s - S_c||_2 <= rtol ||D u* - S_c||_2 or after maxit
+ * constant-coefficient solves (status PP_ERR_NOT_CONVERGED).  info may be
+ * NULL: the call then returns without waiting for the GPU and the iteration
+ * status stays on the device (read it later with pressure_last_info). */
+pp_status pressure_correct(pp_plan plan, const double* us, const double* vs, const double* ws,
+                           const double* rho, const double* S, double dt, double* p,
+                           int warm_start, double* u, double* v, double* w, double rtol,
+                           int maxit, pp_info* info);
+
+/* Adjoint of the converged projection (Eqs. lap_p, corr differentiated at
+ * the fixed point of Algorithm 1).  In: rho, p (the converged pressure of
+ * the forward call with the same rho and dt), gu, gv, gw = dL/du^{n+1}.
+ * Out: gus, gvs, gws = dL/du*, grho = dL/drho (cell field).  The transposed
+ * system is solved by the same Method III loop.  Wall entries of gw are
+ * ignored and those of gws are written as zero. */
+pp_status pressure_solve_adjoint(pp_plan plan, const double* rho, const double* p, double dt,
+                                 const double* gu, const double* gv, const double* gw,
+                                 double* gus, double* gvs, double* gws, double* grho,
+                                 double rtol, int maxit, pp_info* info);
+
+/* Wait for the plan's stream and fill info from the last pressure_correct
+ * or pressure_solve_adjoint call. */
+pp_status pressure_last_info(pp_plan plan, pp_info* info);
+
+/* Per-kernel timing (no counterpart in the paper: instrumentation of this
+ * library).  When enabled, every kernel launch of the plan is bracketed by
+ * CUDA events on the plan's stream; pressure_profile_read waits for the
+ * stream and returns, per kernel name, the launch count and the summed
+ * event-timed duration since the last enable.  The launch counter counts
+ * the plan's own kernel launches whether or not timing is enabled.
+ * out may be NULL to query the count; *n receives the number of entries. */
+typedef struct {
+    char name[32];
+    long long launches;
+    double total_ms;
+} pp_kernel_time;
+
+pp_status pressure_profile_enable(pp_plan plan, int enable);
+pp_status pressure_profile_read(pp_plan plan, pp_kernel_time* out, int max_entries, int* n,
+                                long long* total_launches);
+
+const char* pressure_status_string(pp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -403,7 +403,7 @@ def adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv, gw):
     return u, v, w, grho
 
 
-def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=1000):
+def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=1000, p=None):
     """The same gradients for any grid size, with Algorithm 1 as the solver.
 
     With W_c = diag(dzf) on cells and W_f = diag(dzf of the layer) on x/y
@@ -413,7 +413,8 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
         A mu = -D(B W_f^{-1} g),
     which is the projection equation with u* = -dt B W_f^{-1} g and S = 0.
     Then g_u* = g + W_f G mu (the gauge of mu does not matter).
-    ``p`` is the converged pressure of the forward projection.
+    ``p`` is the converged pressure of the forward projection (computed
+    here with the same tolerance when not given).
     """
     gw = _zero_walls(gw)
     rx, ry, rz = face_density(g, rho)
@@ -428,7 +429,9 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
     gx, gy, gz = gradient(g, mu)
     gus, gvs, gws = gu + wlay * gx, gv + wlay * gy, gw + wz * gz
     gws = _zero_walls(gws)
-    p, _, _, _, info_fwd = method3(g, us, vs, ws, rho, S, dt, rtol=rtol, maxit=maxit)
+    info_fwd = None
+    if p is None:
+        p, _, _, _, info_fwd = method3(g, us, vs, ws, rho, S, dt, rtol=rtol, maxit=maxit)
     px, py, pz = gradient(g, p)
     gbeta = _face_vector(-dt * px * gus, -dt * py * gvs, -dt * pz * gws)
     beta = 1.0 / _face_vector(rx, ry, rz)

@@ -1,0 +1,626 @@
+// C ABI of the pressure-projection library: plans, the Method III driver
+// (Algorithm 1, Sec. 3.3.1), the constant-coefficient solve, the adjoint and
+// host-pointer staging.
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pp_internal.cuh"
+
+using namespace pp;
+
+namespace {
+enum KId { K_RESID, K_CHECK, K_FFTY_F, K_TRI, K_FFTY_I, K_FFTX_I, K_INIT, K_PREP, K_MEANS, K_RHSB,
+           K_RMEAN, K_CORR, K_MIX, K_ADJ_RHS, K_ADJ_FIN, K_ADJ_GRHO, K_COUNT };
+const char* const kNames[K_COUNT] = {
+    "resid_fftx", "check", "ffty_fwd", "tridiag_z", "ffty_inv", "fftx_inv_update", "init_status",
+    "prep_faces", "mean_S", "rhs_b", "remove_mean", "correct", "mixture_density", "adj_rhs",
+    "adj_finish", "adj_grho"};
+const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 3, 1, 1, 1, 1, 1};
+struct Rec { int kid; cudaEvent_t a, b; };
+struct Prof {
+  bool on = false;
+  std::vector<Rec> rec;
+  std::vector<cudaEvent_t> pool;
+  double ms[K_COUNT] = {0};
+  long long n[K_COUNT] = {0};
+  long long launches = 0;
+};
+}  // namespace
+
+struct pp_plan_s {
+  int nx, ny, nz, nxh;
+  double lx, ly, lz, dx, dy;
+  pp_precision prec;
+  cudaStream_t stream;
+  int device;
+  FftDesc fx, fy;
+  Geo geo;
+  Faces faces;
+  // device tables
+  double *d_inv_dzf = nullptr, *d_inv_dzc = nullptr, *d_dzf = nullptr, *d_za = nullptr, *d_zc = nullptr;
+  double *d_lamx = nullptr, *d_lamy = nullptr, *d_invd = nullptr;
+  void *d_twx = nullptr, *d_twy = nullptr;
+  // workspaces
+  void* d_spec = nullptr;
+  double2* d_ybuf = nullptr;
+  double* d_b = nullptr;
+  double* d_red = nullptr;
+  size_t red_len = 0;
+  DevStatus* d_st = nullptr;
+  DevStatus* h_st = nullptr;  // pinned, two slots
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // lazily allocated: host staging (10 face-sized buffers), adjoint scratch
+  double* d_stage[10] = {nullptr};
+  double* d_adj[4] = {nullptr};
+  double last_mean_S = 0.0;
+  Prof prof;
+};
+
+namespace {
+
+bool factor_len(int n, FftDesc* d) {
+  if (n < 1) return false;
+  d->n = n;
+  d->nst = 0;
+  int m = n;
+  const int rads[5] = {8, 4, 2, 3, 5};
+  for (int r : rads) {
+    while (m % r == 0) {
+      if (d->nst >= kMaxStages) return false;
+      d->radix[d->nst++] = r;
+      m /= r;
+    }
+  }
+  if (n == 1) { d->radix[0] = 2; d->nst = 0; }
+  return m == 1;
+}
+
+template <typename T>
+std::vector<C2<T>> twiddles(int n) {
+  std::vector<C2<T>> t(n);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < n; ++m) {
+    const double a = two_pi * (double)m / (double)n;
+    t[m].x = (T)std::cos(a);
+    t[m].y = (T)std::sin(a);
+  }
+  return t;
+}
+
+#define PP_CK(call)                                  \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return PP_ERR_CUDA;       \
+  } while (0)
+
+cudaEvent_t get_event(pp_plan_s* P) {
+  if (!P->prof.pool.empty()) {
+    cudaEvent_t e = P->prof.pool.back();
+    P->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch through f(); count it and, when profiling, bracket it with events.
+template <class F>
+cudaError_t timed(pp_plan_s* P, int kid, F&& f) {
+  P->prof.launches += kLaunches[kid];
+  if (!P->prof.on) return f();
+  cudaEvent_t a = get_event(P), b = get_event(P);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaEventRecord(a, P->stream);
+  if (e != cudaSuccess) return e;
+  e = f();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(b, P->stream);
+  P->prof.rec.push_back({kid, a, b});
+  return e;
+}
+
+#define PP_K(P, KID, expr) PP_CK(timed((P), (KID), [&]() { return (expr); }))
+
+template <typename X>
+pp_status dalloc(X** p, size_t bytes) {
+  if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    (void)cudaGetLastError();
+    return PP_ERR_OOM;
+  }
+  return PP_OK;
+}
+
+size_t ncell(const pp_plan_s* P) { return (size_t)P->nx * P->ny * P->nz; }
+size_t nwface(const pp_plan_s* P) { return (size_t)P->nx * P->ny * (P->nz + 1); }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stage an input: device pointers pass through, host pointers are copied
+// into staging slot `slot` (allocated on first use, sized for a w field).
+pp_status stage_in(pp_plan_s* P, const double* src, size_t n, int slot, const double** out) {
+  if (src == nullptr) { *out = nullptr; return PP_OK; }
+  if (is_device_ptr(src)) { *out = src; return PP_OK; }
+  if (!P->d_stage[slot]) {
+    pp_status s = dalloc(&P->d_stage[slot], nwface(P) * sizeof(double));
+    if (s != PP_OK) return s;
+  }
+  PP_CK(cudaMemcpyAsync(P->d_stage[slot], src, n * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+  *out = P->d_stage[slot];
+  return PP_OK;
+}
+
+pp_status stage_out(pp_plan_s* P, double* dst, int slot, double** out, bool* staged) {
+  *staged = false;
+  if (is_device_ptr(dst)) { *out = dst; return PP_OK; }
+  if (!P->d_stage[slot]) {
+    pp_status s = dalloc(&P->d_stage[slot], nwface(P) * sizeof(double));
+    if (s != PP_OK) return s;
+  }
+  *out = P->d_stage[slot];
+  *staged = true;
+  return PP_OK;
+}
+
+pp_status copy_back(pp_plan_s* P, double* host, const double* dev, size_t n) {
+  PP_CK(cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+  return PP_OK;
+}
+
+pp_status read_info(pp_plan_s* P, pp_info* info) {
+  PP_CK(cudaMemcpyAsync(P->h_st, P->d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, P->stream));
+  PP_CK(cudaStreamSynchronize(P->stream));
+  const DevStatus& s = P->h_st[0];
+  if (info) {
+    const double dt_scale = 1.0;  // e is stored in units of 1/dt; res0/res_l1 are rescaled by the caller
+    info->iters = s.iters;
+    info->res0 = std::sqrt(s.e2_0) * dt_scale;
+    info->res_final = s.rel;
+    info->res_l1_sum = s.e1;
+    info->mean_S_removed = s.mean_S;
+    info->status = s.code;
+  }
+  return (pp_status)s.code;
+}
+
+// One pass of Algorithm 1 after the residual: forward y, z solve, inverse y,
+// inverse x fused with p += delta.
+template <typename T>
+pp_status solve_pass(pp_plan_s* P, double* p, int p_zero) {
+  const Geo& g = P->geo;
+  C2<T>* spec = (C2<T>*)P->d_spec;
+  const C2<T>* twx = (const C2<T>*)P->d_twx;
+  const C2<T>* twy = (const C2<T>*)P->d_twy;
+  double2* ybuf = std::is_same<T, double>::value ? (double2*)P->d_spec : P->d_ybuf;
+  const double scale = 1.0 / ((double)P->nx * (double)P->ny);
+  PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream));
+  PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream));
+  PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream));
+  PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream));
+  return PP_OK;
+}
+
+// Method III loop on device fields: b = D u* - S_c has been formed; faces
+// hold beta of rho.  p is the iterate (zeroed by the caller unless warm).
+template <typename T>
+pp_status method3_loop(pp_plan_s* P, const double* rho, double* p, int warm, double dt, double rtol,
+                       int maxit) {
+  const Geo& g = P->geo;
+  C2<T>* spec = (C2<T>*)P->d_spec;
+  const C2<T>* twx = (const C2<T>*)P->d_twx;
+  const double inv_dt = 1.0 / dt;
+  const int chunk = 4;
+  int polled = 0;
+  bool pending[2] = {false, false};
+  for (int it = 0; it <= maxit; ++it) {
+    int nblk = 0;
+    PP_K(P, K_RESID, launch_resid_fftx<T>(g, P->faces, P->fx, twx, P->d_b, inv_dt, rho, p,
+                                          (it == 0 && !warm) ? 1 : 0, 1, spec, P->d_red, &nblk,
+                                          P->d_st, P->stream));
+    PP_K(P, K_CHECK, launch_check(P->d_st, P->d_red, nblk, rtol, maxit, P->stream));
+    pp_status s = solve_pass<T>(P, p, 0);
+    if (s != PP_OK) return s;
+    if ((it + 1) % chunk == 0) {
+      // Poll the device status without draining the queue: read the slot
+      // recorded one chunk ago.
+      const int slot = polled & 1;
+      PP_CK(cudaMemcpyAsync(&P->h_st[slot], P->d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, P->stream));
+      PP_CK(cudaEventRecord(P->ev[slot], P->stream));
+      pending[slot] = true;
+      const int prev = slot ^ 1;
+      if (pending[prev]) {
+        PP_CK(cudaEventSynchronize(P->ev[prev]));
+        pending[prev] = false;
+        if (P->h_st[prev].done) break;
+      }
+      ++polled;
+    }
+  }
+  return PP_OK;
+}
+
+template <typename T>
+pp_status projection(pp_plan_s* P, const double* us, const double* vs, const double* ws,
+                     const double* rho, const double* S, double dt, double* p, int warm, double* u,
+                     double* v, double* w, double rtol, int maxit) {
+  const Geo& g = P->geo;
+  PP_K(P, K_INIT, launch_init_status(P->d_st, P->stream));
+  PP_K(P, K_PREP, launch_prep_faces(g, rho, P->faces, P->stream));
+  if (S) PP_K(P, K_MEANS, launch_weighted_mean(g, S, P->d_red, &P->d_st->mean_S, P->stream));
+  PP_K(P, K_RHSB, launch_rhs_b(g, us, vs, ws, S, P->d_b, P->d_red, P->d_st, 1.0 / dt, P->stream));
+  if (!warm) PP_CK(cudaMemsetAsync(p, 0, ncell(P) * sizeof(double), P->stream));
+  pp_status s = method3_loop<T>(P, rho, p, warm, dt, rtol, maxit);
+  if (s != PP_OK) return s;
+  PP_K(P, K_RMEAN, launch_remove_mean(g, p, P->d_red, P->d_st, P->stream));
+  if (u) PP_K(P, K_CORR, launch_correct(g, P->faces, us, vs, ws, p, dt, u, v, w, P->stream));
+  return PP_OK;
+}
+
+pp_status check_plan(pp_plan P) {
+  if (P == nullptr) return PP_ERR_INVALID_ARG;
+  return PP_OK;
+}
+
+void free_plan(pp_plan_s* P) {
+  if (!P) return;
+  double* dptrs[] = {P->d_inv_dzf, P->d_inv_dzc, P->d_dzf, P->d_za, P->d_zc, P->d_lamx, P->d_lamy,
+                     P->d_invd, P->d_b, P->d_red, P->faces.cx, P->faces.cy, P->faces.cz};
+  for (double* d : dptrs) if (d) cudaFree(d);
+  if (P->d_twx) cudaFree(P->d_twx);
+  if (P->d_twy) cudaFree(P->d_twy);
+  if (P->d_spec) cudaFree(P->d_spec);
+  if (P->d_ybuf) cudaFree(P->d_ybuf);
+  if (P->d_st) cudaFree(P->d_st);
+  if (P->h_st) cudaFreeHost(P->h_st);
+  for (auto& e : P->ev) if (e) cudaEventDestroy(e);
+  for (double* d : P->d_stage) if (d) cudaFree(d);
+  for (double* d : P->d_adj) if (d) cudaFree(d);
+  for (auto& r : P->prof.rec) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : P->prof.pool) cudaEventDestroy(e);
+  delete P;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pressure_status_string(pp_status s) {
+  switch (s) {
+    case PP_OK: return "ok";
+    case PP_ERR_INVALID_ARG: return "invalid argument";
+    case PP_ERR_UNSUPPORTED: return "unsupported grid or boundary condition";
+    case PP_ERR_NOT_CONVERGED: return "not converged within maxit";
+    case PP_ERR_NUMERIC: return "non-finite residual";
+    case PP_ERR_CUDA: return "CUDA runtime error";
+    case PP_ERR_OOM: return "device allocation failed";
+  }
+  return "unknown status";
+}
+
+pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* stream, pp_plan* out) {
+  if (!grid || !out) return PP_ERR_INVALID_ARG;
+  *out = nullptr;
+  const pp_grid& G = *grid;
+  if (G.nx < 2 || G.ny < 1 || G.nz < 1 || !(G.lx > 0) || !(G.ly > 0) || !(G.lz > 0))
+    return PP_ERR_INVALID_ARG;
+  if (prec != PP_FP64 && prec != PP_MIXED_FP32) return PP_ERR_INVALID_ARG;
+  if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL)
+    return PP_ERR_UNSUPPORTED;
+  if ((G.nx & 1) != 0) return PP_ERR_UNSUPPORTED;
+  if ((long)G.nx * G.ny * (G.nz + 1) > (1L << 31)) return PP_ERR_UNSUPPORTED;
+  pp_plan_s* P = new (std::nothrow) pp_plan_s();
+  if (!P) return PP_ERR_OOM;
+  P->nx = G.nx; P->ny = G.ny; P->nz = G.nz; P->nxh = G.nx / 2 + 1;
+  P->lx = G.lx; P->ly = G.ly; P->lz = G.lz;
+  P->dx = G.lx / G.nx; P->dy = G.ly / G.ny;
+  P->prec = prec;
+  P->stream = (cudaStream_t)stream;
+  if (!factor_len(G.nx, &P->fx) || !factor_len(G.ny, &P->fy)) { delete P; return PP_ERR_UNSUPPORTED; }
+  if (cudaGetDevice(&P->device) != cudaSuccess) { delete P; return PP_ERR_CUDA; }
+
+  // z metrics (Sec. 3 grid; stretched faces allowed)
+  const int nz = G.nz;
+  std::vector<double> zf(nz + 1);
+  if (G.zfaces) {
+    for (int k = 0; k <= nz; ++k) zf[k] = G.zfaces[k];
+    for (int k = 0; k < nz; ++k)
+      if (!(zf[k + 1] > zf[k])) { delete P; return PP_ERR_INVALID_ARG; }
+  } else {
+    for (int k = 0; k <= nz; ++k) zf[k] = G.lz * (double)k / (double)nz;
+  }
+  std::vector<double> dzf(nz), inv_dzf(nz), zcen(nz), inv_dzc(nz + 1, 0.0), za(nz, 0.0), zc(nz, 0.0);
+  for (int k = 0; k < nz; ++k) {
+    dzf[k] = zf[k + 1] - zf[k];
+    inv_dzf[k] = 1.0 / dzf[k];
+    zcen[k] = 0.5 * (zf[k] + zf[k + 1]);
+  }
+  for (int k = 1; k < nz; ++k) inv_dzc[k] = 1.0 / (zcen[k] - zcen[k - 1]);
+  for (int k = 1; k < nz; ++k) za[k] = inv_dzc[k] * inv_dzf[k];
+  for (int k = 0; k < nz - 1; ++k) zc[k] = inv_dzc[k + 1] * inv_dzf[k];
+  const double lz_sum = zf[nz] - zf[0];
+  // modified wavenumbers of the periodic second difference
+  std::vector<double> lamx(P->nxh), lamy(G.ny);
+  const double pi = 3.14159265358979323846264338327950288;
+  for (int k = 0; k < P->nxh; ++k) {
+    const double s = std::sin(pi * (double)k / (double)G.nx);
+    lamx[k] = -4.0 / (P->dx * P->dx) * s * s;
+  }
+  for (int k = 0; k < G.ny; ++k) {
+    const double s = std::sin(pi * (double)k / (double)G.ny);
+    lamy[k] = -4.0 / (P->dy * P->dy) * s * s;
+  }
+
+  pp_status st = PP_OK;
+  const size_t nc = (size_t)G.nx * G.ny * nz;
+  const size_t nw = (size_t)G.nx * G.ny * (nz + 1);
+  const size_t nsp = (size_t)P->nxh * G.ny * nz;
+  const size_t csz = (prec == PP_FP64) ? sizeof(double2) : sizeof(float2);
+  auto up = [&](double** d, const std::vector<double>& h) -> pp_status {
+    pp_status s = dalloc(d, h.size() * sizeof(double));
+    if (s != PP_OK) return s;
+    return cudaMemcpy(*d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess
+               ? PP_OK : PP_ERR_CUDA;
+  };
+  if ((st = up(&P->d_inv_dzf, inv_dzf)) != PP_OK || (st = up(&P->d_inv_dzc, inv_dzc)) != PP_OK ||
+      (st = up(&P->d_dzf, dzf)) != PP_OK || (st = up(&P->d_za, za)) != PP_OK ||
+      (st = up(&P->d_zc, zc)) != PP_OK || (st = up(&P->d_lamx, lamx)) != PP_OK ||
+      (st = up(&P->d_lamy, lamy)) != PP_OK) {
+    free_plan(P);
+    return st;
+  }
+  if (prec == PP_FP64) {
+    auto tx = twiddles<double>(G.nx), ty = twiddles<double>(G.ny);
+    if ((st = dalloc(&P->d_twx, tx.size() * sizeof(double2))) != PP_OK ||
+        (st = dalloc(&P->d_twy, ty.size() * sizeof(double2))) != PP_OK) { free_plan(P); return st; }
+    cudaMemcpy(P->d_twx, tx.data(), tx.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    cudaMemcpy(P->d_twy, ty.data(), ty.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  } else {
+    auto tx = twiddles<float>(G.nx), ty = twiddles<float>(G.ny);
+    if ((st = dalloc(&P->d_twx, tx.size() * sizeof(float2))) != PP_OK ||
+        (st = dalloc(&P->d_twy, ty.size() * sizeof(float2))) != PP_OK) { free_plan(P); return st; }
+    cudaMemcpy(P->d_twx, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaMemcpy(P->d_twy, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  }
+  // residual partial sums: 2 per residual block, or the reduction grid
+  const size_t rpb_min = 2;
+  P->red_len = std::max((size_t)2 * ((size_t)G.ny * nz + rpb_min - 1) / rpb_min + 2,
+                        (size_t)reduce_blocks());
+  if ((st = dalloc(&P->d_invd, nsp * sizeof(double))) != PP_OK ||
+      (st = dalloc(&P->d_spec, nsp * csz)) != PP_OK ||
+      (prec != PP_FP64 && (st = dalloc(&P->d_ybuf, nsp * sizeof(double2))) != PP_OK) ||
+      (st = dalloc(&P->d_b, nc * sizeof(double))) != PP_OK ||
+      (st = dalloc(&P->d_red, P->red_len * sizeof(double))) != PP_OK ||
+      (st = dalloc(&P->faces.cx, nc * sizeof(double))) != PP_OK ||
+      (st = dalloc(&P->faces.cy, nc * sizeof(double))) != PP_OK ||
+      (st = dalloc(&P->faces.cz, nw * sizeof(double))) != PP_OK ||
+      (st = dalloc(&P->d_st, sizeof(DevStatus))) != PP_OK) {
+    free_plan(P);
+    return st;
+  }
+  if (cudaMallocHost((void**)&P->h_st, 2 * sizeof(DevStatus)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    free_plan(P);
+    return PP_ERR_CUDA;
+  }
+  Geo& g = P->geo;
+  g.nx = G.nx; g.ny = G.ny; g.nz = nz; g.nxh = P->nxh;
+  g.dx = P->dx; g.dy = P->dy;
+  g.inv_dx2 = 1.0 / (P->dx * P->dx);
+  g.inv_dy2 = 1.0 / (P->dy * P->dy);
+  g.inv_dzf = P->d_inv_dzf; g.inv_dzc = P->d_inv_dzc; g.dzf = P->d_dzf;
+  g.za = P->d_za; g.zc = P->d_zc; g.lz = lz_sum;
+  if (launch_setup_pivots(g, P->d_lamx, P->d_lamy, P->d_invd, P->stream) != cudaSuccess ||
+      launch_init_status(P->d_st, P->stream) != cudaSuccess ||
+      cudaStreamSynchronize(P->stream) != cudaSuccess) {
+    free_plan(P);
+    return PP_ERR_CUDA;
+  }
+  *out = P;
+  return PP_OK;
+}
+
+pp_status pressure_plan_destroy(pp_plan P) {
+  if (!P) return PP_ERR_INVALID_ARG;
+  cudaStreamSynchronize(P->stream);
+  free_plan(P);
+  return PP_OK;
+}
+
+pp_status pressure_mixture_density(pp_plan P, const double* phi, double rho_g, double rho_l, double* rho) {
+  if (check_plan(P) != PP_OK || !phi || !rho) return PP_ERR_INVALID_ARG;
+  const size_t n = ncell(P);
+  const double* dphi;
+  double* drho;
+  bool staged;
+  pp_status s;
+  if ((s = stage_in(P, phi, n, 0, &dphi)) != PP_OK) return s;
+  if ((s = stage_out(P, rho, 1, &drho, &staged)) != PP_OK) return s;
+  PP_K(P, K_MIX, launch_mixture(dphi, rho_g, rho_l, drho, n, P->stream));
+  if (staged) {
+    if ((s = copy_back(P, rho, drho, n)) != PP_OK) return s;
+    PP_CK(cudaStreamSynchronize(P->stream));
+  }
+  return PP_OK;
+}
+
+pp_status pressure_solve(pp_plan P, const double* f, double* p, pp_info* info) {
+  if (check_plan(P) != PP_OK || !f || !p) return PP_ERR_INVALID_ARG;
+  const size_t n = ncell(P);
+  const double* df;
+  double* dp;
+  bool staged;
+  pp_status s;
+  if ((s = stage_in(P, f, n, 0, &df)) != PP_OK) return s;
+  if ((s = stage_out(P, p, 1, &dp, &staged)) != PP_OK) return s;
+  const Geo& g = P->geo;
+  PP_K(P, K_INIT, launch_init_status(P->d_st, P->stream));
+  if (P->prec == PP_FP64) {
+    PP_K(P, K_RESID, launch_resid_fftx<double>(g, P->faces, P->fx, (const double2*)P->d_twx, df, 1.0, nullptr,
+                                    nullptr, 1, 0, (double2*)P->d_spec, nullptr, nullptr, P->d_st,
+                                    P->stream));
+    if ((s = solve_pass<double>(P, dp, 1)) != PP_OK) return s;
+  } else {
+    PP_K(P, K_RESID, launch_resid_fftx<float>(g, P->faces, P->fx, (const float2*)P->d_twx, df, 1.0, nullptr,
+                                   nullptr, 1, 0, (float2*)P->d_spec, nullptr, nullptr, P->d_st,
+                                   P->stream));
+    if ((s = solve_pass<float>(P, dp, 1)) != PP_OK) return s;
+  }
+  PP_K(P, K_RMEAN, launch_remove_mean(g, dp, P->d_red, P->d_st, P->stream));
+  if (staged && (s = copy_back(P, p, dp, n)) != PP_OK) return s;
+  if (info || staged) {
+    PP_CK(cudaStreamSynchronize(P->stream));
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->iters = 1;
+      info->status = PP_OK;
+    }
+  }
+  return PP_OK;
+}
+
+pp_status pressure_correct(pp_plan P, const double* us, const double* vs, const double* ws,
+                           const double* rho, const double* S, double dt, double* p, int warm_start,
+                           double* u, double* v, double* w, double rtol, int maxit, pp_info* info) {
+  if (check_plan(P) != PP_OK || !us || !vs || !ws || !rho || !p || !u || !v || !w) return PP_ERR_INVALID_ARG;
+  if (!(dt > 0.0) || !(rtol >= 0.0) || maxit < 0) return PP_ERR_INVALID_ARG;
+  const size_t nc = ncell(P), nw = nwface(P);
+  const double *dus, *dvs, *dws, *drho, *dS, *dpin = nullptr;
+  double *dp, *du, *dv, *dw;
+  bool sp, su, sv, sw;
+  pp_status s;
+  if ((s = stage_in(P, us, nc, 0, &dus)) != PP_OK || (s = stage_in(P, vs, nc, 1, &dvs)) != PP_OK ||
+      (s = stage_in(P, ws, nw, 2, &dws)) != PP_OK || (s = stage_in(P, rho, nc, 3, &drho)) != PP_OK ||
+      (s = stage_in(P, S, nc, 4, &dS)) != PP_OK)
+    return s;
+  if ((s = stage_out(P, p, 5, &dp, &sp)) != PP_OK || (s = stage_out(P, u, 6, &du, &su)) != PP_OK ||
+      (s = stage_out(P, v, 7, &dv, &sv)) != PP_OK || (s = stage_out(P, w, 8, &dw, &sw)) != PP_OK)
+    return s;
+  if (warm_start && sp) {
+    if ((s = stage_in(P, p, nc, 9, &dpin)) != PP_OK) return s;
+    PP_CK(cudaMemcpyAsync(dp, dpin, nc * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
+  }
+  if (P->prec == PP_FP64) s = projection<double>(P, dus, dvs, dws, drho, dS, dt, dp, warm_start, du, dv, dw, rtol, maxit);
+  else s = projection<float>(P, dus, dvs, dws, drho, dS, dt, dp, warm_start, du, dv, dw, rtol, maxit);
+  if (s != PP_OK) return s;
+  if (sp && (s = copy_back(P, p, dp, nc)) != PP_OK) return s;
+  if (su && (s = copy_back(P, u, du, nc)) != PP_OK) return s;
+  if (sv && (s = copy_back(P, v, dv, nc)) != PP_OK) return s;
+  if (sw && (s = copy_back(P, w, dw, nw)) != PP_OK) return s;
+  if (info || sp || su || sv || sw) {
+    pp_info tmp;
+    s = read_info(P, &tmp);
+    tmp.res0 *= dt;
+    tmp.res_l1_sum *= dt;
+    if (info) *info = tmp;
+    return s;
+  }
+  return PP_OK;
+}
+
+pp_status pressure_last_info(pp_plan P, pp_info* info) {
+  if (check_plan(P) != PP_OK || !info) return PP_ERR_INVALID_ARG;
+  return read_info(P, info);
+}
+
+pp_status pressure_solve_adjoint(pp_plan P, const double* rho, const double* p, double dt,
+                                 const double* gu, const double* gv, const double* gw, double* gus,
+                                 double* gvs, double* gws, double* grho, double rtol, int maxit,
+                                 pp_info* info) {
+  if (check_plan(P) != PP_OK || !rho || !p || !gu || !gv || !gw || !gus || !gvs || !gws || !grho)
+    return PP_ERR_INVALID_ARG;
+  if (!(dt > 0.0) || !(rtol >= 0.0) || maxit < 0) return PP_ERR_INVALID_ARG;
+  const size_t nc = ncell(P), nw = nwface(P);
+  pp_status s;
+  for (int i = 0; i < 4; ++i) {
+    if (!P->d_adj[i] && (s = dalloc(&P->d_adj[i], nw * sizeof(double))) != PP_OK) return s;
+  }
+  const double *drho, *dp, *dgu, *dgv, *dgw;
+  double *dgus, *dgvs, *dgws, *dgrho;
+  bool s1, s2, s3, s4;
+  if ((s = stage_in(P, rho, nc, 0, &drho)) != PP_OK || (s = stage_in(P, p, nc, 1, &dp)) != PP_OK ||
+      (s = stage_in(P, gu, nc, 2, &dgu)) != PP_OK || (s = stage_in(P, gv, nc, 3, &dgv)) != PP_OK ||
+      (s = stage_in(P, gw, nw, 4, &dgw)) != PP_OK)
+    return s;
+  if ((s = stage_out(P, gus, 5, &dgus, &s1)) != PP_OK || (s = stage_out(P, gvs, 6, &dgvs, &s2)) != PP_OK ||
+      (s = stage_out(P, gws, 7, &dgws, &s3)) != PP_OK || (s = stage_out(P, grho, 8, &dgrho, &s4)) != PP_OK)
+    return s;
+  const Geo& g = P->geo;
+  double *yu = P->d_adj[0], *yv = P->d_adj[1], *yw = P->d_adj[2], *mu = P->d_adj[3];
+  PP_K(P, K_ADJ_RHS, launch_adj_rhs(g, drho, dgu, dgv, dgw, dt, yu, yv, yw, P->stream));
+  // mu solves D(beta G mu) = D(y)/dt: the projection loop with u* = y, S = 0
+  if (P->prec == PP_FP64) s = projection<double>(P, yu, yv, yw, drho, nullptr, dt, mu, 0, nullptr, nullptr, nullptr, rtol, maxit);
+  else s = projection<float>(P, yu, yv, yw, drho, nullptr, dt, mu, 0, nullptr, nullptr, nullptr, rtol, maxit);
+  if (s != PP_OK) return s;
+  // y buffers are free again: reuse them for the face terms of d rho
+  PP_K(P, K_ADJ_FIN, launch_adj_finish(g, drho, dp, mu, dt, dgu, dgv, dgw, dgus, dgvs, dgws, yu, yv, yw, P->stream));
+  PP_K(P, K_ADJ_GRHO, launch_adj_grho(g, yu, yv, yw, dgrho, P->stream));
+  if (s1 && (s = copy_back(P, gus, dgus, nc)) != PP_OK) return s;
+  if (s2 && (s = copy_back(P, gvs, dgvs, nc)) != PP_OK) return s;
+  if (s3 && (s = copy_back(P, gws, dgws, nw)) != PP_OK) return s;
+  if (s4 && (s = copy_back(P, grho, dgrho, nc)) != PP_OK) return s;
+  if (info || s1 || s2 || s3 || s4) {
+    pp_info tmp;
+    s = read_info(P, &tmp);
+    tmp.res0 *= dt;
+    tmp.res_l1_sum *= dt;
+    if (info) *info = tmp;
+    return s;
+  }
+  return PP_OK;
+}
+
+pp_status pressure_profile_enable(pp_plan P, int enable) {
+  if (check_plan(P) != PP_OK) return PP_ERR_INVALID_ARG;
+  PP_CK(cudaStreamSynchronize(P->stream));
+  for (auto& r : P->prof.rec) { P->prof.pool.push_back(r.a); P->prof.pool.push_back(r.b); }
+  P->prof.rec.clear();
+  for (int k = 0; k < K_COUNT; ++k) { P->prof.ms[k] = 0.0; P->prof.n[k] = 0; }
+  P->prof.launches = 0;
+  P->prof.on = enable != 0;
+  return PP_OK;
+}
+
+pp_status pressure_profile_read(pp_plan P, pp_kernel_time* out, int max_entries, int* n,
+                                long long* total_launches) {
+  if (check_plan(P) != PP_OK || !n) return PP_ERR_INVALID_ARG;
+  PP_CK(cudaStreamSynchronize(P->stream));
+  for (auto& r : P->prof.rec) {
+    float ms = 0.f;
+    PP_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    P->prof.ms[r.kid] += ms;
+    P->prof.n[r.kid] += 1;
+    P->prof.pool.push_back(r.a);
+    P->prof.pool.push_back(r.b);
+  }
+  P->prof.rec.clear();
+  int cnt = 0;
+  for (int k = 0; k < K_COUNT; ++k) {
+    if (P->prof.n[k] == 0) continue;
+    if (out && cnt < max_entries) {
+      std::memset(out[cnt].name, 0, sizeof(out[cnt].name));
+      std::strncpy(out[cnt].name, kNames[k], sizeof(out[cnt].name) - 1);
+      out[cnt].launches = P->prof.n[k] * kLaunches[k];
+      out[cnt].total_ms = P->prof.ms[k];
+    }
+    ++cnt;
+  }
+  *n = cnt;
+  if (total_launches) *total_launches = P->prof.launches;
+  return PP_OK;
+}
+
+}  // extern "C"

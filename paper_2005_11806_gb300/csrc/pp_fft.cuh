@@ -1,0 +1,164 @@
+// Shared-memory mixed-radix Stockham FFT (radices 8, 4, 2, 3, 5) used by the
+// x and y transforms of the eigenexpansion solver.  The twiddle table holds
+// (cos, sin)(2 pi m / n), m = 0..n-1, computed on the host in FP64.
+#pragma once
+#include "pp_internal.cuh"
+
+namespace pp {
+
+template <typename T> __device__ __forceinline__ C2<T> mk(T x, T y) { C2<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// multiply by DIR * i  (DIR = -1: -i, DIR = +1: +i)
+template <typename T, int DIR> __device__ __forceinline__ C2<T> mul_i(C2<T> a) {
+  return DIR > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+
+// In-register DFT of size R with kernel exp(DIR * 2 pi i q r / R).
+template <typename T, int DIR, int R> struct Dft;
+
+template <typename T, int DIR> struct Dft<T, DIR, 2> {
+  static __device__ __forceinline__ void run(C2<T>* v) {
+    C2<T> a = v[0], b = v[1];
+    v[0] = cadd<T>(a, b);
+    v[1] = csub<T>(a, b);
+  }
+};
+
+template <typename T, int DIR> struct Dft<T, DIR, 4> {
+  static __device__ __forceinline__ void run(C2<T>* v) {
+    C2<T> s02 = cadd<T>(v[0], v[2]), d02 = csub<T>(v[0], v[2]);
+    C2<T> s13 = cadd<T>(v[1], v[3]), d13 = mul_i<T, DIR>(csub<T>(v[1], v[3]));
+    v[0] = cadd<T>(s02, s13);
+    v[2] = csub<T>(s02, s13);
+    v[1] = cadd<T>(d02, d13);
+    v[3] = csub<T>(d02, d13);
+  }
+};
+
+template <typename T, int DIR> struct Dft<T, DIR, 8> {
+  static __device__ __forceinline__ void run(C2<T>* v) {
+    C2<T> e[4] = {v[0], v[2], v[4], v[6]};
+    C2<T> o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<T, DIR, 4>::run(e);
+    Dft<T, DIR, 4>::run(o);
+    const T h = (T)0.70710678118654752440;  // cos(pi/4)
+    // o[q] *= exp(DIR * 2 pi i q / 8)
+    C2<T> o1 = mk<T>(h * (o[1].x - (T)DIR * o[1].y), h * (o[1].y + (T)DIR * o[1].x));
+    C2<T> o2 = mul_i<T, DIR>(o[2]);
+    C2<T> o3 = mk<T>(h * (-o[3].x - (T)DIR * o[3].y), h * (-o[3].y + (T)DIR * o[3].x));
+    v[0] = cadd<T>(e[0], o[0]); v[4] = csub<T>(e[0], o[0]);
+    v[1] = cadd<T>(e[1], o1);   v[5] = csub<T>(e[1], o1);
+    v[2] = cadd<T>(e[2], o2);   v[6] = csub<T>(e[2], o2);
+    v[3] = cadd<T>(e[3], o3);   v[7] = csub<T>(e[3], o3);
+  }
+};
+
+template <typename T, int DIR> struct Dft<T, DIR, 3> {
+  static __device__ __forceinline__ void run(C2<T>* v) {
+    const T c = (T)-0.5, s = (T)0.86602540378443864676;  // cos, sin(2 pi / 3)
+    C2<T> t1 = cadd<T>(v[1], v[2]);
+    C2<T> t2 = mk<T>(v[0].x + c * t1.x, v[0].y + c * t1.y);
+    C2<T> d = csub<T>(v[1], v[2]);
+    C2<T> t3 = mul_i<T, DIR>(mk<T>(s * d.x, s * d.y));
+    v[0] = cadd<T>(v[0], t1);
+    v[1] = cadd<T>(t2, t3);
+    v[2] = csub<T>(t2, t3);
+  }
+};
+
+template <typename T, int DIR> struct Dft<T, DIR, 5> {
+  static __device__ __forceinline__ void run(C2<T>* v) {
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;  // cos 2pi/5, 4pi/5
+    const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;   // sin 2pi/5, 4pi/5
+    C2<T> a14 = cadd<T>(v[1], v[4]), d14 = csub<T>(v[1], v[4]);
+    C2<T> a23 = cadd<T>(v[2], v[3]), d23 = csub<T>(v[2], v[3]);
+    C2<T> r1 = mk<T>(v[0].x + c1 * a14.x + c2 * a23.x, v[0].y + c1 * a14.y + c2 * a23.y);
+    C2<T> r2 = mk<T>(v[0].x + c2 * a14.x + c1 * a23.x, v[0].y + c2 * a14.y + c1 * a23.y);
+    C2<T> i1 = mul_i<T, DIR>(mk<T>(s1 * d14.x + s2 * d23.x, s1 * d14.y + s2 * d23.y));
+    C2<T> i2 = mul_i<T, DIR>(mk<T>(s2 * d14.x - s1 * d23.x, s2 * d14.y - s1 * d23.y));
+    v[0] = cadd<T>(v[0], cadd<T>(a14, a23));
+    v[1] = cadd<T>(r1, i1);
+    v[4] = csub<T>(r1, i1);
+    v[2] = cadd<T>(r2, i2);
+    v[3] = csub<T>(r2, i2);
+  }
+};
+
+// One Stockham pass of radix R over `nbatch` sequences of length n stored at
+// buf[b * bs + m * es].  BATCH_FAST selects which index consecutive threads
+// walk (the one that is contiguous in shared memory).
+template <typename T, int DIR, int R, bool BATCH_FAST>
+__device__ __forceinline__ void fft_pass(const C2<T>* __restrict__ src, C2<T>* __restrict__ dst, int n,
+                                         int Ns, int nbatch, int es, int bs,
+                                         const C2<T>* __restrict__ tw, int tid, int nth) {
+  const int nb = n / R;
+  const int total = nb * nbatch;
+  const int tws = n / (Ns * R);
+  for (int t = tid; t < total; t += nth) {
+    int bi, j;
+    if (BATCH_FAST) { j = t / nbatch; bi = t - j * nbatch; }
+    else { bi = t / nb; j = t - bi * nb; }
+    const int k = j % Ns;
+    C2<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[bi * bs + (j + r * nb) * es];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C2<T> w = __ldg(&tw[r * k * tws]);
+        w.y = DIR > 0 ? w.y : -w.y;
+        v[r] = cmul<T>(v[r], w);
+      }
+    }
+    Dft<T, DIR, R>::run(v);
+    const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[bi * bs + (base + r * Ns) * es] = v[r];
+  }
+}
+
+// Full transform; returns the buffer (a or b) holding the result.  Every
+// thread of the block must call it (it synchronises between passes).
+template <typename T, int DIR, bool BATCH_FAST>
+__device__ C2<T>* fft_block(C2<T>* a, C2<T>* b, const FftDesc& d, int nbatch, int es, int bs,
+                            const C2<T>* __restrict__ tw, int tid, int nth) {
+  int Ns = 1;
+  C2<T>* src = a;
+  C2<T>* dst = b;
+  for (int s = 0; s < d.nst; ++s) {
+    const int R = d.radix[s];
+    switch (R) {
+      case 8: fft_pass<T, DIR, 8, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+      case 4: fft_pass<T, DIR, 4, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+      case 2: fft_pass<T, DIR, 2, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+      case 3: fft_pass<T, DIR, 3, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+      default: fft_pass<T, DIR, 5, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+    }
+    __syncthreads();
+    C2<T>* t = src; src = dst; dst = t;
+    Ns *= R;
+  }
+  return src;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  // sh: at least 32 entries
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  T r = (threadIdx.x < nw) ? sh[threadIdx.x] : (T)0;
+  if (w == 0) {
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+}  // namespace pp

@@ -1,0 +1,122 @@
+// Internal declarations shared by the CUDA translation units of the
+// pressure-projection library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "pressure_projection.h"
+
+namespace pp {
+
+constexpr int kMaxStages = 16;
+
+// Mixed-radix factorisation of one FFT length (radices 8, 4, 2, 3, 5).
+struct FftDesc {
+  int n;
+  int nst;
+  int radix[kMaxStages];
+};
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using t = double2; };
+template <> struct Cx<float> { using t = float2; };
+template <typename T> using C2 = typename Cx<T>::t;
+
+// Device-resident iteration state of one projection (Algorithm 1's loop
+// control): written by the check kernel, read by every kernel of a pass.
+struct DevStatus {
+  double e2;        // sum of e^2 of the latest residual (e = (D u^s - S_c)/dt)
+  double e1;        // sum of |e|
+  double e2_0;      // sum of (b/dt)^2, b = D u* - S_c
+  double rel;       // sqrt(e2 / e2_0)
+  double mean_S;    // volume-weighted mean of S
+  double pmean;     // volume-weighted mean of p (gauge removal)
+  int iters;        // constant-coefficient solves started
+  int done;         // 1 once the loop has stopped
+  int code;         // pp_status of the loop
+  int pad;
+};
+
+// Geometry and tables on the device (pointers into plan-owned memory).
+struct Geo {
+  int nx, ny, nz, nxh;
+  double dx, dy, inv_dx2, inv_dy2;
+  const double* inv_dzf;  // [nz]   1 / cell width
+  const double* inv_dzc;  // [nz+1] 1 / centre distance across z-face k (0 at walls)
+  const double* dzf;      // [nz]
+  const double* za;       // [nz]   sub-diagonal of L_z
+  const double* zc;       // [nz]   super-diagonal of L_z
+  double lz;
+};
+
+// Face coefficients of D(beta G .): cx = beta_x / dx^2, cy = beta_y / dy^2,
+// cz = beta_z / dzc (0 on the wall faces); divide the z part by dzf.
+struct Faces {
+  double* cx;  // [nz][ny][nx]
+  double* cy;  // [nz][ny][nx]
+  double* cz;  // [nz+1][ny][nx]
+};
+
+// ---- launchers (pp_kernels_*.cu) -------------------------------------
+
+// Residual e = b/dt - D(beta G p) (or e = f when f_only), r = rho * e
+// (or r = e), forward real x-transform of r into spec; block partial sums
+// of e^2 and |e| into red[2*block + {0,1}].  Rows are (k, j) pairs.
+template <typename T>
+cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, const C2<T>* twx,
+                              const double* b, double inv_dt, const double* rho, const double* p,
+                              int p_zero, int scale_rho, C2<T>* spec, double* red, int* nblk_out,
+                              const DevStatus* st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
+                        const DevStatus* st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,
+                           const DevStatus* st, cudaStream_t s);
+// Inverse x-transform; p = scale * z (p_zero) or p += scale * z.
+template <typename T>
+cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
+                            double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s);
+
+cudaError_t launch_setup_pivots(const Geo& g, const double* lamx, const double* lamy, double* invd,
+                                cudaStream_t s);
+
+cudaError_t launch_mixture(const double* phi, double rho_g, double rho_l, double* rho, size_t n,
+                           cudaStream_t s);
+cudaError_t launch_prep_faces(const Geo& g, const double* rho, Faces fc, cudaStream_t s);
+// Sum of dzf * f over cells (block partials) -> st->mean_S = sum / (lz nx ny).
+cudaError_t launch_weighted_mean(const Geo& g, const double* f, double* red, double* out_mean,
+                                 cudaStream_t s);
+// b = D u* - (S - mean_S); partial sums of b^2 -> e2_0.
+cudaError_t launch_rhs_b(const Geo& g, const double* us, const double* vs, const double* ws,
+                         const double* S, double* b, double* red, DevStatus* st, double inv_dt,
+                         cudaStream_t s);
+// Loop control of Algorithm 1 (one block).
+cudaError_t launch_check(DevStatus* st, const double* red, int nblk, double rtol, int maxit,
+                         cudaStream_t s);
+cudaError_t launch_init_status(DevStatus* st, cudaStream_t s);
+// u = us - dt beta G p on all faces (w walls = 0).
+cudaError_t launch_correct(const Geo& g, const Faces& fc, const double* us, const double* vs,
+                           const double* ws, const double* p, double dt, double* u, double* v,
+                           double* w, cudaStream_t s);
+// p -= <p>_V
+cudaError_t launch_remove_mean(const Geo& g, double* p, double* red, DevStatus* st, cudaStream_t s);
+cudaError_t launch_copy_resid_sums(DevStatus* st, const double* red, int nblk, cudaStream_t s);
+
+// Adjoint helpers.
+// y = -dt * beta * W_f^{-1} g on the faces (wall z-faces zero).
+cudaError_t launch_adj_rhs(const Geo& g, const double* rho, const double* gu, const double* gv,
+                           const double* gw, double dt, double* yu, double* yv, double* yw,
+                           cudaStream_t s);
+// gus = g + W_f G mu ; grho from -dt (G p) * gus and d beta / d rho.
+cudaError_t launch_adj_finish(const Geo& g, const double* rho, const double* p, const double* mu,
+                              double dt, const double* gu, const double* gv, const double* gw,
+                              double* gus, double* gvs, double* gws, double* tx, double* ty,
+                              double* tz, cudaStream_t s);
+cudaError_t launch_adj_grho(const Geo& g, const double* tx, const double* ty, const double* tz,
+                            double* grho, cudaStream_t s);
+
+int reduce_blocks();  // number of partial sums the reduction kernels write
+
+}  // namespace pp

@@ -1,0 +1,320 @@
+// Kernels of one constant-coefficient eigenexpansion solve (Sec. 3.3.1:
+// the pressure equation with homogeneous boundary conditions solved exactly
+// by the eigenexpansion method): residual + forward x transform, y
+// transforms, the per-(kx, ky) tridiagonal solve along z, and the inverse x
+// transform fused with the pressure update of Algorithm 1.
+#include "pp_fft.cuh"
+
+namespace pp {
+
+namespace {
+
+inline int rows_per_block(int nx, size_t csize) {
+  // Two shared-memory buffers of (rows/2) complex sequences of length nx.
+  int r = (int)((64 * 1024) / ((size_t)nx * csize));
+  if (r > 64) r = 64;
+  if (r < 2) r = 2;
+  return r & ~1;
+}
+
+inline int ffty_tile(int ny, size_t csize) {
+  int tx = (int)(128 / csize);  // 128-byte row segments
+  while (tx > 1 && (size_t)2 * ny * tx * csize > 100 * 1024) tx >>= 1;
+  return tx;
+}
+
+__device__ __forceinline__ bool stopped(const DevStatus* st) { return st != nullptr && st->done; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Residual of the variable-coefficient equation and forward real x transform.
+//   mode 0: r = f (constant-coefficient solve)
+//   mode 1: e = b/dt - D(beta G p) = (D u^s - S_c)/dt, r = rho e (or e)
+// Two real rows are packed into one complex sequence (re = even row,
+// im = odd row), transformed together and separated afterwards.
+template <typename T>
+__global__ void __launch_bounds__(256) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
+                                                    const C2<T>* __restrict__ twx,
+                                                    const double* __restrict__ b, double inv_dt,
+                                                    const double* __restrict__ rho,
+                                                    const double* __restrict__ p, int mode, int p_zero,
+                                                    int scale_rho, C2<T>* __restrict__ spec,
+                                                    double* __restrict__ red, int rpb,
+                                                    const DevStatus* __restrict__ st) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double shred[32];
+  const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
+  const int nseq = rpb >> 1;
+  C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* bufB = bufA + (size_t)nseq * nx;
+  const long nrows = (long)nz * ny;
+  const long row0 = (long)blockIdx.x * rpb;
+  const size_t plane = (size_t)ny * nx;
+  double s2 = 0.0, s1 = 0.0;
+  for (int t = threadIdx.x; t < rpb * nx; t += blockDim.x) {
+    const int q = t / nx, i = t - q * nx;
+    const long row = row0 + q;
+    double r = 0.0;
+    if (row < nrows) {
+      const size_t c = (size_t)row * nx + i;
+      if (mode == 0) {
+        r = b[c];
+      } else {
+        const int k = (int)(row / ny), j = (int)(row - (long)k * ny);
+        double e = b[c] * inv_dt;
+        if (!p_zero) {
+          const int ip = (i + 1 == nx) ? 0 : i + 1, im = (i == 0) ? nx - 1 : i - 1;
+          const int jp = (j + 1 == ny) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
+          const size_t rowoff = (size_t)row * nx;
+          const size_t kp = (size_t)k * plane;
+          const double pc = p[c];
+          double acc = fc.cx[rowoff + ip] * (p[rowoff + ip] - pc) - fc.cx[c] * (pc - p[rowoff + im]);
+          acc += fc.cy[kp + (size_t)jp * nx + i] * (p[kp + (size_t)jp * nx + i] - pc)
+               - fc.cy[c] * (pc - p[kp + (size_t)jm * nx + i]);
+          double az = 0.0;
+          if (k + 1 < nz) az += fc.cz[c + plane] * (p[c + plane] - pc);
+          if (k > 0) az -= fc.cz[c] * (pc - p[c - plane]);
+          acc += az * g.inv_dzf[k];
+          e -= acc;
+        }
+        s2 += e * e;
+        s1 += fabs(e);
+        r = scale_rho ? rho[c] * e : e;
+      }
+    }
+    C2<T>& z = bufA[(size_t)(q >> 1) * nx + i];
+    if (q & 1) z.y = (T)r; else z.x = (T)r;
+  }
+  if (mode != 0) {
+    const double a2 = block_sum<double>(s2, shred);
+    const double a1 = block_sum<double>(s1, shred);
+    if (threadIdx.x == 0) {
+      red[2 * (size_t)blockIdx.x] = a2;
+      red[2 * (size_t)blockIdx.x + 1] = a1;
+    }
+  }
+  __syncthreads();
+  const C2<T>* res = fft_block<T, -1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
+  for (int t = threadIdx.x; t < nseq * nxh; t += blockDim.x) {
+    const int q = t / nxh, kx = t - q * nxh;
+    const C2<T> Z = res[(size_t)q * nx + kx];
+    const int km = (kx == 0) ? 0 : nx - kx;
+    const C2<T> W = res[(size_t)q * nx + km];
+    // A = (Z + conj W)/2, B = (Z - conj W)/(2i)
+    C2<T> A, B;
+    A.x = (T)0.5 * (Z.x + W.x); A.y = (T)0.5 * (Z.y - W.y);
+    B.x = (T)0.5 * (Z.y + W.y); B.y = (T)-0.5 * (Z.x - W.x);
+    const long ra = row0 + 2 * q;
+    if (ra < nrows) spec[(size_t)ra * nxh + kx] = A;
+    if (ra + 1 < nrows) spec[(size_t)(ra + 1) * nxh + kx] = B;
+  }
+}
+
+// Complex transform along y of one z-plane tile of tx consecutive kx.
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256) k_ffty(Geo g, FftDesc fy, const C2<T>* __restrict__ twy,
+                                              C2<T>* __restrict__ spec, int tx,
+                                              const DevStatus* __restrict__ st) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ny = g.ny, nxh = g.nxh;
+  C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* bufB = bufA + (size_t)ny * tx;
+  const int kx0 = blockIdx.x * tx;
+  const size_t base = (size_t)blockIdx.y * ny * nxh;
+  for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
+    const int y = t / tx, x = t - y * tx;
+    C2<T> v; v.x = (T)0; v.y = (T)0;
+    if (kx0 + x < nxh) v = spec[base + (size_t)y * nxh + kx0 + x];
+    bufA[t] = v;
+  }
+  __syncthreads();
+  const C2<T>* res = fft_block<T, DIR, true>(bufA, bufB, fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
+  for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
+    const int y = t / tx, x = t - y * tx;
+    if (kx0 + x < nxh) spec[base + (size_t)y * nxh + kx0 + x] = res[t];
+  }
+}
+
+// Per-column Thomas solve of (L_z + lambda_x + lambda_y) x = f with the
+// inverse pivots precomputed at plan time.  Column (0, 0) is singular: its
+// right-hand side loses its dzf-weighted mean (compatibility) and its last
+// unknown is pinned (inverse pivot 0); the pressure gauge is fixed later.
+template <typename T, bool ZERO_MODE>
+__device__ __forceinline__ void thomas_column(const Geo& g, const double* __restrict__ invd,
+                                              C2<T>* __restrict__ spec, double2* __restrict__ ybuf,
+                                              size_t col, size_t stride) {
+  const int nz = g.nz;
+  double mr = 0.0, mi = 0.0;
+  if (ZERO_MODE) {
+    for (int k = 0; k < nz; ++k) {
+      const C2<T> f = spec[(size_t)k * stride + col];
+      mr += g.dzf[k] * (double)f.x;
+      mi += g.dzf[k] * (double)f.y;
+    }
+    mr /= g.lz;
+    mi /= g.lz;
+  }
+  C2<T> f = spec[col];
+  double yr = (double)f.x - mr, yi = (double)f.y - mi;
+  ybuf[col] = make_double2(yr, yi);
+  for (int k = 1; k < nz; ++k) {
+    const size_t o = (size_t)k * stride + col;
+    const double m = g.za[k] * invd[o - stride];
+    f = spec[o];
+    yr = ((double)f.x - mr) - m * yr;
+    yi = ((double)f.y - mi) - m * yi;
+    ybuf[o] = make_double2(yr, yi);
+  }
+  size_t o = (size_t)(nz - 1) * stride + col;
+  double d = invd[o];
+  double xr = yr * d, xi = yi * d;
+  C2<T> x; x.x = (T)xr; x.y = (T)xi;
+  spec[o] = x;
+  for (int k = nz - 2; k >= 0; --k) {
+    o = (size_t)k * stride + col;
+    const double2 y = ybuf[o];
+    d = invd[o];
+    const double c = g.zc[k];
+    xr = (y.x - c * xr) * d;
+    xi = (y.y - c * xi) * d;
+    x.x = (T)xr; x.y = (T)xi;
+    spec[o] = x;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_tridiag(Geo g, const double* __restrict__ invd,
+                                                 C2<T>* __restrict__ spec, double2* __restrict__ ybuf,
+                                                 const DevStatus* __restrict__ st) {
+  if (stopped(st)) return;
+  const size_t ncol = (size_t)g.ny * g.nxh;
+  const size_t col = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  if (col == 0) thomas_column<T, true>(g, invd, spec, ybuf, col, ncol);
+  else thomas_column<T, false>(g, invd, spec, ybuf, col, ncol);
+}
+
+// Inverse x transform of two half spectra per complex sequence, then
+// p = scale * z (p_zero) or p += scale * z.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>* __restrict__ twx,
+                                                  const C2<T>* __restrict__ spec, double scale,
+                                                  double* __restrict__ p, int p_zero, int rpb,
+                                                  const DevStatus* __restrict__ st) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
+  const int nseq = rpb >> 1;
+  C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* bufB = bufA + (size_t)nseq * nx;
+  const long nrows = (long)nz * ny;
+  const long row0 = (long)blockIdx.x * rpb;
+  const bool even = (nx & 1) == 0;
+  for (int t = threadIdx.x; t < nseq * nx; t += blockDim.x) {
+    const int q = t / nx, kx = t - q * nx;
+    const long ra = row0 + 2 * q;
+    const bool upper = kx >= nxh;
+    const int m = upper ? nx - kx : kx;
+    C2<T> A, B;
+    A.x = A.y = B.x = B.y = (T)0;
+    if (ra < nrows) A = spec[(size_t)ra * nxh + m];
+    if (ra + 1 < nrows) B = spec[(size_t)(ra + 1) * nxh + m];
+    if (m == 0 || (even && m == nx / 2)) { A.y = (T)0; B.y = (T)0; }
+    if (upper) { A.y = -A.y; B.y = -B.y; }
+    C2<T> Z;
+    Z.x = A.x - B.y;
+    Z.y = A.y + B.x;
+    bufA[t] = Z;
+  }
+  __syncthreads();
+  const C2<T>* res = fft_block<T, 1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
+  for (int t = threadIdx.x; t < rpb * nx; t += blockDim.x) {
+    const int q = t / nx, i = t - q * nx;
+    const long row = row0 + q;
+    if (row >= nrows) continue;
+    const C2<T> z = res[(size_t)(q >> 1) * nx + i];
+    const double val = scale * (double)((q & 1) ? z.y : z.x);
+    const size_t c = (size_t)row * nx + i;
+    p[c] = p_zero ? val : p[c] + val;
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, const C2<T>* twx,
+                              const double* b, double inv_dt, const double* rho, const double* p,
+                              int p_zero, int scale_rho, C2<T>* spec, double* red, int* nblk_out,
+                              const DevStatus* st, cudaStream_t s) {
+  const int rpb = rows_per_block(g.nx, sizeof(C2<T>));
+  const long nrows = (long)g.nz * g.ny;
+  const int nblk = (int)((nrows + rpb - 1) / rpb);
+  const size_t smem = (size_t)rpb * g.nx * sizeof(C2<T>);
+  cudaError_t e = cudaFuncSetAttribute(k_resid_fftx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int mode = (red == nullptr) ? 0 : 1;
+  k_resid_fftx<T><<<nblk, 256, smem, s>>>(g, fc, fx, twx, b, inv_dt, rho, p, mode, p_zero, scale_rho,
+                                          spec, red, rpb, st);
+  if (nblk_out) *nblk_out = nblk;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
+                        const DevStatus* st, cudaStream_t s) {
+  const int tx = ffty_tile(g.ny, sizeof(C2<T>));
+  const size_t smem = (size_t)2 * g.ny * tx * sizeof(C2<T>);
+  dim3 grid((g.nxh + tx - 1) / tx, g.nz);
+  cudaError_t e;
+  if (inverse) {
+    e = cudaFuncSetAttribute(k_ffty<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_ffty<T, 1><<<grid, 256, smem, s>>>(g, fy, twy, spec, tx, st);
+  } else {
+    e = cudaFuncSetAttribute(k_ffty<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_ffty<T, -1><<<grid, 256, smem, s>>>(g, fy, twy, spec, tx, st);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,
+                           const DevStatus* st, cudaStream_t s) {
+  const size_t ncol = (size_t)g.ny * g.nxh;
+  const int nblk = (int)((ncol + 127) / 128);
+  k_tridiag<T><<<nblk, 128, 0, s>>>(g, invd, spec, ybuf, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
+                            double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s) {
+  const int rpb = rows_per_block(g.nx, sizeof(C2<T>));
+  const long nrows = (long)g.nz * g.ny;
+  const int nblk = (int)((nrows + rpb - 1) / rpb);
+  const size_t smem = (size_t)rpb * g.nx * sizeof(C2<T>);
+  cudaError_t e = cudaFuncSetAttribute(k_fftx_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_fftx_inv<T><<<nblk, 256, smem, s>>>(g, fx, twx, spec, scale, p, p_zero, rpb, st);
+  return cudaGetLastError();
+}
+
+#define PP_INST(T)                                                                                   \
+  template cudaError_t launch_resid_fftx<T>(const Geo&, const Faces&, const FftDesc&, const C2<T>*,  \
+                                            const double*, double, const double*, const double*,     \
+                                            int, int, C2<T>*, double*, int*, const DevStatus*,       \
+                                            cudaStream_t);                                           \
+  template cudaError_t launch_ffty<T>(const Geo&, const FftDesc&, const C2<T>*, C2<T>*, int,         \
+                                      const DevStatus*, cudaStream_t);                               \
+  template cudaError_t launch_tridiag<T>(const Geo&, const double*, C2<T>*, double2*,                \
+                                         const DevStatus*, cudaStream_t);                            \
+  template cudaError_t launch_fftx_inv<T>(const Geo&, const FftDesc&, const C2<T>*, const C2<T>*,    \
+                                          double, double*, int, const DevStatus*, cudaStream_t);
+PP_INST(double)
+PP_INST(float)
+#undef PP_INST
+
+}  // namespace pp

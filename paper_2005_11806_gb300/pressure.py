@@ -1,0 +1,224 @@
+"""Python binding of the C ABI in include/pressure_projection.h.
+
+Argument marshalling only: every step of the projection runs in the CUDA
+library ``libpp_gb300.so`` built in-tree by ``build_ext.py``.  Field
+arguments are float64, C-contiguous torch tensors (CUDA or CPU) or numpy
+arrays; CPU/numpy buffers are host pointers, which the library stages
+through its own device buffers.  Loading fails loudly when the library is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpp_gb300.so")
+
+PP_OK, PP_ERR_INVALID_ARG, PP_ERR_UNSUPPORTED, PP_ERR_NOT_CONVERGED = 0, 1, 2, 3
+PP_ERR_NUMERIC, PP_ERR_CUDA, PP_ERR_OOM = 4, 5, 6
+PP_BC_PERIODIC, PP_BC_WALL = 0, 1
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_fp32": 1}
+
+
+class pp_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("zfaces", ctypes.POINTER(ctypes.c_double)), ("bc", ctypes.c_int * 3)]
+
+
+class pp_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("res0", ctypes.c_double), ("res_final", ctypes.c_double),
+                ("res_l1_sum", ctypes.c_double), ("mean_S_removed", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pp_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong),
+                ("total_ms", ctypes.c_double)]
+
+
+class PressureError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {status_string(code)} (pp_status {code})")
+        self.code = code
+
+
+_lib = None
+
+EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_solve",
+           "pressure_mixture_density", "pressure_correct", "pressure_solve_adjoint",
+           "pressure_last_info", "pressure_profile_enable", "pressure_profile_read",
+           "pressure_status_string")
+
+
+def lib():
+    """Load the CUDA library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2005_11806_gb300.build_ext` (no CPU fallback exists)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, d, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    pinfo = ctypes.POINTER(pp_info)
+    L.pressure_plan_create.argtypes = [ctypes.POINTER(pp_grid), i, vp, ctypes.POINTER(vp)]
+    L.pressure_plan_destroy.argtypes = [vp]
+    L.pressure_solve.argtypes = [vp, vp, vp, pinfo]
+    L.pressure_mixture_density.argtypes = [vp, vp, d, d, vp]
+    L.pressure_correct.argtypes = [vp, vp, vp, vp, vp, vp, d, vp, i, vp, vp, vp, d, i, pinfo]
+    L.pressure_solve_adjoint.argtypes = [vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp, d, i, pinfo]
+    L.pressure_last_info.argtypes = [vp, pinfo]
+    L.pressure_profile_enable.argtypes = [vp, i]
+    L.pressure_profile_read.argtypes = [vp, ctypes.POINTER(pp_kernel_time), i,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
+    L.pressure_status_string.argtypes = [i]
+    L.pressure_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS[:-1]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def status_string(code):
+    return lib().pressure_status_string(int(code)).decode()
+
+
+def _ptr(x):
+    """Address of a float64 C-contiguous buffer (torch tensor or numpy)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy fields must be C-contiguous float64")
+        return x.ctypes.data
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensor fields must be contiguous float64")
+        return x.data_ptr()
+    raise TypeError(f"unsupported field type {type(x)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover - torch without CUDA
+        pass
+    return 0
+
+
+def _check(code, what, allow=()):
+    if code != PP_OK and code not in allow:
+        raise PressureError(code, what)
+    return code
+
+
+def pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None):
+    """Create a plan; returns an opaque handle (int).  ``zfaces``: None for a
+    uniform z grid, else nz + 1 increasing face coordinates (host array)."""
+    g = pp_grid()
+    g.nx, g.ny, g.nz = int(nx), int(ny), int(nz)
+    g.lx, g.ly, g.lz = float(lx), float(ly), float(lz)
+    keep = None
+    if zfaces is not None:
+        keep = np.ascontiguousarray(zfaces, dtype=np.float64)
+        if keep.shape != (int(nz) + 1,):
+            raise ValueError("zfaces must hold nz + 1 values")
+        g.zfaces = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    g.bc[0], g.bc[1], g.bc[2] = PP_BC_PERIODIC, PP_BC_PERIODIC, PP_BC_WALL
+    out = ctypes.c_void_p()
+    _check(lib().pressure_plan_create(ctypes.byref(g), PRECISIONS[precision], _stream(stream),
+                                      ctypes.byref(out)), "pressure_plan_create")
+    return out.value
+
+
+def pressure_plan_destroy(plan):
+    _check(lib().pressure_plan_destroy(plan), "pressure_plan_destroy")
+
+
+def pressure_solve(plan, f, p):
+    info = pp_info()
+    _check(lib().pressure_solve(plan, _ptr(f), _ptr(p), ctypes.byref(info)), "pressure_solve")
+    return info.as_dict()
+
+
+def pressure_mixture_density(plan, phi, rho_g, rho_l, rho):
+    _check(lib().pressure_mixture_density(plan, _ptr(phi), float(rho_g), float(rho_l), _ptr(rho)),
+           "pressure_mixture_density")
+
+
+def pressure_correct(plan, us, vs, ws, rho, S, dt, p, u, v, w, rtol=1e-10, maxit=500,
+                     warm_start=False, sync=True, allow_not_converged=False):
+    """Method III projection.  With ``sync=False`` the call only enqueues the
+    work (read the status later with ``pressure_last_info``)."""
+    info = pp_info()
+    code = lib().pressure_correct(plan, _ptr(us), _ptr(vs), _ptr(ws), _ptr(rho), _ptr(S),
+                                  float(dt), _ptr(p), int(bool(warm_start)), _ptr(u), _ptr(v),
+                                  _ptr(w), float(rtol), int(maxit),
+                                  ctypes.byref(info) if sync else None)
+    allow = (PP_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    _check(code, "pressure_correct", allow)
+    return info.as_dict() if sync else None
+
+
+def pressure_last_info(plan):
+    info = pp_info()
+    lib().pressure_last_info(plan, ctypes.byref(info))
+    return info.as_dict()
+
+
+def pressure_solve_adjoint(plan, rho, p, dt, gu, gv, gw, gus, gvs, gws, grho, rtol=1e-10, maxit=500,
+                           allow_not_converged=False):
+    info = pp_info()
+    code = lib().pressure_solve_adjoint(plan, _ptr(rho), _ptr(p), float(dt), _ptr(gu), _ptr(gv),
+                                        _ptr(gw), _ptr(gus), _ptr(gvs), _ptr(gws), _ptr(grho),
+                                        float(rtol), int(maxit), ctypes.byref(info))
+    _check(code, "pressure_solve_adjoint", (PP_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return info.as_dict()
+
+
+def pressure_profile_enable(plan, enable=True):
+    _check(lib().pressure_profile_enable(plan, int(bool(enable))), "pressure_profile_enable")
+
+
+def pressure_profile_read(plan):
+    """Returns ({kernel: (launches, total_ms)}, total_launches)."""
+    n = ctypes.c_int()
+    tot = ctypes.c_longlong()
+    _check(lib().pressure_profile_read(plan, None, 0, ctypes.byref(n), ctypes.byref(tot)),
+           "pressure_profile_read")
+    arr = (pp_kernel_time * max(n.value, 1))()
+    _check(lib().pressure_profile_read(plan, arr, n.value, ctypes.byref(n), ctypes.byref(tot)),
+           "pressure_profile_read")
+    return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms) for k in range(n.value)}, tot.value
+
+
+class Plan:
+    """Owning wrapper of a plan handle."""
+
+    def __init__(self, nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None):
+        self.shape = (int(nz), int(ny), int(nx))
+        self.wshape = (int(nz) + 1, int(ny), int(nx))
+        self.handle = pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces, precision, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pressure_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
