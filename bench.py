@@ -323,7 +323,7 @@ def main():
 # Method III passes the benchmark workload needs in FP64 (measured on the GPU
 # path, whose iterates equal the oracle's); used to scale the oracle's
 # per-pass time in the reference arm.
-REF_ITERS_DEFAULT = 1
+REF_ITERS_DEFAULT = 2447
 
 if __name__ == "__main__":
     sys.exit(main())
