@@ -48,7 +48,8 @@ typedef enum {
     PP_ERR_NOT_CONVERGED = 3, /* maxit reached before the tolerance */
     PP_ERR_NUMERIC = 4,       /* NaN/Inf in the residual */
     PP_ERR_CUDA = 5,          /* a CUDA runtime call failed */
-    PP_ERR_OOM = 6            /* device allocation failed */
+    PP_ERR_OOM = 6,           /* device allocation failed */
+    PP_ERR_TOO_LARGE = 7      /* grid needs more than the fixed no-allocation scratch */
 } pp_status;
 
 typedef enum { PP_BC_PERIODIC = 0, PP_BC_WALL = 1 } pp_bc;
@@ -118,6 +119,24 @@ pp_status pressure_solve_adjoint(pp_plan plan, const double* rho, const double* 
                                  const double* gu, const double* gv, const double* gw,
                                  double* gus, double* gvs, double* gws, double* grho,
                                  double rtol, int maxit, pp_info* info);
+
+/* Constant-coefficient FP64 solve (same result as pressure_solve on an FP64
+ * plan) that allocates no device memory.  The paper has no counterpart: this
+ * entry point serves callers that cannot call cudaMalloc, e.g. code running
+ * while a stream is being captured, hosts whose device memory belongs to an
+ * external pool or budget, or loops that must not enter an allocator.
+ * Working memory is one fixed 16 MiB device array inside the library, held by
+ * every GPU that loads the library until the process exits; grids whose
+ * spectral array, pivots and tables do not fit return PP_ERR_TOO_LARGE
+ * (about 128 x 128 x 64 cells fit).  f and p must be device pointers (host
+ * pointers return PP_ERR_INVALID_ARG); the caller owns them.  Work is
+ * enqueued on `stream` (a cudaStream_t) and the call returns without waiting.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and each overwrites what the previous one left: calls that
+ * may overlap on the GPU (different streams or devices sharing nothing else)
+ * race and must be ordered by the caller. */
+pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f, double* p, void* stream);
 
 /* Wait for the plan's stream and fill info from the last pressure_correct
  * or pressure_solve_adjoint call. */

@@ -306,6 +306,7 @@ const char* pressure_status_string(pp_status s) {
     case PP_ERR_NUMERIC: return "non-finite residual";
     case PP_ERR_CUDA: return "CUDA runtime error";
     case PP_ERR_OOM: return "device allocation failed";
+    case PP_ERR_TOO_LARGE: return "grid too large for the fixed no-allocation scratch (16 MiB)";
   }
   return "unknown status";
 }

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpp_gb300.so")
 
 PP_OK, PP_ERR_INVALID_ARG, PP_ERR_UNSUPPORTED, PP_ERR_NOT_CONVERGED = 0, 1, 2, 3
-PP_ERR_NUMERIC, PP_ERR_CUDA, PP_ERR_OOM = 4, 5, 6
+PP_ERR_NUMERIC, PP_ERR_CUDA, PP_ERR_OOM, PP_ERR_TOO_LARGE = 4, 5, 6, 7
 PP_BC_PERIODIC, PP_BC_WALL = 0, 1
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_fp32": 1}
 
@@ -54,6 +54,7 @@ _lib = None
 EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_solve",
            "pressure_mixture_density", "pressure_correct", "pressure_solve_adjoint",
            "pressure_last_info", "pressure_profile_enable", "pressure_profile_read",
+           "pressure_solve_noalloc",
            "pressure_status_string")
 
 
@@ -78,6 +79,7 @@ def lib():
     L.pressure_profile_enable.argtypes = [vp, i]
     L.pressure_profile_read.argtypes = [vp, ctypes.POINTER(pp_kernel_time), i,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
+    L.pressure_solve_noalloc.argtypes = [ctypes.POINTER(pp_grid), vp, vp, vp]
     L.pressure_status_string.argtypes = [i]
     L.pressure_status_string.restype = ctypes.c_char_p
     for name in EXPORTS[:-1]:
@@ -141,6 +143,29 @@ def pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", 
     _check(lib().pressure_plan_create(ctypes.byref(g), PRECISIONS[precision], _stream(stream),
                                       ctypes.byref(out)), "pressure_plan_create")
     return out.value
+
+
+def _grid(nx, ny, nz, lx, ly, lz, zfaces):
+    g = pp_grid()
+    g.nx, g.ny, g.nz = int(nx), int(ny), int(nz)
+    g.lx, g.ly, g.lz = float(lx), float(ly), float(lz)
+    keep = None
+    if zfaces is not None:
+        keep = np.ascontiguousarray(zfaces, dtype=np.float64)
+        if keep.shape != (int(nz) + 1,):
+            raise ValueError("zfaces must hold nz + 1 values")
+        g.zfaces = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    g.bc[0], g.bc[1], g.bc[2] = PP_BC_PERIODIC, PP_BC_PERIODIC, PP_BC_WALL
+    return g, keep
+
+
+def pressure_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, zfaces=None, stream=None):
+    """FP64 constant-coefficient solve that allocates no device memory (see
+    the header).  f, p: CUDA float64 tensors.  Returns after enqueueing."""
+    g, keep = _grid(nx, ny, nz, lx, ly, lz, zfaces)
+    _check(lib().pressure_solve_noalloc(ctypes.byref(g), _ptr(f), _ptr(p), _stream(stream)),
+           "pressure_solve_noalloc")
+    del keep
 
 
 def pressure_plan_destroy(plan):
