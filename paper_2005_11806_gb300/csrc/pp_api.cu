@@ -20,7 +20,7 @@ const char* const kNames[K_COUNT] = {
     "resid_fftx", "check", "ffty_fwd", "tridiag_z", "ffty_inv", "fftx_inv_update", "init_status",
     "prep_faces", "mean_S", "rhs_b", "remove_mean", "correct", "mixture_density", "adj_rhs",
     "adj_finish", "adj_grho"};
-const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 3, 1, 1, 1, 1, 1};
+const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1};
 struct Rec { int kid; cudaEvent_t a, b; };
 struct Prof {
   bool on = false;
@@ -44,6 +44,7 @@ struct pp_plan_s {
   // device tables
   double *d_inv_dzf = nullptr, *d_inv_dzc = nullptr, *d_dzf = nullptr, *d_za = nullptr, *d_zc = nullptr;
   double *d_lamx = nullptr, *d_lamy = nullptr, *d_invd = nullptr;
+  float* d_inv_dzf_f = nullptr;
   void *d_twx = nullptr, *d_twy = nullptr;
   // workspaces
   void* d_spec = nullptr;
@@ -277,7 +278,10 @@ pp_status check_plan(pp_plan P) {
 void free_plan(pp_plan_s* P) {
   if (!P) return;
   double* dptrs[] = {P->d_inv_dzf, P->d_inv_dzc, P->d_dzf, P->d_za, P->d_zc, P->d_lamx, P->d_lamy,
-                     P->d_invd, P->d_b, P->d_red, P->faces.cx, P->faces.cy, P->faces.cz};
+                     P->d_invd, P->d_b, P->d_red, P->faces.cx, P->faces.cy, P->faces.cz,
+                     P->faces.diag};
+  if (P->faces.rhof) cudaFree(P->faces.rhof);
+  if (P->d_inv_dzf_f) cudaFree(P->d_inv_dzf_f);
   for (double* d : dptrs) if (d) cudaFree(d);
   if (P->d_twx) cudaFree(P->d_twx);
   if (P->d_twy) cudaFree(P->d_twy);
@@ -321,6 +325,7 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL)
     return PP_ERR_UNSUPPORTED;
   if ((G.nx & 1) != 0) return PP_ERR_UNSUPPORTED;
+  if (G.nx > 2048 || G.ny > 2048) return PP_ERR_UNSUPPORTED;  // one line per block in the FFTs
   if ((long)G.nx * G.ny * (G.nz + 1) > (1L << 31)) return PP_ERR_UNSUPPORTED;
   pp_plan_s* P = new (std::nothrow) pp_plan_s();
   if (!P) return PP_ERR_OOM;
@@ -407,6 +412,9 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       (st = dalloc(&P->faces.cx, nc * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->faces.cy, nc * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->faces.cz, nw * sizeof(double))) != PP_OK ||
+      (st = dalloc(&P->faces.diag, nc * sizeof(double))) != PP_OK ||
+      (st = dalloc(&P->faces.rhof, nc * sizeof(float))) != PP_OK ||
+      (st = dalloc(&P->d_inv_dzf_f, (size_t)nz * sizeof(float))) != PP_OK ||
       (st = dalloc(&P->d_st, sizeof(DevStatus))) != PP_OK) {
     free_plan(P);
     return st;
@@ -417,8 +425,17 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
     free_plan(P);
     return PP_ERR_CUDA;
   }
+  {
+    std::vector<float> f32(nz);
+    for (int k = 0; k < nz; ++k) f32[k] = (float)inv_dzf[k];
+    if (cudaMemcpy(P->d_inv_dzf_f, f32.data(), nz * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_plan(P);
+      return PP_ERR_CUDA;
+    }
+  }
   Geo& g = P->geo;
   g.nx = G.nx; g.ny = G.ny; g.nz = nz; g.nxh = P->nxh;
+  g.inv_dzf_f = P->d_inv_dzf_f;
   g.dx = P->dx; g.dy = P->dy;
   g.inv_dx2 = 1.0 / (P->dx * P->dx);
   g.inv_dy2 = 1.0 / (P->dy * P->dy);

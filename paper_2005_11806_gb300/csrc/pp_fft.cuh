@@ -145,6 +145,72 @@ __device__ C2<T>* fft_block(C2<T>* a, C2<T>* b, const FftDesc& d, int nbatch, in
   return src;
 }
 
+// In-place variant: one shared buffer.  Each pass first gathers every
+// butterfly input of the thread into registers, synchronises, then writes
+// the outputs; at most EPT elements per thread per pass (EPT >= nbatch * n /
+// nthreads).  Twiddles are read from `tw` (normally a shared-memory copy).
+template <typename T, int DIR, int R, int EPT, bool BATCH_FAST>
+__device__ __forceinline__ void fft_pass_inplace(C2<T>* buf, int n, int Ns, int nbatch, int es, int bs,
+                                                 const C2<T>* tw, int tid, int nth) {
+  constexpr int BPT = (EPT + R - 1) / R;
+  const int nb = n / R;
+  const int total = nb * nbatch;
+  const int tws = n / (Ns * R);
+  C2<T> v[BPT][R];
+#pragma unroll
+  for (int u = 0; u < BPT; ++u) {
+    const int t = tid + u * nth;
+    if (t < total) {
+      int bi, j;
+      if (BATCH_FAST) { j = t / nbatch; bi = t - j * nbatch; }
+      else { bi = t / nb; j = t - bi * nb; }
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[u][r] = buf[bi * bs + (j + r * nb) * es];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < BPT; ++u) {
+    const int t = tid + u * nth;
+    if (t < total) {
+      int bi, j;
+      if (BATCH_FAST) { j = t / nbatch; bi = t - j * nbatch; }
+      else { bi = t / nb; j = t - bi * nb; }
+      const int k = j % Ns;
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C2<T> w = tw[r * k * tws];
+          w.y = DIR > 0 ? w.y : -w.y;
+          v[u][r] = cmul<T>(v[u][r], w);
+        }
+      }
+      Dft<T, DIR, R>::run(v[u]);
+      const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[bi * bs + (base + r * Ns) * es] = v[u][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int DIR, int EPT, bool BATCH_FAST>
+__device__ void fft_block_inplace(C2<T>* buf, const FftDesc& d, int nbatch, int es, int bs,
+                                  const C2<T>* tw, int tid, int nth) {
+  int Ns = 1;
+  for (int s = 0; s < d.nst; ++s) {
+    const int R = d.radix[s];
+    switch (R) {
+      case 8: fft_pass_inplace<T, DIR, 8, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+      case 4: fft_pass_inplace<T, DIR, 4, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+      case 2: fft_pass_inplace<T, DIR, 2, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+      case 3: fft_pass_inplace<T, DIR, 3, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+      default: fft_pass_inplace<T, DIR, 5, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+    }
+    Ns *= R;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* sh) {
   // sh: at least 32 entries

@@ -47,16 +47,48 @@ struct Geo {
   const double* dzf;      // [nz]
   const double* za;       // [nz]   sub-diagonal of L_z
   const double* zc;       // [nz]   super-diagonal of L_z
+  const float* inv_dzf_f; // [nz]   1 / cell width (FP32 copy)
   double lz;
 };
 
-// Face coefficients of D(beta G .): cx = beta_x / dx^2, cy = beta_y / dy^2,
-// cz = beta_z / dzc (0 on the wall faces); divide the z part by dzf.
+// Coefficients of D(beta G .) with each cell's row multiplied by its width
+// dzf_k (so the z coefficients need no per-cell scaling):
+//   cx = dzf_k beta_x / dx^2, cy = dzf_k beta_y / dy^2 (faces of layer k),
+//   cz = beta_z / dzc (z faces, 0 on the walls),
+//   diag = sum of the six coefficients of the cell, rhof = rho_c in FP32.
 struct Faces {
-  double* cx;  // [nz][ny][nx]
-  double* cy;  // [nz][ny][nx]
-  double* cz;  // [nz+1][ny][nx]
+  double* cx;    // [nz][ny][nx]
+  double* cy;    // [nz][ny][nx]
+  double* cz;    // [nz+1][ny][nx]
+  double* diag;  // [nz][ny][nx]
+  float* rhof;   // [nz][ny][nx]
 };
+
+// Exact FP32 -> FP64 widening done on the integer pipe (the FP64 pipe of this
+// part is the scarce resource).  Subnormal inputs become signed zeros.
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned m = b & 0x7FFFFFu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+  unsigned lo = m << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 0xFFu) hi = sign | 0x7FF00000u | (m >> 3);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// FP64 -> FP32 narrowing on the integer pipe: round half away from zero on
+// the first dropped bit; underflow flushes to zero, overflow/NaN give Inf.
+__device__ __forceinline__ float narrow_f64(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 896;
+  unsigned bits = ((unsigned)e << 23) + (((hi & 0xFFFFFu) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+  if (e <= 0) bits = 0u;
+  if (e >= 255) bits = 0x7F800000u;
+  return __uint_as_float(sign | bits);
+}
 
 // ---- launchers (pp_kernels_*.cu) -------------------------------------
 

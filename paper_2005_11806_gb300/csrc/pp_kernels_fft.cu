@@ -9,19 +9,29 @@ namespace pp {
 
 namespace {
 
-inline int rows_per_block(int nx, size_t csize) {
-  // Two shared-memory buffers of (rows/2) complex sequences of length nx.
-  int r = (int)((64 * 1024) / ((size_t)nx * csize));
-  if (r > 64) r = 64;
-  if (r < 2) r = 2;
-  return r & ~1;
+constexpr int kThreads = 256;
+// FFT elements per block = kEpt * kThreads (two shared buffers of that many
+// complex values).  8 was the fastest of {2, 4, 8, 16} for every kernel in a
+// 512^3 sweep on GB300.
+constexpr int kEpt = 8;
+constexpr int kPrefetchInv = 8;  // p values prefetched per thread in the inverse x kernel
+
+// Rows per block of the x kernels: (rows/2) complex sequences of length nx
+// with at most ept * kThreads elements in the shared buffer.
+inline int rows_per_block(int nx, int ept) {
+  int nseq = (ept * kThreads) / nx;
+  if (nseq > 32) nseq = 32;
+  if (nseq < 1) nseq = 1;
+  return 2 * nseq;
 }
 
-inline int ffty_tile(int ny, size_t csize) {
+// kx columns per y tile: a power of two with tx * ny <= ept * kThreads.
+inline int ffty_tile(int ny, size_t csize, int ept) {
   int tx = (int)(128 / csize);  // 128-byte row segments
-  while (tx > 1 && (size_t)2 * ny * tx * csize > 100 * 1024) tx >>= 1;
+  while (tx > 1 && ny * tx > ept * kThreads) tx >>= 1;
   return tx;
 }
+
 
 __device__ __forceinline__ bool stopped(const DevStatus* st) { return st != nullptr && st->done; }
 
@@ -30,7 +40,10 @@ __device__ __forceinline__ bool stopped(const DevStatus* st) { return st != null
 // ---------------------------------------------------------------------------
 // Residual of the variable-coefficient equation and forward real x transform.
 //   mode 0: r = f (constant-coefficient solve)
-//   mode 1: e = b/dt - D(beta G p) = (D u^s - S_c)/dt, r = rho e (or e)
+//   mode 1: e = (D u^s - S_c)/dt, evaluated in FP64 in the row-scaled form
+//           dzf_k e = b_s - (sum_nb c_nb p_nb - diag p_c), b_s = dzf_k b / dt;
+//           r = rho e (or e).  The mixed path narrows dzf_k e to FP32 and
+//           finishes (scaling, norms, rho) in FP32.
 // Two real rows are packed into one complex sequence (re = even row,
 // im = odd row), transformed together and separated afterwards.
 template <typename T>
@@ -52,44 +65,52 @@ __global__ void __launch_bounds__(256) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
   const long nrows = (long)nz * ny;
   const long row0 = (long)blockIdx.x * rpb;
   const size_t plane = (size_t)ny * nx;
-  double s2 = 0.0, s1 = 0.0;
+  T s2 = (T)0, s1 = (T)0;
+  (void)inv_dt;
   for (int t = threadIdx.x; t < rpb * nx; t += blockDim.x) {
     const int q = t / nx, i = t - q * nx;
     const long row = row0 + q;
-    double r = 0.0;
+    T r = (T)0;
     if (row < nrows) {
       const size_t c = (size_t)row * nx + i;
       if (mode == 0) {
-        r = b[c];
+        r = (T)b[c];
       } else {
         const int k = (int)(row / ny), j = (int)(row - (long)k * ny);
-        double e = b[c] * inv_dt;
+        double ep = b[c];
         if (!p_zero) {
           const int ip = (i + 1 == nx) ? 0 : i + 1, im = (i == 0) ? nx - 1 : i - 1;
           const int jp = (j + 1 == ny) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
           const size_t rowoff = (size_t)row * nx;
           const size_t kp = (size_t)k * plane;
-          const double pc = p[c];
-          double acc = fc.cx[rowoff + ip] * (p[rowoff + ip] - pc) - fc.cx[c] * (pc - p[rowoff + im]);
-          acc += fc.cy[kp + (size_t)jp * nx + i] * (p[kp + (size_t)jp * nx + i] - pc)
-               - fc.cy[c] * (pc - p[kp + (size_t)jm * nx + i]);
-          double az = 0.0;
-          if (k + 1 < nz) az += fc.cz[c + plane] * (p[c + plane] - pc);
-          if (k > 0) az -= fc.cz[c] * (pc - p[c - plane]);
-          acc += az * g.inv_dzf[k];
-          e -= acc;
+          double t = -fc.diag[c] * p[c];
+          t = fma(fc.cx[rowoff + ip], p[rowoff + ip], t);
+          t = fma(fc.cx[c], p[rowoff + im], t);
+          t = fma(fc.cy[kp + (size_t)jp * nx + i], p[kp + (size_t)jp * nx + i], t);
+          t = fma(fc.cy[c], p[kp + (size_t)jm * nx + i], t);
+          if (k + 1 < nz) t = fma(fc.cz[c + plane], p[c + plane], t);
+          if (k > 0) t = fma(fc.cz[c], p[c - plane], t);
+          ep -= t;
         }
-        s2 += e * e;
-        s1 += fabs(e);
-        r = scale_rho ? rho[c] * e : e;
+        if (sizeof(T) == sizeof(float)) {
+          const float e = narrow_f64(ep) * g.inv_dzf_f[k];
+          s2 = fmaf(e, e, (float)s2);
+          s1 += fabsf(e);
+          r = (T)(scale_rho ? fc.rhof[c] * e : e);
+        } else {
+          const double e = ep * g.inv_dzf[k];
+          s2 = (T)fma(e, e, (double)s2);
+          s1 += (T)fabs(e);
+          r = (T)(scale_rho ? rho[c] * e : e);
+        }
       }
     }
     C2<T>& z = bufA[(size_t)(q >> 1) * nx + i];
-    if (q & 1) z.y = (T)r; else z.x = (T)r;
+    if (q & 1) z.y = r; else z.x = r;
   }
   if (mode != 0) {
-    const double a2 = block_sum<double>(s2, shred);
-    const double a1 = block_sum<double>(s1, shred);
+    const double a2 = block_sum<double>((double)s2, shred);
+    const double a1 = block_sum<double>((double)s1, shred);
     if (threadIdx.x == 0) {
       red[2 * (size_t)blockIdx.x] = a2;
       red[2 * (size_t)blockIdx.x + 1] = a1;
@@ -142,52 +163,94 @@ __global__ void __launch_bounds__(256) k_ffty(Geo g, FftDesc fy, const C2<T>* __
 // inverse pivots precomputed at plan time.  Column (0, 0) is singular: its
 // right-hand side loses its dzf-weighted mean (compatibility) and its last
 // unknown is pinned (inverse pivot 0); the pressure gauge is fixed later.
+// Loads run PF levels ahead of the recurrence; FP32 spectra are widened and
+// narrowed on the integer pipe.
+template <typename T> __device__ __forceinline__ double2 to_d2(C2<T> v);
+template <> __device__ __forceinline__ double2 to_d2<double>(double2 v) { return v; }
+template <> __device__ __forceinline__ double2 to_d2<float>(float2 v) {
+  return make_double2(widen_f32(v.x), widen_f32(v.y));
+}
+template <typename T> __device__ __forceinline__ C2<T> from_d(double x, double y);
+template <> __device__ __forceinline__ double2 from_d<double>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ float2 from_d<float>(double x, double y) {
+  return make_float2(narrow_f64(x), narrow_f64(y));
+}
+
 template <typename T, bool ZERO_MODE>
 __device__ __forceinline__ void thomas_column(const Geo& g, const double* __restrict__ invd,
-                                              C2<T>* __restrict__ spec, double2* __restrict__ ybuf,
-                                              size_t col, size_t stride) {
+                                              C2<T>* spec, double2* ybuf, size_t col, size_t stride) {
+  constexpr int PF = 4;
   const int nz = g.nz;
   double mr = 0.0, mi = 0.0;
   if (ZERO_MODE) {
     for (int k = 0; k < nz; ++k) {
-      const C2<T> f = spec[(size_t)k * stride + col];
-      mr += g.dzf[k] * (double)f.x;
-      mi += g.dzf[k] * (double)f.y;
+      const double2 f = to_d2<T>(spec[(size_t)k * stride + col]);
+      mr += g.dzf[k] * f.x;
+      mi += g.dzf[k] * f.y;
     }
     mr /= g.lz;
     mi /= g.lz;
   }
-  C2<T> f = spec[col];
-  double yr = (double)f.x - mr, yi = (double)f.y - mi;
-  ybuf[col] = make_double2(yr, yi);
-  for (int k = 1; k < nz; ++k) {
-    const size_t o = (size_t)k * stride + col;
-    const double m = g.za[k] * invd[o - stride];
-    f = spec[o];
-    yr = ((double)f.x - mr) - m * yr;
-    yi = ((double)f.y - mi) - m * yi;
-    ybuf[o] = make_double2(yr, yi);
+  // forward sweep: y_k = f_k - (a_k / d_{k-1}) y_{k-1}
+  C2<T> fq[PF];
+  double dq[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int k = u < nz ? u : nz - 1;
+    fq[u] = spec[(size_t)k * stride + col];
+    dq[u] = invd[(size_t)k * stride + col];
   }
-  size_t o = (size_t)(nz - 1) * stride + col;
-  double d = invd[o];
-  double xr = yr * d, xi = yi * d;
-  C2<T> x; x.x = (T)xr; x.y = (T)xi;
-  spec[o] = x;
-  for (int k = nz - 2; k >= 0; --k) {
-    o = (size_t)k * stride + col;
-    const double2 y = ybuf[o];
-    d = invd[o];
-    const double c = g.zc[k];
-    xr = (y.x - c * xr) * d;
-    xi = (y.y - c * xi) * d;
-    x.x = (T)xr; x.y = (T)xi;
-    spec[o] = x;
+  double yr = 0.0, yi = 0.0, dprev = 0.0;
+  for (int k0 = 0; k0 < nz; k0 += PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 + u;
+      if (k < nz) {
+        const double2 f = to_d2<T>(fq[u]);
+        const double d = dq[u];
+        const int kn = k + PF < nz ? k + PF : nz - 1;
+        fq[u] = spec[(size_t)kn * stride + col];
+        dq[u] = invd[(size_t)kn * stride + col];
+        const double m = (k == 0) ? 0.0 : g.za[k] * dprev;
+        yr = (f.x - mr) - m * yr;
+        yi = (f.y - mi) - m * yi;
+        ybuf[(size_t)k * stride + col] = make_double2(yr, yi);
+        dprev = d;
+      }
+    }
+  }
+  // back substitution: x_k = (y_k - c_k x_{k+1}) / d_k
+  double xr = yr * dprev, xi = yi * dprev;
+  spec[(size_t)(nz - 1) * stride + col] = from_d<T>(xr, xi);
+  double2 yq[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int k = nz - 2 - u >= 0 ? nz - 2 - u : 0;
+    yq[u] = ybuf[(size_t)k * stride + col];
+    dq[u] = invd[(size_t)k * stride + col];
+  }
+  for (int k0 = nz - 2; k0 >= 0; k0 -= PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 - u;
+      if (k >= 0) {
+        const double2 y = yq[u];
+        const double d = dq[u];
+        const int kn = k - PF >= 0 ? k - PF : 0;
+        yq[u] = ybuf[(size_t)kn * stride + col];
+        dq[u] = invd[(size_t)kn * stride + col];
+        const double c = g.zc[k];
+        xr = (y.x - c * xr) * d;
+        xi = (y.y - c * xi) * d;
+        spec[(size_t)k * stride + col] = from_d<T>(xr, xi);
+      }
+    }
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_tridiag(Geo g, const double* __restrict__ invd,
-                                                 C2<T>* __restrict__ spec, double2* __restrict__ ybuf,
+                                                 C2<T>* spec, double2* ybuf,  // ybuf may alias spec
                                                  const DevStatus* __restrict__ st) {
   if (stopped(st)) return;
   const size_t ncol = (size_t)g.ny * g.nxh;
@@ -198,7 +261,8 @@ __global__ void __launch_bounds__(128) k_tridiag(Geo g, const double* __restrict
 }
 
 // Inverse x transform of two half spectra per complex sequence, then
-// p = scale * z (p_zero) or p += scale * z.
+// p = scale * z (p_zero) or p += scale * z.  The p values a thread updates
+// are loaded before the transform so their latency overlaps it.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>* __restrict__ twx,
                                                   const C2<T>* __restrict__ spec, double scale,
@@ -213,6 +277,16 @@ __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>
   const long nrows = (long)nz * ny;
   const long row0 = (long)blockIdx.x * rpb;
   const bool even = (nx & 1) == 0;
+  const int nout = rpb * nx;
+  constexpr int NP = kPrefetchInv;
+  double pv[NP];
+#pragma unroll
+  for (int u = 0; u < NP; ++u) {
+    const int t = threadIdx.x + u * blockDim.x;
+    const int q = t / nx, i = t - q * nx;
+    pv[u] = 0.0;
+    if (!p_zero && t < nout && row0 + q < nrows) pv[u] = p[(size_t)(row0 + q) * nx + i];
+  }
   for (int t = threadIdx.x; t < nseq * nx; t += blockDim.x) {
     const int q = t / nx, kx = t - q * nx;
     const long ra = row0 + 2 * q;
@@ -231,14 +305,28 @@ __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>
   }
   __syncthreads();
   const C2<T>* res = fft_block<T, 1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
-  for (int t = threadIdx.x; t < rpb * nx; t += blockDim.x) {
+#pragma unroll
+  for (int u = 0; u < NP; ++u) {
+    const int t = threadIdx.x + u * blockDim.x;
     const int q = t / nx, i = t - q * nx;
     const long row = row0 + q;
-    if (row >= nrows) continue;
-    const C2<T> z = res[(size_t)(q >> 1) * nx + i];
-    const double val = scale * (double)((q & 1) ? z.y : z.x);
-    const size_t c = (size_t)row * nx + i;
-    p[c] = p_zero ? val : p[c] + val;
+    if (t < nout && row < nrows) {
+      const C2<T> z = res[(size_t)(q >> 1) * nx + i];
+      const T zv = (q & 1) ? z.y : z.x;
+      const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
+      p[(size_t)row * nx + i] = fma(scale, zd, pv[u]);
+    }
+  }
+  for (int t = threadIdx.x + NP * blockDim.x; t < nout; t += blockDim.x) {  // beyond the prefetch
+    const int q = t / nx, i = t - q * nx;
+    const long row = row0 + q;
+    if (row < nrows) {
+      const C2<T> z = res[(size_t)(q >> 1) * nx + i];
+      const T zv = (q & 1) ? z.y : z.x;
+      const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
+      const size_t c = (size_t)row * nx + i;
+      p[c] = p_zero ? scale * zd : fma(scale, zd, p[c]);
+    }
   }
 }
 
@@ -248,14 +336,14 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
                               const double* b, double inv_dt, const double* rho, const double* p,
                               int p_zero, int scale_rho, C2<T>* spec, double* red, int* nblk_out,
                               const DevStatus* st, cudaStream_t s) {
-  const int rpb = rows_per_block(g.nx, sizeof(C2<T>));
+  const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);
   const size_t smem = (size_t)rpb * g.nx * sizeof(C2<T>);
   cudaError_t e = cudaFuncSetAttribute(k_resid_fftx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int mode = (red == nullptr) ? 0 : 1;
-  k_resid_fftx<T><<<nblk, 256, smem, s>>>(g, fc, fx, twx, b, inv_dt, rho, p, mode, p_zero, scale_rho,
+  k_resid_fftx<T><<<nblk, kThreads, smem, s>>>(g, fc, fx, twx, b, inv_dt, rho, p, mode, p_zero, scale_rho,
                                           spec, red, rpb, st);
   if (nblk_out) *nblk_out = nblk;
   return cudaGetLastError();
@@ -264,18 +352,18 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
 template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
                         const DevStatus* st, cudaStream_t s) {
-  const int tx = ffty_tile(g.ny, sizeof(C2<T>));
+  const int tx = ffty_tile(g.ny, sizeof(C2<T>), kEpt);
   const size_t smem = (size_t)2 * g.ny * tx * sizeof(C2<T>);
   dim3 grid((g.nxh + tx - 1) / tx, g.nz);
   cudaError_t e;
   if (inverse) {
     e = cudaFuncSetAttribute(k_ffty<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_ffty<T, 1><<<grid, 256, smem, s>>>(g, fy, twy, spec, tx, st);
+    k_ffty<T, 1><<<grid, kThreads, smem, s>>>(g, fy, twy, spec, tx, st);
   } else {
     e = cudaFuncSetAttribute(k_ffty<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_ffty<T, -1><<<grid, 256, smem, s>>>(g, fy, twy, spec, tx, st);
+    k_ffty<T, -1><<<grid, kThreads, smem, s>>>(g, fy, twy, spec, tx, st);
   }
   return cudaGetLastError();
 }
@@ -292,13 +380,13 @@ cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double
 template <typename T>
 cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
                             double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s) {
-  const int rpb = rows_per_block(g.nx, sizeof(C2<T>));
+  const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);
   const size_t smem = (size_t)rpb * g.nx * sizeof(C2<T>);
   cudaError_t e = cudaFuncSetAttribute(k_fftx_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_fftx_inv<T><<<nblk, 256, smem, s>>>(g, fx, twx, spec, scale, p, p_zero, rpb, st);
+  k_fftx_inv<T><<<nblk, kThreads, smem, s>>>(g, fx, twx, spec, scale, p, p_zero, rpb, st);
   return cudaGetLastError();
 }
 

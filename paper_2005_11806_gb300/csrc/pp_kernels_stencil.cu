@@ -27,7 +27,8 @@ __global__ void k_mixture(const double* __restrict__ phi, double rho_g, double r
   }
 }
 
-// beta on every face: arithmetic face density, beta = 2 / (rho_a + rho_b).
+// beta on every face: arithmetic face density, beta = 2 / (rho_a + rho_b);
+// x/y coefficients carry the width dzf_k of their layer (row scaling).
 __global__ void k_prep_faces(Geo g, const double* __restrict__ rho, Faces fc) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const size_t plane = (size_t)nx * ny, n = plane * nz;
@@ -36,13 +37,29 @@ __global__ void k_prep_faces(Geo g, const double* __restrict__ rho, Faces fc) {
     const int j = (int)((c / nx) % ny);
     const int k = (int)(c / plane);
     const double r = rho[c];
+    const double w = g.dzf[k];
     const size_t cim = c - i + (i == 0 ? nx - 1 : i - 1);
     const size_t cjm = c - (size_t)j * nx + (size_t)(j == 0 ? ny - 1 : j - 1) * nx;
-    fc.cx[c] = 2.0 / (r + rho[cim]) * g.inv_dx2;
-    fc.cy[c] = 2.0 / (r + rho[cjm]) * g.inv_dy2;
+    fc.cx[c] = 2.0 / (r + rho[cim]) * g.inv_dx2 * w;
+    fc.cy[c] = 2.0 / (r + rho[cjm]) * g.inv_dy2 * w;
     fc.cz[c] = (k == 0) ? 0.0 : 2.0 / (r + rho[c - plane]) * g.inv_dzc[k];
     if (k == nz - 1) fc.cz[c + plane] = 0.0;
+    fc.rhof[c] = (float)r;
   }
+}
+
+// diag = sum of the six (row-scaled) coefficients of each cell.
+__global__ void k_prep_diag(Geo g, Faces fc) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const size_t plane = (size_t)nx * ny, n = plane * nz;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const size_t cip = c - i + (i + 1 == nx ? 0 : i + 1);
+    const size_t cjp = c - (size_t)j * nx + (size_t)(j + 1 == ny ? 0 : j + 1) * nx;
+    fc.diag[c] = ((fc.cx[c] + fc.cx[cip]) + (fc.cy[c] + fc.cy[cjp])) + (fc.cz[c] + fc.cz[c + plane]);
+  }
+  (void)nz;
 }
 
 // Fixed-order partial sums of dzf_k * f (grid of kRedBlocks blocks).
@@ -66,11 +83,12 @@ __global__ void k_finalize(const double* __restrict__ red, int nblk, int stride,
   if (threadIdx.x == 0) *out = scale * s;
 }
 
-// b = D u* - (S - <S>_V); wall values of w* are taken as zero.
+// b_s = dzf_k (D u* - (S - <S>_V)) / dt (row-scaled); wall values of w* are
+// taken as zero; block partial sums of (D u* - S_c)^2.
 __global__ void k_rhs_b(Geo g, const double* __restrict__ us, const double* __restrict__ vs,
                         const double* __restrict__ ws, const double* __restrict__ S,
                         const DevStatus* __restrict__ st, double* __restrict__ b,
-                        double* __restrict__ red) {
+                        double* __restrict__ red, double inv_dt) {
   __shared__ double sh[32];
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const size_t plane = (size_t)nx * ny, n = plane * nz;
@@ -87,7 +105,7 @@ __global__ void k_rhs_b(Geo g, const double* __restrict__ us, const double* __re
     const double whi = (k == nz - 1) ? 0.0 : ws[c + plane];
     double d = (us[cip] - us[c]) * idx + (vs[cjp] - vs[c]) * idy + (whi - wlo) * g.inv_dzf[k];
     if (S != nullptr) d -= (S[c] - meanS);
-    b[c] = d;
+    b[c] = d * g.dzf[k] * inv_dt;
     s2 += d * d;
   }
   s2 = block_sum<double>(s2, sh);
@@ -128,7 +146,6 @@ __global__ void k_correct(Geo g, Faces fc, const double* __restrict__ us, const 
                           double* __restrict__ u, double* __restrict__ v, double* __restrict__ w) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const size_t plane = (size_t)nx * ny, n = plane * nz;
-  const double ax = dt * g.dx, ay = dt * g.dy;  // beta / dx = cx * dx
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % nx);
     const int j = (int)((c / nx) % ny);
@@ -136,6 +153,8 @@ __global__ void k_correct(Geo g, Faces fc, const double* __restrict__ us, const 
     const size_t cim = c - i + (i == 0 ? nx - 1 : i - 1);
     const size_t cjm = c - (size_t)j * nx + (size_t)(j == 0 ? ny - 1 : j - 1) * nx;
     const double pc = p[c];
+    // dt beta_x / dx = dt dx cx / dzf_k (cx carries dzf_k)
+    const double ax = dt * g.dx * g.inv_dzf[k], ay = dt * g.dy * g.inv_dzf[k];
     u[c] = us[c] - ax * fc.cx[c] * (pc - p[cim]);
     v[c] = vs[c] - ay * fc.cy[c] * (pc - p[cjm]);
     w[c] = (k == 0) ? 0.0 : ws[c] - dt * fc.cz[c] * (pc - p[c - plane]);
@@ -250,6 +269,7 @@ cudaError_t launch_mixture(const double* phi, double rho_g, double rho_l, double
 
 cudaError_t launch_prep_faces(const Geo& g, const double* rho, Faces fc, cudaStream_t s) {
   k_prep_faces<<<grid_for((size_t)g.nx * g.ny * g.nz), kThreads, 0, s>>>(g, rho, fc);
+  k_prep_diag<<<grid_for((size_t)g.nx * g.ny * g.nz), kThreads, 0, s>>>(g, fc);
   return cudaGetLastError();
 }
 
@@ -263,7 +283,7 @@ cudaError_t launch_weighted_mean(const Geo& g, const double* f, double* red, dou
 cudaError_t launch_rhs_b(const Geo& g, const double* us, const double* vs, const double* ws,
                          const double* S, double* b, double* red, DevStatus* st, double inv_dt,
                          cudaStream_t s) {
-  k_rhs_b<<<kRedBlocks, kThreads, 0, s>>>(g, us, vs, ws, S, st, b, red);
+  k_rhs_b<<<kRedBlocks, kThreads, 0, s>>>(g, us, vs, ws, S, st, b, red, inv_dt);
   k_finalize<<<1, 1024, 0, s>>>(red, kRedBlocks, 1, 0, inv_dt * inv_dt, &st->e2_0);
   return cudaGetLastError();
 }

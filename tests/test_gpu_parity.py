@@ -264,3 +264,21 @@ def test_adjoint_converged_vs_direct(pp):
     errs = [_rel(a, b) for a, b in zip(got, ref)]
     print("adjoint vs direct", errs, "iters", info["iters"])
     assert max(errs) < 1e-8
+
+
+def test_autograd_function_matches_oracle_gradient(pp):
+    """torch.autograd through ProjectFunction: dL/du*, dL/drho equal the
+    oracle's literal-transpose gradient (L = ||u^{n+1} - u_target||^2)."""
+    from paper_2005_11806_gb300.autograd import project
+    w, rho, g, p0, gu, gv, gw = _adjoint_inputs()
+    ut = w.extra["target"]
+    plan = _plan(pp, w.nx, w.ny, w.nz, w.lx, w.ly, w.zf)
+    us, vs, ws, r = (dev(a).requires_grad_() for a in (w.us, w.vs, w.ws, rho))
+    u, v, ww, p = project(us, vs, ws, r, plan, dev(w.S), w.dt, rtol=1e-12, maxit=3000)
+    tgt = [dev(a) for a in ut]
+    loss = ((u - tgt[0]) ** 2).sum() + ((v - tgt[1]) ** 2).sum() + ((ww[1:-1] - tgt[2][1:-1]) ** 2).sum()
+    loss.backward()
+    ref = orc.adjoint_direct(g, w.us, w.vs, w.ws, rho, w.S, w.dt, 2 * (host(u) - ut[0]),
+                             2 * (host(v) - ut[1]), 2 * (host(ww) - ut[2]))
+    for got, exp in ((us.grad, ref[0]), (vs.grad, ref[1]), (ws.grad, ref[2]), (r.grad, ref[3])):
+        assert _rel(host(got), exp) < 1e-8
