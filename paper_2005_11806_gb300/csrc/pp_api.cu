@@ -50,6 +50,8 @@ struct pp_plan_s {
   void* d_spec = nullptr;
   double2* d_ybuf = nullptr;
   double* d_b = nullptr;
+  double* d_E = nullptr;      // mixed: FP64 residual carried between passes
+  float* d_delta = nullptr;   // mixed: last pressure correction (FP32)
   double* d_red = nullptr;
   size_t red_len = 0;
   DevStatus* d_st = nullptr;
@@ -128,6 +130,10 @@ cudaError_t timed(pp_plan_s* P, int kid, F&& f) {
 
 #define PP_K(P, KID, expr) PP_CK(timed((P), (KID), [&]() { return (expr); }))
 
+// Mixed plans recompute the FP64 residual from p every kExactEvery passes and
+// update it by the FP32 stencil of the last correction in between.
+constexpr int kExactEvery = 10;
+
 template <typename X>
 pp_status dalloc(X** p, size_t bytes) {
   if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
@@ -200,7 +206,7 @@ pp_status read_info(pp_plan_s* P, pp_info* info) {
 // One pass of Algorithm 1 after the residual: forward y, z solve, inverse y,
 // inverse x fused with p += delta.
 template <typename T>
-pp_status solve_pass(pp_plan_s* P, double* p, int p_zero) {
+pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, float* delta = nullptr) {
   const Geo& g = P->geo;
   C2<T>* spec = (C2<T>*)P->d_spec;
   const C2<T>* twx = (const C2<T>*)P->d_twx;
@@ -210,7 +216,7 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero) {
   PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream));
   PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream));
   PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream));
-  PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream));
+  PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream, delta));
   return PP_OK;
 }
 
@@ -224,15 +230,18 @@ pp_status method3_loop(pp_plan_s* P, const double* rho, double* p, int warm, dou
   const C2<T>* twx = (const C2<T>*)P->d_twx;
   const double inv_dt = 1.0 / dt;
   const int chunk = 4;
+  const bool upd = std::is_same<T, float>::value && P->d_E != nullptr;
+  const int kexact = upd ? kExactEvery : 1;
   int polled = 0;
   bool pending[2] = {false, false};
   for (int it = 0; it <= maxit; ++it) {
     int nblk = 0;
     PP_K(P, K_RESID, launch_resid_fftx<T>(g, P->faces, P->fx, twx, P->d_b, inv_dt, rho, p,
                                           (it == 0 && !warm) ? 1 : 0, 1, spec, P->d_red, &nblk,
-                                          P->d_st, P->stream));
-    PP_K(P, K_CHECK, launch_check(P->d_st, P->d_red, nblk, rtol, maxit, P->stream));
-    pp_status s = solve_pass<T>(P, p, 0);
+                                          P->d_st, P->stream, upd ? P->d_E : nullptr,
+                                          upd ? P->d_delta : nullptr));
+    PP_K(P, K_CHECK, launch_check(P->d_st, P->d_red, nblk, rtol, maxit, kexact, P->stream));
+    pp_status s = solve_pass<T>(P, p, 0, upd ? P->d_delta : nullptr);
     if (s != PP_OK) return s;
     if ((it + 1) % chunk == 0) {
       // Poll the device status without draining the queue: read the slot
@@ -281,6 +290,9 @@ void free_plan(pp_plan_s* P) {
                      P->d_invd, P->d_b, P->d_red, P->faces.cx, P->faces.cy, P->faces.cz,
                      P->faces.diag};
   if (P->faces.rhof) cudaFree(P->faces.rhof);
+  float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta};
+  for (float* f : fptrs) if (f) cudaFree(f);
+  if (P->d_E) cudaFree(P->d_E);
   if (P->d_inv_dzf_f) cudaFree(P->d_inv_dzf_f);
   for (double* d : dptrs) if (d) cudaFree(d);
   if (P->d_twx) cudaFree(P->d_twx);
@@ -407,6 +419,12 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   if ((st = dalloc(&P->d_invd, nsp * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->d_spec, nsp * csz)) != PP_OK ||
       (prec != PP_FP64 && (st = dalloc(&P->d_ybuf, nsp * sizeof(double2))) != PP_OK) ||
+      (prec != PP_FP64 && (st = dalloc(&P->d_E, nc * sizeof(double))) != PP_OK) ||
+      (prec != PP_FP64 && (st = dalloc(&P->d_delta, nc * sizeof(float))) != PP_OK) ||
+      (prec != PP_FP64 && (st = dalloc(&P->faces.cxf, nc * sizeof(float))) != PP_OK) ||
+      (prec != PP_FP64 && (st = dalloc(&P->faces.cyf, nc * sizeof(float))) != PP_OK) ||
+      (prec != PP_FP64 && (st = dalloc(&P->faces.czf, nw * sizeof(float))) != PP_OK) ||
+      (prec != PP_FP64 && (st = dalloc(&P->faces.diagf, nc * sizeof(float))) != PP_OK) ||
       (st = dalloc(&P->d_b, nc * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->d_red, P->red_len * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->faces.cx, nc * sizeof(double))) != PP_OK ||

@@ -35,6 +35,8 @@ struct DevStatus {
   int iters;        // constant-coefficient solves started
   int done;         // 1 once the loop has stopped
   int code;         // pp_status of the loop
+  int need_exact;   // 1: the next residual is recomputed from p in FP64
+  int since_exact;  // passes since the last exact residual
   int pad;
 };
 
@@ -56,12 +58,18 @@ struct Geo {
 //   cx = dzf_k beta_x / dx^2, cy = dzf_k beta_y / dy^2 (faces of layer k),
 //   cz = beta_z / dzc (z faces, 0 on the walls),
 //   diag = sum of the six coefficients of the cell, rhof = rho_c in FP32.
+//   cxf, cyf, czf, diagf: FP32 copies for the residual update of the mixed
+//   path (null on FP64 plans).
 struct Faces {
   double* cx;    // [nz][ny][nx]
   double* cy;    // [nz][ny][nx]
   double* cz;    // [nz+1][ny][nx]
   double* diag;  // [nz][ny][nx]
   float* rhof;   // [nz][ny][nx]
+  float* cxf;
+  float* cyf;
+  float* czf;
+  float* diagf;
 };
 
 // Exact FP32 -> FP64 widening done on the integer pipe (the FP64 pipe of this
@@ -95,21 +103,28 @@ __device__ __forceinline__ float narrow_f64(double d) {
 // Residual e = b/dt - D(beta G p) (or e = f when f_only), r = rho * e
 // (or r = e), forward real x-transform of r into spec; block partial sums
 // of e^2 and |e| into red[2*block + {0,1}].  Rows are (k, j) pairs.
+//
+// Mixed path with E != null: E = dzf (D u^s - S_c)/dt is kept in FP64.  When
+// st->need_exact is set it is recomputed from p; otherwise it is updated by
+// E -= A delta with delta = p^s - p^{s-1} (FP32) and the FP32 coefficients.
 template <typename T>
 cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, const C2<T>* twx,
                               const double* b, double inv_dt, const double* rho, const double* p,
                               int p_zero, int scale_rho, C2<T>* spec, double* red, int* nblk_out,
-                              const DevStatus* st, cudaStream_t s);
+                              const DevStatus* st, cudaStream_t s, double* E = nullptr,
+                              const float* delta = nullptr);
 template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
                         const DevStatus* st, cudaStream_t s);
 template <typename T>
 cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,
                            const DevStatus* st, cudaStream_t s);
-// Inverse x-transform; p = scale * z (p_zero) or p += scale * z.
+// Inverse x-transform; p = scale * z (p_zero) or p += scale * z; when delta
+// is not null it also receives scale * z in FP32.
 template <typename T>
 cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
-                            double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s);
+                            double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s,
+                            float* delta = nullptr);
 
 cudaError_t launch_setup_pivots(const Geo& g, const double* lamx, const double* lamy, double* invd,
                                 cudaStream_t s);
@@ -124,9 +139,11 @@ cudaError_t launch_weighted_mean(const Geo& g, const double* f, double* red, dou
 cudaError_t launch_rhs_b(const Geo& g, const double* us, const double* vs, const double* ws,
                          const double* S, double* b, double* red, DevStatus* st, double inv_dt,
                          cudaStream_t s);
-// Loop control of Algorithm 1 (one block).
+// Loop control of Algorithm 1 (one block).  kexact: recompute the residual
+// exactly every kexact passes (<= 1: every pass); convergence is only
+// accepted on an exact residual.
 cudaError_t launch_check(DevStatus* st, const double* red, int nblk, double rtol, int maxit,
-                         cudaStream_t s);
+                         int kexact, cudaStream_t s);
 cudaError_t launch_init_status(DevStatus* st, cudaStream_t s);
 // u = us - dt beta G p on all faces (w walls = 0).
 cudaError_t launch_correct(const Geo& g, const Faces& fc, const double* us, const double* vs,

@@ -54,11 +54,14 @@ __global__ void __launch_bounds__(256) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
                                                     const double* __restrict__ p, int mode, int p_zero,
                                                     int scale_rho, C2<T>* __restrict__ spec,
                                                     double* __restrict__ red, int rpb,
-                                                    const DevStatus* __restrict__ st) {
+                                                    const DevStatus* __restrict__ st,
+                                                    double* __restrict__ E,
+                                                    const float* __restrict__ delta) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double shred[32];
   const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
+  const bool update = (E != nullptr) && !p_zero && !(st != nullptr && st->need_exact);
   const int nseq = rpb >> 1;
   C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* bufB = bufA + (size_t)nseq * nx;
@@ -77,20 +80,35 @@ __global__ void __launch_bounds__(256) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
         r = (T)b[c];
       } else {
         const int k = (int)(row / ny), j = (int)(row - (long)k * ny);
-        double ep = b[c];
-        if (!p_zero) {
-          const int ip = (i + 1 == nx) ? 0 : i + 1, im = (i == 0) ? nx - 1 : i - 1;
-          const int jp = (j + 1 == ny) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
-          const size_t rowoff = (size_t)row * nx;
-          const size_t kp = (size_t)k * plane;
-          double t = -fc.diag[c] * p[c];
-          t = fma(fc.cx[rowoff + ip], p[rowoff + ip], t);
-          t = fma(fc.cx[c], p[rowoff + im], t);
-          t = fma(fc.cy[kp + (size_t)jp * nx + i], p[kp + (size_t)jp * nx + i], t);
-          t = fma(fc.cy[c], p[kp + (size_t)jm * nx + i], t);
-          if (k + 1 < nz) t = fma(fc.cz[c + plane], p[c + plane], t);
-          if (k > 0) t = fma(fc.cz[c], p[c - plane], t);
-          ep -= t;
+        const int ip = (i + 1 == nx) ? 0 : i + 1, im = (i == 0) ? nx - 1 : i - 1;
+        const int jp = (j + 1 == ny) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
+        const size_t rowoff = (size_t)row * nx;
+        const size_t kp = (size_t)k * plane;
+        double ep;
+        if (update) {
+          // E^s = E^{s-1} - A delta, A delta in FP32
+          float t = -fc.diagf[c] * delta[c];
+          t = fmaf(fc.cxf[rowoff + ip], delta[rowoff + ip], t);
+          t = fmaf(fc.cxf[c], delta[rowoff + im], t);
+          t = fmaf(fc.cyf[kp + (size_t)jp * nx + i], delta[kp + (size_t)jp * nx + i], t);
+          t = fmaf(fc.cyf[c], delta[kp + (size_t)jm * nx + i], t);
+          if (k + 1 < nz) t = fmaf(fc.czf[c + plane], delta[c + plane], t);
+          if (k > 0) t = fmaf(fc.czf[c], delta[c - plane], t);
+          ep = E[c] - widen_f32(t);
+          E[c] = ep;
+        } else {
+          ep = b[c];
+          if (!p_zero) {
+            double t = -fc.diag[c] * p[c];
+            t = fma(fc.cx[rowoff + ip], p[rowoff + ip], t);
+            t = fma(fc.cx[c], p[rowoff + im], t);
+            t = fma(fc.cy[kp + (size_t)jp * nx + i], p[kp + (size_t)jp * nx + i], t);
+            t = fma(fc.cy[c], p[kp + (size_t)jm * nx + i], t);
+            if (k + 1 < nz) t = fma(fc.cz[c + plane], p[c + plane], t);
+            if (k > 0) t = fma(fc.cz[c], p[c - plane], t);
+            ep -= t;
+          }
+          if (E != nullptr) E[c] = ep;
         }
         if (sizeof(T) == sizeof(float)) {
           const float e = narrow_f64(ep) * g.inv_dzf_f[k];
@@ -267,11 +285,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>* __restrict__ twx,
                                                   const C2<T>* __restrict__ spec, double scale,
                                                   double* __restrict__ p, int p_zero, int rpb,
-                                                  const DevStatus* __restrict__ st) {
+                                                  const DevStatus* __restrict__ st,
+                                                  float* __restrict__ delta) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
   const int nseq = rpb >> 1;
+  const float scale_f = (float)scale;
   C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* bufB = bufA + (size_t)nseq * nx;
   const long nrows = (long)nz * ny;
@@ -315,6 +335,7 @@ __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>
       const T zv = (q & 1) ? z.y : z.x;
       const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
       p[(size_t)row * nx + i] = fma(scale, zd, pv[u]);
+      if (delta != nullptr) delta[(size_t)row * nx + i] = scale_f * (float)zv;
     }
   }
   for (int t = threadIdx.x + NP * blockDim.x; t < nout; t += blockDim.x) {  // beyond the prefetch
@@ -326,6 +347,7 @@ __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>
       const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
       const size_t c = (size_t)row * nx + i;
       p[c] = p_zero ? scale * zd : fma(scale, zd, p[c]);
+      if (delta != nullptr) delta[c] = scale_f * (float)zv;
     }
   }
 }
@@ -335,7 +357,7 @@ template <typename T>
 cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, const C2<T>* twx,
                               const double* b, double inv_dt, const double* rho, const double* p,
                               int p_zero, int scale_rho, C2<T>* spec, double* red, int* nblk_out,
-                              const DevStatus* st, cudaStream_t s) {
+                              const DevStatus* st, cudaStream_t s, double* E, const float* delta) {
   const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);
@@ -344,7 +366,7 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
   if (e != cudaSuccess) return e;
   const int mode = (red == nullptr) ? 0 : 1;
   k_resid_fftx<T><<<nblk, kThreads, smem, s>>>(g, fc, fx, twx, b, inv_dt, rho, p, mode, p_zero, scale_rho,
-                                          spec, red, rpb, st);
+                                          spec, red, rpb, st, E, delta);
   if (nblk_out) *nblk_out = nblk;
   return cudaGetLastError();
 }
@@ -379,14 +401,15 @@ cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double
 
 template <typename T>
 cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
-                            double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s) {
+                            double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s,
+                            float* delta) {
   const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);
   const size_t smem = (size_t)rpb * g.nx * sizeof(C2<T>);
   cudaError_t e = cudaFuncSetAttribute(k_fftx_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_fftx_inv<T><<<nblk, kThreads, smem, s>>>(g, fx, twx, spec, scale, p, p_zero, rpb, st);
+  k_fftx_inv<T><<<nblk, kThreads, smem, s>>>(g, fx, twx, spec, scale, p, p_zero, rpb, st, delta);
   return cudaGetLastError();
 }
 
@@ -394,13 +417,14 @@ cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, c
   template cudaError_t launch_resid_fftx<T>(const Geo&, const Faces&, const FftDesc&, const C2<T>*,  \
                                             const double*, double, const double*, const double*,     \
                                             int, int, C2<T>*, double*, int*, const DevStatus*,       \
-                                            cudaStream_t);                                           \
+                                            cudaStream_t, double*, const float*);                    \
   template cudaError_t launch_ffty<T>(const Geo&, const FftDesc&, const C2<T>*, C2<T>*, int,         \
                                       const DevStatus*, cudaStream_t);                               \
   template cudaError_t launch_tridiag<T>(const Geo&, const double*, C2<T>*, double2*,                \
                                          const DevStatus*, cudaStream_t);                            \
   template cudaError_t launch_fftx_inv<T>(const Geo&, const FftDesc&, const C2<T>*, const C2<T>*,    \
-                                          double, double*, int, const DevStatus*, cudaStream_t);
+                                          double, double*, int, const DevStatus*, cudaStream_t,      \
+                                          float*);
 PP_INST(double)
 PP_INST(float)
 #undef PP_INST

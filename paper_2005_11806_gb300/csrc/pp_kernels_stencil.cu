@@ -45,6 +45,12 @@ __global__ void k_prep_faces(Geo g, const double* __restrict__ rho, Faces fc) {
     fc.cz[c] = (k == 0) ? 0.0 : 2.0 / (r + rho[c - plane]) * g.inv_dzc[k];
     if (k == nz - 1) fc.cz[c + plane] = 0.0;
     fc.rhof[c] = (float)r;
+    if (fc.cxf != nullptr) {
+      fc.cxf[c] = (float)fc.cx[c];
+      fc.cyf[c] = (float)fc.cy[c];
+      fc.czf[c] = (float)fc.cz[c];
+      if (k == nz - 1) fc.czf[c + plane] = 0.0f;
+    }
   }
 }
 
@@ -58,6 +64,7 @@ __global__ void k_prep_diag(Geo g, Faces fc) {
     const size_t cip = c - i + (i + 1 == nx ? 0 : i + 1);
     const size_t cjp = c - (size_t)j * nx + (size_t)(j + 1 == ny ? 0 : j + 1) * nx;
     fc.diag[c] = ((fc.cx[c] + fc.cx[cip]) + (fc.cy[c] + fc.cy[cjp])) + (fc.cz[c] + fc.cz[c + plane]);
+    if (fc.diagf != nullptr) fc.diagf[c] = (float)fc.diag[c];
   }
   (void)nz;
 }
@@ -115,10 +122,12 @@ __global__ void k_rhs_b(Geo g, const double* __restrict__ us, const double* __re
 __global__ void k_init_status(DevStatus* st) {
   st->e2 = 0; st->e1 = 0; st->e2_0 = 0; st->rel = 0; st->mean_S = 0; st->pmean = 0;
   st->iters = 0; st->done = 0; st->code = PP_OK; st->pad = 0;
+  st->need_exact = 1; st->since_exact = 0;
 }
 
 // Loop control of Algorithm 1: reduce the residual partial sums, decide.
-__global__ void k_check(DevStatus* st, const double* __restrict__ red, int nblk, double rtol, int maxit) {
+__global__ void k_check(DevStatus* st, const double* __restrict__ red, int nblk, double rtol, int maxit,
+                        int kexact) {
   __shared__ double sh[32];
   if (st->done) return;
   double s2 = 0.0, s1 = 0.0;
@@ -134,10 +143,23 @@ __global__ void k_check(DevStatus* st, const double* __restrict__ red, int nblk,
   const double e20 = st->e2_0;
   const double rel = (e20 > 0.0) ? sqrt(s2 / e20) : 0.0;
   st->rel = rel;
+  const int exact = st->need_exact;
   if (!isfinite(s2) || !isfinite(e20)) { st->done = 1; st->code = PP_ERR_NUMERIC; }
-  else if (e20 == 0.0 || rel <= rtol) { st->done = 1; st->code = PP_OK; }
+  else if (e20 == 0.0 || (rel <= rtol && exact)) { st->done = 1; st->code = PP_OK; }
   else if (st->iters >= maxit) { st->done = 1; st->code = PP_ERR_NOT_CONVERGED; }
-  else st->iters += 1;
+  else {
+    st->iters += 1;
+    if (kexact <= 1) {
+      st->need_exact = 1;
+    } else if (exact) {
+      st->need_exact = 0;
+      st->since_exact = 1;
+    } else {
+      st->since_exact += 1;
+      // an updated residual below the tolerance is confirmed by an exact one
+      st->need_exact = (rel <= rtol || st->since_exact >= kexact) ? 1 : 0;
+    }
+  }
 }
 
 // u = u* - dt beta G p  (Eq. corr); w wall planes are written as zero.
@@ -289,8 +311,8 @@ cudaError_t launch_rhs_b(const Geo& g, const double* us, const double* vs, const
 }
 
 cudaError_t launch_check(DevStatus* st, const double* red, int nblk, double rtol, int maxit,
-                         cudaStream_t s) {
-  k_check<<<1, 1024, 0, s>>>(st, red, nblk, rtol, maxit);
+                         int kexact, cudaStream_t s) {
+  k_check<<<1, 1024, 0, s>>>(st, red, nblk, rtol, maxit, kexact);
   return cudaGetLastError();
 }
 
