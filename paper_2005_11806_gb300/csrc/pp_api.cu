@@ -43,7 +43,7 @@ struct pp_plan_s {
   Faces faces;
   // device tables
   double *d_inv_dzf = nullptr, *d_inv_dzc = nullptr, *d_dzf = nullptr, *d_za = nullptr, *d_zc = nullptr;
-  double *d_lamx = nullptr, *d_lamy = nullptr, *d_invd = nullptr;
+  double *d_lamx = nullptr, *d_lamy = nullptr, *d_invd = nullptr, *d_mtab = nullptr;
   float* d_inv_dzf_f = nullptr;
   void *d_twx = nullptr, *d_twy = nullptr;
   // workspaces
@@ -80,6 +80,7 @@ bool factor_len(int n, FftDesc* d) {
     }
   }
   if (n == 1) { d->radix[0] = 2; d->nst = 0; }
+  d->pow2 = (n & (n - 1)) == 0;
   return m == 1;
 }
 
@@ -211,10 +212,11 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, float* delta = nullptr
   C2<T>* spec = (C2<T>*)P->d_spec;
   const C2<T>* twx = (const C2<T>*)P->d_twx;
   const C2<T>* twy = (const C2<T>*)P->d_twy;
-  double2* ybuf = std::is_same<T, double>::value ? (double2*)P->d_spec : P->d_ybuf;
+  // the split solve (mtab present) keeps its intermediate in the spectrum
+  double2* ybuf = (double2*)P->d_spec;
   const double scale = 1.0 / ((double)P->nx * (double)P->ny);
   PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream));
-  PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream));
+  PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab));
   PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream));
   PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream, delta));
   return PP_OK;
@@ -287,7 +289,7 @@ pp_status check_plan(pp_plan P) {
 void free_plan(pp_plan_s* P) {
   if (!P) return;
   double* dptrs[] = {P->d_inv_dzf, P->d_inv_dzc, P->d_dzf, P->d_za, P->d_zc, P->d_lamx, P->d_lamy,
-                     P->d_invd, P->d_b, P->d_red, P->faces.cx, P->faces.cy, P->faces.cz,
+                     P->d_invd, P->d_mtab, P->d_b, P->d_red, P->faces.cx, P->faces.cy, P->faces.cz,
                      P->faces.diag};
   if (P->faces.rhof) cudaFree(P->faces.rhof);
   float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta};
@@ -417,8 +419,8 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   P->red_len = std::max((size_t)2 * ((size_t)G.ny * nz + rpb_min - 1) / rpb_min + 2,
                         (size_t)reduce_blocks());
   if ((st = dalloc(&P->d_invd, nsp * sizeof(double))) != PP_OK ||
+      (st = dalloc(&P->d_mtab, nsp * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->d_spec, nsp * csz)) != PP_OK ||
-      (prec != PP_FP64 && (st = dalloc(&P->d_ybuf, nsp * sizeof(double2))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->d_E, nc * sizeof(double))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->d_delta, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->faces.cxf, nc * sizeof(float))) != PP_OK) ||
@@ -459,7 +461,7 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   g.inv_dy2 = 1.0 / (P->dy * P->dy);
   g.inv_dzf = P->d_inv_dzf; g.inv_dzc = P->d_inv_dzc; g.dzf = P->d_dzf;
   g.za = P->d_za; g.zc = P->d_zc; g.lz = lz_sum;
-  if (launch_setup_pivots(g, P->d_lamx, P->d_lamy, P->d_invd, P->stream) != cudaSuccess ||
+  if (launch_setup_pivots(g, P->d_lamx, P->d_lamy, P->d_invd, P->stream, P->d_mtab) != cudaSuccess ||
       launch_init_status(P->d_st, P->stream) != cudaSuccess ||
       cudaStreamSynchronize(P->stream) != cudaSuccess) {
     free_plan(P);

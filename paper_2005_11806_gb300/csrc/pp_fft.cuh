@@ -90,19 +90,31 @@ template <typename T, int DIR> struct Dft<T, DIR, 5> {
 
 // One Stockham pass of radix R over `nbatch` sequences of length n stored at
 // buf[b * bs + m * es].  BATCH_FAST selects which index consecutive threads
-// walk (the one that is contiguous in shared memory).
-template <typename T, int DIR, int R, bool BATCH_FAST>
+// walk (the one that is contiguous in shared memory).  POW2: n, Ns and (for
+// BATCH_FAST) nbatch are powers of two, so divisions become shifts
+// (lg_* are their base-2 logarithms).
+template <typename T, int DIR, int R, bool BATCH_FAST, bool POW2>
 __device__ __forceinline__ void fft_pass(const C2<T>* __restrict__ src, C2<T>* __restrict__ dst, int n,
-                                         int Ns, int nbatch, int es, int bs,
+                                         int Ns, int lg_ns, int nbatch, int lg_nbatch, int es, int bs,
                                          const C2<T>* __restrict__ tw, int tid, int nth) {
   const int nb = n / R;
   const int total = nb * nbatch;
   const int tws = n / (Ns * R);
+  constexpr int LR = R == 8 ? 3 : R == 4 ? 2 : 1;
+  const int lg_nb = POW2 ? (31 - __clz(nb)) : 0;
   for (int t = tid; t < total; t += nth) {
-    int bi, j;
-    if (BATCH_FAST) { j = t / nbatch; bi = t - j * nbatch; }
-    else { bi = t / nb; j = t - bi * nb; }
-    const int k = j % Ns;
+    int bi, j, k, jq;
+    if (POW2) {
+      if (BATCH_FAST) { j = t >> lg_nbatch; bi = t & (nbatch - 1); }
+      else { bi = t >> lg_nb; j = t & (nb - 1); }
+      k = j & (Ns - 1);
+      jq = j >> lg_ns;
+    } else {
+      if (BATCH_FAST) { j = t / nbatch; bi = t - j * nbatch; }
+      else { bi = t / nb; j = t - bi * nb; }
+      jq = j / Ns;
+      k = j - jq * Ns;
+    }
     C2<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[bi * bs + (j + r * nb) * es];
@@ -115,7 +127,7 @@ __device__ __forceinline__ void fft_pass(const C2<T>* __restrict__ src, C2<T>* _
       }
     }
     Dft<T, DIR, R>::run(v);
-    const int base = (j / Ns) * Ns * R + k;
+    const int base = POW2 ? ((jq << (lg_ns + LR)) + k) : (jq * Ns * R + k);
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[bi * bs + (base + r * Ns) * es] = v[r];
   }
@@ -126,89 +138,34 @@ __device__ __forceinline__ void fft_pass(const C2<T>* __restrict__ src, C2<T>* _
 template <typename T, int DIR, bool BATCH_FAST>
 __device__ C2<T>* fft_block(C2<T>* a, C2<T>* b, const FftDesc& d, int nbatch, int es, int bs,
                             const C2<T>* __restrict__ tw, int tid, int nth) {
-  int Ns = 1;
+  int Ns = 1, lg_ns = 0;
+  const bool pow2 = d.pow2 && (!BATCH_FAST || (nbatch & (nbatch - 1)) == 0);
+  const int lg_nbatch = 31 - __clz(nbatch);
   C2<T>* src = a;
   C2<T>* dst = b;
   for (int s = 0; s < d.nst; ++s) {
     const int R = d.radix[s];
-    switch (R) {
-      case 8: fft_pass<T, DIR, 8, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
-      case 4: fft_pass<T, DIR, 4, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
-      case 2: fft_pass<T, DIR, 2, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
-      case 3: fft_pass<T, DIR, 3, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
-      default: fft_pass<T, DIR, 5, BATCH_FAST>(src, dst, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
+    if (pow2) {
+      switch (R) {
+        case 8: fft_pass<T, DIR, 8, BATCH_FAST, true>(src, dst, d.n, Ns, lg_ns, nbatch, lg_nbatch, es, bs, tw, tid, nth); break;
+        case 4: fft_pass<T, DIR, 4, BATCH_FAST, true>(src, dst, d.n, Ns, lg_ns, nbatch, lg_nbatch, es, bs, tw, tid, nth); break;
+        default: fft_pass<T, DIR, 2, BATCH_FAST, true>(src, dst, d.n, Ns, lg_ns, nbatch, lg_nbatch, es, bs, tw, tid, nth); break;
+      }
+    } else {
+      switch (R) {
+        case 8: fft_pass<T, DIR, 8, BATCH_FAST, false>(src, dst, d.n, Ns, 0, nbatch, 0, es, bs, tw, tid, nth); break;
+        case 4: fft_pass<T, DIR, 4, BATCH_FAST, false>(src, dst, d.n, Ns, 0, nbatch, 0, es, bs, tw, tid, nth); break;
+        case 2: fft_pass<T, DIR, 2, BATCH_FAST, false>(src, dst, d.n, Ns, 0, nbatch, 0, es, bs, tw, tid, nth); break;
+        case 3: fft_pass<T, DIR, 3, BATCH_FAST, false>(src, dst, d.n, Ns, 0, nbatch, 0, es, bs, tw, tid, nth); break;
+        default: fft_pass<T, DIR, 5, BATCH_FAST, false>(src, dst, d.n, Ns, 0, nbatch, 0, es, bs, tw, tid, nth); break;
+      }
     }
     __syncthreads();
     C2<T>* t = src; src = dst; dst = t;
     Ns *= R;
+    lg_ns += (R == 8) ? 3 : (R == 4) ? 2 : 1;
   }
   return src;
-}
-
-// In-place variant: one shared buffer.  Each pass first gathers every
-// butterfly input of the thread into registers, synchronises, then writes
-// the outputs; at most EPT elements per thread per pass (EPT >= nbatch * n /
-// nthreads).  Twiddles are read from `tw` (normally a shared-memory copy).
-template <typename T, int DIR, int R, int EPT, bool BATCH_FAST>
-__device__ __forceinline__ void fft_pass_inplace(C2<T>* buf, int n, int Ns, int nbatch, int es, int bs,
-                                                 const C2<T>* tw, int tid, int nth) {
-  constexpr int BPT = (EPT + R - 1) / R;
-  const int nb = n / R;
-  const int total = nb * nbatch;
-  const int tws = n / (Ns * R);
-  C2<T> v[BPT][R];
-#pragma unroll
-  for (int u = 0; u < BPT; ++u) {
-    const int t = tid + u * nth;
-    if (t < total) {
-      int bi, j;
-      if (BATCH_FAST) { j = t / nbatch; bi = t - j * nbatch; }
-      else { bi = t / nb; j = t - bi * nb; }
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[u][r] = buf[bi * bs + (j + r * nb) * es];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int u = 0; u < BPT; ++u) {
-    const int t = tid + u * nth;
-    if (t < total) {
-      int bi, j;
-      if (BATCH_FAST) { j = t / nbatch; bi = t - j * nbatch; }
-      else { bi = t / nb; j = t - bi * nb; }
-      const int k = j % Ns;
-      if (Ns > 1) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          C2<T> w = tw[r * k * tws];
-          w.y = DIR > 0 ? w.y : -w.y;
-          v[u][r] = cmul<T>(v[u][r], w);
-        }
-      }
-      Dft<T, DIR, R>::run(v[u]);
-      const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) buf[bi * bs + (base + r * Ns) * es] = v[u][r];
-    }
-  }
-  __syncthreads();
-}
-
-template <typename T, int DIR, int EPT, bool BATCH_FAST>
-__device__ void fft_block_inplace(C2<T>* buf, const FftDesc& d, int nbatch, int es, int bs,
-                                  const C2<T>* tw, int tid, int nth) {
-  int Ns = 1;
-  for (int s = 0; s < d.nst; ++s) {
-    const int R = d.radix[s];
-    switch (R) {
-      case 8: fft_pass_inplace<T, DIR, 8, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
-      case 4: fft_pass_inplace<T, DIR, 4, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
-      case 2: fft_pass_inplace<T, DIR, 2, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
-      case 3: fft_pass_inplace<T, DIR, 3, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
-      default: fft_pass_inplace<T, DIR, 5, EPT, BATCH_FAST>(buf, d.n, Ns, nbatch, es, bs, tw, tid, nth); break;
-    }
-    Ns *= R;
-  }
 }
 
 template <typename T>

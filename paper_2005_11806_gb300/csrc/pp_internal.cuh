@@ -15,6 +15,7 @@ constexpr int kMaxStages = 16;
 struct FftDesc {
   int n;
   int nst;
+  int pow2;      // 1 when n is a power of two (all radices 8, 4, 2)
   int radix[kMaxStages];
 };
 
@@ -116,9 +117,11 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
 template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
                         const DevStatus* st, cudaStream_t s);
+// With mtab (multipliers m_k = a_k / d_{k-1}) the real and imaginary parts
+// run in separate threads; without it one thread solves a whole column.
 template <typename T>
 cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,
-                           const DevStatus* st, cudaStream_t s);
+                           const DevStatus* st, cudaStream_t s, const double* mtab = nullptr);
 // Inverse x-transform; p = scale * z (p_zero) or p += scale * z; when delta
 // is not null it also receives scale * z in FP32.
 template <typename T>
@@ -126,8 +129,10 @@ cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, c
                             double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s,
                             float* delta = nullptr);
 
+// Inverse Thomas pivots; when mtab is not null also the multipliers
+// m_k = a_k / d_{k-1} (m_0 = 0).
 cudaError_t launch_setup_pivots(const Geo& g, const double* lamx, const double* lamy, double* invd,
-                                cudaStream_t s);
+                                cudaStream_t s, double* mtab = nullptr);
 
 cudaError_t launch_mixture(const double* phi, double rho_g, double rho_l, double* rho, size_t n,
                            cudaStream_t s);

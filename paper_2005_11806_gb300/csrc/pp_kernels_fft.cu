@@ -65,66 +65,75 @@ __global__ void __launch_bounds__(256) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
   const int nseq = rpb >> 1;
   C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* bufB = bufA + (size_t)nseq * nx;
-  const long nrows = (long)nz * ny;
+  const int nrows = nz * ny;
   const long row0 = (long)blockIdx.x * rpb;
   const size_t plane = (size_t)ny * nx;
   T s2 = (T)0, s1 = (T)0;
   (void)inv_dt;
-  for (int t = threadIdx.x; t < rpb * nx; t += blockDim.x) {
-    const int q = t / nx, i = t - q * nx;
-    const long row = row0 + q;
-    T r = (T)0;
-    if (row < nrows) {
-      const size_t c = (size_t)row * nx + i;
-      if (mode == 0) {
-        r = (T)b[c];
-      } else {
-        const int k = (int)(row / ny), j = (int)(row - (long)k * ny);
-        const int ip = (i + 1 == nx) ? 0 : i + 1, im = (i == 0) ? nx - 1 : i - 1;
-        const int jp = (j + 1 == ny) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
-        const size_t rowoff = (size_t)row * nx;
-        const size_t kp = (size_t)k * plane;
-        double ep;
-        if (update) {
-          // E^s = E^{s-1} - A delta, A delta in FP32
-          float t = -fc.diagf[c] * delta[c];
-          t = fmaf(fc.cxf[rowoff + ip], delta[rowoff + ip], t);
-          t = fmaf(fc.cxf[c], delta[rowoff + im], t);
-          t = fmaf(fc.cyf[kp + (size_t)jp * nx + i], delta[kp + (size_t)jp * nx + i], t);
-          t = fmaf(fc.cyf[c], delta[kp + (size_t)jm * nx + i], t);
-          if (k + 1 < nz) t = fmaf(fc.czf[c + plane], delta[c + plane], t);
-          if (k > 0) t = fmaf(fc.czf[c], delta[c - plane], t);
-          ep = E[c] - widen_f32(t);
-          E[c] = ep;
+  // thread -> (row offset, first column); index math is done once per row
+  const int tpr = nx < (int)blockDim.x ? nx : (int)blockDim.x;
+  const int rows_par = blockDim.x / tpr;
+  const int qoff = threadIdx.x / tpr, i0 = threadIdx.x - qoff * tpr;
+  for (int q = qoff; q < rpb && qoff < rows_par; q += rows_par) {
+    const int row = (int)row0 + q;
+    const bool valid = row < nrows;
+    const int k = valid ? row / ny : 0, j = valid ? row - k * ny : 0;
+    const int jp = (j + 1 == ny) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
+    const size_t rowoff = (size_t)row * nx;
+    const size_t kp = (size_t)k * plane;
+    const size_t rowp = kp + (size_t)jp * nx, rowm = kp + (size_t)jm * nx;
+    const float idzf_f = (mode != 0 && sizeof(T) == sizeof(float)) ? g.inv_dzf_f[k] : 0.f;
+    const double idzf = (mode != 0 && sizeof(T) == sizeof(double)) ? g.inv_dzf[k] : 0.0;
+    for (int i = i0; i < nx; i += tpr) {
+      T r = (T)0;
+      if (valid) {
+        const size_t c = rowoff + i;
+        if (mode == 0) {
+          r = (T)b[c];
         } else {
-          ep = b[c];
-          if (!p_zero) {
-            double t = -fc.diag[c] * p[c];
-            t = fma(fc.cx[rowoff + ip], p[rowoff + ip], t);
-            t = fma(fc.cx[c], p[rowoff + im], t);
-            t = fma(fc.cy[kp + (size_t)jp * nx + i], p[kp + (size_t)jp * nx + i], t);
-            t = fma(fc.cy[c], p[kp + (size_t)jm * nx + i], t);
-            if (k + 1 < nz) t = fma(fc.cz[c + plane], p[c + plane], t);
-            if (k > 0) t = fma(fc.cz[c], p[c - plane], t);
-            ep -= t;
+          const int ip = (i + 1 == nx) ? 0 : i + 1, im = (i == 0) ? nx - 1 : i - 1;
+          double ep;
+          if (update) {
+            // E^s = E^{s-1} - A delta, A delta in FP32
+            float t = -fc.diagf[c] * delta[c];
+            t = fmaf(fc.cxf[rowoff + ip], delta[rowoff + ip], t);
+            t = fmaf(fc.cxf[c], delta[rowoff + im], t);
+            t = fmaf(fc.cyf[rowp + i], delta[rowp + i], t);
+            t = fmaf(fc.cyf[c], delta[rowm + i], t);
+            if (k + 1 < nz) t = fmaf(fc.czf[c + plane], delta[c + plane], t);
+            if (k > 0) t = fmaf(fc.czf[c], delta[c - plane], t);
+            ep = E[c] - widen_f32(t);
+            E[c] = ep;
+          } else {
+            ep = b[c];
+            if (!p_zero) {
+              double t = -fc.diag[c] * p[c];
+              t = fma(fc.cx[rowoff + ip], p[rowoff + ip], t);
+              t = fma(fc.cx[c], p[rowoff + im], t);
+              t = fma(fc.cy[rowp + i], p[rowp + i], t);
+              t = fma(fc.cy[c], p[rowm + i], t);
+              if (k + 1 < nz) t = fma(fc.cz[c + plane], p[c + plane], t);
+              if (k > 0) t = fma(fc.cz[c], p[c - plane], t);
+              ep -= t;
+            }
+            if (E != nullptr) E[c] = ep;
           }
-          if (E != nullptr) E[c] = ep;
-        }
-        if (sizeof(T) == sizeof(float)) {
-          const float e = narrow_f64(ep) * g.inv_dzf_f[k];
-          s2 = fmaf(e, e, (float)s2);
-          s1 += fabsf(e);
-          r = (T)(scale_rho ? fc.rhof[c] * e : e);
-        } else {
-          const double e = ep * g.inv_dzf[k];
-          s2 = (T)fma(e, e, (double)s2);
-          s1 += (T)fabs(e);
-          r = (T)(scale_rho ? rho[c] * e : e);
+          if (sizeof(T) == sizeof(float)) {
+            const float e = narrow_f64(ep) * idzf_f;
+            s2 = fmaf(e, e, (float)s2);
+            s1 += fabsf(e);
+            r = (T)(scale_rho ? fc.rhof[c] * e : e);
+          } else {
+            const double e = ep * idzf;
+            s2 = (T)fma(e, e, (double)s2);
+            s1 += (T)fabs(e);
+            r = (T)(scale_rho ? rho[c] * e : e);
+          }
         }
       }
+      C2<T>& z = bufA[(size_t)(q >> 1) * nx + i];
+      if (q & 1) z.y = r; else z.x = r;
     }
-    C2<T>& z = bufA[(size_t)(q >> 1) * nx + i];
-    if (q & 1) z.y = r; else z.x = r;
   }
   if (mode != 0) {
     const double a2 = block_sum<double>((double)s2, shred);
@@ -278,6 +287,86 @@ __global__ void __launch_bounds__(128) k_tridiag(Geo g, const double* __restrict
   else thomas_column<T, false>(g, invd, spec, ybuf, col, ncol);
 }
 
+// The same solve with the real and imaginary parts of a column in two
+// threads (twice the parallelism) and the elimination multipliers
+// m_k = a_k / d_{k-1} read from a table: per scalar one FP64 FMA forward and
+// one FMA + one multiply backward.  The recurrences run in FP64 registers;
+// the forward-sweep values are stored in place in the spectrum's own
+// precision (FP32 on mixed plans, like the spectrum the solve reads and
+// writes).  Scalar view: spec as T[nz][2 ncol].
+template <typename T>
+__global__ void __launch_bounds__(128) k_tridiag_split(Geo g, const double* __restrict__ mtab,
+                                                       const double* __restrict__ invd, T* spec,
+                                                       const DevStatus* __restrict__ st) {
+  if (stopped(st)) return;
+  constexpr int PF = 4;
+  const size_t ncol = (size_t)g.ny * g.nxh;
+  const size_t sid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // scalar column
+  if (sid >= 2 * ncol) return;
+  const size_t col = sid >> 1;
+  const size_t stride = 2 * ncol;
+  const int nz = g.nz;
+  auto ld = [&](size_t o) -> double {
+    if (sizeof(T) == sizeof(float)) return widen_f32((float)spec[o]);
+    return (double)spec[o];
+  };
+  auto stv = [&](size_t o, double v) {
+    if (sizeof(T) == sizeof(float)) spec[o] = (T)narrow_f64(v);
+    else spec[o] = (T)v;
+  };
+  if (col == 0) {  // singular (0, 0) column: remove the dzf-weighted mean first
+    double mean = 0.0;
+    for (int k = 0; k < nz; ++k) mean += g.dzf[k] * ld((size_t)k * stride + sid);
+    mean /= g.lz;
+    for (int k = 0; k < nz; ++k) stv((size_t)k * stride + sid, ld((size_t)k * stride + sid) - mean);
+  }
+  double fq[PF], mq[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int k = u < nz ? u : nz - 1;
+    fq[u] = ld((size_t)k * stride + sid);
+    mq[u] = mtab[(size_t)k * ncol + col];
+  }
+  double y = 0.0;
+  for (int k0 = 0; k0 < nz; k0 += PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 + u;
+      if (k < nz) {
+        const double f = fq[u], m = mq[u];
+        const int kn = k + PF < nz ? k + PF : nz - 1;
+        fq[u] = ld((size_t)kn * stride + sid);
+        mq[u] = mtab[(size_t)kn * ncol + col];
+        y = fma(-m, y, f);
+        if (k < nz - 1) stv((size_t)k * stride + sid, y);
+      }
+    }
+  }
+  double x = y * invd[(size_t)(nz - 1) * ncol + col];
+  stv((size_t)(nz - 1) * stride + sid, x);
+  double yq[PF], dq[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int k = nz - 2 - u >= 0 ? nz - 2 - u : 0;
+    yq[u] = ld((size_t)k * stride + sid);
+    dq[u] = invd[(size_t)k * ncol + col];
+  }
+  for (int k0 = nz - 2; k0 >= 0; k0 -= PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 - u;
+      if (k >= 0) {
+        const double yy = yq[u], d = dq[u];
+        const int kn = k - PF >= 0 ? k - PF : 0;
+        yq[u] = ld((size_t)kn * stride + sid);
+        dq[u] = invd[(size_t)kn * ncol + col];
+        x = fma(-g.zc[k], x, yy) * d;
+        stv((size_t)k * stride + sid, x);
+      }
+    }
+  }
+}
+
 // Inverse x transform of two half spectra per complex sequence, then
 // p = scale * z (p_zero) or p += scale * z.  The p values a thread updates
 // are loaded before the transform so their latency overlaps it.
@@ -298,17 +387,24 @@ __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>
   const long row0 = (long)blockIdx.x * rpb;
   const bool even = (nx & 1) == 0;
   const int nout = rpb * nx;
+  const int lgx = ((nx & (nx - 1)) == 0) ? 31 - __clz(nx) : -1;
+  auto split = [&](int t, int& q, int& i) {
+    if (lgx >= 0) { q = t >> lgx; i = t & (nx - 1); }
+    else { q = t / nx; i = t - q * nx; }
+  };
   constexpr int NP = kPrefetchInv;
   double pv[NP];
 #pragma unroll
   for (int u = 0; u < NP; ++u) {
     const int t = threadIdx.x + u * blockDim.x;
-    const int q = t / nx, i = t - q * nx;
+    int q, i;
+    split(t, q, i);
     pv[u] = 0.0;
     if (!p_zero && t < nout && row0 + q < nrows) pv[u] = p[(size_t)(row0 + q) * nx + i];
   }
   for (int t = threadIdx.x; t < nseq * nx; t += blockDim.x) {
-    const int q = t / nx, kx = t - q * nx;
+    int q, kx;
+    split(t, q, kx);
     const long ra = row0 + 2 * q;
     const bool upper = kx >= nxh;
     const int m = upper ? nx - kx : kx;
@@ -328,7 +424,8 @@ __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>
 #pragma unroll
   for (int u = 0; u < NP; ++u) {
     const int t = threadIdx.x + u * blockDim.x;
-    const int q = t / nx, i = t - q * nx;
+    int q, i;
+    split(t, q, i);
     const long row = row0 + q;
     if (t < nout && row < nrows) {
       const C2<T> z = res[(size_t)(q >> 1) * nx + i];
@@ -339,7 +436,8 @@ __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>
     }
   }
   for (int t = threadIdx.x + NP * blockDim.x; t < nout; t += blockDim.x) {  // beyond the prefetch
-    const int q = t / nx, i = t - q * nx;
+    int q, i;
+    split(t, q, i);
     const long row = row0 + q;
     if (row < nrows) {
       const C2<T> z = res[(size_t)(q >> 1) * nx + i];
@@ -392,10 +490,15 @@ cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>
 
 template <typename T>
 cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,
-                           const DevStatus* st, cudaStream_t s) {
+                           const DevStatus* st, cudaStream_t s, const double* mtab) {
   const size_t ncol = (size_t)g.ny * g.nxh;
-  const int nblk = (int)((ncol + 127) / 128);
-  k_tridiag<T><<<nblk, 128, 0, s>>>(g, invd, spec, ybuf, st);
+  if (mtab != nullptr) {
+    const int nblk = (int)((2 * ncol + 127) / 128);
+    k_tridiag_split<T><<<nblk, 128, 0, s>>>(g, mtab, invd, reinterpret_cast<T*>(spec), st);
+  } else {
+    const int nblk = (int)((ncol + 127) / 128);
+    k_tridiag<T><<<nblk, 128, 0, s>>>(g, invd, spec, ybuf, st);
+  }
   return cudaGetLastError();
 }
 
@@ -421,7 +524,7 @@ cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, c
   template cudaError_t launch_ffty<T>(const Geo&, const FftDesc&, const C2<T>*, C2<T>*, int,         \
                                       const DevStatus*, cudaStream_t);                               \
   template cudaError_t launch_tridiag<T>(const Geo&, const double*, C2<T>*, double2*,                \
-                                         const DevStatus*, cudaStream_t);                            \
+                                         const DevStatus*, cudaStream_t, const double*);             \
   template cudaError_t launch_fftx_inv<T>(const Geo&, const FftDesc&, const C2<T>*, const C2<T>*,    \
                                           double, double*, int, const DevStatus*, cudaStream_t,      \
                                           float*);

@@ -192,16 +192,19 @@ __global__ void k_sub_mean(double* __restrict__ p, size_t n, const DevStatus* __
 
 // Inverse Thomas pivots of (L_z + lambda_x(kx) + lambda_y(ky)) per column.
 __global__ void k_setup_pivots(Geo g, const double* __restrict__ lamx, const double* __restrict__ lamy,
-                               double* __restrict__ invd) {
+                               double* __restrict__ invd, double* __restrict__ mtab) {
   const size_t ncol = (size_t)g.ny * g.nxh;
   const size_t col = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= ncol) return;
   const int j = (int)(col / g.nxh), kx = (int)(col % g.nxh);
   const double lam = lamx[kx] + lamy[j];
   double d = -(g.za[0] + g.zc[0]) + lam;
+  if (mtab != nullptr) mtab[col] = 0.0;
   if (col == 0 && g.nz == 1) { invd[0] = 0.0; return; }
   invd[col] = 1.0 / d;
   for (int k = 1; k < g.nz; ++k) {
+    const double dinv_prev = invd[(size_t)(k - 1) * ncol + col];
+    if (mtab != nullptr) mtab[(size_t)k * ncol + col] = g.za[k] * dinv_prev;
     d = (-(g.za[k] + g.zc[k]) + lam) - g.za[k] * g.zc[k - 1] / d;
     const bool pin = (col == 0 && k == g.nz - 1);  // singular (0, 0) column: pin the last unknown
     invd[(size_t)k * ncol + col] = pin ? 0.0 : 1.0 / d;
@@ -337,9 +340,9 @@ cudaError_t launch_remove_mean(const Geo& g, double* p, double* red, DevStatus* 
 }
 
 cudaError_t launch_setup_pivots(const Geo& g, const double* lamx, const double* lamy, double* invd,
-                                cudaStream_t s) {
+                                cudaStream_t s, double* mtab) {
   const size_t ncol = (size_t)g.ny * g.nxh;
-  k_setup_pivots<<<(int)((ncol + 127) / 128), 128, 0, s>>>(g, lamx, lamy, invd);
+  k_setup_pivots<<<(int)((ncol + 127) / 128), 128, 0, s>>>(g, lamx, lamy, invd, mtab);
   return cudaGetLastError();
 }
 

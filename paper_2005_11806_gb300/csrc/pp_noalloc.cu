@@ -55,6 +55,7 @@ bool factor(int n, FftDesc* d) {
       d->radix[d->nst++] = r;
       m /= r;
     }
+  d->pow2 = (n & (n - 1)) == 0;
   return m == 1;
 }
 
