@@ -138,6 +138,35 @@ pp_status pressure_solve_adjoint(pp_plan plan, const double* rho, const double* 
  * race and must be ordered by the caller. */
 pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f, double* p, void* stream);
 
+/* ---- batched projections of independent grids -------------------------
+ * Method III projections (Algorithm 1, Sec. 3.3.1) of ngrids independent
+ * grids of different sizes, mixed precision only (PP_MIXED_FP32), solved
+ * together: each stage of a pass is one grouped launch over the tiles of all
+ * grids, and one call is one CUDA graph launch holding the set-up, a
+ * device-side while loop over passes (each grid stops at its own tolerance
+ * or maxit; the loop ends when all have stopped) and the correction.
+ * Creation allocates every workspace, computes every grid's tables, times
+ * candidate tile sizes of the transform kernels on the batch and keeps the
+ * fastest, and builds the graph.  Fields of all grids are packed: grid g's
+ * cell fields start at element cell_offset[g] of every packed cell buffer,
+ * its w field at wface_offset[g] of the packed w buffer
+ * (pressure_batch_layout).  Packed buffers are device pointers.  The
+ * correct call waits for the GPU and fills infos[ngrids] (may be NULL); it
+ * returns PP_OK when every grid converged, else the first failing status. */
+typedef struct pp_batch_s* pp_batch;
+
+pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision prec, void* stream,
+                                pp_batch* out);
+/* cell_offset, wface_offset: ngrids entries each (may be NULL); totals[2] =
+ * packed cell and w lengths; tiles[2] = the tuner's elements-per-thread
+ * choice for the x and y transform kernels. */
+pp_status pressure_batch_layout(pp_batch batch, long long* cell_offset, long long* wface_offset,
+                                long long* totals, int* tiles);
+pp_status pressure_batch_correct(pp_batch batch, const double* us, const double* vs, const double* ws,
+                                 const double* rho, const double* S, double dt, double* p, double* u,
+                                 double* v, double* w, double rtol, int maxit, pp_info* infos);
+pp_status pressure_batch_destroy(pp_batch batch);
+
 /* Wait for the plan's stream and fill info from the last pressure_correct
  * or pressure_solve_adjoint call. */
 pp_status pressure_last_info(pp_plan plan, pp_info* info);

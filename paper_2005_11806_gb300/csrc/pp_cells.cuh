@@ -1,0 +1,128 @@
+// Per-cell bodies of the stencil kernels, shared by the single-grid kernels
+// (pp_kernels_stencil.cu) and the grouped multi-grid kernels (pp_batch.cu).
+#pragma once
+#include "pp_fft.cuh"
+
+namespace pp {
+
+struct CellIdx {
+  int i, j, k;
+  size_t cim, cip, cjm, cjp;
+};
+
+__device__ __forceinline__ CellIdx cell_index(const Geo& g, size_t c) {
+  const int nx = g.nx, ny = g.ny;
+  const size_t plane = (size_t)nx * ny;
+  CellIdx x;
+  x.i = (int)(c % nx);
+  x.j = (int)((c / nx) % ny);
+  x.k = (int)(c / plane);
+  x.cim = c - x.i + (x.i == 0 ? nx - 1 : x.i - 1);
+  x.cip = c - x.i + (x.i + 1 == nx ? 0 : x.i + 1);
+  x.cjm = c - (size_t)x.j * nx + (size_t)(x.j == 0 ? ny - 1 : x.j - 1) * nx;
+  x.cjp = c - (size_t)x.j * nx + (size_t)(x.j + 1 == ny ? 0 : x.j + 1) * nx;
+  return x;
+}
+
+// Face coefficients of cell c (beta = 2/(rho_a + rho_b) on its x-, y- and
+// z-face "below", x/y coefficients scaled by the layer width dzf_k).
+__device__ __forceinline__ void cell_prep_faces(const Geo& g, const double* __restrict__ rho,
+                                                const Faces& fc, size_t c) {
+  const CellIdx x = cell_index(g, c);
+  const size_t plane = (size_t)g.nx * g.ny;
+  const double r = rho[c];
+  const double w = g.dzf[x.k];
+  fc.cx[c] = 2.0 / (r + rho[x.cim]) * g.inv_dx2 * w;
+  fc.cy[c] = 2.0 / (r + rho[x.cjm]) * g.inv_dy2 * w;
+  fc.cz[c] = (x.k == 0) ? 0.0 : 2.0 / (r + rho[c - plane]) * g.inv_dzc[x.k];
+  if (x.k == g.nz - 1) fc.cz[c + plane] = 0.0;
+  fc.rhof[c] = (float)r;
+  if (fc.cxf != nullptr) {
+    fc.cxf[c] = (float)fc.cx[c];
+    fc.cyf[c] = (float)fc.cy[c];
+    fc.czf[c] = (float)fc.cz[c];
+    if (x.k == g.nz - 1) fc.czf[c + plane] = 0.0f;
+  }
+}
+
+// diag = sum of the six (row-scaled) coefficients of cell c.
+__device__ __forceinline__ void cell_prep_diag(const Geo& g, const Faces& fc, size_t c) {
+  const CellIdx x = cell_index(g, c);
+  const size_t plane = (size_t)g.nx * g.ny;
+  fc.diag[c] = ((fc.cx[c] + fc.cx[x.cip]) + (fc.cy[c] + fc.cy[x.cjp])) + (fc.cz[c] + fc.cz[c + plane]);
+  if (fc.diagf != nullptr) fc.diagf[c] = (float)fc.diag[c];
+}
+
+// d = D u* - (S - meanS) at cell c (wall values of w* taken as zero); stores
+// the row-scaled b_s = dzf_k d / dt and returns d.
+__device__ __forceinline__ double cell_rhs_b(const Geo& g, const double* __restrict__ us,
+                                             const double* __restrict__ vs,
+                                             const double* __restrict__ ws,
+                                             const double* __restrict__ S, double meanS,
+                                             double* __restrict__ b, double inv_dt, size_t c) {
+  const CellIdx x = cell_index(g, c);
+  const size_t plane = (size_t)g.nx * g.ny;
+  const double wlo = (x.k == 0) ? 0.0 : ws[c];
+  const double whi = (x.k == g.nz - 1) ? 0.0 : ws[c + plane];
+  double d = (us[x.cip] - us[c]) / g.dx + (vs[x.cjp] - vs[c]) / g.dy + (whi - wlo) * g.inv_dzf[x.k];
+  if (S != nullptr) d -= (S[c] - meanS);
+  b[c] = d * g.dzf[x.k] * inv_dt;
+  return d;
+}
+
+// u = u* - dt beta G p at the faces of cell c (Eq. corr); w walls = 0.
+__device__ __forceinline__ void cell_correct(const Geo& g, const Faces& fc,
+                                             const double* __restrict__ us,
+                                             const double* __restrict__ vs,
+                                             const double* __restrict__ ws,
+                                             const double* __restrict__ p, double dt,
+                                             double* __restrict__ u, double* __restrict__ v,
+                                             double* __restrict__ w, size_t c) {
+  const CellIdx x = cell_index(g, c);
+  const size_t plane = (size_t)g.nx * g.ny;
+  const double pc = p[c];
+  // dt beta_x / dx = dt dx cx / dzf_k (cx carries dzf_k)
+  const double ax = dt * g.dx * g.inv_dzf[x.k], ay = dt * g.dy * g.inv_dzf[x.k];
+  u[c] = us[c] - ax * fc.cx[c] * (pc - p[x.cim]);
+  v[c] = vs[c] - ay * fc.cy[c] * (pc - p[x.cjm]);
+  w[c] = (x.k == 0) ? 0.0 : ws[c] - dt * fc.cz[c] * (pc - p[c - plane]);
+  if (x.k == g.nz - 1) w[c + plane] = 0.0;
+}
+
+// Loop control of Algorithm 1 for one grid, run by thread 0 with the
+// reduced residual sums s2 (sum e^2) and s1 (sum |e|).  kexact: recompute
+// the residual exactly every kexact passes (<= 1: every pass); convergence
+// is only accepted on an exact residual.
+__device__ __forceinline__ void status_update(DevStatus* st, double s2, double s1, double rtol,
+                                              int maxit, int kexact) {
+  st->e2 = s2;
+  st->e1 = s1;
+  const double e20 = st->e2_0;
+  const double rel = (e20 > 0.0) ? sqrt(s2 / e20) : 0.0;
+  st->rel = rel;
+  const int exact = st->need_exact;
+  if (!isfinite(s2) || !isfinite(e20)) { st->done = 1; st->code = PP_ERR_NUMERIC; }
+  else if (e20 == 0.0 || (rel <= rtol && exact)) { st->done = 1; st->code = PP_OK; }
+  else if (st->iters >= maxit) { st->done = 1; st->code = PP_ERR_NOT_CONVERGED; }
+  else {
+    st->iters += 1;
+    if (kexact <= 1) {
+      st->need_exact = 1;
+    } else if (exact) {
+      st->need_exact = 0;
+      st->since_exact = 1;
+    } else {
+      st->since_exact += 1;
+      // an updated residual below the tolerance is confirmed by an exact one
+      st->need_exact = (rel <= rtol || st->since_exact >= kexact) ? 1 : 0;
+    }
+  }
+}
+
+__device__ __forceinline__ void status_init(DevStatus* st) {
+  st->e2 = 0; st->e1 = 0; st->e2_0 = 0; st->rel = 0; st->mean_S = 0; st->pmean = 0;
+  st->iters = 0; st->done = 0; st->code = PP_OK; st->pad = 0;
+  st->need_exact = 1; st->since_exact = 0;
+}
+
+}  // namespace pp

@@ -2,7 +2,7 @@
 // (Eq. 22), face coefficients, the loop-invariant right-hand side of
 // Algorithm 1, its loop control, the correction step (Eq. corr), the gauge
 // removal, the adjoint stencils and the Thomas pivots of the z solve.
-#include "pp_fft.cuh"
+#include "pp_cells.cuh"
 
 namespace pp {
 
@@ -30,43 +30,16 @@ __global__ void k_mixture(const double* __restrict__ phi, double rho_g, double r
 // beta on every face: arithmetic face density, beta = 2 / (rho_a + rho_b);
 // x/y coefficients carry the width dzf_k of their layer (row scaling).
 __global__ void k_prep_faces(Geo g, const double* __restrict__ rho, Faces fc) {
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const size_t plane = (size_t)nx * ny, n = plane * nz;
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const int k = (int)(c / plane);
-    const double r = rho[c];
-    const double w = g.dzf[k];
-    const size_t cim = c - i + (i == 0 ? nx - 1 : i - 1);
-    const size_t cjm = c - (size_t)j * nx + (size_t)(j == 0 ? ny - 1 : j - 1) * nx;
-    fc.cx[c] = 2.0 / (r + rho[cim]) * g.inv_dx2 * w;
-    fc.cy[c] = 2.0 / (r + rho[cjm]) * g.inv_dy2 * w;
-    fc.cz[c] = (k == 0) ? 0.0 : 2.0 / (r + rho[c - plane]) * g.inv_dzc[k];
-    if (k == nz - 1) fc.cz[c + plane] = 0.0;
-    fc.rhof[c] = (float)r;
-    if (fc.cxf != nullptr) {
-      fc.cxf[c] = (float)fc.cx[c];
-      fc.cyf[c] = (float)fc.cy[c];
-      fc.czf[c] = (float)fc.cz[c];
-      if (k == nz - 1) fc.czf[c + plane] = 0.0f;
-    }
-  }
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    cell_prep_faces(g, rho, fc, c);
 }
 
 // diag = sum of the six (row-scaled) coefficients of each cell.
 __global__ void k_prep_diag(Geo g, Faces fc) {
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const size_t plane = (size_t)nx * ny, n = plane * nz;
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const size_t cip = c - i + (i + 1 == nx ? 0 : i + 1);
-    const size_t cjp = c - (size_t)j * nx + (size_t)(j + 1 == ny ? 0 : j + 1) * nx;
-    fc.diag[c] = ((fc.cx[c] + fc.cx[cip]) + (fc.cy[c] + fc.cy[cjp])) + (fc.cz[c] + fc.cz[c + plane]);
-    if (fc.diagf != nullptr) fc.diagf[c] = (float)fc.diag[c];
-  }
-  (void)nz;
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    cell_prep_diag(g, fc, c);
 }
 
 // Fixed-order partial sums of dzf_k * f (grid of kRedBlocks blocks).
@@ -97,33 +70,18 @@ __global__ void k_rhs_b(Geo g, const double* __restrict__ us, const double* __re
                         const DevStatus* __restrict__ st, double* __restrict__ b,
                         double* __restrict__ red, double inv_dt) {
   __shared__ double sh[32];
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const size_t plane = (size_t)nx * ny, n = plane * nz;
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
   const double meanS = st->mean_S;
-  const double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
   double s2 = 0.0;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const int k = (int)(c / plane);
-    const size_t cip = c - i + (i + 1 == nx ? 0 : i + 1);
-    const size_t cjp = c - (size_t)j * nx + (size_t)(j + 1 == ny ? 0 : j + 1) * nx;
-    const double wlo = (k == 0) ? 0.0 : ws[c];
-    const double whi = (k == nz - 1) ? 0.0 : ws[c + plane];
-    double d = (us[cip] - us[c]) * idx + (vs[cjp] - vs[c]) * idy + (whi - wlo) * g.inv_dzf[k];
-    if (S != nullptr) d -= (S[c] - meanS);
-    b[c] = d * g.dzf[k] * inv_dt;
+    const double d = cell_rhs_b(g, us, vs, ws, S, meanS, b, inv_dt, c);
     s2 += d * d;
   }
   s2 = block_sum<double>(s2, sh);
   if (threadIdx.x == 0) red[blockIdx.x] = s2;
 }
 
-__global__ void k_init_status(DevStatus* st) {
-  st->e2 = 0; st->e1 = 0; st->e2_0 = 0; st->rel = 0; st->mean_S = 0; st->pmean = 0;
-  st->iters = 0; st->done = 0; st->code = PP_OK; st->pad = 0;
-  st->need_exact = 1; st->since_exact = 0;
-}
+__global__ void k_init_status(DevStatus* st) { status_init(st); }
 
 // Loop control of Algorithm 1: reduce the residual partial sums, decide.
 __global__ void k_check(DevStatus* st, const double* __restrict__ red, int nblk, double rtol, int maxit,
@@ -138,50 +96,16 @@ __global__ void k_check(DevStatus* st, const double* __restrict__ red, int nblk,
   s2 = block_sum<double>(s2, sh);
   s1 = block_sum<double>(s1, sh);
   if (threadIdx.x != 0) return;
-  st->e2 = s2;
-  st->e1 = s1;
-  const double e20 = st->e2_0;
-  const double rel = (e20 > 0.0) ? sqrt(s2 / e20) : 0.0;
-  st->rel = rel;
-  const int exact = st->need_exact;
-  if (!isfinite(s2) || !isfinite(e20)) { st->done = 1; st->code = PP_ERR_NUMERIC; }
-  else if (e20 == 0.0 || (rel <= rtol && exact)) { st->done = 1; st->code = PP_OK; }
-  else if (st->iters >= maxit) { st->done = 1; st->code = PP_ERR_NOT_CONVERGED; }
-  else {
-    st->iters += 1;
-    if (kexact <= 1) {
-      st->need_exact = 1;
-    } else if (exact) {
-      st->need_exact = 0;
-      st->since_exact = 1;
-    } else {
-      st->since_exact += 1;
-      // an updated residual below the tolerance is confirmed by an exact one
-      st->need_exact = (rel <= rtol || st->since_exact >= kexact) ? 1 : 0;
-    }
-  }
+  status_update(st, s2, s1, rtol, maxit, kexact);
 }
 
 // u = u* - dt beta G p  (Eq. corr); w wall planes are written as zero.
 __global__ void k_correct(Geo g, Faces fc, const double* __restrict__ us, const double* __restrict__ vs,
                           const double* __restrict__ ws, const double* __restrict__ p, double dt,
                           double* __restrict__ u, double* __restrict__ v, double* __restrict__ w) {
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const size_t plane = (size_t)nx * ny, n = plane * nz;
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const int k = (int)(c / plane);
-    const size_t cim = c - i + (i == 0 ? nx - 1 : i - 1);
-    const size_t cjm = c - (size_t)j * nx + (size_t)(j == 0 ? ny - 1 : j - 1) * nx;
-    const double pc = p[c];
-    // dt beta_x / dx = dt dx cx / dzf_k (cx carries dzf_k)
-    const double ax = dt * g.dx * g.inv_dzf[k], ay = dt * g.dy * g.inv_dzf[k];
-    u[c] = us[c] - ax * fc.cx[c] * (pc - p[cim]);
-    v[c] = vs[c] - ay * fc.cy[c] * (pc - p[cjm]);
-    w[c] = (k == 0) ? 0.0 : ws[c] - dt * fc.cz[c] * (pc - p[c - plane]);
-    if (k == nz - 1) w[c + plane] = 0.0;
-  }
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    cell_correct(g, fc, us, vs, ws, p, dt, u, v, w, c);
 }
 
 __global__ void k_sub_mean(double* __restrict__ p, size_t n, const DevStatus* __restrict__ st) {

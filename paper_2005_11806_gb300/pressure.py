@@ -54,7 +54,8 @@ _lib = None
 EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_solve",
            "pressure_mixture_density", "pressure_correct", "pressure_solve_adjoint",
            "pressure_last_info", "pressure_profile_enable", "pressure_profile_read",
-           "pressure_solve_noalloc",
+           "pressure_solve_noalloc", "pressure_batch_create", "pressure_batch_layout",
+           "pressure_batch_correct", "pressure_batch_destroy",
            "pressure_status_string")
 
 
@@ -80,6 +81,12 @@ def lib():
     L.pressure_profile_read.argtypes = [vp, ctypes.POINTER(pp_kernel_time), i,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
     L.pressure_solve_noalloc.argtypes = [ctypes.POINTER(pp_grid), vp, vp, vp]
+    ll = ctypes.c_longlong
+    L.pressure_batch_create.argtypes = [ctypes.POINTER(pp_grid), i, i, vp, ctypes.POINTER(vp)]
+    L.pressure_batch_layout.argtypes = [vp, ctypes.POINTER(ll), ctypes.POINTER(ll), ctypes.POINTER(ll),
+                                        ctypes.POINTER(ctypes.c_int)]
+    L.pressure_batch_correct.argtypes = [vp, vp, vp, vp, vp, vp, d, vp, vp, vp, vp, d, i, pinfo]
+    L.pressure_batch_destroy.argtypes = [vp]
     L.pressure_status_string.argtypes = [i]
     L.pressure_status_string.restype = ctypes.c_char_p
     for name in EXPORTS[:-1]:
@@ -227,6 +234,55 @@ def pressure_profile_read(plan):
     _check(lib().pressure_profile_read(plan, arr, n.value, ctypes.byref(n), ctypes.byref(tot)),
            "pressure_profile_read")
     return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms) for k in range(n.value)}, tot.value
+
+
+class Batch:
+    """Batched projections of independent grids (packed field buffers).
+
+    ``grids``: list of dicts with nx, ny, nz, lx, ly, lz and optional zfaces.
+    """
+
+    def __init__(self, grids, precision="mixed", stream=None):
+        self.n = len(grids)
+        arr = (pp_grid * self.n)()
+        self._keep = []
+        for k, gd in enumerate(grids):
+            g, keep = _grid(gd["nx"], gd["ny"], gd["nz"], gd["lx"], gd["ly"], gd["lz"], gd.get("zfaces"))
+            arr[k] = g
+            self._keep.append(keep)
+        out = ctypes.c_void_p()
+        _check(lib().pressure_batch_create(arr, self.n, PRECISIONS[precision], _stream(stream),
+                                           ctypes.byref(out)), "pressure_batch_create")
+        self.handle = out.value
+        co = (ctypes.c_longlong * self.n)()
+        wo = (ctypes.c_longlong * self.n)()
+        tot = (ctypes.c_longlong * 2)()
+        tiles = (ctypes.c_int * 2)()
+        _check(lib().pressure_batch_layout(self.handle, co, wo, tot, tiles), "pressure_batch_layout")
+        self.cell_offset = list(co)
+        self.wface_offset = list(wo)
+        self.ncell, self.nwface = tot[0], tot[1]
+        self.tiles = (tiles[0], tiles[1])
+
+    def correct(self, us, vs, ws, rho, S, dt, p, u, v, w, rtol=1e-10, maxit=500,
+                allow_not_converged=False):
+        infos = (pp_info * self.n)()
+        code = lib().pressure_batch_correct(self.handle, _ptr(us), _ptr(vs), _ptr(ws), _ptr(rho), _ptr(S),
+                                            float(dt), _ptr(p), _ptr(u), _ptr(v), _ptr(w), float(rtol),
+                                            int(maxit), infos)
+        _check(code, "pressure_batch_correct", (PP_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return [infos[k].as_dict() for k in range(self.n)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().pressure_batch_destroy(self.handle), "pressure_batch_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:
