@@ -162,6 +162,9 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
  * choice for the x and y transform kernels. */
 pp_status pressure_batch_layout(pp_batch batch, long long* cell_offset, long long* wface_offset,
                                 long long* totals, int* tiles);
+/* Eq. 22 over the packed cell fields of every grid (device pointers). */
+pp_status pressure_batch_mixture_density(pp_batch batch, const double* phi, double rho_g, double rho_l,
+                                         double* rho);
 pp_status pressure_batch_correct(pp_batch batch, const double* us, const double* vs, const double* ws,
                                  const double* rho, const double* S, double dt, double* p, double* u,
                                  double* v, double* w, double rtol, int maxit, pp_info* infos);

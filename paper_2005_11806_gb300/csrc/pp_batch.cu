@@ -595,6 +595,13 @@ pp_status pressure_batch_layout(pp_batch B, long long* cell_offset, long long* w
   return PP_OK;
 }
 
+pp_status pressure_batch_mixture_density(pp_batch B, const double* phi, double rho_g, double rho_l,
+                                         double* rho) {
+  if (!B || !phi || !rho || !is_device(phi) || !is_device(rho)) return PP_ERR_INVALID_ARG;
+  PP_CK(launch_mixture(phi, rho_g, rho_l, rho, (size_t)B->ncell_tot, B->stream));
+  return PP_OK;
+}
+
 pp_status pressure_batch_correct(pp_batch B, const double* us, const double* vs, const double* ws,
                                  const double* rho, const double* S, double dt, double* p, double* u,
                                  double* v, double* w, double rtol, int maxit, pp_info* infos) {

@@ -55,7 +55,7 @@ EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_solve",
            "pressure_mixture_density", "pressure_correct", "pressure_solve_adjoint",
            "pressure_last_info", "pressure_profile_enable", "pressure_profile_read",
            "pressure_solve_noalloc", "pressure_batch_create", "pressure_batch_layout",
-           "pressure_batch_correct", "pressure_batch_destroy",
+           "pressure_batch_correct", "pressure_batch_destroy", "pressure_batch_mixture_density",
            "pressure_status_string")
 
 
@@ -87,6 +87,7 @@ def lib():
                                         ctypes.POINTER(ctypes.c_int)]
     L.pressure_batch_correct.argtypes = [vp, vp, vp, vp, vp, vp, d, vp, vp, vp, vp, d, i, pinfo]
     L.pressure_batch_destroy.argtypes = [vp]
+    L.pressure_batch_mixture_density.argtypes = [vp, vp, d, d, vp]
     L.pressure_status_string.argtypes = [i]
     L.pressure_status_string.restype = ctypes.c_char_p
     for name in EXPORTS[:-1]:
@@ -263,6 +264,10 @@ class Batch:
         self.wface_offset = list(wo)
         self.ncell, self.nwface = tot[0], tot[1]
         self.tiles = (tiles[0], tiles[1])
+
+    def mixture_density(self, phi, rho_g, rho_l, rho):
+        _check(lib().pressure_batch_mixture_density(self.handle, _ptr(phi), float(rho_g), float(rho_l),
+                                                    _ptr(rho)), "pressure_batch_mixture_density")
 
     def correct(self, us, vs, ws, rho, S, dt, p, u, v, w, rtol=1e-10, maxit=500,
                 allow_not_converged=False):

@@ -88,7 +88,8 @@ def spheres_phi(nx, ny, nz, lx, ly, zf, spheres, nsub=4):
     """Volume fraction of a union of non-overlapping spheres: the fraction of
     the nsub^3 sub-cell centres of each cell inside a sphere (values m/nsub^3).
     x and y are periodic; z is bounded by the walls.  ``spheres`` is a list of
-    (cx, cy, cz, r)."""
+    (cx, cy, cz, r).  Cells whose every sub-cell centre is provably inside
+    (or outside) are set to 1 (or 0) without sampling."""
     phi = np.zeros((nz, ny, nx))
     dx, dy = lx / nx, ly / ny
     off = (np.arange(nsub) + 0.5) / nsub
@@ -100,14 +101,51 @@ def spheres_phi(nx, ny, nz, lx, ly, zf, spheres, nsub=4):
         ii = np.arange(i0, i1)
         jj = np.arange(j0, j1)
         kk = np.arange(k0, k1)
-        xs = ((ii[:, None] + off[None, :]) * dx - cx).ravel()            # (ni*nsub)
-        ys = ((jj[:, None] + off[None, :]) * dy - cy).ravel()
-        zs = (zf[kk][:, None] + off[None, :] * (zf[kk + 1] - zf[kk])[:, None] - cz).ravel()
-        inside = (zs[:, None, None] ** 2 + ys[None, :, None] ** 2 + xs[None, None, :] ** 2) <= r * r
-        cnt = inside.reshape(len(kk), nsub, len(jj), nsub, len(ii), nsub).sum(axis=(1, 3, 5))
-        frac = cnt / float(nsub ** 3)
+        dzk = zf[kk + 1] - zf[kk]
+        # cell-centre distances and the largest sub-cell-centre offset
+        xc = (ii + 0.5) * dx - cx
+        yc = (jj + 0.5) * dy - cy
+        zc = 0.5 * (zf[kk] + zf[kk + 1]) - cz
+        dist = np.sqrt(zc[:, None, None] ** 2 + yc[None, :, None] ** 2 + xc[None, None, :] ** 2)
+        reach = (0.5 - 0.5 / nsub) * np.sqrt(dzk[:, None, None] ** 2 + dy * dy + dx * dx)
+        frac = np.zeros(dist.shape)
+        frac[dist + reach <= r] = 1.0
+        edge = np.argwhere((dist + reach > r) & (dist - reach <= r))
+        if len(edge):
+            ke, je, ie = edge[:, 0], edge[:, 1], edge[:, 2]
+            sx = (ii[ie][:, None] + off[None, :]) * dx - cx                       # (m, nsub)
+            sy = (jj[je][:, None] + off[None, :]) * dy - cy
+            sz = zf[kk[ke]][:, None] + off[None, :] * dzk[ke][:, None] - cz
+            inside = (sz[:, :, None, None] ** 2 + sy[:, None, :, None] ** 2
+                      + sx[:, None, None, :] ** 2) <= r * r
+            frac[ke, je, ie] = inside.reshape(len(edge), -1).sum(axis=1) / float(nsub ** 3)
         phi[np.ix_(kk, jj % ny, ii % nx)] += frac
     return np.minimum(phi, 1.0)
+
+
+def batch_case(count=96, seed=1004, ratio=1000.0, dt=1e-3, sizes=(64, 96, 128, 160, 192)):
+    """Independent grids for batched solves: N drawn from ``sizes`` for x and
+    y, nz = N a with a ~ U[1, 2] rounded up to a multiple of 8, unit x/y
+    period, lz = nz/N (cubic cells), walls in z.  Each grid holds one liquid
+    droplet (radius U[0.1, 0.25] of the period) in gas at ratio ``ratio``:1
+    and a random-divergence predicted velocity (N(0, 1) faces, mean-removed);
+    S = 0."""
+    rng = np.random.Generator(np.random.PCG64(seed + 10))
+    out = []
+    for gi in range(count):
+        n = int(sizes[rng.integers(0, len(sizes))])
+        a = rng.uniform(1.0, 2.0)
+        nz = int(math.ceil(n * a / 8.0) * 8)
+        lz = nz / n
+        zf = uniform_zfaces(nz, lz)
+        r = rng.uniform(0.1, 0.25)
+        h = 1.0 / n
+        c = (rng.uniform(0, 1), rng.uniform(0, 1), rng.uniform(r + 2 * h, lz - r - 2 * h))
+        drop = spheres_phi(n, n, nz, 1.0, 1.0, zf, [(c[0], c[1], c[2], r)])
+        us, vs, ws = random_faces(n, n, nz, 1.0, seed + 100 * (gi + 1), remove_mean=True)
+        out.append(Workload(f"batch grid {gi}: {n}x{n}x{nz}, droplet r={r:.3f}", n, n, nz, 1.0, 1.0, zf,
+                            dt, us, vs, ws, 1.0 - drop, 1.0, ratio, np.zeros((nz, n, n))))
+    return out
 
 
 def gas_source(phi):
