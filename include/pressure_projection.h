@@ -56,7 +56,10 @@ typedef enum { PP_BC_PERIODIC = 0, PP_BC_WALL = 1 } pp_bc;
 
 typedef enum {
     PP_FP64 = 0,       /* every step in FP64 */
-    PP_MIXED_FP32 = 1  /* x/y transforms in FP32; residual, z solve and p in FP64 */
+    PP_MIXED_FP32 = 1, /* x/y transforms in FP32; residual, z solve and p in FP64 */
+    PP_MIXED_TC = 2    /* as PP_MIXED_FP32, but the z solve is the eigenvector expansion
+                          along z (x = V diag(1/(mu + lambda)) V^T W f) as BF16x3 split
+                          products on the tensor cores with FP32 accumulation; nz <= 512 */
 } pp_precision;
 
 typedef struct {

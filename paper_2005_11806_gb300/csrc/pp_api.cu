@@ -62,6 +62,11 @@ struct pp_plan_s {
   double* d_adj[4] = {nullptr};
   double last_mean_S = 0.0;
   Prof prof;
+  bool z_tc = false;           // tensor-core z solve (PP_MIXED_TC)
+  ZEigen ze{};
+  float* d_mu = nullptr;
+  unsigned char* d_za1 = nullptr;
+  unsigned char* d_za2 = nullptr;
 };
 
 namespace {
@@ -192,6 +197,7 @@ pp_status read_info(pp_plan_s* P, pp_info* info) {
   PP_CK(cudaMemcpyAsync(P->h_st, P->d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, P->stream));
   PP_CK(cudaStreamSynchronize(P->stream));
   const DevStatus& s = P->h_st[0];
+  if (s.pad != 0) return PP_ERR_CUDA;  // a device-side bounded wait ran out
   if (info) {
     const double dt_scale = 1.0;  // e is stored in units of 1/dt; res0/res_l1 are rescaled by the caller
     info->iters = s.iters;
@@ -216,7 +222,11 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, float* delta = nullptr
   double2* ybuf = (double2*)P->d_spec;
   const double scale = 1.0 / ((double)P->nx * (double)P->ny);
   PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream));
-  PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab));
+  if (P->z_tc) {
+    PP_K(P, K_TRI, launch_zgemm(g, P->ze, reinterpret_cast<float2*>(spec), P->d_st, P->stream));
+  } else {
+    PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab));
+  }
   PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream));
   PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream, delta));
   return PP_OK;
@@ -295,6 +305,9 @@ void free_plan(pp_plan_s* P) {
   float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta};
   for (float* f : fptrs) if (f) cudaFree(f);
   if (P->d_E) cudaFree(P->d_E);
+  if (P->d_mu) cudaFree(P->d_mu);
+  if (P->d_za1) cudaFree(P->d_za1);
+  if (P->d_za2) cudaFree(P->d_za2);
   if (P->d_inv_dzf_f) cudaFree(P->d_inv_dzf_f);
   for (double* d : dptrs) if (d) cudaFree(d);
   if (P->d_twx) cudaFree(P->d_twx);
@@ -335,7 +348,8 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   const pp_grid& G = *grid;
   if (G.nx < 2 || G.ny < 1 || G.nz < 1 || !(G.lx > 0) || !(G.ly > 0) || !(G.lz > 0))
     return PP_ERR_INVALID_ARG;
-  if (prec != PP_FP64 && prec != PP_MIXED_FP32) return PP_ERR_INVALID_ARG;
+  if (prec != PP_FP64 && prec != PP_MIXED_FP32 && prec != PP_MIXED_TC) return PP_ERR_INVALID_ARG;
+  if (prec == PP_MIXED_TC && G.nz > 512) return PP_ERR_UNSUPPORTED;
   if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL)
     return PP_ERR_UNSUPPORTED;
   if ((G.nx & 1) != 0) return PP_ERR_UNSUPPORTED;
@@ -461,6 +475,32 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   g.inv_dy2 = 1.0 / (P->dy * P->dy);
   g.inv_dzf = P->d_inv_dzf; g.inv_dzc = P->d_inv_dzc; g.dzf = P->d_dzf;
   g.za = P->d_za; g.zc = P->d_zc; g.lz = lz_sum;
+  if (prec == PP_MIXED_TC) {
+    int nzp = 0, zm = 0;
+    std::vector<float> mu;
+    std::vector<uint16_t> a1, a2;
+    if (!build_zeigen_host(nz, dzf.data(), inv_dzc.data(), &nzp, mu, &zm, a1, a2)) {
+      free_plan(P);
+      return PP_ERR_NUMERIC;
+    }
+    if ((st = dalloc(&P->d_mu, mu.size() * sizeof(float))) != PP_OK ||
+        (st = dalloc(&P->d_za1, a1.size() * sizeof(uint16_t))) != PP_OK ||
+        (st = dalloc(&P->d_za2, a2.size() * sizeof(uint16_t))) != PP_OK ||
+        cudaMemcpy(P->d_mu, mu.data(), mu.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P->d_za1, a1.data(), a1.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P->d_za2, a2.data(), a2.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_plan(P);
+      return st != PP_OK ? st : PP_ERR_CUDA;
+    }
+    P->z_tc = true;
+    P->ze.nzp = nzp;
+    P->ze.mu = P->d_mu;
+    P->ze.zero_mode = zm;
+    P->ze.lamx = P->d_lamx;
+    P->ze.lamy = P->d_lamy;
+    P->ze.a1 = P->d_za1;
+    P->ze.a2 = P->d_za2;
+  }
   if (launch_setup_pivots(g, P->d_lamx, P->d_lamy, P->d_invd, P->stream, P->d_mtab) != cudaSuccess ||
       launch_init_status(P->d_st, P->stream) != cudaSuccess ||
       cudaStreamSynchronize(P->stream) != cudaSuccess) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <vector>
 
 #include "pressure_projection.h"
 
@@ -172,5 +173,21 @@ cudaError_t launch_adj_grho(const Geo& g, const double* tx, const double* ty, co
                             double* grho, cudaStream_t s);
 
 int reduce_blocks();  // number of partial sums the reduction kernels write
+
+// Tables of the tensor-core z solve (pp_zgemm.cu).
+struct ZEigen {
+  int nzp;                  // nz padded to a multiple of 128
+  const float* mu;          // [nzp] eigenvalues of L_z (0 on padded modes)
+  int zero_mode;            // index of the zero eigenvalue
+  const double* lamx;       // [nxh]
+  const double* lamy;       // [ny]
+  const unsigned char* a1;  // bf16 hi/lo tiles of V^T W
+  const unsigned char* a2;  // bf16 hi/lo tiles of V
+};
+cudaError_t launch_zgemm(const Geo& g, const ZEigen& ze, float2* spec, DevStatus* st, cudaStream_t s);
+size_t zgemm_smem_bytes(int nzp);
+// Host: eigen decomposition of L_z and the bf16 hi/lo tiles of V^T W and V.
+bool build_zeigen_host(int nz, const double* dzf, const double* inv_dzc, int* nzp_out, std::vector<float>& mu_out,
+                       int* zero_mode, std::vector<uint16_t>& a1, std::vector<uint16_t>& a2);
 
 }  // namespace pp

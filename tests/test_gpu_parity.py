@@ -282,3 +282,39 @@ def test_autograd_function_matches_oracle_gradient(pp):
                              2 * (host(v) - ut[1]), 2 * (host(ww) - ut[2]))
     for got, exp in ((us.grad, ref[0]), (vs.grad, ref[1]), (ws.grad, ref[2]), (r.grad, ref[3])):
         assert _rel(host(got), exp) < 1e-8
+
+
+# --- tensor-core z solve (eigenvector expansion along z, BF16x3 products) --
+
+@pytest.mark.parametrize("dims,stretch", [((32, 32, 40), 1.5), ((48, 40, 128), 2.0), ((64, 64, 64), None)])
+def test_tc_constant_solve_vs_oracle(pp, dims, stretch):
+    """The tensor-core z expansion solves the constant-coefficient equation;
+    its error is that of BF16x3 products (2^-16 relative per product)."""
+    nx, ny, nz = dims
+    zf = wl.uniform_zfaces(nz, 1.0) if stretch is None else wl.tanh_zfaces(nz, 1.0, stretch)
+    g = orc.Grid(nx, ny, nz, 1.0, 1.0, zf)
+    f = np.random.default_rng(nz).standard_normal(g.shape)
+    ref = orc.solve_constant(g, f)
+    plan = _plan(pp, nx, ny, nz, 1.0, 1.0, zf, "mixed_tc")
+    p = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    pp.pressure_solve(plan.handle, dev(f), p)
+    err = _rel(host(p), ref)
+    print("tc constant solve rel err", dims, err)
+    assert err < 1e-3
+
+
+@pytest.mark.parametrize("stretched", [False, True])
+def test_projection_tc_vs_oracle(pp, stretched):
+    """Method III with the tensor-core z solve still reaches a relative
+    residual of 1e-10 (evaluated in FP64) and the FP64 oracle's solution."""
+    w, rho = _sphere_case(48, 1000.0, stretched, 40)
+    g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf)
+    p0, u0, v0, w0, oinfo = orc.method3(g, w.us, w.vs, w.ws, rho, w.S, w.dt, rtol=1e-13, maxit=3000)
+    info, p, u, v, ww = _run_gpu(pp, w, rho, "mixed_tc", rtol=1e-10, maxit=3000)
+    print("tc projection iters", info["iters"], "oracle(1e-13)", oinfo["iters"])
+    assert info["status"] == 0 and info["res_final"] <= 1e-10
+    Sc = w.S - orc.volume_mean(g, w.S)
+    d0 = orc.divergence(g, w.us, w.vs, w.ws) - Sc
+    assert np.linalg.norm(orc.divergence(g, u, v, ww) - Sc) <= 1.0001e-10 * np.linalg.norm(d0)
+    for a, b in ((u, u0), (v, v0), (ww, w0)):
+        assert _rel(a, b) < 1e-9
