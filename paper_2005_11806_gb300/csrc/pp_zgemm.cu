@@ -104,6 +104,14 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16_raw& hi, __nv_
 // half spectrum (FP32), all nz rows (padded to nzp, a multiple of 128).
 //   a1: (V^T W) tiles, a2: V tiles, each [mt][kc] chunk = 128 x 64 bf16 hi
 //   then lo in the no-swizzle K-major core layout (32 KB contiguous).
+// Pipeline: thread 0 streams the A chunks of both products through a
+// kStages-deep shared ring (bulk copies, full/empty mbarriers) and issues
+// the MMAs; all threads convert the next B chunk of the first product while
+// the current one is in use.  The second product consumes the scaled first
+// product one 64-mode chunk at a time (double-buffered), produced from TMEM
+// by the two warps that own those lanes.
+constexpr int kStages = 5;
+
 __global__ void __launch_bounds__(kThreadsZ, 1) k_zgemm(float* spec, long long ncols, int nz, int nzp, int nxh,
                                                       const float* __restrict__ mu, int zero_mode,
                                                       const double* __restrict__ lamx,
@@ -112,20 +120,37 @@ __global__ void __launch_bounds__(kThreadsZ, 1) k_zgemm(float* spec, long long n
                                                       const unsigned char* __restrict__ a2, DevStatus* st) {
   if (st != nullptr && st->done) return;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[2];
+  // barriers: [0, S) full, [S, 2S) empty, 2S+{0,1} B free, 2S+{2,3} G free, 2S+4 D1 done, 2S+5 D2 done
+  __shared__ __align__(8) uint64_t bars[2 * kStages + 6];
   __shared__ uint32_t taddr_s;
   __shared__ int fail_s;
-  unsigned char* sA = smem;                          // 32 KB
-  unsigned char* sB = smem + kChunkBytesA;           // 16 KB
-  unsigned char* sG = sB + kChunkBytesB;             // 64 x nzp hi + lo
+  __shared__ float lam_s[kTileN / 2];  // lambda_x + lambda_y per complex column
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kStages;
+  uint64_t* bfree = bars + 2 * kStages;
+  uint64_t* gfree = bars + 2 * kStages + 2;
+  uint64_t* d1done = bars + 2 * kStages + 4;
+  uint64_t* d2done = bars + 2 * kStages + 5;
+  unsigned char* sA0 = smem;                                  // kStages x 32 KB ring
+  unsigned char* sB0 = smem + kStages * kChunkBytesA;         // 2 x 16 KB (first product B)
+  unsigned char* sG0 = sB0 + 2 * kChunkBytesB;                // 2 x 16 KB (second product B)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nmt = nzp / kTileM, nkc = nzp / kChunkK;
+  const int nch1 = nkc * nmt;
+  const int nch = 2 * nch1;
   const long long col0 = (long long)blockIdx.x * kTileN;
-  const uint32_t sbo_g = (uint32_t)(nzp / 8) * 128u;  // 8-row group stride of the G tile
-  const uint32_t gbytes_half = (uint32_t)kTileN * nzp * 2u;
+  if (tid < kTileN / 2) {
+    const long long cc = (col0 >> 1) + tid;
+    float l = 0.f;
+    if (2 * cc < ncols) {
+      const int jj = (int)(cc / nxh), kx = (int)(cc - (long long)jj * nxh);
+      l = (float)(lamx[kx] + lamy[jj]);
+    }
+    lam_s[tid] = l;
+  }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&bars[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&bars[1])), "r"(1));
+    for (int i = 0; i < 2 * kStages + 6; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&bars[i])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fail_s = 0;
   }
@@ -140,61 +165,102 @@ __global__ void __launch_bounds__(kThreadsZ, 1) k_zgemm(float* spec, long long n
   const uint32_t tbase = taddr_s;
   const uint32_t d1 = tbase, d2 = tbase + 256;
   const uint32_t idesc = idesc_bf16(kTileM, kTileN);
-  uint32_t ph_a = 0, ph_m = 0;
-  bool ok = true;
 
-  // ---- GEMM 1: D1[mode][n] = sum_level (V^T W)[mode][level] F[level][n] ----
-  for (int kc = 0; kc < nkc && ok; ++kc) {
-    for (int e = tid; e < kTileN * kChunkK; e += kThreadsZ) {
-      const int kl = e / kTileN, n = e - kl * kTileN;
-      const int lev = kc * kChunkK + kl;
-      const long long col = col0 + n;
-      const float x = (lev < nz && col < ncols) ? spec[(long long)lev * ncols + col] : 0.f;
+  // chunk i: first product (i < nch1): kc = i / nmt, mt = i % nmt (A1 tile mt, kc);
+  // second product: j = i - nch1, kc = j / nmt, lt = j % nmt (A2 tile lt, kc)
+  auto chunk_src = [&](int i) -> const unsigned char* {
+    const int j = i < nch1 ? i : i - nch1;
+    const int kc = j / nmt, t = j - kc * nmt;
+    return (i < nch1 ? a1 : a2) + ((size_t)t * nkc + kc) * kChunkBytesA;
+  };
+  auto issue_copy = [&](int i) {  // thread 0 only
+    const int s = i % kStages;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(&full[s])), "r"(kChunkBytesA) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(sA0 + s * kChunkBytesA)), "l"(chunk_src(i)), "r"(kChunkBytesA),
+                    "r"(smem_u32(&full[s])) : "memory");
+  };
+  // thread 0: wait for chunk i, issue its 12 MMAs, release its stage on
+  // completion, and refill the stage of chunk i - 1 (whose MMAs precede these)
+  auto run_chunk = [&](int i, uint32_t dtile, uint32_t b_hi, uint32_t b_lo, bool first) {
+    if (fail_s) return;
+    const int s = i % kStages;
+    if (!mbar_wait(&full[s], (uint32_t)((i / kStages) & 1))) { fail_s = 1; return; }
+    tc_fence_after();
+    const uint32_t a_hi = smem_u32(sA0 + s * kChunkBytesA), a_lo = a_hi + kChunkBytesA / 2;
+#pragma unroll
+    for (int k = 0; k < kChunkK / 16; ++k) {
+      const uint32_t acc = (first && k == 0) ? 0u : 1u;
+      const uint32_t o = (uint32_t)k * 256u;
+      mma_bf16(dtile, smem_desc(a_hi + o, 128, 1024), smem_desc(b_hi + o, 128, 1024), idesc, acc);
+      mma_bf16(dtile, smem_desc(a_hi + o, 128, 1024), smem_desc(b_lo + o, 128, 1024), idesc, 1u);
+      mma_bf16(dtile, smem_desc(a_lo + o, 128, 1024), smem_desc(b_hi + o, 128, 1024), idesc, 1u);
+    }
+    mma_commit(&empty[s]);
+    const int r = i - 1 + kStages;  // refill the stage chunk i - 1 used
+    if (i >= 1 && r < nch) {
+      const int sp = (i - 1) % kStages;
+      if (!mbar_wait(&empty[sp], (uint32_t)(((i - 1) / kStages) & 1))) { fail_s = 1; return; }
+      issue_copy(r);
+    }
+  };
+  auto convert_b = [&](int kc) {  // all threads; every load issued before use
+    constexpr int PER = kTileN * kChunkK / kThreadsZ;
+    unsigned char* sB = sB0 + (kc & 1) * kChunkBytesB;
+    const int n = tid & (kTileN - 1), kl0 = tid / kTileN;
+    const long long col = col0 + n;
+    float x[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int lev = kc * kChunkK + kl0 + u * (kThreadsZ / kTileN);
+      x[u] = (lev < nz && col < ncols) ? spec[(long long)lev * ncols + col] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int kl = kl0 + u * (kThreadsZ / kTileN);
       __nv_bfloat16_raw hi, lo;
-      split_bf16(x, hi, lo);
+      split_bf16(x[u], hi, lo);
       const uint32_t o = core_off(n, kl, 1024u);
       *reinterpret_cast<__nv_bfloat16_raw*>(sB + o) = hi;
       *reinterpret_cast<__nv_bfloat16_raw*>(sB + kChunkBytesB / 2 + o) = lo;
     }
     fence_async_smem();
-    __syncthreads();
-    for (int mt = 0; mt < nmt && ok; ++mt) {
-      if (tid == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                     :: "r"(smem_u32(&bars[0])), "r"(kChunkBytesA) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(smem_u32(sA)), "l"(a1 + ((size_t)mt * nkc + kc) * kChunkBytesA), "r"(kChunkBytesA),
-                        "r"(smem_u32(&bars[0])) : "memory");
-        if (!mbar_wait(&bars[0], ph_a)) fail_s = 1;
-        tc_fence_after();
-        if (!fail_s) {
-          const uint32_t a_hi = smem_u32(sA), a_lo = a_hi + kChunkBytesA / 2;
-          const uint32_t b_hi = smem_u32(sB), b_lo = b_hi + kChunkBytesB / 2;
-#pragma unroll
-          for (int s = 0; s < kChunkK / 16; ++s) {
-            const uint32_t acc = (kc > 0 || s > 0) ? 1u : 0u;
-            const uint32_t step = (uint32_t)s * 256u;
-            mma_bf16(d1 + mt * kTileN, smem_desc(a_hi + step, 128, 1024), smem_desc(b_hi + step, 128, 1024), idesc, acc);
-            mma_bf16(d1 + mt * kTileN, smem_desc(a_hi + step, 128, 1024), smem_desc(b_lo + step, 128, 1024), idesc, 1u);
-            mma_bf16(d1 + mt * kTileN, smem_desc(a_lo + step, 128, 1024), smem_desc(b_hi + step, 128, 1024), idesc, 1u);
-          }
-        }
-        mma_commit(&bars[1]);
-        if (!mbar_wait(&bars[1], ph_m)) fail_s = 1;
-      }
-      ph_a ^= 1u;
-      ph_m ^= 1u;
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      ok = (fail_s == 0);
-    }
-  }
+  };
 
-  // ---- scale by 1/(mu + lambda) and stage G (K-major over modes) ----------
-  if (ok) {
-    for (int mt = 0; mt < nmt; ++mt) {
-      const int m = mt * kTileM + warp * 32 + lane;  // this thread's TMEM lane = mode
+  if (tid == 0)
+    for (int i = 0; i < kStages && i < nch; ++i) issue_copy(i);
+  convert_b(0);
+  __syncthreads();
+
+  // ---- first product: D1[mode][n] = sum_level (V^T W)[mode][level] F[level][n] ----
+  for (int kc = 0; kc < nkc; ++kc) {
+    if (tid == 0) {
+      const uint32_t b_hi = smem_u32(sB0 + (kc & 1) * kChunkBytesB), b_lo = b_hi + kChunkBytesB / 2;
+      for (int mt = 0; mt < nmt; ++mt) run_chunk(kc * nmt + mt, d1 + mt * kTileN, b_hi, b_lo, kc == 0);
+      mma_commit(&bfree[kc & 1]);
+    }
+    if (kc + 1 < nkc) {
+      if (kc >= 1 && !mbar_wait(&bfree[(kc + 1) & 1], (uint32_t)(((kc - 1) >> 1) & 1))) fail_s = 1;
+      convert_b(kc + 1);
+    }
+    __syncthreads();
+    if (fail_s) break;
+  }
+  if (tid == 0) mma_commit(d1done);
+  if (!fail_s && !mbar_wait(d1done, 0)) fail_s = 1;
+  tc_fence_after();
+  __syncthreads();
+
+  // ---- second product, one 64-mode chunk of the scaled first product at a time ----
+  for (int kc = 0; kc < nkc && !fail_s; ++kc) {
+    // modes kc*64 .. +64 are TMEM lanes (kc & 1)*64 .. +64 of D1 tile kc / 2
+    const int mt = kc >> 1, wbase = (kc & 1) * 2;
+    unsigned char* sG = sG0 + (kc & 1) * kChunkBytesB;
+    if (warp == wbase || warp == wbase + 1) {
+      if (kc >= 2 && !mbar_wait(&gfree[kc & 1], (uint32_t)(((kc - 2) >> 1) & 1))) fail_s = 1;
+      const int ml = (warp - wbase) * 32 + lane;  // mode within the chunk
+      const int m = kc * kChunkK + ml;
       const float mum = mu[m < nzp ? m : 0];
       for (int c16 = 0; c16 < kTileN / 16; ++c16) {
         float v[16];
@@ -202,63 +268,35 @@ __global__ void __launch_bounds__(kThreadsZ, 1) k_zgemm(float* spec, long long n
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int n = c16 * 16 + q;
-          const long long cc = (col0 + n) >> 1;  // complex column
-          const int jj = (int)(cc / nxh), kx = (int)(cc - (long long)jj * nxh);
           const bool in = (col0 + n) < ncols && m < nz;
-          float inv = 0.f;
-          if (in && !(m == zero_mode && cc == 0)) inv = 1.0f / (mum + (float)(lamx[kx] + lamy[jj]));
+          const bool zero = (m == zero_mode) && ((col0 + n) >> 1) == 0;
+          const float inv = (in && !zero) ? 1.0f / (mum + lam_s[n >> 1]) : 0.f;
           __nv_bfloat16_raw hi, lo;
           split_bf16(v[q] * inv, hi, lo);
-          const uint32_t o = core_off(n, m, sbo_g);
+          const uint32_t o = core_off(n, ml, 1024u);
           *reinterpret_cast<__nv_bfloat16_raw*>(sG + o) = hi;
-          *reinterpret_cast<__nv_bfloat16_raw*>(sG + gbytes_half + o) = lo;
+          *reinterpret_cast<__nv_bfloat16_raw*>(sG + kChunkBytesB / 2 + o) = lo;
         }
       }
+      fence_async_smem();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && !fail_s) {
+      const uint32_t g_hi = smem_u32(sG), g_lo = g_hi + kChunkBytesB / 2;
+      for (int lt = 0; lt < nmt; ++lt) run_chunk(nch1 + kc * nmt + lt, d2 + lt * kTileN, g_hi, g_lo, kc == 0);
+      mma_commit(&gfree[kc & 1]);
     }
   }
-  fence_async_smem();
-  tc_fence_before();
+  if (tid == 0) mma_commit(d2done);
   __syncthreads();
+  if (!fail_s && !mbar_wait(d2done, 0)) fail_s = 1;
   tc_fence_after();
-
-  // ---- GEMM 2: D2[level][n] = sum_mode V[level][mode] G[mode][n] ----------
-  for (int lt = 0; lt < nmt && ok; ++lt) {
-    for (int kc = 0; kc < nkc && ok; ++kc) {
-      if (tid == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                     :: "r"(smem_u32(&bars[0])), "r"(kChunkBytesA) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(smem_u32(sA)), "l"(a2 + ((size_t)lt * nkc + kc) * kChunkBytesA), "r"(kChunkBytesA),
-                        "r"(smem_u32(&bars[0])) : "memory");
-        if (!mbar_wait(&bars[0], ph_a)) fail_s = 1;
-        tc_fence_after();
-        if (!fail_s) {
-          const uint32_t a_hi = smem_u32(sA), a_lo = a_hi + kChunkBytesA / 2;
-          const uint32_t g_hi = smem_u32(sG), g_lo = g_hi + gbytes_half;
-#pragma unroll
-          for (int s = 0; s < kChunkK / 16; ++s) {
-            const uint32_t acc = (kc > 0 || s > 0) ? 1u : 0u;
-            const uint32_t astep = (uint32_t)s * 256u;
-            const uint32_t gstep = (uint32_t)kc * (kChunkK / 8) * 128u + (uint32_t)s * 256u;
-            mma_bf16(d2 + lt * kTileN, smem_desc(a_hi + astep, 128, 1024), smem_desc(g_hi + gstep, 128, sbo_g), idesc, acc);
-            mma_bf16(d2 + lt * kTileN, smem_desc(a_hi + astep, 128, 1024), smem_desc(g_lo + gstep, 128, sbo_g), idesc, 1u);
-            mma_bf16(d2 + lt * kTileN, smem_desc(a_lo + astep, 128, 1024), smem_desc(g_hi + gstep, 128, sbo_g), idesc, 1u);
-          }
-        }
-        mma_commit(&bars[1]);
-        if (!mbar_wait(&bars[1], ph_m)) fail_s = 1;
-      }
-      ph_a ^= 1u;
-      ph_m ^= 1u;
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      ok = (fail_s == 0);
-    }
-  }
+  __syncthreads();
 
   // ---- write x back in place ----------------------------------------------
-  if (ok) {
+  if (!fail_s) {
     for (int lt = 0; lt < nmt; ++lt) {
       const int lev = lt * kTileM + warp * 32 + lane;
       for (int c16 = 0; c16 < kTileN / 16; ++c16) {
@@ -274,10 +312,10 @@ __global__ void __launch_bounds__(kThreadsZ, 1) k_zgemm(float* spec, long long n
       }
     }
   } else if (tid == 0) {
-    // a bounded wait ran out: let in-flight copies and MMAs finish (bounded),
-    // report it (the host returns PP_ERR_CUDA), then free TMEM below
-    mbar_wait(&bars[0], ph_a);
-    mbar_wait(&bars[1], ph_m);
+    // a bounded wait ran out: give in-flight copies and MMAs a bounded chance
+    // to finish, report it (the host returns PP_ERR_CUDA), then free TMEM
+    mma_commit(d2done);
+    mbar_wait(d2done, 1);
     if (st != nullptr) st->pad = 1;
   }
   tc_fence_before();
@@ -285,7 +323,10 @@ __global__ void __launch_bounds__(kThreadsZ, 1) k_zgemm(float* spec, long long n
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(512) : "memory");
 }
 
-size_t zgemm_smem_bytes(int nzp) { return (size_t)kChunkBytesA + kChunkBytesB + (size_t)kTileN * nzp * 4; }
+size_t zgemm_smem_bytes(int nzp) {
+  (void)nzp;
+  return (size_t)kStages * kChunkBytesA + 4 * (size_t)kChunkBytesB;
+}
 
 cudaError_t launch_zgemm(const Geo& g, const ZEigen& ze, float2* spec, DevStatus* st, cudaStream_t s) {
   const long long ncols = 2LL * g.ny * g.nxh;
