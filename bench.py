@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_tc"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--bubbles", type=int, default=200)
     ap.add_argument("--ratio", type=float, default=1000.0)
@@ -114,6 +114,9 @@ def algorithmic(kernel, w, precision):
     npts = w.nx * w.ny * w.nz
     nsp = (w.nx // 2 + 1) * w.ny * w.nz
     cs = 16 if precision == "fp64" else 8
+    if kernel == "tridiag_z" and precision == "mixed_tc":
+        # tensor-core z expansion: two real GEMMs (nz x nz) per column, BF16x3
+        return {"bytes": 2 * cs * nsp, "fp64_flops": 0, "tensor_flops": 3 * 2 * 2 * w.nz * 2 * nsp}
     if kernel == "resid_fftx":
         # reads b, rho, p, cx, cy, cz (FP64); writes the half spectrum
         return {"bytes": 48 * npts + cs * nsp, "fp64_flops": 24 * npts}

@@ -168,6 +168,67 @@ __device__ C2<T>* fft_block(C2<T>* a, C2<T>* b, const FftDesc& d, int nbatch, in
   return src;
 }
 
+// Compile-time variant for power-of-two N (radices 8, then one 4 or 2):
+// every index is a constant shift/mask, strides are template arguments.
+template <int N> struct Log2 { static constexpr int value = 1 + Log2<N / 2>::value; };
+template <> struct Log2<1> { static constexpr int value = 0; };
+template <int N, int S> struct Pow2Radix {  // radix of pass S for length N
+  static constexpr int rem = Log2<N>::value - 3 * S;
+  static constexpr int value = rem >= 3 ? 8 : (rem == 2 ? 4 : 2);
+};
+template <int N> struct Pow2Passes { static constexpr int value = (Log2<N>::value + 2) / 3; };
+
+template <typename T, int DIR, int R, bool BATCH_FAST, int N, int NS, int NBATCH, int ES, int BS>
+__device__ __forceinline__ void fft_pass_fixed(const C2<T>* __restrict__ src, C2<T>* __restrict__ dst,
+                                               const C2<T>* __restrict__ tw, int tid, int nth) {
+  constexpr int NB = N / R;
+  constexpr int TOTAL = NB * NBATCH;
+  constexpr int TWS = N / (NS * R);
+  for (int t = tid; t < TOTAL; t += nth) {
+    int bi, j;
+    if (BATCH_FAST) { j = t / NBATCH; bi = t % NBATCH; }
+    else { bi = t / NB; j = t % NB; }
+    const int k = j % NS;
+    C2<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[bi * BS + (j + r * NB) * ES];
+    if (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C2<T> w = __ldg(&tw[r * k * TWS]);
+        w.y = DIR > 0 ? w.y : -w.y;
+        v[r] = cmul<T>(v[r], w);
+      }
+    }
+    Dft<T, DIR, R>::run(v);
+    const int base = (j / NS) * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[bi * BS + (base + r * NS) * ES] = v[r];
+  }
+}
+
+template <typename T, int DIR, bool BATCH_FAST, int N, int NBATCH, int ES, int BS, int S, int NS>
+__device__ __forceinline__ void fft_fixed_from(C2<T>*& src, C2<T>*& dst, const C2<T>* __restrict__ tw,
+                                               int tid, int nth) {
+  if constexpr (S < Pow2Passes<N>::value) {
+    constexpr int R = Pow2Radix<N, S>::value;
+    fft_pass_fixed<T, DIR, R, BATCH_FAST, N, NS, NBATCH, ES, BS>(src, dst, tw, tid, nth);
+    __syncthreads();
+    C2<T>* t = src; src = dst; dst = t;
+    fft_fixed_from<T, DIR, BATCH_FAST, N, NBATCH, ES, BS, S + 1, NS * R>(src, dst, tw, tid, nth);
+  }
+}
+
+// Full compile-time transform; returns the buffer holding the result.
+template <typename T, int DIR, bool BATCH_FAST, int N, int NBATCH, int ES, int BS>
+__device__ __forceinline__ C2<T>* fft_block_fixed(C2<T>* a, C2<T>* b, const C2<T>* __restrict__ tw, int tid,
+                                                  int nth) {
+  C2<T>* src = a;
+  C2<T>* dst = b;
+  fft_fixed_from<T, DIR, BATCH_FAST, N, NBATCH, ES, BS, 0, 1>(src, dst, tw, tid, nth);
+  return src;
+}
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* sh) {
   // sh: at least 32 entries

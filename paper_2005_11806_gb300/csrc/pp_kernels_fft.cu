@@ -24,11 +24,11 @@ __global__ void __launch_bounds__(256) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
 
 template <typename T, int DIR>
 __global__ void __launch_bounds__(256) k_ffty(Geo g, FftDesc fy, const C2<T>* __restrict__ twy,
-                                              C2<T>* __restrict__ spec, int tx,
+                                              C2<T>* __restrict__ spec, int tx, long long ntiles,
                                               const DevStatus* __restrict__ st) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_ffty<T, DIR>(g, fy, twy, spec, tx, blockIdx.x, blockIdx.y, smem_raw);
+  stage_ffty_persistent<T, DIR>(g, fy, twy, spec, tx, ntiles, blockIdx.x, gridDim.x, smem_raw);
 }
 
 template <typename T>
@@ -86,17 +86,23 @@ template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
                         const DevStatus* st, cudaStream_t s) {
   const int tx = ffty_tile(g.ny, sizeof(C2<T>), kEpt);
-  const size_t smem = (size_t)2 * g.ny * tx * sizeof(C2<T>);
-  dim3 grid((g.nxh + tx - 1) / tx, g.nz);
+  const size_t smem = (size_t)3 * g.ny * tx * sizeof(C2<T>);
+  const long long ntiles = (long long)((g.nxh + tx - 1) / tx) * g.nz;
+  // persistent grid: as many blocks as fit on the GPU at this shared-memory size
+  int per_sm = (int)((200 * 1024) / smem);
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 8) per_sm = 8;
+  long long nblk = (long long)152 * per_sm;
+  if (nblk > ntiles) nblk = ntiles;
   cudaError_t e;
   if (inverse) {
     e = cudaFuncSetAttribute(k_ffty<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_ffty<T, 1><<<grid, kThreads, smem, s>>>(g, fy, twy, spec, tx, st);
+    k_ffty<T, 1><<<(int)nblk, kThreads, smem, s>>>(g, fy, twy, spec, tx, ntiles, st);
   } else {
     e = cudaFuncSetAttribute(k_ffty<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_ffty<T, -1><<<grid, kThreads, smem, s>>>(g, fy, twy, spec, tx, st);
+    k_ffty<T, -1><<<(int)nblk, kThreads, smem, s>>>(g, fy, twy, spec, tx, ntiles, st);
   }
   return cudaGetLastError();
 }

@@ -35,6 +35,40 @@ inline int ffty_tile(int ny, size_t csize, int ept) {
 
 __device__ __forceinline__ bool stopped(const DevStatus* st) { return st != nullptr && st->done; }
 
+// Transform dispatch: compile-time passes for the power-of-two lengths and
+// batch shapes the default block sizes produce, the generic mixed-radix
+// passes otherwise (same passes in the same order, so the same results).
+#define PP_TRY_FIXED(NN, NBB)                                                                       \
+  if (n == NN && nbatch == NBB) {                                                                   \
+    if (BATCH_FAST) return fft_block_fixed<T, DIR, true, NN, NBB, NBB, 1>(a, b, tw, tid, nth);      \
+    return fft_block_fixed<T, DIR, false, NN, NBB, 1, NN>(a, b, tw, tid, nth);                      \
+  }
+
+template <typename T, int DIR, bool BATCH_FAST>
+__device__ __forceinline__ C2<T>* fft_dispatch(C2<T>* a, C2<T>* b, const FftDesc& d, int nbatch, int es, int bs,
+                                               const C2<T>* __restrict__ tw, int tid, int nth) {
+  const int n = d.n;
+  const bool shape_ok = BATCH_FAST ? (es == nbatch && bs == 1) : (es == 1 && bs == n);
+  if (shape_ok) {
+    if (BATCH_FAST) {
+      PP_TRY_FIXED(512, 4)
+      PP_TRY_FIXED(256, 8)
+      PP_TRY_FIXED(128, 16)
+      PP_TRY_FIXED(128, 8)
+      PP_TRY_FIXED(64, 16)
+      PP_TRY_FIXED(64, 8)
+    } else {
+      PP_TRY_FIXED(512, 4)
+      PP_TRY_FIXED(256, 8)
+      PP_TRY_FIXED(128, 16)
+      PP_TRY_FIXED(64, 32)
+      PP_TRY_FIXED(32, 32)
+    }
+  }
+  return fft_block<T, DIR, BATCH_FAST>(a, b, d, nbatch, es, bs, tw, tid, nth);
+}
+#undef PP_TRY_FIXED
+
 // ---------------------------------------------------------------------------
 // Residual of the variable-coefficient equation and forward real x transform.
 //   mode 0: r = f (constant-coefficient solve)
@@ -139,7 +173,7 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
     }
   }
   __syncthreads();
-  const C2<T>* res = fft_block<T, -1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
+  const C2<T>* res = fft_dispatch<T, -1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
   for (int t = threadIdx.x; t < nseq * nxh; t += blockDim.x) {
     const int q = t / nxh, kx = t - q * nxh;
     const C2<T> Z = res[(size_t)q * nx + kx];
@@ -172,10 +206,78 @@ __device__ __forceinline__ void stage_ffty(const Geo& g, const FftDesc& fy, cons
     bufA[t] = v;
   }
   __syncthreads();
-  const C2<T>* res = fft_block<T, DIR, true>(bufA, bufB, fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
+  const C2<T>* res = fft_dispatch<T, DIR, true>(bufA, bufB, fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
   for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
     const int y = t / tx, x = t - y * tx;
     if (kx0 + x < nxh) spec[base + (size_t)y * nxh + kx0 + x] = res[t];
+  }
+}
+
+// Persistent y transform: each block walks the (kx tile, z plane) tiles
+// with stride gridDim.x over three rotating shared buffers: while the
+// current tile is transformed in two of them, the next tile is copied into
+// the third by cp.async.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+               :: "r"((uint32_t)__cvta_generic_to_shared(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void ffty_issue_tile(const Geo& g, const C2<T>* __restrict__ spec, int tx, int ntx,
+                                                long long tile, C2<T>* buf) {
+  const int ny = g.ny, nxh = g.nxh;
+  const int bz = (int)(tile / ntx), bx = (int)(tile - (long long)bz * ntx);
+  const int kx0 = bx * tx;
+  const size_t base = (size_t)bz * ny * nxh;
+  for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
+    const int y = t / tx, x = t - y * tx;
+    if (kx0 + x < nxh) {
+      if (sizeof(C2<T>) == 8) cp_async8(&buf[t], &spec[base + (size_t)y * nxh + kx0 + x]);
+      else {
+        cp_async8(&buf[t], &spec[base + (size_t)y * nxh + kx0 + x]);
+        cp_async8(reinterpret_cast<char*>(&buf[t]) + 8,
+                  reinterpret_cast<const char*>(&spec[base + (size_t)y * nxh + kx0 + x]) + 8);
+      }
+    } else {
+      buf[t].x = (T)0;
+      buf[t].y = (T)0;
+    }
+  }
+  cp_async_commit();
+}
+
+template <typename T, int DIR>
+__device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDesc& fy,
+                                                      const C2<T>* __restrict__ twy, C2<T>* spec, int tx,
+                                                      long long ntiles, long long first, long long stride,
+                                                      unsigned char* smem_raw) {
+  const int ny = g.ny, nxh = g.nxh;
+  const int ntx = (nxh + tx - 1) / tx;
+  const size_t tsz = (size_t)ny * tx;
+  C2<T>* X[3] = {reinterpret_cast<C2<T>*>(smem_raw), reinterpret_cast<C2<T>*>(smem_raw) + tsz,
+                 reinterpret_cast<C2<T>*>(smem_raw) + 2 * tsz};
+  int L = 0, Q = 1, F = 2;
+  if (first < ntiles) ffty_issue_tile<T>(g, spec, tx, ntx, first, X[L]);
+  for (long long tile = first; tile < ntiles; tile += stride) {
+    cp_async_wait_all();
+    __syncthreads();
+    const long long next = tile + stride;
+    if (next < ntiles) ffty_issue_tile<T>(g, spec, tx, ntx, next, X[F]);
+    const C2<T>* res = fft_dispatch<T, DIR, true>(X[L], X[Q], fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
+    const int bz = (int)(tile / ntx), bx = (int)(tile - (long long)bz * ntx);
+    const int kx0 = bx * tx;
+    const size_t base = (size_t)bz * ny * nxh;
+    for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
+      const int y = t / tx, x = t - y * tx;
+      if (kx0 + x < nxh) spec[base + (size_t)y * nxh + kx0 + x] = res[t];
+    }
+    __syncthreads();
+    // rotate: the prefetched buffer holds the next tile; the other two are free
+    const int nl = F;
+    F = L;
+    L = nl;
   }
 }
 
@@ -397,7 +499,7 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
     bufA[t] = Z;
   }
   __syncthreads();
-  const C2<T>* res = fft_block<T, 1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
+  const C2<T>* res = fft_dispatch<T, 1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
 #pragma unroll
   for (int u = 0; u < NP; ++u) {
     const int t = threadIdx.x + u * blockDim.x;
