@@ -20,7 +20,7 @@ grid, velocities on faces, scalar fields at cell centres):
   centre is the midpoint of its faces, ``dzf[k]`` is the width of cell k and
   ``dzc[k]`` the distance between the centres that share the z-face k.
 
-Readings of points the paper leaves open (each one listed in the design doc):
+Readings of points the paper leaves open:
 
 * the density on a face is the arithmetic mean of its two cells, so the
   centred form of ``u . grad(rho)`` used by Method III is
