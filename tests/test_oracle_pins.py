@@ -203,6 +203,35 @@ def test_constant_density_one_iteration():
     assert _rel(p, pc) < 1e-12
 
 
+@pytest.mark.parametrize("method", ["method1", "method2"])
+def test_methods_1_2_reach_direct_solution(method):
+    """Methods I and II converge to the same discrete solution (their fixed
+    point is Eq. lap_p too); Method I's modified correction then agrees with
+    Eq. corr to the tolerance."""
+    g, us, vs, ws, rho, S = _small_case(12, 10, 14, 1.5, 10.0)
+    dt = 1e-3
+    p, u, v, w, info = getattr(orc, method)(g, us, vs, ws, rho, S, dt, rtol=1e-13)
+    assert info["res_hist"][-1] <= 1e-13
+    pd, ud, vd, wd = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    assert _rel(p, pd) < 1e-10
+    for a, b in ((u, ud), (v, vd), (w, wd)):
+        assert _rel(a, b) < 1e-10
+
+
+def test_methods_share_first_pass_with_constant_density():
+    """rho = const: all three scalings coincide and one pass is exact."""
+    g = _grid(10, 8, 12, beta=1.5)
+    rng = np.random.default_rng(12)
+    us, vs = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    ws = rng.standard_normal((g.nz + 1, g.ny, g.nx)); ws[0] = ws[-1] = 0
+    rho = np.full(g.shape, 2.0)
+    S = np.zeros(g.shape)
+    out = [f(g, us, vs, ws, rho, S, 1e-3, rtol=1e-12) for f in (orc.method1, orc.method2, orc.method3)]
+    for p, u, v, w, info in out:
+        assert info["iters"] == 1
+        assert _rel(p, out[2][0]) < 1e-12
+
+
 # --- adjoint --------------------------------------------------------------
 
 def _loss(g, us, vs, ws, rho, S, dt, tgt):
