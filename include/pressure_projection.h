@@ -62,6 +62,21 @@ typedef enum {
                           products on the tensor cores with FP32 accumulation; nz <= 512 */
 } pp_precision;
 
+/* Recast of the variable-coefficient Eq. lap_p into a constant-coefficient
+ * iteration (Sec. 3.3.1).  All three are the same iteration
+ *     L p^{s+1} = L p^s + r~ (D u^s - S_c) / dt,  u^s = u* - dt beta G p^s,
+ * with a different scaling r~ of the residual:
+ *   PP_METHOD_III: r~ = rho_c, the cell density (Eq. new_poisson; the default);
+ *   PP_METHOD_I:   r~ = min rho over the grid (Eq. poisson_me1), and the
+ *                  velocity is the modified correction of Eq. poisson_me2,
+ *                  which uses the last and the second-to-last iterate;
+ *   PP_METHOD_II:  r~ = 2 rho_min rho_max / (rho_min + rho_max), the
+ *                  harmonic mean of the two phase densities taken as the
+ *                  extremes of rho (Eq. poisson_laizet), then Eq. corr.
+ * The stopping test is the relative norm of D u^s - S_c for all three, so
+ * their pass counts compare. */
+typedef enum { PP_METHOD_III = 0, PP_METHOD_I = 1, PP_METHOD_II = 2 } pp_method;
+
 typedef struct {
     int nx, ny, nz;        /* cells; nx, ny have prime factors in {2,3,5}; nx even */
     double lx, ly, lz;     /* domain lengths */
@@ -89,6 +104,13 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
 
 pp_status pressure_plan_destroy(pp_plan plan);
 
+/* Select the iteration of pressure_correct and pressure_solve_adjoint
+ * (pp_method; plans start with PP_METHOD_III).  Method I on an FP64 plan
+ * allocates one more FP64 cell field here (the last increment of p).
+ * Returns PP_ERR_INVALID_ARG for an unknown method, PP_ERR_OOM when that
+ * allocation fails. */
+pp_status pressure_plan_set_method(pp_plan plan, int method);
+
 /* Constant-coefficient solve by the eigenexpansion method (Sec. 3.3.1):
  * the zero-mean p with D G p = f - <f>_V.  f, p: cell fields. */
 pp_status pressure_solve(pp_plan plan, const double* f, double* p, pp_info* info);
@@ -98,7 +120,8 @@ pp_status pressure_solve(pp_plan plan, const double* f, double* p, pp_info* info
 pp_status pressure_mixture_density(pp_plan plan, const double* phi, double rho_g, double rho_l,
                                    double* rho);
 
-/* Method III projection (Algorithm 1, Sec. 3.3.1; Eqs. new_poisson, corr).
+/* Method III projection (Algorithm 1, Sec. 3.3.1; Eqs. new_poisson, corr),
+ * or Method I or II when pressure_plan_set_method selected one.
  * In: us, vs, ws (u*, faces; ws wall planes are taken as zero), rho (cell
  * density, > 0), S (divergence target, Eq. 34; may be NULL for zero), dt > 0,
  * p (cell field; used as the initial iterate when warm_start != 0).

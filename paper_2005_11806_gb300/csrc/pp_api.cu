@@ -15,12 +15,12 @@ using namespace pp;
 
 namespace {
 enum KId { K_RESID, K_CHECK, K_FFTY_F, K_TRI, K_FFTY_I, K_FFTX_I, K_INIT, K_PREP, K_MEANS, K_RHSB,
-           K_RMEAN, K_CORR, K_MIX, K_ADJ_RHS, K_ADJ_FIN, K_ADJ_GRHO, K_COUNT };
+           K_RMEAN, K_CORR, K_MIX, K_ADJ_RHS, K_ADJ_FIN, K_ADJ_GRHO, K_RHOT, K_COUNT };
 const char* const kNames[K_COUNT] = {
     "resid_fftx", "check", "ffty_fwd", "tridiag_z", "ffty_inv", "fftx_inv_update", "init_status",
     "prep_faces", "mean_S", "rhs_b", "remove_mean", "correct", "mixture_density", "adj_rhs",
-    "adj_finish", "adj_grho"};
-const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1};
+    "adj_finish", "adj_grho", "rho_tilde"};
+const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1, 2};
 struct Rec { int kid; cudaEvent_t a, b; };
 struct Prof {
   bool on = false;
@@ -52,6 +52,12 @@ struct pp_plan_s {
   double* d_b = nullptr;
   double* d_E = nullptr;      // mixed: FP64 residual carried between passes
   float* d_delta = nullptr;   // mixed: last pressure correction (FP32)
+  // iteration of Sec. 3.3.1 (pp_method); Methods I and II scale the residual
+  // by the device scalar d_rho_tilde, Method I keeps the last increment of p
+  // (d_delta on mixed plans, d_delta64 on FP64 plans) for Eq. poisson_me2
+  int method = PP_METHOD_III;
+  double* d_rho_tilde = nullptr;
+  double* d_delta64 = nullptr;
   double* d_red = nullptr;
   size_t red_len = 0;
   DevStatus* d_st = nullptr;
@@ -213,7 +219,7 @@ pp_status read_info(pp_plan_s* P, pp_info* info) {
 // One pass of Algorithm 1 after the residual: forward y, z solve, inverse y,
 // inverse x fused with p += delta.
 template <typename T>
-pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, float* delta = nullptr) {
+pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr) {
   const Geo& g = P->geo;
   C2<T>* spec = (C2<T>*)P->d_spec;
   const C2<T>* twx = (const C2<T>*)P->d_twx;
@@ -232,8 +238,19 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, float* delta = nullptr
   return PP_OK;
 }
 
+// Buffer that receives each pass's increment of p: the FP32 one of the
+// mixed residual update, or the FP64 one Method I keeps on FP64 plans.
+template <typename T> T* increment_buffer(pp_plan_s* P, bool upd);
+template <> float* increment_buffer<float>(pp_plan_s* P, bool upd) {
+  return (upd || P->method == PP_METHOD_I) ? P->d_delta : nullptr;
+}
+template <> double* increment_buffer<double>(pp_plan_s* P, bool) {
+  return P->method == PP_METHOD_I ? P->d_delta64 : nullptr;
+}
+
 // Method III loop on device fields: b = D u* - S_c has been formed; faces
 // hold beta of rho.  p is the iterate (zeroed by the caller unless warm).
+// With P->method = I or II the same loop runs with the constant scaling.
 template <typename T>
 pp_status method3_loop(pp_plan_s* P, const double* rho, double* p, int warm, double dt, double rtol,
                        int maxit) {
@@ -244,6 +261,7 @@ pp_status method3_loop(pp_plan_s* P, const double* rho, double* p, int warm, dou
   const int chunk = 4;
   const bool upd = std::is_same<T, float>::value && P->d_E != nullptr;
   const int kexact = upd ? kExactEvery : 1;
+  T* dl = increment_buffer<T>(P, upd);
   int polled = 0;
   bool pending[2] = {false, false};
   for (int it = 0; it <= maxit; ++it) {
@@ -253,7 +271,7 @@ pp_status method3_loop(pp_plan_s* P, const double* rho, double* p, int warm, dou
                                           P->d_st, P->stream, upd ? P->d_E : nullptr,
                                           upd ? P->d_delta : nullptr));
     PP_K(P, K_CHECK, launch_check(P->d_st, P->d_red, nblk, rtol, maxit, kexact, P->stream));
-    pp_status s = solve_pass<T>(P, p, 0, upd ? P->d_delta : nullptr);
+    pp_status s = solve_pass<T>(P, p, 0, dl);
     if (s != PP_OK) return s;
     if ((it + 1) % chunk == 0) {
       // Poll the device status without draining the queue: read the slot
@@ -281,13 +299,25 @@ pp_status projection(pp_plan_s* P, const double* us, const double* vs, const dou
   const Geo& g = P->geo;
   PP_K(P, K_INIT, launch_init_status(P->d_st, P->stream));
   PP_K(P, K_PREP, launch_prep_faces(g, rho, P->faces, P->stream));
+  if (P->method != PP_METHOD_III) {
+    PP_K(P, K_RHOT, launch_rho_tilde(g, rho, P->method, P->d_red, P->d_rho_tilde, P->stream));
+    // Method I's correction reads the last increment: zero it in case the
+    // loop stops before its first pass
+    T* dl = increment_buffer<T>(P, false);
+    if (P->method == PP_METHOD_I) PP_CK(cudaMemsetAsync(dl, 0, ncell(P) * sizeof(T), P->stream));
+  }
   if (S) PP_K(P, K_MEANS, launch_weighted_mean(g, S, P->d_red, &P->d_st->mean_S, P->stream));
   PP_K(P, K_RHSB, launch_rhs_b(g, us, vs, ws, S, P->d_b, P->d_red, P->d_st, 1.0 / dt, P->stream));
   if (!warm) PP_CK(cudaMemsetAsync(p, 0, ncell(P) * sizeof(double), P->stream));
   pp_status s = method3_loop<T>(P, rho, p, warm, dt, rtol, maxit);
   if (s != PP_OK) return s;
   PP_K(P, K_RMEAN, launch_remove_mean(g, p, P->d_red, P->d_st, P->stream));
-  if (u) PP_K(P, K_CORR, launch_correct(g, P->faces, us, vs, ws, p, dt, u, v, w, P->stream));
+  if (u && P->method == PP_METHOD_I) {
+    PP_K(P, K_CORR, launch_correct_method1<T>(g, P->faces, us, vs, ws, p, increment_buffer<T>(P, false), dt,
+                                              u, v, w, P->stream));
+  } else if (u) {
+    PP_K(P, K_CORR, launch_correct(g, P->faces, us, vs, ws, p, dt, u, v, w, P->stream));
+  }
   return PP_OK;
 }
 
@@ -300,7 +330,7 @@ void free_plan(pp_plan_s* P) {
   if (!P) return;
   double* dptrs[] = {P->d_inv_dzf, P->d_inv_dzc, P->d_dzf, P->d_za, P->d_zc, P->d_lamx, P->d_lamy,
                      P->d_invd, P->d_mtab, P->d_b, P->d_red, P->faces.cx, P->faces.cy, P->faces.cz,
-                     P->faces.diag};
+                     P->faces.diag, P->d_rho_tilde, P->d_delta64};
   if (P->faces.rhof) cudaFree(P->faces.rhof);
   float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta};
   for (float* f : fptrs) if (f) cudaFree(f);
@@ -515,6 +545,22 @@ pp_status pressure_plan_destroy(pp_plan P) {
   if (!P) return PP_ERR_INVALID_ARG;
   cudaStreamSynchronize(P->stream);
   free_plan(P);
+  return PP_OK;
+}
+
+pp_status pressure_plan_set_method(pp_plan P, int method) {
+  if (check_plan(P) != PP_OK) return PP_ERR_INVALID_ARG;
+  if (method != PP_METHOD_III && method != PP_METHOD_I && method != PP_METHOD_II) return PP_ERR_INVALID_ARG;
+  if (method != PP_METHOD_III && P->d_rho_tilde == nullptr) {
+    pp_status s = dalloc(&P->d_rho_tilde, sizeof(double));
+    if (s != PP_OK) return s;
+  }
+  if (method == PP_METHOD_I && P->prec == PP_FP64 && P->d_delta64 == nullptr) {
+    pp_status s = dalloc(&P->d_delta64, ncell(P) * sizeof(double));
+    if (s != PP_OK) return s;
+  }
+  P->method = method;
+  P->faces.rho_tilde = (method == PP_METHOD_III) ? nullptr : P->d_rho_tilde;
   return PP_OK;
 }
 

@@ -62,6 +62,8 @@ struct Geo {
 //   diag = sum of the six coefficients of the cell, rhof = rho_c in FP32.
 //   cxf, cyf, czf, diagf: FP32 copies for the residual update of the mixed
 //   path (null on FP64 plans).
+//   rho_tilde: device scalar that replaces rho_c as the scaling of the
+//   residual (Methods I and II of Sec. 3.3.1); null selects Method III.
 struct Faces {
   double* cx;    // [nz][ny][nx]
   double* cy;    // [nz][ny][nx]
@@ -72,6 +74,7 @@ struct Faces {
   float* cyf;
   float* czf;
   float* diagf;
+  const double* rho_tilde;
 };
 
 // Exact FP32 -> FP64 widening done on the integer pipe (the FP64 pipe of this
@@ -124,11 +127,11 @@ template <typename T>
 cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,
                            const DevStatus* st, cudaStream_t s, const double* mtab = nullptr);
 // Inverse x-transform; p = scale * z (p_zero) or p += scale * z; when delta
-// is not null it also receives scale * z in FP32.
+// is not null it also receives scale * z in the transform's precision T.
 template <typename T>
 cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
                             double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s,
-                            float* delta = nullptr);
+                            T* delta = nullptr);
 
 // Inverse Thomas pivots; when mtab is not null also the multipliers
 // m_k = a_k / d_{k-1} (m_0 = 0).
@@ -138,6 +141,20 @@ cudaError_t launch_setup_pivots(const Geo& g, const double* lamx, const double* 
 cudaError_t launch_mixture(const double* phi, double rho_g, double rho_l, double* rho, size_t n,
                            cudaStream_t s);
 cudaError_t launch_prep_faces(const Geo& g, const double* rho, Faces fc, cudaStream_t s);
+// Constant density of Methods I and II (Sec. 3.3.1) into *out: the minimum
+// of rho (method 1) or the harmonic mean of its minimum and maximum, i.e. of
+// the two phase densities (method 2).  red holds at least reduce_blocks()
+// pairs of partial sums.
+cudaError_t launch_rho_tilde(const Geo& g, const double* rho, int method, double* red, double* out,
+                             cudaStream_t s);
+// Modified correction of Method I (Eq. poisson_me2) from the last iterate p
+// and its last increment delta = p - p^q:
+//   u = u* - dt [G p / rho0 + (beta - 1/rho0) G p^q]
+//     = u* - dt beta G p + dt (beta - 1/rho0) G delta.
+template <typename T>
+cudaError_t launch_correct_method1(const Geo& g, const Faces& fc, const double* us, const double* vs,
+                                   const double* ws, const double* p, const T* delta, double dt,
+                                   double* u, double* v, double* w, cudaStream_t s);
 // Sum of dzf * f over cells (block partials) -> st->mean_S = sum / (lz nx ny).
 cudaError_t launch_weighted_mean(const Geo& g, const double* f, double* red, double* out_mean,
                                  cudaStream_t s);

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>
                                                   const C2<T>* __restrict__ spec, double scale,
                                                   double* __restrict__ p, int p_zero, int rpb,
                                                   const DevStatus* __restrict__ st,
-                                                  float* __restrict__ delta) {
+                                                  T* __restrict__ delta) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   stage_fftx_inv<T>(g, fx, twx, spec, scale, p, p_zero, rpb, blockIdx.x, delta, smem_raw);
@@ -124,7 +124,7 @@ cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double
 template <typename T>
 cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
                             double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s,
-                            float* delta) {
+                            T* delta) {
   const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);
@@ -146,7 +146,7 @@ cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, c
                                          const DevStatus*, cudaStream_t, const double*);             \
   template cudaError_t launch_fftx_inv<T>(const Geo&, const FftDesc&, const C2<T>*, const C2<T>*,    \
                                           double, double*, int, const DevStatus*, cudaStream_t,      \
-                                          float*);
+                                          T*);
 PP_INST(double)
 PP_INST(float)
 #undef PP_INST

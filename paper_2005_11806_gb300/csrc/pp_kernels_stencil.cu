@@ -135,6 +135,67 @@ __global__ void k_setup_pivots(Geo g, const double* __restrict__ lamx, const dou
   }
 }
 
+// ---- Methods I and II (Sec. 3.3.1) -------------------------------------------
+constexpr int kExtBlocks = kRedBlocks / 2;  // (min, max) pairs fit the partial-sum buffer
+
+// Block partial minimum and maximum of rho into red[2 b], red[2 b + 1].
+__global__ void k_rho_extrema(size_t n, const double* __restrict__ rho, double* __restrict__ red) {
+  __shared__ double smin[kThreads / 32], smax[kThreads / 32];
+  double lo = INFINITY, hi = -INFINITY;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const double r = rho[c];
+    lo = fmin(lo, r);
+    hi = fmax(hi, r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { smin[wid] = lo; smax[wid] = hi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { lo = fmin(lo, smin[k]); hi = fmax(hi, smax[k]); }
+    red[2 * (size_t)blockIdx.x] = lo;
+    red[2 * (size_t)blockIdx.x + 1] = hi;
+  }
+}
+
+// rho0 = min rho (Method I, Eq. poisson_me1); the harmonic mean
+// 2 rho_min rho_max / (rho_min + rho_max) of the two phase densities
+// (Method II, Eq. poisson_laizet).  One thread.
+__global__ void k_rho_tilde(const double* __restrict__ red, int nblk, int method, double* __restrict__ out) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int b = 0; b < nblk; ++b) {
+    lo = fmin(lo, red[2 * (size_t)b]);
+    hi = fmax(hi, red[2 * (size_t)b + 1]);
+  }
+  *out = (method == 1) ? lo : 2.0 * lo * hi / (lo + hi);
+}
+
+// Eq. poisson_me2 with p^q = p - delta:
+//   u = u* - dt beta G p + dt (beta - 1/rho0) G delta  on every face.
+// beta is recovered from the row-scaled coefficients: cx = dzf_k beta / dx^2,
+// cy = dzf_k beta / dy^2, cz = beta / dzc.
+template <typename T>
+__global__ void k_correct_method1(Geo g, Faces fc, const double* __restrict__ us,
+                                  const double* __restrict__ vs, const double* __restrict__ ws,
+                                  const double* __restrict__ p, const T* __restrict__ delta, double dt,
+                                  double* __restrict__ u, double* __restrict__ v, double* __restrict__ w) {
+  const size_t plane = (size_t)g.nx * g.ny, n = plane * g.nz;
+  const double ir0 = 1.0 / *fc.rho_tilde;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    cell_correct(g, fc, us, vs, ws, p, dt, u, v, w, c);
+    const CellIdx x = cell_index(g, c);
+    const double idzf = g.inv_dzf[x.k];
+    const double dc = (double)delta[c];
+    const double bx = fc.cx[c] * idzf / g.inv_dx2, by = fc.cy[c] * idzf / g.inv_dy2;
+    u[c] += dt * (bx - ir0) * (dc - (double)delta[x.cim]) / g.dx;
+    v[c] += dt * (by - ir0) * (dc - (double)delta[x.cjm]) / g.dy;
+    if (x.k > 0) w[c] += dt * (fc.cz[c] - ir0 * g.inv_dzc[x.k]) * (dc - (double)delta[c - plane]);
+  }
+}
+
 // ---- adjoint ---------------------------------------------------------------
 // y = -dt * beta * W_f^{-1} g  (W_f = dzf of the layer on x/y faces, dzc on
 // interior z faces; wall z-faces zero).
@@ -254,6 +315,29 @@ cudaError_t launch_correct(const Geo& g, const Faces& fc, const double* us, cons
   k_correct<<<grid_for((size_t)g.nx * g.ny * g.nz), kThreads, 0, s>>>(g, fc, us, vs, ws, p, dt, u, v, w);
   return cudaGetLastError();
 }
+
+cudaError_t launch_rho_tilde(const Geo& g, const double* rho, int method, double* red, double* out,
+                             cudaStream_t s) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  k_rho_extrema<<<kExtBlocks, kThreads, 0, s>>>(n, rho, red);
+  k_rho_tilde<<<1, 1, 0, s>>>(red, kExtBlocks, method, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_correct_method1(const Geo& g, const Faces& fc, const double* us, const double* vs,
+                                   const double* ws, const double* p, const T* delta, double dt,
+                                   double* u, double* v, double* w, cudaStream_t s) {
+  k_correct_method1<T><<<grid_for((size_t)g.nx * g.ny * g.nz), kThreads, 0, s>>>(g, fc, us, vs, ws, p, delta,
+                                                                               dt, u, v, w);
+  return cudaGetLastError();
+}
+template cudaError_t launch_correct_method1<double>(const Geo&, const Faces&, const double*, const double*,
+                                                    const double*, const double*, const double*, double,
+                                                    double*, double*, double*, cudaStream_t);
+template cudaError_t launch_correct_method1<float>(const Geo&, const Faces&, const double*, const double*,
+                                                   const double*, const double*, const float*, double,
+                                                   double*, double*, double*, cudaStream_t);
 
 cudaError_t launch_remove_mean(const Geo& g, double* p, double* red, DevStatus* st, cudaStream_t s) {
   cudaError_t e = launch_weighted_mean(g, p, red, &st->pmean, s);

@@ -99,6 +99,10 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
   const long row0 = (long)blk * rpb;
   const size_t plane = (size_t)ny * nx;
   T s2 = (T)0, s1 = (T)0;
+  // constant scaling of Methods I and II (one device scalar for all cells)
+  const bool const_scale = fc.rho_tilde != nullptr;
+  const double rt = (const_scale && mode != 0) ? *fc.rho_tilde : 0.0;
+  const float rt_f = (float)rt;
   // thread -> (row offset, first column); index math is done once per row
   const int tpr = nx < (int)blockDim.x ? nx : (int)blockDim.x;
   const int rows_par = blockDim.x / tpr;
@@ -151,12 +155,12 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
             const float e = narrow_f64(ep) * idzf_f;
             s2 = fmaf(e, e, (float)s2);
             s1 += fabsf(e);
-            r = (T)(scale_rho ? fc.rhof[c] * e : e);
+            r = (T)(scale_rho ? (const_scale ? rt_f : fc.rhof[c]) * e : e);
           } else {
             const double e = ep * idzf;
             s2 = (T)fma(e, e, (double)s2);
             s1 += (T)fabs(e);
-            r = (T)(scale_rho ? rho[c] * e : e);
+            r = (T)(scale_rho ? (const_scale ? rt : rho[c]) * e : e);
           }
         }
       }
@@ -456,7 +460,7 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
                                                const C2<T>* __restrict__ twx,
                                                const C2<T>* __restrict__ spec, double scale,
                                                double* __restrict__ p, int p_zero, int rpb, int blk,
-                                               float* __restrict__ delta, unsigned char* smem_raw) {
+                                               T* __restrict__ delta, unsigned char* smem_raw) {
   const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
   const int nseq = rpb >> 1;
   const float scale_f = (float)scale;
@@ -511,7 +515,8 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
       const T zv = (q & 1) ? z.y : z.x;
       const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
       p[(size_t)row * nx + i] = fma(scale, zd, pv[u]);
-      if (delta != nullptr) delta[(size_t)row * nx + i] = scale_f * (float)zv;
+      if (delta != nullptr)
+        delta[(size_t)row * nx + i] = (sizeof(T) == sizeof(float)) ? (T)(scale_f * (float)zv) : (T)(scale * zd);
     }
   }
   for (int t = threadIdx.x + NP * blockDim.x; t < nout; t += blockDim.x) {  // beyond the prefetch

@@ -21,6 +21,8 @@ PP_OK, PP_ERR_INVALID_ARG, PP_ERR_UNSUPPORTED, PP_ERR_NOT_CONVERGED = 0, 1, 2, 3
 PP_ERR_NUMERIC, PP_ERR_CUDA, PP_ERR_OOM, PP_ERR_TOO_LARGE = 4, 5, 6, 7
 PP_BC_PERIODIC, PP_BC_WALL = 0, 1
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_fp32": 1, "mixed_tc": 2}
+# iterations of Sec. 3.3.1: Method III (Eq. new_poisson), I (Eq. poisson_me1), II (Eq. poisson_laizet)
+METHODS = {"III": 0, "I": 1, "II": 2}
 
 
 class pp_grid(ctypes.Structure):
@@ -51,7 +53,7 @@ class PressureError(RuntimeError):
 
 _lib = None
 
-EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_solve",
+EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_plan_set_method", "pressure_solve",
            "pressure_mixture_density", "pressure_correct", "pressure_solve_adjoint",
            "pressure_last_info", "pressure_profile_enable", "pressure_profile_read",
            "pressure_solve_noalloc", "pressure_batch_create", "pressure_batch_layout",
@@ -72,6 +74,7 @@ def lib():
     pinfo = ctypes.POINTER(pp_info)
     L.pressure_plan_create.argtypes = [ctypes.POINTER(pp_grid), i, vp, ctypes.POINTER(vp)]
     L.pressure_plan_destroy.argtypes = [vp]
+    L.pressure_plan_set_method.argtypes = [vp, i]
     L.pressure_solve.argtypes = [vp, vp, vp, pinfo]
     L.pressure_mixture_density.argtypes = [vp, vp, d, d, vp]
     L.pressure_correct.argtypes = [vp, vp, vp, vp, vp, vp, d, vp, i, vp, vp, vp, d, i, pinfo]
@@ -178,6 +181,12 @@ def pressure_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, zfaces=None, stream=Non
 
 def pressure_plan_destroy(plan):
     _check(lib().pressure_plan_destroy(plan), "pressure_plan_destroy")
+
+
+def pressure_plan_set_method(plan, method):
+    """method: "III" (default), "I" or "II" (or the pp_method integer)."""
+    code = METHODS[method] if isinstance(method, str) else int(method)
+    _check(lib().pressure_plan_set_method(plan, code), "pressure_plan_set_method")
 
 
 def pressure_solve(plan, f, p):
@@ -293,10 +302,13 @@ class Batch:
 class Plan:
     """Owning wrapper of a plan handle."""
 
-    def __init__(self, nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None):
+    def __init__(self, nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None,
+                 method="III"):
         self.shape = (int(nz), int(ny), int(nx))
         self.wshape = (int(nz) + 1, int(ny), int(nx))
         self.handle = pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces, precision, stream)
+        if method != "III":
+            pressure_plan_set_method(self.handle, method)
 
     def close(self):
         if getattr(self, "handle", None):
