@@ -38,7 +38,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_tc"])
+    ap.add_argument("--method", default="III", choices=["III", "II", "I"],
+                    help="iteration of Sec. 3.3.1 (Method III is the measured one; I and II compare)")
     ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--nz", type=int, default=0, help="cells along z (default: n)")
     ap.add_argument("--bubbles", type=int, default=200)
     ap.add_argument("--ratio", type=float, default=1000.0)
     ap.add_argument("--rtol", type=float, default=1e-10)
@@ -56,11 +59,11 @@ def parse():
 def workload(args):
     from paper_2005_11806_gb300 import workloads as wl
     return wl.bubbles_case(n=args.n, nbubbles=args.bubbles, seed=1003, beta=1.5,
-                           rho_g=1.0, rho_l=args.ratio)
+                           rho_g=1.0, rho_l=args.ratio, nz=args.nz or None)
 
 
 def config_dict(args, w):
-    return {"workload": f"{w.name}; Method III to rel. residual <= {args.rtol:g}",
+    return {"workload": f"{w.name}; Method {args.method} to rel. residual <= {args.rtol:g}",
             "grid": [w.nx, w.ny, w.nz], "domain": "[0,2pi]^3, tanh(1.5) z",
             "bubbles": args.bubbles, "density_ratio": args.ratio, "rtol": args.rtol,
             "precision": args.precision, "l2": "inputs larger than L2 (1.07 GB per field)",
@@ -157,7 +160,7 @@ def run_ours(args, rank, world, local_rank):
     lz = float(w.zf[-1] - w.zf[0])
 
     def make_plan(prec):
-        return pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, lz, zfaces=w.zf, precision=prec)
+        return pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, lz, zfaces=w.zf, precision=prec, method=args.method)
 
     def step(plan):
         pp.pressure_mixture_density(plan.handle, phi, w.rho_g, w.rho_l, rho)

@@ -50,12 +50,17 @@ struct pp_plan_s {
   void* d_spec = nullptr;
   double2* d_ybuf = nullptr;
   double* d_b = nullptr;
-  double* d_E = nullptr;      // mixed: FP64 residual carried between passes
+  float* d_E = nullptr;       // mixed: residual carried between passes (FP32)
   float* d_delta = nullptr;   // mixed: last pressure correction (FP32)
   // iteration of Sec. 3.3.1 (pp_method); Methods I and II scale the residual
   // by the device scalar d_rho_tilde, Method I keeps the last increment of p
   // (d_delta on mixed plans, d_delta64 on FP64 plans) for Eq. poisson_me2
   int method = PP_METHOD_III;
+  // mixed plans: FP32 Thomas tables of the well-conditioned z columns
+  float *d_mtab_f = nullptr, *d_invd_f = nullptr, *d_zc_f = nullptr;
+  int* d_low = nullptr;
+  TriF32 tri32{};
+  bool use_tri32 = false;
   double* d_rho_tilde = nullptr;
   double* d_delta64 = nullptr;
   double* d_red = nullptr;
@@ -231,7 +236,8 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr) {
   if (P->z_tc) {
     PP_K(P, K_TRI, launch_zgemm(g, P->ze, reinterpret_cast<float2*>(spec), P->d_st, P->stream));
   } else {
-    PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab));
+    PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab,
+                                     P->use_tri32 ? &P->tri32 : nullptr));
   }
   PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream));
   PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream, delta));
@@ -332,7 +338,9 @@ void free_plan(pp_plan_s* P) {
                      P->d_invd, P->d_mtab, P->d_b, P->d_red, P->faces.cx, P->faces.cy, P->faces.cz,
                      P->faces.diag, P->d_rho_tilde, P->d_delta64};
   if (P->faces.rhof) cudaFree(P->faces.rhof);
-  float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta};
+  if (P->d_low) cudaFree(P->d_low);
+  float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta,
+                    P->d_mtab_f, P->d_invd_f, P->d_zc_f};
   for (float* f : fptrs) if (f) cudaFree(f);
   if (P->d_E) cudaFree(P->d_E);
   if (P->d_mu) cudaFree(P->d_mu);
@@ -465,12 +473,11 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   if ((st = dalloc(&P->d_invd, nsp * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->d_mtab, nsp * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->d_spec, nsp * csz)) != PP_OK ||
-      (prec != PP_FP64 && (st = dalloc(&P->d_E, nc * sizeof(double))) != PP_OK) ||
+      (prec != PP_FP64 && (st = dalloc(&P->d_E, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->d_delta, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->faces.cxf, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->faces.cyf, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->faces.czf, nw * sizeof(float))) != PP_OK) ||
-      (prec != PP_FP64 && (st = dalloc(&P->faces.diagf, nc * sizeof(float))) != PP_OK) ||
       (st = dalloc(&P->d_b, nc * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->d_red, P->red_len * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->faces.cx, nc * sizeof(double))) != PP_OK ||
@@ -536,6 +543,35 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       cudaStreamSynchronize(P->stream) != cudaSuccess) {
     free_plan(P);
     return PP_ERR_CUDA;
+  }
+  if (prec == PP_MIXED_FP32) {
+    double dmax = 0.0;
+    for (int k = 0; k < nz; ++k) dmax = std::max(dmax, za[k] + zc[k]);
+    std::vector<float> zcf(nz);
+    for (int k = 0; k < nz; ++k) zcf[k] = (float)zc[k];
+    const double thr = 2.0 * dmax / 512.0;
+    const std::vector<int> low = tri_low_columns(lamx, lamy, thr);
+    if ((st = dalloc(&P->d_low, low.size() * sizeof(int))) != PP_OK ||
+        cudaMemcpy(P->d_low, low.data(), low.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (st = dalloc(&P->d_mtab_f, nsp * sizeof(float))) != PP_OK ||
+        (st = dalloc(&P->d_invd_f, nsp * sizeof(float))) != PP_OK ||
+        (st = dalloc(&P->d_zc_f, (size_t)nz * sizeof(float))) != PP_OK ||
+        cudaMemcpy(P->d_zc_f, zcf.data(), nz * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        launch_narrow(P->d_mtab, P->d_mtab_f, nsp, P->stream) != cudaSuccess ||
+        launch_narrow(P->d_invd, P->d_invd_f, nsp, P->stream) != cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess) {
+      free_plan(P);
+      return st != PP_OK ? st : PP_ERR_CUDA;
+    }
+    P->tri32.mtab = P->d_mtab_f;
+    P->tri32.invd = P->d_invd_f;
+    P->tri32.zc = P->d_zc_f;
+    P->tri32.lamx = P->d_lamx;
+    P->tri32.lamy = P->d_lamy;
+    P->tri32.thr = thr;
+    P->tri32.low = P->d_low;
+    P->tri32.nlow = (int)low.size();
+    P->use_tri32 = true;
   }
   *out = P;
   return PP_OK;

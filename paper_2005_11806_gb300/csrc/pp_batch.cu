@@ -31,8 +31,9 @@ struct GridDev {
   const float2* twy;
   const double* invd;
   const double* mtab;
+  TriF32 tri;  // FP32 tables of the well-conditioned z columns
   float2* spec;
-  double* E;
+  float* E;
   float* delta;
   double* b;
   double* red;
@@ -169,12 +170,11 @@ __global__ void __launch_bounds__(256) kb_ffty(GridDev* G, const int2* __restric
   stage_ffty<float, DIR>(d.g, d.fy, d.twy, d.spec, d.tx, bx, bz, smem_raw);
 }
 
-__global__ void __launch_bounds__(kTriThreads, 16) kb_tridiag(GridDev* G, const int2* __restrict__ work) {
+__global__ void __launch_bounds__(kTriThreads, 8) kb_tridiag(GridDev* G, const int2* __restrict__ work) {
   const int2 w = work[blockIdx.x];
   const GridDev& d = G[w.x];
   if (d.st->done) return;
-  stage_tridiag_split<float>(d.g, d.mtab, d.invd, reinterpret_cast<float*>(d.spec),
-                             (size_t)w.y * kTriThreads + threadIdx.x);
+  stage_tridiag_mixed(d.g, d.mtab, d.invd, d.tri, d.spec, w.y);
 }
 
 __global__ void __launch_bounds__(256) kb_fftx_inv(GridDev* G, const int2* __restrict__ work) {
@@ -239,6 +239,7 @@ struct pp_batch_s {
   std::vector<long long> cell_off, wface_off;
   long long ncell_tot = 0, nwface_tot = 0;
   unsigned char* pool = nullptr;   // every per-grid buffer and table
+  int* d_low = nullptr;            // ill-conditioned z columns of every grid
   GridDev* d_dev = nullptr;
   GridDev* h_dev = nullptr;        // pinned mirror
   BatchCtl* d_ctl = nullptr;
@@ -260,6 +261,7 @@ void free_batch(pp_batch_s* B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
   if (B->pool) cudaFree(B->pool);
+  if (B->d_low) cudaFree(B->d_low);
   if (B->d_dev) cudaFree(B->d_dev);
   if (B->d_ctl) cudaFree(B->d_ctl);
   int2* ws[] = {B->w_cells, B->w_x, B->w_y, B->w_z};
@@ -458,8 +460,8 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
 
   // pool layout: per grid, every buffer and table
   struct Off {
-    size_t spec, E, delta, b, red, st, cx, cy, cz, diag, rhof, cxf, cyf, czf, diagf, invd, mtab,
-        twx, twy, idzf, idzc, dzf, za, zc, idzff, lamx, lamy;
+    size_t spec, E, delta, b, red, st, cx, cy, cz, diag, rhof, cxf, cyf, czf, invd, mtab,
+        twx, twy, idzf, idzc, dzf, za, zc, idzff, lamx, lamy, mtabf, invdf, zcf;
   };
   std::vector<Off> off(ngrids);
   Carve cv;
@@ -476,20 +478,24 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     B->ncell_tot += (long long)nc;
     B->nwface_tot += (long long)nw;
     Off& o = off[i];
+    // E is FP32; it gets 8 bytes a cell to double as the stand-in p of the tuning runs
     o.spec = cv.take(nsp * sizeof(float2)); o.E = cv.take(nc * 8); o.delta = cv.take(nc * 4);
     o.b = cv.take(nc * 8); o.red = cv.take(nred * 8); o.st = cv.take(sizeof(DevStatus));
     o.cx = cv.take(nc * 8); o.cy = cv.take(nc * 8); o.cz = cv.take(nw * 8); o.diag = cv.take(nc * 8);
     o.rhof = cv.take(nc * 4); o.cxf = cv.take(nc * 4); o.cyf = cv.take(nc * 4); o.czf = cv.take(nw * 4);
-    o.diagf = cv.take(nc * 4); o.invd = cv.take(nsp * 8); o.mtab = cv.take(nsp * 8);
+    o.invd = cv.take(nsp * 8); o.mtab = cv.take(nsp * 8);
     o.twx = cv.take((size_t)G.nx * sizeof(float2)); o.twy = cv.take((size_t)G.ny * sizeof(float2));
     o.idzf = cv.take((size_t)G.nz * 8); o.idzc = cv.take((size_t)(G.nz + 1) * 8); o.dzf = cv.take((size_t)G.nz * 8);
     o.za = cv.take((size_t)G.nz * 8); o.zc = cv.take((size_t)G.nz * 8); o.idzff = cv.take((size_t)G.nz * 4);
     o.lamx = cv.take((size_t)(G.nx / 2 + 1) * 8); o.lamy = cv.take((size_t)G.ny * 8);
+    o.mtabf = cv.take(nsp * 4); o.invdf = cv.take(nsp * 4); o.zcf = cv.take((size_t)G.nz * 4);
   }
   if (cudaMalloc((void**)&B->pool, cv.off) != cudaSuccess) { free_batch(B); return PP_ERR_OOM; }
   if (cudaMemset(B->pool, 0, cv.off) != cudaSuccess) { free_batch(B); return PP_ERR_CUDA; }
 
   std::vector<int2> wc, wz;
+  std::vector<int> low_all;     // ill-conditioned z columns of every grid, concatenated
+  std::vector<size_t> low_off;
   const double pi = 3.14159265358979323846264338327950288;
   const double two_pi = 2.0 * pi;
   for (int i = 0; i < ngrids; ++i) {
@@ -503,7 +509,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     for (int k = 0; k < nz; ++k)
       if (!(zf[k + 1] > zf[k])) { free_batch(B); return PP_ERR_INVALID_ARG; }
     std::vector<double> dzf(nz), idzf(nz), zcen(nz), idzc(nz + 1, 0.0), za(nz, 0.0), zc(nz, 0.0);
-    std::vector<float> idzff(nz);
+    std::vector<float> idzff(nz), zcf(nz);
     for (int k = 0; k < nz; ++k) {
       dzf[k] = zf[k + 1] - zf[k];
       idzf[k] = 1.0 / dzf[k];
@@ -513,6 +519,8 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     for (int k = 1; k < nz; ++k) idzc[k] = 1.0 / (zcen[k] - zcen[k - 1]);
     for (int k = 1; k < nz; ++k) za[k] = idzc[k] * idzf[k];
     for (int k = 0; k < nz - 1; ++k) zc[k] = idzc[k + 1] * idzf[k];
+    double dmax = 0.0;
+    for (int k = 0; k < nz; ++k) { zcf[k] = (float)zc[k]; dmax = std::max(dmax, za[k] + zc[k]); }
     const double dx = G.lx / nx, dy = G.ly / ny;
     std::vector<double> lamx(nxh), lamy(ny);
     for (int k = 0; k < nxh; ++k) { const double sn = std::sin(pi * k / nx); lamx[k] = -4.0 / (dx * dx) * sn * sn; }
@@ -525,7 +533,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
         {o.dzf, dzf.data(), dzf.size() * 8}, {o.idzf, idzf.data(), idzf.size() * 8},
         {o.idzc, idzc.data(), idzc.size() * 8}, {o.za, za.data(), za.size() * 8}, {o.zc, zc.data(), zc.size() * 8},
         {o.idzff, idzff.data(), idzff.size() * 4}, {o.lamx, lamx.data(), lamx.size() * 8},
-        {o.lamy, lamy.data(), lamy.size() * 8}};
+        {o.lamy, lamy.data(), lamy.size() * 8}, {o.zcf, zcf.data(), zcf.size() * 4}};
     for (const Up& u : ups)
       if (cudaMemcpy(P + u.off, u.src, u.bytes, cudaMemcpyHostToDevice) != cudaSuccess) { free_batch(B); return PP_ERR_CUDA; }
     Geo& g = d.g;
@@ -536,25 +544,47 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     g.inv_dzf_f = (const float*)(P + o.idzff); g.lz = zf[nz] - zf[0];
     d.fc.cx = (double*)(P + o.cx); d.fc.cy = (double*)(P + o.cy); d.fc.cz = (double*)(P + o.cz);
     d.fc.diag = (double*)(P + o.diag); d.fc.rhof = (float*)(P + o.rhof); d.fc.cxf = (float*)(P + o.cxf);
-    d.fc.cyf = (float*)(P + o.cyf); d.fc.czf = (float*)(P + o.czf); d.fc.diagf = (float*)(P + o.diagf);
+    d.fc.cyf = (float*)(P + o.cyf); d.fc.czf = (float*)(P + o.czf);
     factor(nx, &d.fx);
     factor(ny, &d.fy);
     d.twx = (const float2*)(P + o.twx); d.twy = (const float2*)(P + o.twy);
     d.invd = (const double*)(P + o.invd); d.mtab = (const double*)(P + o.mtab);
-    d.spec = (float2*)(P + o.spec); d.E = (double*)(P + o.E); d.delta = (float*)(P + o.delta);
+    d.spec = (float2*)(P + o.spec); d.E = (float*)(P + o.E); d.delta = (float*)(P + o.delta);
     d.b = (double*)(P + o.b); d.red = (double*)(P + o.red); d.st = (DevStatus*)(P + o.st);
     d.ncell = (long long)nx * ny * nz;
     d.nchunk = (int)((d.ncell + kChunk - 1) / kChunk);
     d.scale = 1.0 / ((double)nx * ny);
     for (int c = 0; c < d.nchunk; ++c) wc.push_back(make_int2(i, c));
-    const size_t ncol2 = 2 * (size_t)nxh * ny;
-    for (size_t b = 0; b < (ncol2 + kTriThreads - 1) / kTriThreads; ++b) wz.push_back(make_int2(i, (int)b));
+    const size_t ncol = (size_t)nxh * ny;
+    const std::vector<int> lowi = tri_low_columns(lamx, lamy, 2.0 * dmax / 512.0);
+    low_off.push_back(low_all.size());
+    low_all.insert(low_all.end(), lowi.begin(), lowi.end());
+    d.tri.nlow = (int)lowi.size();
+    for (int b = 0; b < tri_mixed_blocks(ncol, d.tri.nlow); ++b) wz.push_back(make_int2(i, b));
+    const size_t nsp = (size_t)nxh * ny * nz;
     if (launch_setup_pivots(g, (const double*)(P + o.lamx), (const double*)(P + o.lamy), (double*)(P + o.invd),
-                            B->cap, (double*)(P + o.mtab)) != cudaSuccess) { free_batch(B); return PP_ERR_CUDA; }
+                            B->cap, (double*)(P + o.mtab)) != cudaSuccess ||
+        launch_narrow((const double*)(P + o.mtab), (float*)(P + o.mtabf), nsp, B->cap) != cudaSuccess ||
+        launch_narrow((const double*)(P + o.invd), (float*)(P + o.invdf), nsp, B->cap) != cudaSuccess) {
+      free_batch(B);
+      return PP_ERR_CUDA;
+    }
+    d.tri.mtab = (const float*)(P + o.mtabf);
+    d.tri.invd = (const float*)(P + o.invdf);
+    d.tri.zc = (const float*)(P + o.zcf);
+    d.tri.lamx = (const double*)(P + o.lamx);
+    d.tri.lamy = (const double*)(P + o.lamy);
+    d.tri.thr = 2.0 * dmax / 512.0;
     // stand-ins for the per-call pointers while tuning: plan-owned, zeroed
-    d.p = d.E; d.rho = d.b; d.us = d.vs = d.b; d.ws = d.fc.cz; d.S = nullptr; d.u = d.v = d.w = nullptr;
+    d.p = (double*)(P + o.E); d.rho = d.b; d.us = d.vs = d.b; d.ws = d.fc.cz; d.S = nullptr; d.u = d.v = d.w = nullptr;
     d.dt = 1.0; d.inv_dt = 1.0;
   }
+  if (cudaMalloc((void**)&B->d_low, low_all.size() * sizeof(int)) != cudaSuccess) { free_batch(B); return PP_ERR_OOM; }
+  if (cudaMemcpy(B->d_low, low_all.data(), low_all.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_batch(B);
+    return PP_ERR_CUDA;
+  }
+  for (int i = 0; i < ngrids; ++i) B->h_dev[i].tri.low = B->d_low + low_off[i];
   pp_status s;
   if ((s = upload_list(wc, &B->w_cells, &B->n_cells)) != PP_OK || (s = upload_list(wz, &B->w_z, &B->n_z)) != PP_OK) {
     free_batch(B);

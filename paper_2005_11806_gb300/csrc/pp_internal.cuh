@@ -60,8 +60,9 @@ struct Geo {
 //   cx = dzf_k beta_x / dx^2, cy = dzf_k beta_y / dy^2 (faces of layer k),
 //   cz = beta_z / dzc (z faces, 0 on the walls),
 //   diag = sum of the six coefficients of the cell, rhof = rho_c in FP32.
-//   cxf, cyf, czf, diagf: FP32 copies for the residual update of the mixed
-//   path (null on FP64 plans).
+//   cxf, cyf, czf: FP32 copies for the residual update of the mixed path
+//   (null on FP64 plans); diagf: FP32 diagonal when not null (unused by the
+//   solver's own kernels).
 //   rho_tilde: device scalar that replaces rho_c as the scaling of the
 //   residual (Methods I and II of Sec. 3.3.1); null selects Method III.
 struct Faces {
@@ -109,23 +110,50 @@ __device__ __forceinline__ float narrow_f64(double d) {
 // (or r = e), forward real x-transform of r into spec; block partial sums
 // of e^2 and |e| into red[2*block + {0,1}].  Rows are (k, j) pairs.
 //
-// Mixed path with E != null: E = dzf (D u^s - S_c)/dt is kept in FP64.  When
-// st->need_exact is set it is recomputed from p; otherwise it is updated by
-// E -= A delta with delta = p^s - p^{s-1} (FP32) and the FP32 coefficients.
+// Mixed path with E != null: E = dzf (D u^s - S_c)/dt is kept in FP32.  When
+// st->need_exact is set it is recomputed from p in FP64 (and stored
+// narrowed); otherwise it is updated by E -= A delta with
+// delta = p^s - p^{s-1} and the FP32 coefficients.
 template <typename T>
 cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, const C2<T>* twx,
                               const double* b, double inv_dt, const double* rho, const double* p,
                               int p_zero, int scale_rho, C2<T>* spec, double* red, int* nblk_out,
-                              const DevStatus* st, cudaStream_t s, double* E = nullptr,
+                              const DevStatus* st, cudaStream_t s, float* E = nullptr,
                               const float* delta = nullptr);
 template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
                         const DevStatus* st, cudaStream_t s);
+// FP32 Thomas tables for the well-conditioned z columns of mixed plans.  A
+// column (kx, ky) has the shift lambda = lambda_x(kx) + lambda_y(ky) <= 0;
+// the eigenvalues of its system lie in [lambda - 2 Dmax, lambda] with
+// Dmax = max_k (za_k + zc_k), so |lambda| >= thr = 2 Dmax / 512 bounds its
+// condition number by 513, and such a column runs in FP32.  The others,
+// the singular (0, 0) column among them, keep the FP64 recurrences.
+struct TriF32 {
+  const float* mtab;   // [nz][ny][nxh] multipliers m_k (FP32 copy)
+  const float* invd;   // [nz][ny][nxh] inverse pivots (FP32 copy)
+  const float* zc;     // [nz] super-diagonal of L_z (FP32 copy)
+  const double* lamx;  // [nxh]
+  const double* lamy;  // [ny]
+  double thr;
+  const int* low;      // [nlow] the columns with |lambda| < thr, column 0 first
+  int nlow;
+};
+// Columns (index ky * nxh + kx) that keep FP64: |lambda| < thr, and column 0.
+std::vector<int> tri_low_columns(const std::vector<double>& lamx, const std::vector<double>& lamy,
+                                 double thr);
+// Blocks of 128 threads of the mixed z solve.
+inline int tri_mixed_blocks(size_t ncol, int nlow) { return (nlow + 3) / 4 + (int)((ncol + 127) / 128); }
+
 // With mtab (multipliers m_k = a_k / d_{k-1}) the real and imaginary parts
 // run in separate threads; without it one thread solves a whole column.
+// With f32 (mixed plans) the well-conditioned columns run in FP32.
 template <typename T>
 cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,
-                           const DevStatus* st, cudaStream_t s, const double* mtab = nullptr);
+                           const DevStatus* st, cudaStream_t s, const double* mtab = nullptr,
+                           const TriF32* f32 = nullptr);
+// dst[i] = (float) src[i], i < n.
+cudaError_t launch_narrow(const double* src, float* dst, size_t n, cudaStream_t s);
 // Inverse x-transform; p = scale * z (p_zero) or p += scale * z; when delta
 // is not null it also receives scale * z in the transform's precision T.
 template <typename T>

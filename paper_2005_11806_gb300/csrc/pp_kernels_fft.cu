@@ -1,5 +1,7 @@
 // Single-grid kernels of the eigenexpansion solve and Algorithm 1's pass;
 // each is a thin wrapper around a stage of pp_stages.cuh.
+#include <cmath>
+
 #include "pp_stages.cuh"
 
 namespace pp {
@@ -13,7 +15,7 @@ __global__ void __launch_bounds__(256) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
                                                     int scale_rho, C2<T>* __restrict__ spec,
                                                     double* __restrict__ red, int rpb,
                                                     const DevStatus* __restrict__ st,
-                                                    double* __restrict__ E,
+                                                    float* __restrict__ E,
                                                     const float* __restrict__ delta) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -48,7 +50,25 @@ __global__ void __launch_bounds__(128, 16) k_tridiag_split(Geo g, const double* 
                                                            const double* __restrict__ invd, T* spec,
                                                            const DevStatus* __restrict__ st) {
   if (stopped(st)) return;
-  stage_tridiag_split<T>(g, mtab, invd, spec, (size_t)blockIdx.x * blockDim.x + threadIdx.x);
+  __shared__ double shm[34];
+  double m0 = 0.0;
+  if (blockIdx.x == 0) {  // holds column 0 (scalars 0 and 1)
+    zero_column_means<T>(g, spec, 2 * (size_t)g.ny * g.nxh, shm);
+    if (threadIdx.x < 2) m0 = shm[32 + threadIdx.x];
+  }
+  stage_tridiag_split<T>(g, mtab, invd, spec, (size_t)blockIdx.x * blockDim.x + threadIdx.x, m0);
+}
+
+__global__ void __launch_bounds__(128, 8) k_tridiag_mixed(Geo g, const double* __restrict__ mtab,
+                                                         const double* __restrict__ invd, TriF32 f,
+                                                         float2* spec, const DevStatus* __restrict__ st) {
+  if (stopped(st)) return;
+  stage_tridiag_mixed(g, mtab, invd, f, spec, blockIdx.x);
+}
+
+__global__ void k_narrow(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
 }
 
 template <typename T>
@@ -67,7 +87,7 @@ template <typename T>
 cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, const C2<T>* twx,
                               const double* b, double inv_dt, const double* rho, const double* p,
                               int p_zero, int scale_rho, C2<T>* spec, double* red, int* nblk_out,
-                              const DevStatus* st, cudaStream_t s, double* E, const float* delta) {
+                              const DevStatus* st, cudaStream_t s, float* E, const float* delta) {
   const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);
@@ -109,15 +129,35 @@ cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>
 
 template <typename T>
 cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,
-                           const DevStatus* st, cudaStream_t s, const double* mtab) {
+                           const DevStatus* st, cudaStream_t s, const double* mtab, const TriF32* f32) {
   const size_t ncol = (size_t)g.ny * g.nxh;
-  if (mtab != nullptr) {
+  if (mtab != nullptr && f32 != nullptr && sizeof(T) == sizeof(float)) {
+    k_tridiag_mixed<<<tri_mixed_blocks(ncol, f32->nlow), 128, 0, s>>>(g, mtab, invd, *f32,
+                                                                     reinterpret_cast<float2*>(spec), st);
+  } else if (mtab != nullptr) {
     const int nblk = (int)((2 * ncol + 127) / 128);
     k_tridiag_split<T><<<nblk, 128, 0, s>>>(g, mtab, invd, reinterpret_cast<T*>(spec), st);
   } else {
     const int nblk = (int)((ncol + 127) / 128);
     k_tridiag<T><<<nblk, 128, 0, s>>>(g, invd, spec, ybuf, st);
   }
+  return cudaGetLastError();
+}
+
+std::vector<int> tri_low_columns(const std::vector<double>& lamx, const std::vector<double>& lamy,
+                                 double thr) {
+  std::vector<int> low{0};
+  const int nxh = (int)lamx.size(), ny = (int)lamy.size();
+  for (int j = 0; j < ny; ++j)
+    for (int kx = 0; kx < nxh; ++kx)
+      if ((j != 0 || kx != 0) && std::fabs(lamx[kx] + lamy[j]) < thr) low.push_back(j * nxh + kx);
+  return low;
+}
+
+cudaError_t launch_narrow(const double* src, float* dst, size_t n, cudaStream_t s) {
+  size_t nb = (n + 255) / 256;
+  if (nb > (size_t)152 * 32) nb = (size_t)152 * 32;
+  k_narrow<<<(int)(nb == 0 ? 1 : nb), 256, 0, s>>>(src, dst, n);
   return cudaGetLastError();
 }
 
@@ -139,11 +179,12 @@ cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, c
   template cudaError_t launch_resid_fftx<T>(const Geo&, const Faces&, const FftDesc&, const C2<T>*,  \
                                             const double*, double, const double*, const double*,     \
                                             int, int, C2<T>*, double*, int*, const DevStatus*,       \
-                                            cudaStream_t, double*, const float*);                    \
+                                            cudaStream_t, float*, const float*);                    \
   template cudaError_t launch_ffty<T>(const Geo&, const FftDesc&, const C2<T>*, C2<T>*, int,         \
                                       const DevStatus*, cudaStream_t);                               \
   template cudaError_t launch_tridiag<T>(const Geo&, const double*, C2<T>*, double2*,                \
-                                         const DevStatus*, cudaStream_t, const double*);             \
+                                         const DevStatus*, cudaStream_t, const double*,              \
+                                         const TriF32*);                                             \
   template cudaError_t launch_fftx_inv<T>(const Geo&, const FftDesc&, const C2<T>*, const C2<T>*,    \
                                           double, double*, int, const DevStatus*, cudaStream_t,      \
                                           T*);

@@ -76,6 +76,9 @@ __device__ __forceinline__ C2<T>* fft_dispatch(C2<T>* a, C2<T>* b, const FftDesc
 //           dzf_k e = b_s - (sum_nb c_nb p_nb - diag p_c), b_s = dzf_k b / dt;
 //           r = rho e (or e).  The mixed path narrows dzf_k e to FP32 and
 //           finishes (scaling, norms, rho) in FP32.
+//   Mixed path with E: E = dzf_k e is kept in FP32.  An exact pass stores
+//   the FP64 value narrowed; an update pass subtracts A delta, evaluated in
+//   FP32 as sum_nb c_nb (delta_nb - delta_c) (no diagonal needed).
 // Two real rows are packed into one complex sequence (re = even row,
 // im = odd row), transformed together and separated afterwards.
 template <typename T>
@@ -86,7 +89,7 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
                                                  const double* __restrict__ p, int mode, int p_zero,
                                                  int scale_rho, C2<T>* __restrict__ spec,
                                                  double* __restrict__ red, int rpb, int blk,
-                                                 bool need_exact, double* __restrict__ E,
+                                                 bool need_exact, float* __restrict__ E,
                                                  const float* __restrict__ delta,
                                                  unsigned char* smem_raw) {
   __shared__ double shred[32];
@@ -125,18 +128,19 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
           r = (T)b[c];
         } else {
           const int ip = (i + 1 == nx) ? 0 : i + 1, im = (i == 0) ? nx - 1 : i - 1;
-          double ep;
+          double ep = 0.0;
+          float ev = 0.f;  // FP32 dzf_k e of the mixed path
           if (update) {
             // E^s = E^{s-1} - A delta, A delta in FP32
-            float t = -fc.diagf[c] * delta[c];
-            t = fmaf(fc.cxf[rowoff + ip], delta[rowoff + ip], t);
-            t = fmaf(fc.cxf[c], delta[rowoff + im], t);
-            t = fmaf(fc.cyf[rowp + i], delta[rowp + i], t);
-            t = fmaf(fc.cyf[c], delta[rowm + i], t);
-            if (k + 1 < nz) t = fmaf(fc.czf[c + plane], delta[c + plane], t);
-            if (k > 0) t = fmaf(fc.czf[c], delta[c - plane], t);
-            ep = E[c] - widen_f32(t);
-            E[c] = ep;
+            const float dc = delta[c];
+            float t = fc.cxf[rowoff + ip] * (delta[rowoff + ip] - dc);
+            t = fmaf(fc.cxf[c], delta[rowoff + im] - dc, t);
+            t = fmaf(fc.cyf[rowp + i], delta[rowp + i] - dc, t);
+            t = fmaf(fc.cyf[c], delta[rowm + i] - dc, t);
+            if (k + 1 < nz) t = fmaf(fc.czf[c + plane], delta[c + plane] - dc, t);
+            if (k > 0) t = fmaf(fc.czf[c], delta[c - plane] - dc, t);
+            ev = E[c] - t;
+            E[c] = ev;
           } else {
             ep = b[c];
             if (!p_zero) {
@@ -149,10 +153,13 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
               if (k > 0) t = fma(fc.cz[c], p[c - plane], t);
               ep -= t;
             }
-            if (E != nullptr) E[c] = ep;
+            if (sizeof(T) == sizeof(float)) {
+              ev = narrow_f64(ep);
+              if (E != nullptr) E[c] = ev;
+            }
           }
           if (sizeof(T) == sizeof(float)) {
-            const float e = narrow_f64(ep) * idzf_f;
+            const float e = ev * idzf_f;
             s2 = fmaf(e, e, (float)s2);
             s1 += fabsf(e);
             r = (T)(scale_rho ? (const_scale ? rt_f : fc.rhof[c]) * e : e);
@@ -374,17 +381,40 @@ __device__ __forceinline__ void thomas_column(const Geo& g, const double* __rest
   }
 }
 
+// dzf-weighted z means of the real and imaginary parts of column 0 (scalar
+// view T[nz][2 ncol]), reduced by the whole block; returned in sh[0], sh[1]
+// (sh: at least 34 entries) after a barrier.  Every thread must call it.
+template <typename T>
+__device__ __forceinline__ void zero_column_means(const Geo& g, const T* spec, size_t stride, double* sh) {
+  double sx = 0.0, sy = 0.0;
+  for (int k = threadIdx.x; k < g.nz; k += blockDim.x) {
+    sx += g.dzf[k] * (double)spec[(size_t)k * stride];
+    sy += g.dzf[k] * (double)spec[(size_t)k * stride + 1];
+  }
+  sx = block_sum<double>(sx, sh);
+  __syncthreads();
+  sy = block_sum<double>(sy, sh);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sh[32] = sx / g.lz;
+    sh[33] = sy / g.lz;
+  }
+  __syncthreads();
+}
+
 // The same solve with the real and imaginary parts of a column in two
 // threads (twice the parallelism) and the elimination multipliers
 // m_k = a_k / d_{k-1} read from a table: per scalar one FP64 FMA forward and
 // one FMA + one multiply backward.  The recurrences run in FP64 registers;
 // the forward-sweep values are stored in place in the spectrum's own
 // precision (FP32 on mixed plans, like the spectrum the solve reads and
-// writes).  Scalar view: spec as T[nz][2 ncol].
+// writes).  Scalar view: spec as T[nz][2 ncol].  m0 is subtracted from every
+// right-hand-side value: the dzf-weighted z mean of the singular (0, 0)
+// column, 0 for every other column.
 template <typename T>
 __device__ __forceinline__ void stage_tridiag_split(const Geo& g, const double* __restrict__ mtab,
                                                     const double* __restrict__ invd, T* spec,
-                                                    size_t sid) {
+                                                    size_t sid, double m0 = 0.0) {
   constexpr int PF = 4;
   const size_t ncol = (size_t)g.ny * g.nxh;
   if (sid >= 2 * ncol) return;
@@ -399,12 +429,6 @@ __device__ __forceinline__ void stage_tridiag_split(const Geo& g, const double* 
     if (sizeof(T) == sizeof(float)) spec[o] = (T)narrow_f64(v);
     else spec[o] = (T)v;
   };
-  if (col == 0) {  // singular (0, 0) column: remove the dzf-weighted mean first
-    double mean = 0.0;
-    for (int k = 0; k < nz; ++k) mean += g.dzf[k] * ld((size_t)k * stride + sid);
-    mean /= g.lz;
-    for (int k = 0; k < nz; ++k) stv((size_t)k * stride + sid, ld((size_t)k * stride + sid) - mean);
-  }
   double fq[PF], mq[PF];
 #pragma unroll
   for (int u = 0; u < PF; ++u) {
@@ -422,7 +446,7 @@ __device__ __forceinline__ void stage_tridiag_split(const Geo& g, const double* 
         const int kn = k + PF < nz ? k + PF : nz - 1;
         fq[u] = ld((size_t)kn * stride + sid);
         mq[u] = mtab[(size_t)kn * ncol + col];
-        y = fma(-m, y, f);
+        y = fma(-m, y, f - m0);
         if (k < nz - 1) stv((size_t)k * stride + sid, y);
       }
     }
@@ -450,6 +474,189 @@ __device__ __forceinline__ void stage_tridiag_split(const Geo& g, const double* 
       }
     }
   }
+}
+
+// One ill-conditioned column of a mixed plan, solved by a whole warp in
+// FP64.  Both sweeps of the Thomas elimination are first-order affine
+// recurrences,
+//   forward   y_k = -m_k y_{k-1} + f_k                (y_{-1} = 0),
+//   backward  x_k = -c_k d_k x_{k+1} + d_k y_k        (x_{nz-1} = d_{nz-1} y_{nz-1}),
+// so each lane composes the maps of its R = ceil(nz/32) consecutive rows, a
+// shuffle scan combines the lanes' maps, and each lane replays its rows from
+// the value entering its segment.  The values stay FP32 in memory (the
+// intermediate y too, as in stage_tridiag_split); the recurrences run in
+// FP64.  Column 0 (the singular (0, 0) system, its last pivot pinned) first
+// loses its dzf-weighted z mean.
+__device__ __forceinline__ void tridiag_col_warp64(const Geo& g, const double* __restrict__ mtab,
+                                                   const double* __restrict__ invd, float2* spec,
+                                                   size_t col, size_t ncol) {
+  const int lane = threadIdx.x & 31;
+  const int nz = g.nz;
+  const int R = (nz + 31) >> 5;
+  const int k0 = lane * R < nz ? lane * R : nz;
+  const int k1 = k0 + R < nz ? k0 + R : nz;
+  auto at = [&](int k) { return (size_t)k * ncol + col; };
+  double m0x = 0.0, m0y = 0.0;
+  if (col == 0) {
+    double sx = 0.0, sy = 0.0;
+    for (int k = k0; k < k1; ++k) {
+      const float2 v = spec[at(k)];
+      sx += g.dzf[k] * widen_f32(v.x);
+      sy += g.dzf[k] * widen_f32(v.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    m0x = sx / g.lz;
+    m0y = sy / g.lz;
+  }
+  // forward: compose y -> a y + b over the lane's rows, then scan the lanes
+  double A = 1.0, Bx = 0.0, By = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    const double a = -mtab[at(k)];
+    const float2 f = spec[at(k)];
+    Bx = fma(a, Bx, widen_f32(f.x) - m0x);
+    By = fma(a, By, widen_f32(f.y) - m0y);
+    A *= a;
+  }
+  for (int d = 1; d < 32; d <<= 1) {  // inclusive scan, earlier lanes' maps applied first
+    const double Ap = __shfl_up_sync(0xffffffffu, A, d);
+    const double Bxp = __shfl_up_sync(0xffffffffu, Bx, d);
+    const double Byp = __shfl_up_sync(0xffffffffu, By, d);
+    if (lane >= d) {
+      Bx = fma(A, Bxp, Bx);
+      By = fma(A, Byp, By);
+      A *= Ap;
+    }
+  }
+  double yx = __shfl_up_sync(0xffffffffu, Bx, 1), yy = __shfl_up_sync(0xffffffffu, By, 1);
+  if (lane == 0) { yx = 0.0; yy = 0.0; }
+  for (int k = k0; k < k1; ++k) {
+    const double a = -mtab[at(k)];
+    const float2 f = spec[at(k)];
+    yx = fma(a, yx, widen_f32(f.x) - m0x);
+    yy = fma(a, yy, widen_f32(f.y) - m0y);
+    spec[at(k)] = make_float2(narrow_f64(yx), narrow_f64(yy));
+  }
+  __syncwarp();
+  // backward: maps x_{k+1} -> x_k over the lane's rows from the top down
+  auto row_map = [&](int k, double& a, double& bx, double& by) {
+    const float2 yv = spec[at(k)];
+    const double d = invd[at(k)];
+    a = (k == nz - 1) ? 0.0 : -g.zc[k] * d;
+    bx = d * widen_f32(yv.x);
+    by = d * widen_f32(yv.y);
+  };
+  A = 1.0; Bx = 0.0; By = 0.0;
+  for (int k = k1 - 1; k >= k0; --k) {
+    double a, bx, by;
+    row_map(k, a, bx, by);
+    Bx = fma(a, Bx, bx);
+    By = fma(a, By, by);
+    A *= a;
+  }
+  for (int d = 1; d < 32; d <<= 1) {  // inclusive scan, later lanes' maps applied first
+    const double Ap = __shfl_down_sync(0xffffffffu, A, d);
+    const double Bxp = __shfl_down_sync(0xffffffffu, Bx, d);
+    const double Byp = __shfl_down_sync(0xffffffffu, By, d);
+    if (lane + d < 32) {
+      Bx = fma(A, Bxp, Bx);
+      By = fma(A, Byp, By);
+      A *= Ap;
+    }
+  }
+  double xx = __shfl_down_sync(0xffffffffu, Bx, 1), xy = __shfl_down_sync(0xffffffffu, By, 1);
+  if (lane == 31) { xx = 0.0; xy = 0.0; }
+  // every lane reads its own rows' y before any lane overwrites them
+  for (int k = k1 - 1; k >= k0; --k) {
+    double a, bx, by;
+    row_map(k, a, bx, by);
+    xx = fma(a, xx, bx);
+    xy = fma(a, xy, by);
+    spec[at(k)] = make_float2(narrow_f64(xx), narrow_f64(xy));
+  }
+}
+
+// Mixed plans, one thread per (kx, ky) column holding both components, in
+// FP32 with FP32 tables (float2 loads and stores of the spectrum).  Only the well-conditioned columns (TriF32) take this path;
+// column 0 and the other ill-conditioned columns are left to
+// tridiag_col_warp64.
+__device__ __forceinline__ void stage_tridiag_col32(const Geo& g, const TriF32& f, float2* spec, size_t col) {
+  constexpr int PF = 1;  // deeper register prefetch (2-16 rows) measured slower at 512^3
+  const size_t ncol = (size_t)g.ny * g.nxh;
+  if (col >= ncol) return;
+  const int j = (int)(col / (size_t)g.nxh);
+  const int kx = (int)(col - (size_t)j * g.nxh);
+  if (col == 0 || fabs(f.lamx[kx] + f.lamy[j]) < f.thr) return;
+  const int nz = g.nz;
+  float2 fq[PF];
+  float mq[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int k = u < nz ? u : nz - 1;
+    fq[u] = spec[(size_t)k * ncol + col];
+    mq[u] = f.mtab[(size_t)k * ncol + col];
+  }
+  float2 y = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < nz; k0 += PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 + u;
+      if (k < nz) {
+        const float2 fv = fq[u];
+        const float m = mq[u];
+        const int kn = k + PF < nz ? k + PF : nz - 1;
+        fq[u] = spec[(size_t)kn * ncol + col];
+        mq[u] = f.mtab[(size_t)kn * ncol + col];
+        y.x = fmaf(-m, y.x, fv.x);
+        y.y = fmaf(-m, y.y, fv.y);
+        if (k < nz - 1) spec[(size_t)k * ncol + col] = y;
+      }
+    }
+  }
+  const float dl = f.invd[(size_t)(nz - 1) * ncol + col];
+  float2 x = make_float2(y.x * dl, y.y * dl);
+  spec[(size_t)(nz - 1) * ncol + col] = x;
+  float2 yq[PF];
+  float dq[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int k = nz - 2 - u >= 0 ? nz - 2 - u : 0;
+    yq[u] = spec[(size_t)k * ncol + col];
+    dq[u] = f.invd[(size_t)k * ncol + col];
+  }
+  for (int k0 = nz - 2; k0 >= 0; k0 -= PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 - u;
+      if (k >= 0) {
+        const float2 yy = yq[u];
+        const float d = dq[u], c = f.zc[k];
+        const int kn = k - PF >= 0 ? k - PF : 0;
+        yq[u] = spec[(size_t)kn * ncol + col];
+        dq[u] = f.invd[(size_t)kn * ncol + col];
+        x.x = fmaf(-c, x.x, yy.x) * d;
+        x.y = fmaf(-c, x.y, yy.y) * d;
+        spec[(size_t)k * ncol + col] = x;
+      }
+    }
+  }
+}
+
+// Block b of the mixed z solve: the first nblk_low blocks give one warp to
+// each ill-conditioned column of the list (scheduled first: their chains are
+// the longest), the rest one thread to each column.  Block-uniform branch.
+__device__ __forceinline__ void stage_tridiag_mixed(const Geo& g, const double* __restrict__ mtab,
+                                                    const double* __restrict__ invd, const TriF32& f,
+                                                    float2* spec, int b) {
+  const int nblk_low = (f.nlow + 3) >> 2;
+  if (b < nblk_low) {
+    const int w = b * 4 + (threadIdx.x >> 5);
+    if (w < f.nlow) tridiag_col_warp64(g, mtab, invd, spec, (size_t)f.low[w], (size_t)g.ny * g.nxh);
+    return;
+  }
+  stage_tridiag_col32(g, f, spec, (size_t)(b - nblk_low) * blockDim.x + threadIdx.x);
 }
 
 // Inverse x transform of two half spectra per complex sequence, then

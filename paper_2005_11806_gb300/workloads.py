@@ -200,16 +200,19 @@ def place_bubbles(count, lx, ly, lz, nx, nz_min_cell, rmin, rmax, rng, gap_cells
 
 
 def bubbles_case(n=512, nbubbles=200, seed=1003, dt=1e-3, beta=1.5, rmin=0.05, rmax=0.12,
-                 rho_g=1.0, rho_l=1000.0, lz=2 * math.pi):
-    """Bubbly field in a (2 pi)^3 box with tanh-stretched z."""
+                 rho_g=1.0, rho_l=1000.0, lz=2 * math.pi, nz=None):
+    """Bubbly field in a (2 pi)^3 box with tanh-stretched z (n^2 x nz cells,
+    nz = n by default)."""
     L = 2 * math.pi
-    zf = tanh_zfaces(n, lz, beta)
+    nz = nz or n
+    zf = tanh_zfaces(nz, lz, beta)
     rng = np.random.Generator(np.random.PCG64(seed + 10))
     spheres = place_bubbles(nbubbles, L, L, lz, n, float(np.min(np.diff(zf))), rmin, rmax, rng)
-    phi = spheres_phi(n, n, n, L, L, zf, spheres)
-    us, vs, ws = random_faces(n, n, n, 0.1, seed)
-    return Workload(f"{nbubbles} bubbles {n}^3 tanh(beta={beta:g}) z, rho {rho_l:g}:{rho_g:g}",
-                    n, n, n, L, L, zf, dt, us, vs, ws, phi, rho_g, rho_l, gas_source(phi),
+    phi = spheres_phi(n, n, nz, L, L, zf, spheres)
+    us, vs, ws = random_faces(n, n, nz, 0.1, seed)
+    size = f"{n}^3" if nz == n else f"{n}x{n}x{nz}"
+    return Workload(f"{nbubbles} bubbles {size} tanh(beta={beta:g}) z, rho {rho_l:g}:{rho_g:g}",
+                    n, n, nz, L, L, zf, dt, us, vs, ws, phi, rho_g, rho_l, gas_source(phi),
                     extra={"spheres": spheres})
 
 
