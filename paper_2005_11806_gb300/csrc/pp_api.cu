@@ -15,12 +15,12 @@ using namespace pp;
 
 namespace {
 enum KId { K_RESID, K_CHECK, K_FFTY_F, K_TRI, K_FFTY_I, K_FFTX_I, K_INIT, K_PREP, K_MEANS, K_RHSB,
-           K_RMEAN, K_CORR, K_MIX, K_ADJ_RHS, K_ADJ_FIN, K_ADJ_GRHO, K_RHOT, K_COUNT };
+           K_RMEAN, K_CORR, K_MIX, K_ADJ_RHS, K_ADJ_FIN, K_ADJ_GRHO, K_RHOT, K_FOLD, K_COUNT };
 const char* const kNames[K_COUNT] = {
     "resid_fftx", "check", "ffty_fwd", "tridiag_z", "ffty_inv", "fftx_inv_update", "init_status",
     "prep_faces", "mean_S", "rhs_b", "remove_mean", "correct", "mixture_density", "adj_rhs",
-    "adj_finish", "adj_grho", "rho_tilde"};
-const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1, 2};
+    "adj_finish", "adj_grho", "rho_tilde", "fold_pending"};
+const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1, 2, 1};
 struct Rec { int kid; cudaEvent_t a, b; };
 struct Prof {
   bool on = false;
@@ -52,6 +52,7 @@ struct pp_plan_s {
   double* d_b = nullptr;
   float* d_E = nullptr;       // mixed: residual carried between passes (FP32)
   float* d_delta = nullptr;   // mixed: last pressure correction (FP32)
+  float* d_sdelta = nullptr;  // mixed: sum of the corrections not yet added to p
   // iteration of Sec. 3.3.1 (pp_method); Methods I and II scale the residual
   // by the device scalar d_rho_tilde, Method I keeps the last increment of p
   // (d_delta on mixed plans, d_delta64 on FP64 plans) for Eq. poisson_me2
@@ -224,7 +225,7 @@ pp_status read_info(pp_plan_s* P, pp_info* info) {
 // One pass of Algorithm 1 after the residual: forward y, z solve, inverse y,
 // inverse x fused with p += delta.
 template <typename T>
-pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr) {
+pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr, float* sdelta = nullptr) {
   const Geo& g = P->geo;
   C2<T>* spec = (C2<T>*)P->d_spec;
   const C2<T>* twx = (const C2<T>*)P->d_twx;
@@ -240,7 +241,8 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr) {
                                      P->use_tri32 ? &P->tri32 : nullptr));
   }
   PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream));
-  PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream, delta));
+  PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream, delta,
+                                       sdelta));
   return PP_OK;
 }
 
@@ -277,7 +279,7 @@ pp_status method3_loop(pp_plan_s* P, const double* rho, double* p, int warm, dou
                                           P->d_st, P->stream, upd ? P->d_E : nullptr,
                                           upd ? P->d_delta : nullptr));
     PP_K(P, K_CHECK, launch_check(P->d_st, P->d_red, nblk, rtol, maxit, kexact, P->stream));
-    pp_status s = solve_pass<T>(P, p, 0, dl);
+    pp_status s = solve_pass<T>(P, p, 0, dl, upd ? P->d_sdelta : nullptr);
     if (s != PP_OK) return s;
     if ((it + 1) % chunk == 0) {
       // Poll the device status without draining the queue: read the slot
@@ -317,6 +319,8 @@ pp_status projection(pp_plan_s* P, const double* us, const double* vs, const dou
   if (!warm) PP_CK(cudaMemsetAsync(p, 0, ncell(P) * sizeof(double), P->stream));
   pp_status s = method3_loop<T>(P, rho, p, warm, dt, rtol, maxit);
   if (s != PP_OK) return s;
+  if (std::is_same<T, float>::value && P->d_E != nullptr)
+    PP_K(P, K_FOLD, launch_fold_pending(g, p, P->d_sdelta, P->d_st, P->stream));
   PP_K(P, K_RMEAN, launch_remove_mean(g, p, P->d_red, P->d_st, P->stream));
   if (u && P->method == PP_METHOD_I) {
     PP_K(P, K_CORR, launch_correct_method1<T>(g, P->faces, us, vs, ws, p, increment_buffer<T>(P, false), dt,
@@ -339,7 +343,7 @@ void free_plan(pp_plan_s* P) {
                      P->faces.diag, P->d_rho_tilde, P->d_delta64};
   if (P->faces.rhof) cudaFree(P->faces.rhof);
   if (P->d_low) cudaFree(P->d_low);
-  float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta,
+  float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta, P->d_sdelta,
                     P->d_mtab_f, P->d_invd_f, P->d_zc_f};
   for (float* f : fptrs) if (f) cudaFree(f);
   if (P->d_E) cudaFree(P->d_E);
@@ -475,6 +479,7 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       (st = dalloc(&P->d_spec, nsp * csz)) != PP_OK ||
       (prec != PP_FP64 && (st = dalloc(&P->d_E, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->d_delta, nc * sizeof(float))) != PP_OK) ||
+      (prec != PP_FP64 && (st = dalloc(&P->d_sdelta, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->faces.cxf, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->faces.cyf, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->faces.czf, nw * sizeof(float))) != PP_OK) ||

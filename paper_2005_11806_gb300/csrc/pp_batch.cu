@@ -35,6 +35,7 @@ struct GridDev {
   float2* spec;
   float* E;
   float* delta;
+  float* sdelta;  // increments not yet added to p (lazy update, stage_fftx_inv)
   double* b;
   double* red;
   DevStatus* st;
@@ -182,7 +183,16 @@ __global__ void __launch_bounds__(256) kb_fftx_inv(GridDev* G, const int2* __res
   const int2 w = work[blockIdx.x];
   const GridDev& d = G[w.x];
   if (d.st->done) return;
-  stage_fftx_inv<float>(d.g, d.fx, d.twx, d.spec, d.scale, d.p, 0, d.rpb, w.y, d.delta, smem_raw);
+  stage_fftx_inv<float>(d.g, d.fx, d.twx, d.spec, d.scale, d.p, 0, d.rpb, w.y, d.delta, d.sdelta,
+                        d.st->need_exact != 0, d.st->since_exact <= 1, smem_raw);
+}
+
+// p += sdelta for the grids whose last residual was an updated one.
+__global__ void kb_fold(GridDev* G, const int2* __restrict__ work) {
+  const int2 w = work[blockIdx.x];
+  const GridDev& d = G[w.x];
+  if (d.st->last_exact) return;
+  PP_CHUNK_LOOP(d, w) d.p[c] += widen_f32(d.sdelta[c]);
 }
 
 // Loop control of the device-side while loop: continue while any grid is
@@ -331,6 +341,7 @@ cudaError_t launch_pre(pp_batch_s* B, cudaStream_t s) {
 }
 
 cudaError_t launch_post(pp_batch_s* B, cudaStream_t s) {
+  kb_fold<<<B->n_cells, kThreads, 0, s>>>(B->d_dev, B->w_cells);
   kb_weighted_partial<<<B->n_cells, kThreads, 0, s>>>(B->d_dev, B->w_cells, 1);
   kb_finalize<<<B->n, 1024, 0, s>>>(B->d_dev, 1);
   kb_fill_p<<<B->n_cells, kThreads, 0, s>>>(B->d_dev, B->w_cells, 1);
@@ -460,7 +471,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
 
   // pool layout: per grid, every buffer and table
   struct Off {
-    size_t spec, E, delta, b, red, st, cx, cy, cz, diag, rhof, cxf, cyf, czf, invd, mtab,
+    size_t spec, E, delta, sdelta, b, red, st, cx, cy, cz, diag, rhof, cxf, cyf, czf, invd, mtab,
         twx, twy, idzf, idzc, dzf, za, zc, idzff, lamx, lamy, mtabf, invdf, zcf;
   };
   std::vector<Off> off(ngrids);
@@ -480,6 +491,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     Off& o = off[i];
     // E is FP32; it gets 8 bytes a cell to double as the stand-in p of the tuning runs
     o.spec = cv.take(nsp * sizeof(float2)); o.E = cv.take(nc * 8); o.delta = cv.take(nc * 4);
+    o.sdelta = cv.take(nc * 4);
     o.b = cv.take(nc * 8); o.red = cv.take(nred * 8); o.st = cv.take(sizeof(DevStatus));
     o.cx = cv.take(nc * 8); o.cy = cv.take(nc * 8); o.cz = cv.take(nw * 8); o.diag = cv.take(nc * 8);
     o.rhof = cv.take(nc * 4); o.cxf = cv.take(nc * 4); o.cyf = cv.take(nc * 4); o.czf = cv.take(nw * 4);
@@ -550,6 +562,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     d.twx = (const float2*)(P + o.twx); d.twy = (const float2*)(P + o.twy);
     d.invd = (const double*)(P + o.invd); d.mtab = (const double*)(P + o.mtab);
     d.spec = (float2*)(P + o.spec); d.E = (float*)(P + o.E); d.delta = (float*)(P + o.delta);
+    d.sdelta = (float*)(P + o.sdelta);
     d.b = (double*)(P + o.b); d.red = (double*)(P + o.red); d.st = (DevStatus*)(P + o.st);
     d.ncell = (long long)nx * ny * nz;
     d.nchunk = (int)((d.ncell + kChunk - 1) / kChunk);

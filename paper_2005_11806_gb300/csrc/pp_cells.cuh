@@ -101,6 +101,7 @@ __device__ __forceinline__ void status_update(DevStatus* st, double s2, double s
   const double rel = (e20 > 0.0) ? sqrt(s2 / e20) : 0.0;
   st->rel = rel;
   const int exact = st->need_exact;
+  st->last_exact = exact;
   if (!isfinite(s2) || !isfinite(e20)) { st->done = 1; st->code = PP_ERR_NUMERIC; }
   else if (e20 == 0.0 || (rel <= rtol && exact)) { st->done = 1; st->code = PP_OK; }
   else if (st->iters >= maxit) { st->done = 1; st->code = PP_ERR_NOT_CONVERGED; }
@@ -122,7 +123,7 @@ __device__ __forceinline__ void status_update(DevStatus* st, double s2, double s
 __device__ __forceinline__ void status_init(DevStatus* st) {
   st->e2 = 0; st->e1 = 0; st->e2_0 = 0; st->rel = 0; st->mean_S = 0; st->pmean = 0;
   st->iters = 0; st->done = 0; st->code = PP_OK; st->pad = 0;
-  st->need_exact = 1; st->since_exact = 0;
+  st->need_exact = 1; st->since_exact = 0; st->last_exact = 1;
 }
 
 }  // namespace pp

@@ -39,6 +39,7 @@ struct DevStatus {
   int code;         // pp_status of the loop
   int need_exact;   // 1: the next residual is recomputed from p in FP64
   int since_exact;  // passes since the last exact residual
+  int last_exact;   // 1: the latest residual was an exact one
   int pad;
 };
 
@@ -156,10 +157,16 @@ cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double
 cudaError_t launch_narrow(const double* src, float* dst, size_t n, cudaStream_t s);
 // Inverse x-transform; p = scale * z (p_zero) or p += scale * z; when delta
 // is not null it also receives scale * z in the transform's precision T.
+// With sdelta (mixed plans) p is updated only before an exact residual and
+// the increments in between are summed into sdelta (FP32); see
+// stage_fftx_inv.  launch_fold_pending adds a sum still pending when the
+// loop has stopped.
 template <typename T>
 cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
                             double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s,
-                            T* delta = nullptr);
+                            T* delta = nullptr, float* sdelta = nullptr);
+cudaError_t launch_fold_pending(const Geo& g, double* p, const float* sdelta, const DevStatus* st,
+                                cudaStream_t s);
 
 // Inverse Thomas pivots; when mtab is not null also the multipliers
 // m_k = a_k / d_{k-1} (m_0 = 0).

@@ -66,6 +66,15 @@ __global__ void __launch_bounds__(128, 8) k_tridiag_mixed(Geo g, const double* _
   stage_tridiag_mixed(g, mtab, invd, f, spec, blockIdx.x);
 }
 
+// p += sdelta when the last residual of the loop was an updated one (the
+// increments since the last exact residual are still pending).
+__global__ void k_fold_pending(size_t n, double* __restrict__ p, const float* __restrict__ sdelta,
+                               const DevStatus* __restrict__ st) {
+  if (st->last_exact) return;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    p[c] += widen_f32(sdelta[c]);
+}
+
 __global__ void k_narrow(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
@@ -76,10 +85,14 @@ __global__ void __launch_bounds__(256) k_fftx_inv(Geo g, FftDesc fx, const C2<T>
                                                   const C2<T>* __restrict__ spec, double scale,
                                                   double* __restrict__ p, int p_zero, int rpb,
                                                   const DevStatus* __restrict__ st,
-                                                  T* __restrict__ delta) {
+                                                  T* __restrict__ delta, float* __restrict__ sdelta) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_fftx_inv<T>(g, fx, twx, spec, scale, p, p_zero, rpb, blockIdx.x, delta, smem_raw);
+  const bool lazy = sdelta != nullptr && st != nullptr;
+  const bool fold = lazy && st->need_exact != 0;
+  const bool fresh = lazy && st->since_exact <= 1;
+  stage_fftx_inv<T>(g, fx, twx, spec, scale, p, p_zero, rpb, blockIdx.x, delta, lazy ? sdelta : nullptr,
+                    fold, fresh, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -154,6 +167,15 @@ std::vector<int> tri_low_columns(const std::vector<double>& lamx, const std::vec
   return low;
 }
 
+cudaError_t launch_fold_pending(const Geo& g, double* p, const float* sdelta, const DevStatus* st,
+                                cudaStream_t s) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  size_t nb = (n + 255) / 256;
+  if (nb > (size_t)152 * 32) nb = (size_t)152 * 32;
+  k_fold_pending<<<(int)(nb == 0 ? 1 : nb), 256, 0, s>>>(n, p, sdelta, st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_narrow(const double* src, float* dst, size_t n, cudaStream_t s) {
   size_t nb = (n + 255) / 256;
   if (nb > (size_t)152 * 32) nb = (size_t)152 * 32;
@@ -164,14 +186,14 @@ cudaError_t launch_narrow(const double* src, float* dst, size_t n, cudaStream_t 
 template <typename T>
 cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
                             double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s,
-                            T* delta) {
+                            T* delta, float* sdelta) {
   const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);
   const size_t smem = (size_t)rpb * g.nx * sizeof(C2<T>);
   cudaError_t e = cudaFuncSetAttribute(k_fftx_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_fftx_inv<T><<<nblk, kThreads, smem, s>>>(g, fx, twx, spec, scale, p, p_zero, rpb, st, delta);
+  k_fftx_inv<T><<<nblk, kThreads, smem, s>>>(g, fx, twx, spec, scale, p, p_zero, rpb, st, delta, sdelta);
   return cudaGetLastError();
 }
 
@@ -187,7 +209,7 @@ cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, c
                                          const TriF32*);                                             \
   template cudaError_t launch_fftx_inv<T>(const Geo&, const FftDesc&, const C2<T>*, const C2<T>*,    \
                                           double, double*, int, const DevStatus*, cudaStream_t,      \
-                                          T*);
+                                          T*, float*);
 PP_INST(double)
 PP_INST(float)
 #undef PP_INST

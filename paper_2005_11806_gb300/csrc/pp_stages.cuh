@@ -661,13 +661,23 @@ __device__ __forceinline__ void stage_tridiag_mixed(const Geo& g, const double* 
 
 // Inverse x transform of two half spectra per complex sequence, then
 // p = scale * z (p_zero) or p += scale * z.  The p values a thread updates
-// are loaded before the transform so their latency overlaps it.
+// are loaded before the transform so their latency overlaps it.  delta (if
+// not null) receives the increment scale * z in the precision T.
+//
+// Mixed path (sdelta not null): p is only brought up to date where an
+// exact residual needs it.  sdelta holds the FP32 sum of the increments
+// since p was last updated:
+//   fold  (the next residual is exact): p += sdelta + increment (FP64);
+//   else: sdelta = increment (fresh: p was updated last pass) or
+//         sdelta += increment.
+// With fresh set, fold ignores sdelta.
 template <typename T>
 __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
                                                const C2<T>* __restrict__ twx,
                                                const C2<T>* __restrict__ spec, double scale,
                                                double* __restrict__ p, int p_zero, int rpb, int blk,
-                                               T* __restrict__ delta, unsigned char* smem_raw) {
+                                               T* __restrict__ delta, float* __restrict__ sdelta,
+                                               bool fold, bool fresh, unsigned char* smem_raw) {
   const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
   const int nseq = rpb >> 1;
   const float scale_f = (float)scale;
@@ -678,19 +688,39 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
   const bool even = (nx & 1) == 0;
   const int nout = rpb * nx;
   const int lgx = ((nx & (nx - 1)) == 0) ? 31 - __clz(nx) : -1;
+  const bool lazy = sdelta != nullptr;
+  const bool need_p = !p_zero && (!lazy || fold);   // p is read
+  const bool need_s = lazy && !fresh;               // sdelta is read
   auto split = [&](int t, int& q, int& i) {
     if (lgx >= 0) { q = t >> lgx; i = t & (nx - 1); }
     else { q = t / nx; i = t - q * nx; }
   };
+  // one output value: zv = unscaled inverse transform at cell c
+  auto emit = [&](size_t c, T zv, double pv, float sv) {
+    const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
+    const float inc_f = scale_f * (float)zv;
+    if (!lazy) {
+      p[c] = fma(scale, zd, pv);
+    } else if (fold) {
+      p[c] = fma(scale, zd, pv + widen_f32(sv));
+    } else {
+      sdelta[c] = sv + inc_f;
+    }
+    if (delta != nullptr) delta[c] = (sizeof(T) == sizeof(float)) ? (T)inc_f : (T)(scale * zd);
+  };
   constexpr int NP = kPrefetchInv;
   double pv[NP];
+  float sv[NP];
 #pragma unroll
   for (int u = 0; u < NP; ++u) {
     const int t = threadIdx.x + u * blockDim.x;
     int q, i;
     split(t, q, i);
     pv[u] = 0.0;
-    if (!p_zero && t < nout && row0 + q < nrows) pv[u] = p[(size_t)(row0 + q) * nx + i];
+    sv[u] = 0.f;
+    const bool in = t < nout && row0 + q < nrows;
+    if (need_p && in) pv[u] = p[(size_t)(row0 + q) * nx + i];
+    if (need_s && in) sv[u] = sdelta[(size_t)(row0 + q) * nx + i];
   }
   for (int t = threadIdx.x; t < nseq * nx; t += blockDim.x) {
     int q, kx;
@@ -719,11 +749,7 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
     const long row = row0 + q;
     if (t < nout && row < nrows) {
       const C2<T> z = res[(size_t)(q >> 1) * nx + i];
-      const T zv = (q & 1) ? z.y : z.x;
-      const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
-      p[(size_t)row * nx + i] = fma(scale, zd, pv[u]);
-      if (delta != nullptr)
-        delta[(size_t)row * nx + i] = (sizeof(T) == sizeof(float)) ? (T)(scale_f * (float)zv) : (T)(scale * zd);
+      emit((size_t)row * nx + i, (q & 1) ? z.y : z.x, pv[u], sv[u]);
     }
   }
   for (int t = threadIdx.x + NP * blockDim.x; t < nout; t += blockDim.x) {  // beyond the prefetch
@@ -732,14 +758,10 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
     const long row = row0 + q;
     if (row < nrows) {
       const C2<T> z = res[(size_t)(q >> 1) * nx + i];
-      const T zv = (q & 1) ? z.y : z.x;
-      const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
       const size_t c = (size_t)row * nx + i;
-      p[c] = p_zero ? scale * zd : fma(scale, zd, p[c]);
-      if (delta != nullptr) delta[c] = scale_f * (float)zv;
+      emit(c, (q & 1) ? z.y : z.x, need_p ? p[c] : 0.0, need_s ? sdelta[c] : 0.f);
     }
   }
 }
-
 
 }  // namespace pp
