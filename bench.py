@@ -31,13 +31,31 @@ sys.path.insert(0, ROOT)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x FP64 FMA/clk x 2 flop x max clock
 
 
+def max_over_ranks(x, device):
+    """Maximum of x over the ranks of the default process group; x itself
+    when no group is initialised or the world has one rank."""
+    import torch
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gpts(cells_per_rank, world, ms):
+    """Whole-job throughput: every rank solves its own replica of the
+    workload, so the job processes world x cells in the slowest rank's time."""
+    return world * cells_per_rank / (ms / 1e3) / 1e9
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_tc"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_tc", "mixed_z64"])
     ap.add_argument("--method", default="III", choices=["III", "II", "I"],
                     help="iteration of Sec. 3.3.1 (Method III is the measured one; I and II compare)")
     ap.add_argument("--n", type=int, default=512)
@@ -112,10 +130,11 @@ class ClockSampler:
 
 
 def algorithmic(kernel, w, precision):
-    """Algorithmic bytes and FP64 flops of one launch of each kernel.  Mixed
+    """Algorithmic bytes and FP64 flops of one launch of each kernel (what
+    the step must move: every field read or written once per launch).  Mixed
     plans recompute the residual exactly every 10th pass and update it in the
-    others, so the residual kernel's figures are the average over that
-    cycle."""
+    others, and bring p up to date only before an exact residual, so the
+    residual and inverse-x figures are averages over that 10-pass cycle."""
     npts = w.nx * w.ny * w.nz
     nsp = (w.nx // 2 + 1) * w.ny * w.nz
     cs = 16 if precision == "fp64" else 8  # bytes per spectral complex value
@@ -123,20 +142,27 @@ def algorithmic(kernel, w, precision):
         if precision == "fp64":
             # b, p, cx, cy, cz, diag, rho (FP64) + FP64 half spectrum; stencil 7 FMA + 5, x-FFT
             return {"bytes": 56 * npts + cs * nsp, "fp64_flops": 19 * npts + 45 * npts}
-        exact = {"bytes": 60 * npts, "fp64_flops": 15 * npts}   # b, p, 4 coefficient fields, rhof, E write
-        update = {"bytes": 40 * npts, "fp64_flops": 1 * npts}   # E r/w, delta, 4 FP32 coefficients, rhof
-        return {"bytes": int(0.1 * exact["bytes"] + 0.9 * update["bytes"]) + cs * nsp,
-                "fp64_flops": int(0.1 * exact["fp64_flops"] + 0.9 * update["fp64_flops"])}
+        exact = 56 * npts     # b, p, cx, cy, cz, diag (FP64), rhof; E written (FP32)
+        update = 28 * npts    # E read + write, delta, cxf, cyf, czf, rhof (FP32)
+        return {"bytes": int(0.1 * exact + 0.9 * update) + cs * nsp, "fp64_flops": int(0.1 * 15 * npts)}
     if kernel in ("ffty_fwd", "ffty_inv"):
         return {"bytes": 2 * cs * nsp, "fp64_flops": 0 if precision != "fp64" else 45 * npts}
     if kernel == "tridiag_z":
         if precision == "mixed_tc":
             return {"bytes": 2 * cs * nsp, "fp64_flops": 0, "tensor_flops": 3 * 2 * 2 * w.nz * 2 * nsp}
-        # f in, x out, multipliers and inverse pivots (FP64), forward values stored and reread
-        return {"bytes": (4 * cs + 16) * nsp, "fp64_flops": 6 * nsp}
+        if precision in ("fp64", "mixed_z64"):
+            # f in, forward values out and back in, x out; multipliers and inverse pivots (FP64)
+            return {"bytes": (4 * cs + 16) * nsp, "fp64_flops": 6 * nsp}
+        # same traffic with FP32 values and FP32 tables (well-conditioned columns)
+        return {"bytes": (4 * cs + 8) * nsp, "fp64_flops": 0}
     if kernel == "fftx_inv_update":
-        return {"bytes": cs * nsp + 16 * npts + (4 * npts if precision != "fp64" else 0),
-                "fp64_flops": 2 * npts}
+        if precision == "fp64":
+            return {"bytes": cs * nsp + 16 * npts, "fp64_flops": 2 * npts}
+        fold = 24 * npts      # p read + write (FP64), sum of increments read, increment written
+        fresh = 8 * npts      # sum of increments written, increment written
+        accum = 12 * npts     # sum of increments read + written, increment written
+        return {"bytes": int(0.1 * fold + 0.1 * fresh + 0.8 * accum) + cs * nsp,
+                "fp64_flops": int(0.1 * 2 * npts)}
     return None
 
 
@@ -186,16 +212,13 @@ def run_ours(args, rank, world, local_rank):
         ms = e0.elapsed_time(e1) / steps
         kern, launches = pp.pressure_profile_read(plan.handle)
         pp.pressure_profile_enable(plan.handle, False)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
         return ms, infos, kern, launches, clocks
 
     plan = make_plan(args.precision)
     ms, infos, kern, launches, clocks = timed(plan, args.steps, args.warmup, True)
     info = infos[-1]
-    value = world * npts / (ms / 1e3) / 1e9
+    value = whole_job_gpts(npts, world, ms)
 
     # dominant kernel and its roofline (live CUDA-event durations)
     dom = max(kern.items(), key=lambda kv: kv[1][1])
@@ -236,7 +259,8 @@ def run_ours(args, rank, world, local_rank):
            "value": round(value, 5), "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+           "dtype": {"fp64": "f64", "mixed_tc": "f64+f32+bf16"}.get(args.precision, "f64+f32"),
+           "data": "synthetic",
            "config": config_dict(args, w),
            "iterations": info["iters"], "res_final": info["res_final"], "status": info["status"],
            "per_iteration_gpts": round(world * npts * info["iters"] / (ms / 1e3) / 1e9, 4),
@@ -248,7 +272,7 @@ def run_ours(args, rank, world, local_rank):
         plan.close()
         plan64 = make_plan("fp64")
         ms64, infos64, kern64, _, clocks64 = timed(plan64, args.compare_steps, 1, True)
-        out["fp64"] = {"value": round(world * npts / (ms64 / 1e3) / 1e9, 5), "ms_per_step": round(ms64, 3),
+        out["fp64"] = {"value": round(whole_job_gpts(npts, world, ms64), 5), "ms_per_step": round(ms64, 3),
                        "iterations": infos64[-1]["iters"], "res_final": infos64[-1]["res_final"],
                        "steps": args.compare_steps, "warmup": 1, "clocks": clocks64,
                        "kernels": {k: {"launches": n, "total_ms": round(t, 3)} for k, (n, t) in kern64.items()}}
@@ -271,12 +295,14 @@ def run_ours(args, rank, world, local_rank):
                                        hv, hw, rtol=args.rtol, maxit=args.maxit, allow_not_converged=True)
         e2e_step()
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t = time.perf_counter()
         e2e_step()
         torch.cuda.synchronize()
-        es = time.perf_counter() - t
+        es_ms = max_over_ranks((time.perf_counter() - t) * 1e3, dev)
         nc, nw = npts * 8, (w.nz + 1) * w.ny * w.nx * 8
-        out["e2e"] = {"value": round(world * npts / es / 1e9, 5), "unit": "Gpts/s",
+        out["e2e"] = {"value": round(whole_job_gpts(npts, world, es_ms), 5), "unit": "Gpts/s",
                       "h2d_bytes_per_step": 5 * nc + nw, "d2h_bytes_per_step": 4 * nc + nw,
                       "steps": 1, "warmup": 1}
     plan.close()
@@ -326,14 +352,10 @@ def run_batch(args, rank, world, local_rank):
     e1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, torch.device("cuda", local_rank))
     its = [i["iters"] for i in infos]
     out = {"metric": "batched pressure-solve Gpts/s: 96 mixed-size grids, rel. residual <=1e-10",
-           "value": round(world * B.ncell / (ms / 1e3) / 1e9, 5), "unit": "Gpts/s", "n_gpus": world,
+           "value": round(whole_job_gpts(B.ncell, world, ms), 5), "unit": "Gpts/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
            "config": {"workload": "96 grids N in {64,96,128,160,192}, z aspect U[1,2], one droplet each, "

@@ -56,10 +56,17 @@ typedef enum { PP_BC_PERIODIC = 0, PP_BC_WALL = 1 } pp_bc;
 
 typedef enum {
     PP_FP64 = 0,       /* every step in FP64 */
-    PP_MIXED_FP32 = 1, /* x/y transforms in FP32; residual, z solve and p in FP64 */
-    PP_MIXED_TC = 2    /* as PP_MIXED_FP32, but the z solve is the eigenvector expansion
+    PP_MIXED_FP32 = 1, /* x/y transforms in FP32; the residual is recomputed exactly in
+                          FP64 every 10th pass and updated in FP32 in between (convergence
+                          is only accepted on an exact residual); p is kept in FP64; the z
+                          tridiagonal solve runs in FP32 on the well-conditioned (kx, ky)
+                          columns (condition number <= 513) and in FP64 on the others,
+                          the pinned zero mode among them */
+    PP_MIXED_TC = 2,   /* as PP_MIXED_FP32, but the z solve is the eigenvector expansion
                           along z (x = V diag(1/(mu + lambda)) V^T W f) as BF16x3 split
                           products on the tensor cores with FP32 accumulation; nz <= 512 */
+    PP_MIXED_Z64 = 3   /* as PP_MIXED_FP32, but every z column is solved with FP64
+                          recurrences (values stored in FP32) */
 } pp_precision;
 
 /* Recast of the variable-coefficient Eq. lap_p into a constant-coefficient

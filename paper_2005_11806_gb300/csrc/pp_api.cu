@@ -390,7 +390,8 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   const pp_grid& G = *grid;
   if (G.nx < 2 || G.ny < 1 || G.nz < 1 || !(G.lx > 0) || !(G.ly > 0) || !(G.lz > 0))
     return PP_ERR_INVALID_ARG;
-  if (prec != PP_FP64 && prec != PP_MIXED_FP32 && prec != PP_MIXED_TC) return PP_ERR_INVALID_ARG;
+  if (prec != PP_FP64 && prec != PP_MIXED_FP32 && prec != PP_MIXED_TC && prec != PP_MIXED_Z64)
+    return PP_ERR_INVALID_ARG;
   if (prec == PP_MIXED_TC && G.nz > 512) return PP_ERR_UNSUPPORTED;
   if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL)
     return PP_ERR_UNSUPPORTED;

@@ -7,7 +7,7 @@
 namespace pp {
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
+__global__ void __launch_bounds__(256, 4) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
                                                     const C2<T>* __restrict__ twx,
                                                     const double* __restrict__ b,
                                                     const double* __restrict__ rho,

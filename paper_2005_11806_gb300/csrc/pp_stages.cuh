@@ -70,6 +70,82 @@ __device__ __forceinline__ C2<T>* fft_dispatch(C2<T>* a, C2<T>* b, const FftDesc
 #undef PP_TRY_FIXED
 
 // ---------------------------------------------------------------------------
+// Update pass of the mixed residual for nx % 4 == 0, vectorised: each thread
+// takes the two rows of one complex sequence and four consecutive cells of
+// each (16-byte loads of E, delta and the FP32 coefficients, all issued
+// before the arithmetic), subtracts A delta = sum_nb c_nb (delta_nb -
+// delta_c) from E, and writes the scaled residual of both rows as two
+// interleaved complex pairs.  Same per-cell arithmetic as the scalar path.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+__device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc, float* __restrict__ E,
+                                                  const float* __restrict__ delta, int scale_rho,
+                                                  bool const_scale, float rt_f, long row0, int rpb,
+                                                  float2* bufA, float& s2, float& s1) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long nrows = (long)nz * ny;
+  const size_t plane = (size_t)nx * ny;
+  const int t4 = nx >> 2;
+  const int npairs = rpb >> 1;
+  for (int w = threadIdx.x; w < npairs * t4; w += blockDim.x) {
+    const int qp = w / t4;
+    const int i = (w - qp * t4) << 2;
+    float4 rr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long row = row0 + 2 * qp + h;
+      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < nrows) {
+        const int k = (int)(row / ny), j = (int)(row - (long)k * ny);
+        const int jp = (j + 1 == ny) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
+        const size_t rowoff = (size_t)row * nx;
+        const size_t kp = (size_t)k * plane;
+        const size_t c = rowoff + i;
+        const size_t cyp = kp + (size_t)jp * nx + i, cym = kp + (size_t)jm * nx + i;
+        const int il = (i == 0) ? nx - 1 : i - 1, ir = (i + 4 == nx) ? 0 : i + 4;
+        const float4 d = ld4(delta + c);
+        const float dl = delta[rowoff + il], dr = delta[rowoff + ir];
+        const float4 cx = ld4(fc.cxf + c);
+        const float cxr = fc.cxf[rowoff + ir];
+        const float4 dyp = ld4(delta + cyp), dym = ld4(delta + cym);
+        const float4 cyp4 = ld4(fc.cyf + cyp), cym4 = ld4(fc.cyf + c);
+        const bool up = k + 1 < nz, dn = k > 0;
+        float4 dzp = d, czp = make_float4(0.f, 0.f, 0.f, 0.f), dzm = d, czm = czp;
+        if (up) { dzp = ld4(delta + c + plane); czp = ld4(fc.czf + c + plane); }
+        if (dn) { dzm = ld4(delta + c - plane); czm = ld4(fc.czf + c); }
+        float4 e = ld4(E + c);
+        const float4 rh = scale_rho && !const_scale ? ld4(fc.rhof + c) : make_float4(rt_f, rt_f, rt_f, rt_f);
+        const float idzf = g.inv_dzf_f[k];
+        auto cell = [&](float dc, float dxm, float dxp, float cxm, float cxp, float dypv, float cypv,
+                        float dymv, float cymv, float dzpv, float czpv, float dzmv, float czmv, float& ev,
+                        float rhv) -> float {
+          float t = cxp * (dxp - dc);
+          t = fmaf(cxm, dxm - dc, t);
+          t = fmaf(cypv, dypv - dc, t);
+          t = fmaf(cymv, dymv - dc, t);
+          t = fmaf(czpv, dzpv - dc, t);
+          t = fmaf(czmv, dzmv - dc, t);
+          ev = ev - t;
+          const float ee = ev * idzf;
+          s2 = fmaf(ee, ee, s2);
+          s1 += fabsf(ee);
+          return scale_rho ? rhv * ee : ee;
+        };
+        r.x = cell(d.x, dl, d.y, cx.x, cx.y, dyp.x, cyp4.x, dym.x, cym4.x, dzp.x, czp.x, dzm.x, czm.x, e.x, rh.x);
+        r.y = cell(d.y, d.x, d.z, cx.y, cx.z, dyp.y, cyp4.y, dym.y, cym4.y, dzp.y, czp.y, dzm.y, czm.y, e.y, rh.y);
+        r.z = cell(d.z, d.y, d.w, cx.z, cx.w, dyp.z, cyp4.z, dym.z, cym4.z, dzp.z, czp.z, dzm.z, czm.z, e.z, rh.z);
+        r.w = cell(d.w, d.z, dr, cx.w, cxr, dyp.w, cyp4.w, dym.w, cym4.w, dzp.w, czp.w, dzm.w, czm.w, e.w, rh.w);
+        *reinterpret_cast<float4*>(E + c) = e;
+      }
+      rr[h] = r;
+    }
+    float4* dst = reinterpret_cast<float4*>(bufA + (size_t)qp * nx + i);
+    dst[0] = make_float4(rr[0].x, rr[1].x, rr[0].y, rr[1].y);
+    dst[1] = make_float4(rr[0].z, rr[1].z, rr[0].w, rr[1].w);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Residual of the variable-coefficient equation and forward real x transform.
 //   mode 0: r = f (constant-coefficient solve)
 //   mode 1: e = (D u^s - S_c)/dt, evaluated in FP64 in the row-scaled form
@@ -110,7 +186,15 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
   const int tpr = nx < (int)blockDim.x ? nx : (int)blockDim.x;
   const int rows_par = blockDim.x / tpr;
   const int qoff = threadIdx.x / tpr, i0 = threadIdx.x - qoff * tpr;
-  for (int q = qoff; q < rpb && qoff < rows_par; q += rows_par) {
+  const bool vec = update && sizeof(T) == sizeof(float) && (nx & 3) == 0;
+  if (vec) {
+    float a2 = 0.f, a1 = 0.f;
+    resid_update_vec4(g, fc, E, delta, scale_rho, const_scale, rt_f, row0, rpb,
+                      reinterpret_cast<float2*>(bufA), a2, a1);
+    s2 = (T)a2;
+    s1 = (T)a1;
+  }
+  for (int q = qoff; !vec && q < rpb && qoff < rows_par; q += rows_par) {
     const int row = (int)row0 + q;
     const bool valid = row < nrows;
     const int k = valid ? row / ny : 0, j = valid ? row - k * ny : 0;

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libpp_gb300.so")
 PP_OK, PP_ERR_INVALID_ARG, PP_ERR_UNSUPPORTED, PP_ERR_NOT_CONVERGED = 0, 1, 2, 3
 PP_ERR_NUMERIC, PP_ERR_CUDA, PP_ERR_OOM, PP_ERR_TOO_LARGE = 4, 5, 6, 7
 PP_BC_PERIODIC, PP_BC_WALL = 0, 1
-PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_fp32": 1, "mixed_tc": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_fp32": 1, "mixed_tc": 2, "mixed_z64": 3}
 # iterations of Sec. 3.3.1: Method III (Eq. new_poisson), I (Eq. poisson_me1), II (Eq. poisson_laizet)
 METHODS = {"III": 0, "I": 1, "II": 2}
 

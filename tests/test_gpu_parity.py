@@ -164,14 +164,15 @@ def test_projection_fp64_converged_vs_oracle(pp, n, ratio, stretched, nz):
     assert np.linalg.norm(orc.divergence(g, u, v, ww) - Sc) <= 1.0001e-12 * np.linalg.norm(d0)
 
 
-@pytest.mark.parametrize("stretched", [False, True])
-def test_projection_mixed_vs_oracle(pp, stretched):
+@pytest.mark.parametrize("stretched,precision", [(False, "mixed"), (True, "mixed"), (True, "mixed_z64")])
+def test_projection_mixed_vs_oracle(pp, stretched, precision):
     """Mixed precision + FP64 residual: reaches 1e-10 and matches the FP64
-    oracle's converged solution."""
+    oracle's converged solution (mixed_z64: FP64 recurrences in every z
+    column)."""
     w, rho = _sphere_case(48, 1000.0, stretched, 40)
     g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf)
     p0, u0, v0, w0, _ = orc.method3(g, w.us, w.vs, w.ws, rho, w.S, w.dt, rtol=1e-13, maxit=3000)
-    info, p, u, v, ww = _run_gpu(pp, w, rho, "mixed", rtol=1e-10, maxit=3000)
+    info, p, u, v, ww = _run_gpu(pp, w, rho, precision, rtol=1e-10, maxit=3000)
     assert info["status"] == 0 and info["res_final"] <= 1e-10
     Sc = w.S - orc.volume_mean(g, w.S)
     d0 = orc.divergence(g, w.us, w.vs, w.ws) - Sc
