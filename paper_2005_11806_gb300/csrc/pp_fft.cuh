@@ -229,6 +229,82 @@ __device__ __forceinline__ C2<T>* fft_block_fixed(C2<T>* a, C2<T>* b, const C2<T
   return src;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 fast path for the compile-time power-of-two shapes.  Buffers and the
+// twiddle table are addressed by element offsets into the block's dynamic
+// shared memory (one float2 array), so every access is a 32-bit shared
+// access whose constant strides fold into immediate offsets; pointers chosen
+// at run time (rotating buffers) would leave the compiler generic 64-bit
+// addressing.  The twiddle table tw[m] = (cos, sin)(2 pi m / N), m < N,
+// sits in shared memory too.  A radix-8 butterfly loads w, w^2 and w^4 from
+// it and forms w^3, w^5, w^6, w^7 by complex products.
+__device__ __forceinline__ float2* smem_f2() {
+  extern __shared__ __align__(16) float2 pp_dyn_smem_f2[];
+  return pp_dyn_smem_f2;
+}
+
+template <int DIR>
+__device__ __forceinline__ float2 tw_dir(float2 w) { return make_float2(w.x, DIR > 0 ? w.y : -w.y); }
+
+template <int DIR, int R, bool BATCH_FAST, int N, int NS, int NBATCH, int ES, int BS>
+__device__ __forceinline__ void fft_pass_smem(int src, int dst, int twb, int tid, int nth) {
+  float2* S = smem_f2();
+  constexpr int NB = N / R;
+  constexpr int TOTAL = NB * NBATCH;
+  constexpr int TWS = N / (NS * R);
+  for (int t = tid; t < TOTAL; t += nth) {
+    int bi, j;
+    if (BATCH_FAST) { j = t / NBATCH; bi = t % NBATCH; }
+    else { bi = t / NB; j = t % NB; }
+    const int k = j % NS;
+    const int sb = src + bi * BS + j * ES;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = S[sb + r * NB * ES];
+    if (NS > 1) {
+      const int tk = twb + k * TWS;
+      float2 w[R];
+      w[1] = tw_dir<DIR>(S[tk]);
+      if (R >= 4) {
+        w[2] = tw_dir<DIR>(S[tk + k * TWS]);
+        w[3] = cmul<float>(w[1], w[2]);
+      }
+      if (R == 8) {
+        w[4] = tw_dir<DIR>(S[tk + 3 * k * TWS]);
+        w[5] = cmul<float>(w[1], w[4]);
+        w[6] = cmul<float>(w[2], w[4]);
+        w[7] = cmul<float>(w[3], w[4]);
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul<float>(v[r], w[r]);
+    }
+    Dft<float, DIR, R>::run(v);
+    const int db = dst + bi * BS + ((j / NS) * NS * R + k) * ES;
+#pragma unroll
+    for (int r = 0; r < R; ++r) S[db + r * NS * ES] = v[r];
+  }
+}
+
+template <int DIR, bool BATCH_FAST, int N, int NBATCH, int ES, int BS, int S_, int NS>
+__device__ __forceinline__ void fft_smem_from(int& src, int& dst, int twb, int tid, int nth) {
+  if constexpr (S_ < Pow2Passes<N>::value) {
+    constexpr int R = Pow2Radix<N, S_>::value;
+    fft_pass_smem<DIR, R, BATCH_FAST, N, NS, NBATCH, ES, BS>(src, dst, twb, tid, nth);
+    __syncthreads();
+    const int t = src; src = dst; dst = t;
+    fft_smem_from<DIR, BATCH_FAST, N, NBATCH, ES, BS, S_ + 1, NS * R>(src, dst, twb, tid, nth);
+  }
+}
+
+// Full transform on buffers at element offsets a and b; returns the offset
+// of the buffer holding the result.  Every thread of the block calls it.
+template <int DIR, bool BATCH_FAST, int N, int NBATCH, int ES, int BS>
+__device__ __forceinline__ int fft_block_smem(int a, int b, int twb, int tid, int nth) {
+  int src = a, dst = b;
+  fft_smem_from<DIR, BATCH_FAST, N, NBATCH, ES, BS, 0, 1>(src, dst, twb, tid, nth);
+  return src;
+}
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* sh) {
   // sh: at least 32 entries

@@ -6,6 +6,8 @@
 // The single-grid kernels (pp_kernels_fft.cu) and the grouped multi-grid
 // kernels (pp_batch.cu) both call these.
 #pragma once
+#include <type_traits>
+
 #include "pp_fft.cuh"
 
 namespace pp {
@@ -69,6 +71,54 @@ __device__ __forceinline__ C2<T>* fft_dispatch(C2<T>* a, C2<T>* b, const FftDesc
 }
 #undef PP_TRY_FIXED
 
+// FP32 fast path (fft_block_smem) for the same shapes; returns the element
+// offset of the result buffer, or -1 when the shape has no fast path (the
+// caller then runs fft_dispatch).  twb: offset of the N-entry twiddle table.
+#define PP_TRY_SMEM(NN, NBB)                                                                        \
+  if (n == NN && nbatch == NBB) {                                                                   \
+    if (BATCH_FAST) return fft_block_smem<DIR, true, NN, NBB, NBB, 1>(a, b, twb, tid, nth);         \
+    return fft_block_smem<DIR, false, NN, NBB, 1, NN>(a, b, twb, tid, nth);                         \
+  }
+
+template <int DIR, bool BATCH_FAST>
+__device__ __forceinline__ int fft_dispatch_smem(int a, int b, int twb, const FftDesc& d, int nbatch, int es,
+                                                 int bs, int tid, int nth) {
+  const int n = d.n;
+  const bool shape_ok = BATCH_FAST ? (es == nbatch && bs == 1) : (es == 1 && bs == n);
+  if (!shape_ok) return -1;
+  if (BATCH_FAST) {
+    PP_TRY_SMEM(512, 4)
+    PP_TRY_SMEM(256, 8)
+    PP_TRY_SMEM(128, 16)
+    PP_TRY_SMEM(128, 8)
+    PP_TRY_SMEM(64, 16)
+    PP_TRY_SMEM(64, 8)
+  } else {
+    PP_TRY_SMEM(512, 4)
+    PP_TRY_SMEM(256, 8)
+    PP_TRY_SMEM(128, 16)
+    PP_TRY_SMEM(64, 32)
+    PP_TRY_SMEM(32, 32)
+  }
+  return -1;
+}
+#undef PP_TRY_SMEM
+
+// Whether fft_dispatch_smem has a fast path for this shape (host and device).
+__host__ __device__ inline bool fft_smem_shape(int n, int nbatch, bool batch_fast) {
+  if (batch_fast)
+    return (n == 512 && nbatch == 4) || (n == 256 && nbatch == 8) || (n == 128 && (nbatch == 16 || nbatch == 8)) ||
+           (n == 64 && (nbatch == 16 || nbatch == 8));
+  return (n == 512 && nbatch == 4) || (n == 256 && nbatch == 8) || (n == 128 && nbatch == 16) ||
+         (n == 64 && nbatch == 32) || (n == 32 && nbatch == 32);
+}
+
+// Copies the N-entry twiddle table into shared memory at element offset twb.
+__device__ __forceinline__ void load_twiddles_smem(const float2* __restrict__ tw, int n, int twb) {
+  float2* S = smem_f2();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S[twb + i] = tw[i];
+}
+
 // ---------------------------------------------------------------------------
 // Update pass of the mixed residual for nx % 4 == 0, vectorised: each thread
 // takes the two rows of one complex sequence and four consecutive cells of
@@ -87,8 +137,9 @@ __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc,
   const size_t plane = (size_t)nx * ny;
   const int t4 = nx >> 2;
   const int npairs = rpb >> 1;
+  const int lg4 = ((t4 & (t4 - 1)) == 0) ? 31 - __clz(t4) : -1;
   for (int w = threadIdx.x; w < npairs * t4; w += blockDim.x) {
-    const int qp = w / t4;
+    const int qp = lg4 >= 0 ? (w >> lg4) : w / t4;
     const int i = (w - qp * t4) << 2;
     float4 rr[2];
 #pragma unroll
@@ -187,6 +238,13 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
   const int rows_par = blockDim.x / tpr;
   const int qoff = threadIdx.x / tpr, i0 = threadIdx.x - qoff * tpr;
   const bool vec = update && sizeof(T) == sizeof(float) && (nx & 3) == 0;
+  // FP32 fast transform: twiddle table after the two buffers
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const int twb = 2 * nseq * nx;
+  const bool fast = F32 && fft_smem_shape(nx, nseq, false);
+  if constexpr (F32) {
+    if (fast) load_twiddles_smem(twx, nx, twb);
+  }
   if (vec) {
     float a2 = 0.f, a1 = 0.f;
     resid_update_vec4(g, fc, E, delta, scale_rho, const_scale, rt_f, row0, rpb,
@@ -268,9 +326,17 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
     }
   }
   __syncthreads();
-  const C2<T>* res = fft_dispatch<T, -1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
-  for (int t = threadIdx.x; t < nseq * nxh; t += blockDim.x) {
-    const int q = t / nxh, kx = t - q * nxh;
+  const C2<T>* res = nullptr;
+  if constexpr (F32) {
+    if (fast)
+      res = smem_f2() + fft_dispatch_smem<-1, false>(0, nseq * nx, twb, fx, nseq, 1, nx, threadIdx.x, blockDim.x);
+  }
+  if (!fast) res = fft_dispatch<T, -1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
+  // (q, kx) walked incrementally: no division by the odd nxh per element
+  int q = threadIdx.x / nxh, kx = threadIdx.x - q * nxh;
+  const int dq = blockDim.x / nxh, dkx = blockDim.x - dq * nxh;
+  for (; q < nseq; q += dq, kx += dkx) {
+    if (kx >= nxh) { kx -= nxh; ++q; if (q >= nseq) break; }
     const C2<T> Z = res[(size_t)q * nx + kx];
     const int km = (kx == 0) ? 0 : nx - kx;
     const C2<T> W = res[(size_t)q * nx + km];
@@ -294,6 +360,12 @@ __device__ __forceinline__ void stage_ffty(const Geo& g, const FftDesc& fy, cons
   C2<T>* bufB = bufA + (size_t)ny * tx;
   const int kx0 = bx * tx;
   const size_t base = (size_t)bz * ny * nxh;
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const int twb = 2 * ny * tx;
+  const bool fast = F32 && fft_smem_shape(ny, tx, true);
+  if constexpr (F32) {
+    if (fast) load_twiddles_smem(twy, ny, twb);
+  }
   for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
     const int y = t / tx, x = t - y * tx;
     C2<T> v; v.x = (T)0; v.y = (T)0;
@@ -301,7 +373,11 @@ __device__ __forceinline__ void stage_ffty(const Geo& g, const FftDesc& fy, cons
     bufA[t] = v;
   }
   __syncthreads();
-  const C2<T>* res = fft_dispatch<T, DIR, true>(bufA, bufB, fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
+  const C2<T>* res = nullptr;
+  if constexpr (F32) {
+    if (fast) res = smem_f2() + fft_dispatch_smem<DIR, true>(0, ny * tx, twb, fy, tx, tx, 1, threadIdx.x, blockDim.x);
+  }
+  if (!fast) res = fft_dispatch<T, DIR, true>(bufA, bufB, fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
   for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
     const int y = t / tx, x = t - y * tx;
     if (kx0 + x < nxh) spec[base + (size_t)y * nxh + kx0 + x] = res[t];
@@ -350,17 +426,28 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
                                                       unsigned char* smem_raw) {
   const int ny = g.ny, nxh = g.nxh;
   const int ntx = (nxh + tx - 1) / tx;
-  const size_t tsz = (size_t)ny * tx;
-  C2<T>* X[3] = {reinterpret_cast<C2<T>*>(smem_raw), reinterpret_cast<C2<T>*>(smem_raw) + tsz,
-                 reinterpret_cast<C2<T>*>(smem_raw) + 2 * tsz};
-  int L = 0, Q = 1, F = 2;
-  if (first < ntiles) ffty_issue_tile<T>(g, spec, tx, ntx, first, X[L]);
+  const int tsz = ny * tx;
+  C2<T>* X0 = reinterpret_cast<C2<T>*>(smem_raw);
+  // element offsets of the three buffers, rotated (no pointer array: the
+  // transforms then address shared memory directly)
+  int L = 0, Q = tsz, F = 2 * tsz;
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const int twb = 3 * tsz;
+  const bool fast = F32 && fft_smem_shape(ny, tx, true);
+  if constexpr (F32) {
+    if (fast) load_twiddles_smem(twy, ny, twb);
+  }
+  if (first < ntiles) ffty_issue_tile<T>(g, spec, tx, ntx, first, X0 + L);
   for (long long tile = first; tile < ntiles; tile += stride) {
     cp_async_wait_all();
     __syncthreads();
     const long long next = tile + stride;
-    if (next < ntiles) ffty_issue_tile<T>(g, spec, tx, ntx, next, X[F]);
-    const C2<T>* res = fft_dispatch<T, DIR, true>(X[L], X[Q], fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
+    if (next < ntiles) ffty_issue_tile<T>(g, spec, tx, ntx, next, X0 + F);
+    const C2<T>* res = nullptr;
+    if constexpr (F32) {
+      if (fast) res = smem_f2() + fft_dispatch_smem<DIR, true>(L, Q, twb, fy, tx, tx, 1, threadIdx.x, blockDim.x);
+    }
+    if (!fast) res = fft_dispatch<T, DIR, true>(X0 + L, X0 + Q, fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
     const int bz = (int)(tile / ntx), bx = (int)(tile - (long long)bz * ntx);
     const int kx0 = bx * tx;
     const size_t base = (size_t)bz * ny * nxh;
@@ -774,6 +861,12 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
   const int lgx = ((nx & (nx - 1)) == 0) ? 31 - __clz(nx) : -1;
   const bool lazy = sdelta != nullptr;
   const bool need_p = !p_zero && (!lazy || fold);   // p is read
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const int twb = 2 * nseq * nx;
+  const bool fast = F32 && fft_smem_shape(nx, nseq, false);
+  if constexpr (F32) {
+    if (fast) load_twiddles_smem(twx, nx, twb);
+  }
   const bool need_s = lazy && !fresh;               // sdelta is read
   auto split = [&](int t, int& q, int& i) {
     if (lgx >= 0) { q = t >> lgx; i = t & (nx - 1); }
@@ -824,7 +917,11 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
     bufA[t] = Z;
   }
   __syncthreads();
-  const C2<T>* res = fft_dispatch<T, 1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
+  const C2<T>* res = nullptr;
+  if constexpr (F32) {
+    if (fast) res = smem_f2() + fft_dispatch_smem<1, false>(0, nseq * nx, twb, fx, nseq, 1, nx, threadIdx.x, blockDim.x);
+  }
+  if (!fast) res = fft_dispatch<T, 1, false>(bufA, bufB, fx, nseq, 1, nx, twx, threadIdx.x, blockDim.x);
 #pragma unroll
   for (int u = 0; u < NP; ++u) {
     const int t = threadIdx.x + u * blockDim.x;
