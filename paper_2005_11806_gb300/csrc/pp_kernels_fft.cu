@@ -25,7 +25,9 @@ __global__ void __launch_bounds__(256, 4) k_resid_fftx(Geo g, Faces fc, FftDesc 
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(256) k_ffty(Geo g, FftDesc fy, const C2<T>* __restrict__ twy,
+// Three blocks per SM (FP32: 52 KB of buffers each at ny = 512) measured
+// faster than four; the bound also keeps the register count from deciding it.
+__global__ void __launch_bounds__(256, sizeof(T) == sizeof(float) ? 3 : 2) k_ffty(Geo g, FftDesc fy, const C2<T>* __restrict__ twy,
                                               C2<T>* __restrict__ spec, int tx, long long ntiles,
                                               const DevStatus* __restrict__ st) {
   if (stopped(st)) return;
@@ -122,22 +124,19 @@ cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>
   const int tx = ffty_tile(g.ny, sizeof(C2<T>), kEpt);
   const size_t smem = (size_t)3 * g.ny * tx * sizeof(C2<T>) + (sizeof(T) == sizeof(float) ? g.ny * sizeof(float2) : 0);
   const long long ntiles = (long long)((g.nxh + tx - 1) / tx) * g.nz;
-  // persistent grid: as many blocks as fit on the GPU at this shared-memory size
-  int per_sm = (int)((200 * 1024) / smem);
+  // persistent grid: exactly the blocks that are resident at once (shared
+  // memory and registers both counted), so no block waits for a second wave
+  auto kern = inverse ? k_ffty<T, 1> : k_ffty<T, -1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, nsm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem)) != cudaSuccess) return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 8) per_sm = 8;
-  long long nblk = (long long)152 * per_sm;
+  long long nblk = (long long)nsm * per_sm;
   if (nblk > ntiles) nblk = ntiles;
-  cudaError_t e;
-  if (inverse) {
-    e = cudaFuncSetAttribute(k_ffty<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_ffty<T, 1><<<(int)nblk, kThreads, smem, s>>>(g, fy, twy, spec, tx, ntiles, st);
-  } else {
-    e = cudaFuncSetAttribute(k_ffty<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_ffty<T, -1><<<(int)nblk, kThreads, smem, s>>>(g, fy, twy, spec, tx, ntiles, st);
-  }
+  kern<<<(int)nblk, kThreads, smem, s>>>(g, fy, twy, spec, tx, ntiles, st);
   return cudaGetLastError();
 }
 

@@ -360,6 +360,7 @@ __device__ __forceinline__ void stage_ffty(const Geo& g, const FftDesc& fy, cons
   C2<T>* bufB = bufA + (size_t)ny * tx;
   const int kx0 = bx * tx;
   const size_t base = (size_t)bz * ny * nxh;
+  const int lg_tx = 31 - __clz(tx);  // tx is a power of two (ffty_tile)
   constexpr bool F32 = std::is_same<T, float>::value;
   const int twb = 2 * ny * tx;
   const bool fast = F32 && fft_smem_shape(ny, tx, true);
@@ -367,7 +368,7 @@ __device__ __forceinline__ void stage_ffty(const Geo& g, const FftDesc& fy, cons
     if (fast) load_twiddles_smem(twy, ny, twb);
   }
   for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
-    const int y = t / tx, x = t - y * tx;
+    const int y = t >> lg_tx, x = t & (tx - 1);
     C2<T> v; v.x = (T)0; v.y = (T)0;
     if (kx0 + x < nxh) v = spec[base + (size_t)y * nxh + kx0 + x];
     bufA[t] = v;
@@ -379,7 +380,7 @@ __device__ __forceinline__ void stage_ffty(const Geo& g, const FftDesc& fy, cons
   }
   if (!fast) res = fft_dispatch<T, DIR, true>(bufA, bufB, fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
   for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
-    const int y = t / tx, x = t - y * tx;
+    const int y = t >> lg_tx, x = t & (tx - 1);
     if (kx0 + x < nxh) spec[base + (size_t)y * nxh + kx0 + x] = res[t];
   }
 }
@@ -402,8 +403,9 @@ __device__ __forceinline__ void ffty_issue_tile(const Geo& g, const C2<T>* __res
   const int bz = (int)(tile / ntx), bx = (int)(tile - (long long)bz * ntx);
   const int kx0 = bx * tx;
   const size_t base = (size_t)bz * ny * nxh;
+  const int lg_tx = 31 - __clz(tx);  // tx is a power of two (ffty_tile)
   for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
-    const int y = t / tx, x = t - y * tx;
+    const int y = t >> lg_tx, x = t & (tx - 1);
     if (kx0 + x < nxh) {
       if (sizeof(C2<T>) == 8) cp_async8(&buf[t], &spec[base + (size_t)y * nxh + kx0 + x]);
       else {
@@ -427,6 +429,7 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
   const int ny = g.ny, nxh = g.nxh;
   const int ntx = (nxh + tx - 1) / tx;
   const int tsz = ny * tx;
+  const int lg_tx = 31 - __clz(tx);  // tx is a power of two (ffty_tile)
   C2<T>* X0 = reinterpret_cast<C2<T>*>(smem_raw);
   // element offsets of the three buffers, rotated (no pointer array: the
   // transforms then address shared memory directly)
@@ -452,7 +455,7 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
     const int kx0 = bx * tx;
     const size_t base = (size_t)bz * ny * nxh;
     for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
-      const int y = t / tx, x = t - y * tx;
+      const int y = t >> lg_tx, x = t & (tx - 1);
       if (kx0 + x < nxh) spec[base + (size_t)y * nxh + kx0 + x] = res[t];
     }
     __syncthreads();
