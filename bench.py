@@ -132,9 +132,9 @@ class ClockSampler:
 def algorithmic(kernel, w, precision):
     """Algorithmic bytes and FP64 flops of one launch of each kernel (what
     the step must move: every field read or written once per launch).  Mixed
-    plans recompute the residual exactly every 10th pass and update it in the
+    plans recompute the residual exactly every 20th pass and update it in the
     others, and bring p up to date only before an exact residual, so the
-    residual and inverse-x figures are averages over that 10-pass cycle."""
+    residual and inverse-x figures are averages over that 20-pass cycle."""
     npts = w.nx * w.ny * w.nz
     nsp = (w.nx // 2 + 1) * w.ny * w.nz
     cs = 16 if precision == "fp64" else 8  # bytes per spectral complex value
@@ -144,7 +144,7 @@ def algorithmic(kernel, w, precision):
             return {"bytes": 56 * npts + cs * nsp, "fp64_flops": 19 * npts + 45 * npts}
         exact = 56 * npts     # b, p, cx, cy, cz, diag (FP64), rhof; E written (FP32)
         update = 28 * npts    # E read + write, delta, cxf, cyf, czf, rhof (FP32)
-        return {"bytes": int(0.1 * exact + 0.9 * update) + cs * nsp, "fp64_flops": int(0.1 * 15 * npts)}
+        return {"bytes": int(0.05 * exact + 0.95 * update) + cs * nsp, "fp64_flops": int(0.05 * 15 * npts)}
     if kernel in ("ffty_fwd", "ffty_inv"):
         return {"bytes": 2 * cs * nsp, "fp64_flops": 0 if precision != "fp64" else 45 * npts}
     if kernel == "tridiag_z":
@@ -161,8 +161,8 @@ def algorithmic(kernel, w, precision):
         fold = 24 * npts      # p read + write (FP64), sum of increments read, increment written
         fresh = 8 * npts      # sum of increments written, increment written
         accum = 12 * npts     # sum of increments read + written, increment written
-        return {"bytes": int(0.1 * fold + 0.1 * fresh + 0.8 * accum) + cs * nsp,
-                "fp64_flops": int(0.1 * 2 * npts)}
+        return {"bytes": int(0.05 * fold + 0.05 * fresh + 0.9 * accum) + cs * nsp,
+                "fp64_flops": int(0.05 * 2 * npts)}
     return None
 
 

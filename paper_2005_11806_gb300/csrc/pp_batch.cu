@@ -21,7 +21,7 @@ namespace {
 
 constexpr int kChunk = 2048;  // cells per block of the elementwise grouped kernels
 constexpr int kTriThreads = 128;
-constexpr int kExactEveryBatch = 10;
+constexpr int kExactEveryBatch = 20;
 
 struct GridDev {
   Geo g;
@@ -137,7 +137,7 @@ __global__ void kb_correct(GridDev* G, const int2* __restrict__ work) {
   PP_CHUNK_LOOP(d, w) cell_correct(d.g, d.fc, d.us, d.vs, d.ws, d.p, d.dt, d.u, d.v, d.w, c);
 }
 
-__global__ void __launch_bounds__(256) kb_resid(GridDev* G, const int2* __restrict__ work) {
+__global__ void __launch_bounds__(256, 4) kb_resid(GridDev* G, const int2* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int2 w = work[blockIdx.x];
   const GridDev& d = G[w.x];

@@ -318,11 +318,13 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
     }
   }
   if (mode != 0) {
-    const double a2 = block_sum<double>((double)s2, shred);
-    const double a1 = block_sum<double>((double)s1, shred);
+    // block partial sums of e^2 and |e|: in the arithmetic's own precision
+    // (FP32 shuffles on mixed plans: the FP64 pipe is the scarce one)
+    const T a2 = block_sum<T>(s2, reinterpret_cast<T*>(shred));
+    const T a1 = block_sum<T>(s1, reinterpret_cast<T*>(shred));
     if (threadIdx.x == 0) {
-      red[2 * (size_t)blk] = a2;
-      red[2 * (size_t)blk + 1] = a1;
+      red[2 * (size_t)blk] = (double)a2;
+      red[2 * (size_t)blk + 1] = (double)a1;
     }
   }
   __syncthreads();
@@ -845,13 +847,17 @@ __device__ __forceinline__ void stage_tridiag_mixed(const Geo& g, const double* 
 //   else: sdelta = increment (fresh: p was updated last pass) or
 //         sdelta += increment.
 // With fresh set, fold ignores sdelta.
-template <typename T>
-__device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
-                                               const C2<T>* __restrict__ twx,
-                                               const C2<T>* __restrict__ spec, double scale,
-                                               double* __restrict__ p, int p_zero, int rpb, int blk,
-                                               T* __restrict__ delta, float* __restrict__ sdelta,
-                                               bool fold, bool fresh, unsigned char* smem_raw) {
+// Update modes of the inverse x stage (compile-time, so each pass runs only
+// its own arithmetic).
+enum InvMode { kInvPlain = 0, kInvFold = 1, kInvFoldFresh = 2, kInvFresh = 3, kInvAccum = 4 };
+
+template <typename T, int MODE>
+__device__ __forceinline__ void stage_fftx_inv_m(const Geo& g, const FftDesc& fx,
+                                                 const C2<T>* __restrict__ twx,
+                                                 const C2<T>* __restrict__ spec, double scale,
+                                                 double* __restrict__ p, int p_zero, int rpb, int blk,
+                                                 T* __restrict__ delta, float* __restrict__ sdelta,
+                                                 unsigned char* smem_raw) {
   const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
   const int nseq = rpb >> 1;
   const float scale_f = (float)scale;
@@ -862,31 +868,34 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
   const bool even = (nx & 1) == 0;
   const int nout = rpb * nx;
   const int lgx = ((nx & (nx - 1)) == 0) ? 31 - __clz(nx) : -1;
-  const bool lazy = sdelta != nullptr;
-  const bool need_p = !p_zero && (!lazy || fold);   // p is read
+  const bool need_p = !p_zero && MODE <= kInvFoldFresh;            // p is read
+  constexpr bool need_s = MODE == kInvFold || MODE == kInvAccum;  // sdelta is read
+  // p is prefetched in the plain mode of FP64 plans (every pass); the fold
+  // passes of mixed plans (one in twenty) read it where it is used, which keeps
+  // their registers within the other modes' budget
+  const bool pre_p = need_p && MODE == kInvPlain && sizeof(T) == sizeof(double);
   constexpr bool F32 = std::is_same<T, float>::value;
   const int twb = 2 * nseq * nx;
   const bool fast = F32 && fft_smem_shape(nx, nseq, false);
   if constexpr (F32) {
     if (fast) load_twiddles_smem(twx, nx, twb);
   }
-  const bool need_s = lazy && !fresh;               // sdelta is read
   auto split = [&](int t, int& q, int& i) {
     if (lgx >= 0) { q = t >> lgx; i = t & (nx - 1); }
     else { q = t / nx; i = t - q * nx; }
   };
   // one output value: zv = unscaled inverse transform at cell c
   auto emit = [&](size_t c, T zv, double pv, float sv) {
-    const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
     const float inc_f = scale_f * (float)zv;
-    if (!lazy) {
-      p[c] = fma(scale, zd, pv);
-    } else if (fold) {
-      p[c] = fma(scale, zd, pv + widen_f32(sv));
+    if constexpr (MODE <= kInvFoldFresh) {
+      const double zd = (sizeof(T) == sizeof(float)) ? widen_f32((float)zv) : (double)zv;
+      if constexpr (MODE == kInvFold) p[c] = fma(scale, zd, pv + widen_f32(sv));
+      else p[c] = fma(scale, zd, pv);
+      if (delta != nullptr) delta[c] = (sizeof(T) == sizeof(float)) ? (T)inc_f : (T)(scale * zd);
     } else {
-      sdelta[c] = sv + inc_f;
+      sdelta[c] = (MODE == kInvAccum) ? sv + inc_f : inc_f;
+      if (delta != nullptr) delta[c] = (T)inc_f;
     }
-    if (delta != nullptr) delta[c] = (sizeof(T) == sizeof(float)) ? (T)inc_f : (T)(scale * zd);
   };
   constexpr int NP = kPrefetchInv;
   double pv[NP];
@@ -899,7 +908,7 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
     pv[u] = 0.0;
     sv[u] = 0.f;
     const bool in = t < nout && row0 + q < nrows;
-    if (need_p && in) pv[u] = p[(size_t)(row0 + q) * nx + i];
+    if (pre_p && in) pv[u] = p[(size_t)(row0 + q) * nx + i];
     if (need_s && in) sv[u] = sdelta[(size_t)(row0 + q) * nx + i];
   }
   for (int t = threadIdx.x; t < nseq * nx; t += blockDim.x) {
@@ -933,7 +942,8 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
     const long row = row0 + q;
     if (t < nout && row < nrows) {
       const C2<T> z = res[(size_t)(q >> 1) * nx + i];
-      emit((size_t)row * nx + i, (q & 1) ? z.y : z.x, pv[u], sv[u]);
+      const size_t c = (size_t)row * nx + i;
+      emit(c, (q & 1) ? z.y : z.x, pre_p ? pv[u] : (need_p ? p[c] : 0.0), sv[u]);
     }
   }
   for (int t = threadIdx.x + NP * blockDim.x; t < nout; t += blockDim.x) {  // beyond the prefetch
@@ -946,6 +956,28 @@ __device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx,
       emit(c, (q & 1) ? z.y : z.x, need_p ? p[c] : 0.0, need_s ? sdelta[c] : 0.f);
     }
   }
+}
+
+// Mode dispatch (block-uniform): sdelta null -> plain update of p.
+template <typename T>
+__device__ __forceinline__ void stage_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* __restrict__ twx,
+                                               const C2<T>* __restrict__ spec, double scale,
+                                               double* __restrict__ p, int p_zero, int rpb, int blk,
+                                               T* __restrict__ delta, float* __restrict__ sdelta,
+                                               bool fold, bool fresh, unsigned char* smem_raw) {
+  if (sizeof(T) == sizeof(double) || sdelta == nullptr) {  // FP64 plans: plain only
+    stage_fftx_inv_m<T, kInvPlain>(g, fx, twx, spec, scale, p, p_zero, rpb, blk, delta, sdelta, smem_raw);
+    return;
+  }
+  if constexpr (sizeof(T) == sizeof(double)) return;
+  if (fold && !fresh)
+    stage_fftx_inv_m<T, kInvFold>(g, fx, twx, spec, scale, p, p_zero, rpb, blk, delta, sdelta, smem_raw);
+  else if (fold)
+    stage_fftx_inv_m<T, kInvFoldFresh>(g, fx, twx, spec, scale, p, p_zero, rpb, blk, delta, sdelta, smem_raw);
+  else if (fresh)
+    stage_fftx_inv_m<T, kInvFresh>(g, fx, twx, spec, scale, p, p_zero, rpb, blk, delta, sdelta, smem_raw);
+  else
+    stage_fftx_inv_m<T, kInvAccum>(g, fx, twx, spec, scale, p, p_zero, rpb, blk, delta, sdelta, smem_raw);
 }
 
 }  // namespace pp
