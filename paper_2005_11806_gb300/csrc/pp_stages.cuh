@@ -911,22 +911,35 @@ __device__ __forceinline__ void stage_fftx_inv_m(const Geo& g, const FftDesc& fx
     if (pre_p && in) pv[u] = p[(size_t)(row0 + q) * nx + i];
     if (need_s && in) sv[u] = sdelta[(size_t)(row0 + q) * nx + i];
   }
-  for (int t = threadIdx.x; t < nseq * nx; t += blockDim.x) {
-    int q, kx;
-    split(t, q, kx);
-    const long ra = row0 + 2 * q;
-    const bool upper = kx >= nxh;
-    const int m = upper ? nx - kx : kx;
-    C2<T> A, B;
-    A.x = A.y = B.x = B.y = (T)0;
-    if (ra < nrows) A = spec[(size_t)ra * nxh + m];
-    if (ra + 1 < nrows) B = spec[(size_t)(ra + 1) * nxh + m];
-    if (m == 0 || (even && m == nx / 2)) { A.y = (T)0; B.y = (T)0; }
-    if (upper) { A.y = -A.y; B.y = -B.y; }
-    C2<T> Z;
-    Z.x = A.x - B.y;
-    Z.y = A.y + B.x;
-    bufA[t] = Z;
+  // Z = A + i B from the two half spectra; each stored coefficient m also
+  // gives its mirror nx - m (conjugates), so it is loaded once.  (q, m) is
+  // walked incrementally over the nseq x nxh stored coefficients.
+  {
+    int q = threadIdx.x / nxh, m = threadIdx.x - q * nxh;
+    const int dq = blockDim.x / nxh, dm = blockDim.x - dq * nxh;
+    for (; q < nseq; q += dq, m += dm) {
+      if (m >= nxh) { m -= nxh; ++q; if (q >= nseq) break; }
+      const long ra = row0 + 2 * q;
+      C2<T> A, B;
+      A.x = A.y = B.x = B.y = (T)0;
+      if (ra < nrows) A = spec[(size_t)ra * nxh + m];
+      if (ra + 1 < nrows) B = spec[(size_t)(ra + 1) * nxh + m];
+      C2<T>* row = bufA + (size_t)q * nx;
+      if (m == 0 || (even && m == nx / 2)) {
+        C2<T> Z;
+        Z.x = A.x;
+        Z.y = B.x;
+        row[m] = Z;
+      } else {
+        C2<T> Z, Zm;
+        Z.x = A.x - B.y;
+        Z.y = A.y + B.x;
+        Zm.x = A.x + B.y;   // mirror: A, B conjugated
+        Zm.y = B.x - A.y;
+        row[m] = Z;
+        if (m < nx - m) row[nx - m] = Zm;
+      }
+    }
   }
   __syncthreads();
   const C2<T>* res = nullptr;
