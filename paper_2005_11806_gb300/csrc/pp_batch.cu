@@ -303,11 +303,17 @@ pp_status build_fft_lists(pp_batch_s* B, int ept_x, int ept_y) {
     const int nrows = d.g.nz * d.g.ny;
     d.nblk_x = (nrows + d.rpb - 1) / d.rpb;
     for (int b = 0; b < d.nblk_x; ++b) wx.push_back(make_int2(i, b));
-    sx = std::max(sx, (size_t)(d.rpb + 1) * d.g.nx * sizeof(float2));  // + twiddle table
+    {  // buffer A, buffer B written padded, twiddle table
+      const int nbuf = (d.rpb / 2) * d.g.nx;
+      sx = std::max(sx, (size_t)(nbuf + fft_pad_elems(nbuf) + d.g.nx) * sizeof(float2));
+    }
     d.tx = ffty_tile(d.g.ny, sizeof(float2), ept_y);
     d.ntx = (d.g.nxh + d.tx - 1) / d.tx;
     for (int b = 0; b < d.ntx * d.g.nz; ++b) wy.push_back(make_int2(i, b));
-    sy = std::max(sy, (size_t)(2 * d.tx + 1) * d.g.ny * sizeof(float2));
+    {
+      const int tsz = d.g.ny * d.tx;
+      sy = std::max(sy, (size_t)(tsz + fft_pad_elems(tsz) + d.g.ny) * sizeof(float2));
+    }
   }
   B->smem_x = sx;
   B->smem_y = sy;
@@ -604,7 +610,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     return s;
   }
   // largest tuning candidate + the largest twiddle table
-  const int smem_max = (int)(2 * 16 * kThreads * sizeof(float2) + 2048 * sizeof(float2));
+  const int smem_max = (int)((16 * kThreads + fft_pad_elems(16 * kThreads) + 2048) * sizeof(float2));
   if (cudaFuncSetAttribute(kb_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
       cudaFuncSetAttribute(kb_fftx_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
       cudaFuncSetAttribute(kb_ffty<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||

@@ -246,21 +246,43 @@ __device__ __forceinline__ float2* smem_f2() {
 template <int DIR>
 __device__ __forceinline__ float2 tw_dir(float2 w) { return make_float2(w.x, DIR > 0 ? w.y : -w.y); }
 
-template <int DIR, int R, bool BATCH_FAST, int N, int NS, int NBATCH, int ES, int BS>
+// Bank-conflict padding of the first pass's output.  That pass writes each
+// butterfly's R = 8 outputs to R consecutive positions (stride R*ES between
+// threads), a 16-way (x layout) or 8-way (batched y layout) conflict.  The
+// buffer it writes therefore holds one gap of PU elements after every PG
+// elements (PG = 8 ES, PU = ES), which spreads those writes over all banks;
+// the second pass reads through the same map.  Buffers written padded hold
+// 9/8 of their elements (fft_pad_elems).
+template <bool BATCH_FAST, int NBATCH>
+struct FftPad {
+  static constexpr int PG = BATCH_FAST ? 8 * NBATCH : 8;
+  static constexpr int PU = BATCH_FAST ? NBATCH : 1;
+  static __device__ __forceinline__ int map(int pos) { return pos + (pos / PG) * PU; }
+};
+__host__ __device__ inline int fft_pad_elems(int n) { return n + n / 8; }
+
+template <int DIR, int R, bool BATCH_FAST, int N, int NS, int NBATCH, int ES, int BS, bool PIN, bool POUT>
 __device__ __forceinline__ void fft_pass_smem(int src, int dst, int twb, int tid, int nth) {
   float2* S = smem_f2();
+  using Pad = FftPad<BATCH_FAST, NBATCH>;
   constexpr int NB = N / R;
   constexpr int TOTAL = NB * NBATCH;
   constexpr int TWS = N / (NS * R);
+  // a padded input is read at stride NB*ES, a multiple of PG: the gaps add a
+  // constant per r, so the offsets stay compile-time
+  constexpr int IN_STEP = PIN ? NB * ES + (NB * ES / Pad::PG) * Pad::PU : NB * ES;
+  static_assert(!PIN || (NB * ES) % Pad::PG == 0, "padded reads need strides that are multiples of PG");
+  static_assert(!POUT || NS == 1, "only the first pass writes padded");
   for (int t = tid; t < TOTAL; t += nth) {
     int bi, j;
     if (BATCH_FAST) { j = t / NBATCH; bi = t % NBATCH; }
     else { bi = t / NB; j = t % NB; }
     const int k = j % NS;
-    const int sb = src + bi * BS + j * ES;
+    const int rel_in = bi * BS + j * ES;
+    const int sb = src + (PIN ? Pad::map(rel_in) : rel_in);
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = S[sb + r * NB * ES];
+    for (int r = 0; r < R; ++r) v[r] = S[sb + r * IN_STEP];
     if (NS > 1) {
       const int tk = twb + k * TWS;
       float2 w[R];
@@ -279,7 +301,9 @@ __device__ __forceinline__ void fft_pass_smem(int src, int dst, int twb, int tid
       for (int r = 1; r < R; ++r) v[r] = cmul<float>(v[r], w[r]);
     }
     Dft<float, DIR, R>::run(v);
-    const int db = dst + bi * BS + ((j / NS) * NS * R + k) * ES;
+    const int rel_out = bi * BS + ((j / NS) * NS * R + k) * ES;
+    // first pass: the R outputs of a butterfly stay inside one PG group
+    const int db = dst + (POUT ? Pad::map(rel_out) : rel_out);
 #pragma unroll
     for (int r = 0; r < R; ++r) S[db + r * NS * ES] = v[r];
   }
@@ -289,15 +313,19 @@ template <int DIR, bool BATCH_FAST, int N, int NBATCH, int ES, int BS, int S_, i
 __device__ __forceinline__ void fft_smem_from(int& src, int& dst, int twb, int tid, int nth) {
   if constexpr (S_ < Pow2Passes<N>::value) {
     constexpr int R = Pow2Radix<N, S_>::value;
-    fft_pass_smem<DIR, R, BATCH_FAST, N, NS, NBATCH, ES, BS>(src, dst, twb, tid, nth);
+    constexpr bool PIN = S_ == 1 && Pow2Radix<N, 0>::value == 8;
+    constexpr bool POUT = S_ == 0 && Pow2Passes<N>::value > 1 && R == 8;
+    fft_pass_smem<DIR, R, BATCH_FAST, N, NS, NBATCH, ES, BS, PIN, POUT>(src, dst, twb, tid, nth);
     __syncthreads();
     const int t = src; src = dst; dst = t;
     fft_smem_from<DIR, BATCH_FAST, N, NBATCH, ES, BS, S_ + 1, NS * R>(src, dst, twb, tid, nth);
   }
 }
 
-// Full transform on buffers at element offsets a and b; returns the offset
-// of the buffer holding the result.  Every thread of the block calls it.
+// Full transform on buffers at element offsets a and b (b holds
+// fft_pad_elems(its size) elements: the first pass writes it padded);
+// returns the offset of the buffer holding the result, unpadded.  Every
+// thread of the block calls it.
 template <int DIR, bool BATCH_FAST, int N, int NBATCH, int ES, int BS>
 __device__ __forceinline__ int fft_block_smem(int a, int b, int twb, int tid, int nth) {
   int src = a, dst = b;

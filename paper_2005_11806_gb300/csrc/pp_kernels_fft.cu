@@ -106,8 +106,12 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
   const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);
-  // two transform buffers, then (FP32) the twiddle table of the fast path
-  const size_t smem = (size_t)rpb * g.nx * sizeof(C2<T>) + (sizeof(T) == sizeof(float) ? g.nx * sizeof(float2) : 0);
+  // two transform buffers, then (FP32) the padding of the second buffer and
+  // the twiddle table of the fast path
+  const size_t nbuf = (size_t)(rpb / 2) * g.nx;
+  const size_t smem = (sizeof(T) == sizeof(float))
+                          ? (nbuf + fft_pad_elems((int)nbuf) + g.nx) * sizeof(float2)
+                          : 2 * nbuf * sizeof(C2<T>);
   cudaError_t e = cudaFuncSetAttribute(k_resid_fftx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int mode = (red == nullptr) ? 0 : 1;
@@ -122,7 +126,10 @@ template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
                         const DevStatus* st, cudaStream_t s) {
   const int tx = ffty_tile(g.ny, sizeof(C2<T>), kEpt);
-  const size_t smem = (size_t)3 * g.ny * tx * sizeof(C2<T>) + (sizeof(T) == sizeof(float) ? g.ny * sizeof(float2) : 0);
+  const int tsz = g.ny * tx;
+  const size_t smem = (sizeof(T) == sizeof(float))
+                          ? ((size_t)2 * tsz + fft_pad_elems(tsz) + g.ny) * sizeof(float2)
+                          : (size_t)3 * tsz * sizeof(C2<T>);
   const long long ntiles = (long long)((g.nxh + tx - 1) / tx) * g.nz;
   // persistent grid: exactly the blocks that are resident at once (shared
   // memory and registers both counted), so no block waits for a second wave
@@ -190,8 +197,12 @@ cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, c
   const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);
-  // two transform buffers, then (FP32) the twiddle table of the fast path
-  const size_t smem = (size_t)rpb * g.nx * sizeof(C2<T>) + (sizeof(T) == sizeof(float) ? g.nx * sizeof(float2) : 0);
+  // two transform buffers, then (FP32) the padding of the second buffer and
+  // the twiddle table of the fast path
+  const size_t nbuf = (size_t)(rpb / 2) * g.nx;
+  const size_t smem = (sizeof(T) == sizeof(float))
+                          ? (nbuf + fft_pad_elems((int)nbuf) + g.nx) * sizeof(float2)
+                          : 2 * nbuf * sizeof(C2<T>);
   cudaError_t e = cudaFuncSetAttribute(k_fftx_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_fftx_inv<T><<<nblk, kThreads, smem, s>>>(g, fx, twx, spec, scale, p, p_zero, rpb, st, delta, sdelta);

@@ -238,9 +238,10 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
   const int rows_par = blockDim.x / tpr;
   const int qoff = threadIdx.x / tpr, i0 = threadIdx.x - qoff * tpr;
   const bool vec = update && sizeof(T) == sizeof(float) && (nx & 3) == 0;
-  // FP32 fast transform: twiddle table after the two buffers
+  // FP32 fast transform: buffer A, buffer B (written padded by the first
+  // pass: fft_pad_elems), then the twiddle table
   constexpr bool F32 = std::is_same<T, float>::value;
-  const int twb = 2 * nseq * nx;
+  const int twb = nseq * nx + fft_pad_elems(nseq * nx);
   const bool fast = F32 && fft_smem_shape(nx, nseq, false);
   if constexpr (F32) {
     if (fast) load_twiddles_smem(twx, nx, twb);
@@ -364,7 +365,7 @@ __device__ __forceinline__ void stage_ffty(const Geo& g, const FftDesc& fy, cons
   const size_t base = (size_t)bz * ny * nxh;
   const int lg_tx = 31 - __clz(tx);  // tx is a power of two (ffty_tile)
   constexpr bool F32 = std::is_same<T, float>::value;
-  const int twb = 2 * ny * tx;
+  const int twb = ny * tx + fft_pad_elems(ny * tx);  // buffer B is written padded
   const bool fast = F32 && fft_smem_shape(ny, tx, true);
   if constexpr (F32) {
     if (fast) load_twiddles_smem(twy, ny, twb);
@@ -435,9 +436,11 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
   C2<T>* X0 = reinterpret_cast<C2<T>*>(smem_raw);
   // element offsets of the three buffers, rotated (no pointer array: the
   // transforms then address shared memory directly)
-  int L = 0, Q = tsz, F = 2 * tsz;
+  // Q, the scratch buffer of the transform, is written padded by its first
+  // pass and holds fft_pad_elems(tsz) elements; L and F (tsz each) rotate
+  int L = 0, Q = tsz, F = tsz + fft_pad_elems(tsz);
   constexpr bool F32 = std::is_same<T, float>::value;
-  const int twb = 3 * tsz;
+  const int twb = 2 * tsz + fft_pad_elems(tsz);
   const bool fast = F32 && fft_smem_shape(ny, tx, true);
   if constexpr (F32) {
     if (fast) load_twiddles_smem(twy, ny, twb);
@@ -875,7 +878,7 @@ __device__ __forceinline__ void stage_fftx_inv_m(const Geo& g, const FftDesc& fx
   // their registers within the other modes' budget
   const bool pre_p = need_p && MODE == kInvPlain && sizeof(T) == sizeof(double);
   constexpr bool F32 = std::is_same<T, float>::value;
-  const int twb = 2 * nseq * nx;
+  const int twb = nseq * nx + fft_pad_elems(nseq * nx);  // buffer B is written padded
   const bool fast = F32 && fft_smem_shape(nx, nseq, false);
   if constexpr (F32) {
     if (fast) load_twiddles_smem(twx, nx, twb);
