@@ -436,11 +436,14 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
   C2<T>* X0 = reinterpret_cast<C2<T>*>(smem_raw);
   // element offsets of the three buffers, rotated (no pointer array: the
   // transforms then address shared memory directly)
-  // Q, the scratch buffer of the transform, is written padded by its first
-  // pass and holds fft_pad_elems(tsz) elements; L and F (tsz each) rotate
-  int L = 0, Q = tsz, F = tsz + fft_pad_elems(tsz);
+  // FP32 fast path: Q, the scratch buffer of the transform, is written
+  // padded by its first pass and holds fft_pad_elems(tsz) elements, then the
+  // twiddle table follows; otherwise three plain buffers.  L and F (tsz
+  // each) rotate.  The launcher sizes shared memory for the same layout.
   constexpr bool F32 = std::is_same<T, float>::value;
-  const int twb = 2 * tsz + fft_pad_elems(tsz);
+  const int qsz = F32 ? fft_pad_elems(tsz) : tsz;
+  int L = 0, Q = tsz, F = tsz + qsz;
+  const int twb = 2 * tsz + qsz;
   const bool fast = F32 && fft_smem_shape(ny, tx, true);
   if constexpr (F32) {
     if (fast) load_twiddles_smem(twy, ny, twb);
