@@ -166,6 +166,18 @@ def algorithmic(kernel, w, precision):
     return None
 
 
+# DRAM bytes per cell of k_resid_fftx on mixed plans, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the 512 x 512 x 128 case:
+# the same kernel, block shape and grid per plane as at 512^3, so the bytes
+# scale with the cells processed.  One updated-residual pass and one exact
+# pass; the launch average follows the 20-pass cycle.  Captured with
+#   ncu --set full --clock-control none -k regex:"k_resid_fftx|k_ffty|k_tridiag_mixed|k_fftx_inv" -s 20 -c 5
+#   ncu --set full --clock-control none -k regex:"k_resid_fftx" -s 20 -c 1
+# on  python bench.py --n 512 --nz 128 --steps 1 --warmup 0 --maxit 21 --no-cpu-baseline --no-e2e --no-compare
+# (summary: profiles/pass_kernels_bubbles512x512x128_full.md).
+RESID_DRAM_B_PER_CELL = {"update": 35.11, "exact": 69.52}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -252,6 +264,10 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": name,
                 "avg_launch_ms": round(avg_s * 1e3, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if name == "resid_fftx" and args.precision == "mixed":
+        per_cell = 0.95 * RESID_DRAM_B_PER_CELL["update"] + 0.05 * RESID_DRAM_B_PER_CELL["exact"]
+        roof["traffic"] = int(per_cell * npts)
+        roof["traffic_source"] = "ncu DRAM bytes per cell at 512x512x128, scaled to the launch's cells"
     kernels = {k: {"launches": n, "total_ms": round(t, 3), "avg_ms": round(t / n, 4),
                    "share": round(t / sum(x[1] for x in kern.values()), 4)} for k, (n, t) in kern.items()}
 
