@@ -31,7 +31,10 @@ Readings of points the paper leaves open:
   by removing its volume-weighted mean;
 * Algorithm 1 is read as: iteration s uses ``u^s`` (``u^0 = u*``) to produce
   ``p^{s+1}`` and ``u^{s+1}``; it stops on the relative L2 norm of
-  ``D u^{s+1} - S_c`` (the paper's L1 sum is reported too).
+  ``D u^{s+1} - S_c`` (the paper's L1 sum is reported too);
+* the conduction term ``div(k grad T)`` of Eqs. 30 and 34 is ``D(k_f G T)``
+  with the arithmetic face mean of k (the same operator as the pressure's);
+  the z walls are adiabatic (zero heat flux), x and y periodic.
 
 Pins (tests/test_oracle_pins.py): the single-mode closed form, dense LU
 solves of systems assembled entry by entry, exact-linear-field identities of
@@ -50,6 +53,7 @@ __all__ = [
     "Grid", "mixture_density", "divergence", "gradient", "face_density",
     "volume_mean", "laplacian", "solve_constant", "method3", "projection_direct",
     "correct_velocity", "adjoint_direct", "adjoint_method3", "method1", "method2",
+    "conduction", "gas_volume", "p0_rate", "dp0dt_extrapolate", "divergence_source",
 ]
 
 
@@ -503,3 +507,43 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
     beta = 1.0 / _face_vector(rx, ry, rz)
     grho = _beta_to_rho(g, beta, gbeta)
     return gus, gvs, gws, grho, {"fwd": info_fwd, "adj": info_adj}
+
+
+# ---------------------------------------------------------------------------
+# The divergence source from the thermodynamics (Sec. 2, final_p0; Sec. 3.2,
+# Eqs. 30 and v_gas; Sec. 3.3, Eq. 34 and the extrapolation of dp0/dt)
+
+def conduction(g, kc, T):
+    """div(k grad T) at the cell centres, second-order central: D(k_f G T)
+    with k_f the arithmetic mean of the two cells of a face; G T is zero on
+    the z walls (adiabatic walls)."""
+    kx, ky, kz = face_density(g, kc)
+    gx, gy, gz = gradient(g, T)
+    return divergence(g, kx * gx, ky * gy, kz * gz)
+
+
+def gas_volume(g, phi):
+    """Eq. v_gas: V_g = sum of Phi dV over the cells (dV = dx dy dzf_k)."""
+    return float(np.sum(phi * g.cell_volume()))
+
+
+def p0_rate(g, phi, kc, T, u, v, w, p0, gamma):
+    """Eq. 30 (final_p0 with the volume integrals as cell sums):
+    RP = (gamma / V_g) [ (gamma - 1)/gamma sum Phi div(k grad T) dV
+                         - p0 sum Phi div(u) dV ]."""
+    dv = g.cell_volume()
+    vg = gas_volume(g, phi)
+    a = float(np.sum(phi * conduction(g, kc, T) * dv))
+    b = float(np.sum(phi * divergence(g, u, v, w) * dv))
+    return gamma / vg * ((gamma - 1.0) / gamma * a - p0 * b)
+
+
+def dp0dt_extrapolate(rp_n, rp_nm1, dt_new, dt_old):
+    """Sec. 3.3: (dp0/dt)^{n+1} ~ (1 + dt^{n+1}/dt^n) RP^n - (dt^{n+1}/dt^n) RP^{n-1}."""
+    r = dt_new / dt_old
+    return (1.0 + r) * rp_n - r * rp_nm1
+
+
+def divergence_source(g, phi, kc, T, p0, gamma, dp0dt):
+    """Eq. 34: S = (1/p0) [ (gamma - 1)/gamma div(k grad T) - (1/gamma) dp0/dt ] Phi."""
+    return ((gamma - 1.0) / gamma * conduction(g, kc, T) - dp0dt / gamma) * phi / p0

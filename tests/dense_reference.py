@@ -81,3 +81,38 @@ def divergence_loops(nx, ny, nz, lx, ly, zf, u, v, w):
                                 + (v[k, (j + 1) % ny, i] - v[k, j, i]) / dy
                                 + (w[k + 1, j, i] - w[k, j, i]) / dzf[k])
     return out
+
+
+def assemble_conduction(nx, ny, nz, lx, ly, zf, kc):
+    """Matrix of T -> D(k_f G T) with k_f the arithmetic mean of the two
+    cells of a face (kc indexed [k][j][i]); no flux through the z walls,
+    periodic x and y."""
+    dx, dy = lx / nx, ly / ny
+    dzf, zc = metrics(nz, zf)
+    n = nx * ny * nz
+
+    def idx(i, j, k):
+        return (k * ny + (j % ny)) * nx + (i % nx)
+
+    A = np.zeros((n, n))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                r = idx(i, j, k)
+                for di in (+1, -1):
+                    kf = 0.5 * (kc[k][j][i] + kc[k][j][(i + di) % nx])
+                    A[r, idx(i + di, j, k)] += kf / (dx * dx)
+                    A[r, r] -= kf / (dx * dx)
+                for dj in (+1, -1):
+                    kf = 0.5 * (kc[k][j][i] + kc[k][(j + dj) % ny][i])
+                    A[r, idx(i, j + dj, k)] += kf / (dy * dy)
+                    A[r, r] -= kf / (dy * dy)
+                for dk in (+1, -1):
+                    kk = k + dk
+                    if kk < 0 or kk >= nz:
+                        continue  # adiabatic wall
+                    kf = 0.5 * (kc[k][j][i] + kc[kk][j][i])
+                    b = kf / (abs(zc[kk] - zc[k]) * dzf[k])
+                    A[r, idx(i, j, kk)] += b
+                    A[r, r] -= b
+    return A

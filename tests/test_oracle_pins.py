@@ -312,3 +312,93 @@ def test_planted_gradient_sign_is_caught(monkeypatch):
     monkeypatch.setattr(orc, "gradient", planted)
     with pytest.raises(AssertionError):
         test_single_mode_closed_form((24, 20, 16), (3, 2, 1), (0.3, -1.1))
+
+
+# --- divergence source from the thermodynamics (Eqs. 30, 34, v_gas) -------
+
+def test_conduction_single_mode_closed_form():
+    """Constant k on a uniform grid: D(k G T) of a discrete eigenmode is k
+    times its modified-wavenumber eigenvalue (Neumann cosine in z)."""
+    nx, ny, nz, a, b, c, kap = 16, 12, 10, 3, 2, 4, 2.5
+    g = _grid(nx, ny, nz)
+    i = np.arange(nx)[None, None, :]; j = np.arange(ny)[None, :, None]; k = np.arange(nz)[:, None, None]
+    T = np.cos(2 * np.pi * a * i / nx) * np.cos(2 * np.pi * b * j / ny) * np.cos(np.pi * c * (k + 0.5) / nz)
+    lam = -4 * (nx ** 2 * np.sin(np.pi * a / nx) ** 2 + ny ** 2 * np.sin(np.pi * b / ny) ** 2
+                + nz ** 2 * np.sin(np.pi * c / (2 * nz)) ** 2)
+    got = orc.conduction(g, np.full(g.shape, kap), T)
+    assert _rel(got, kap * lam * T) < 1e-12
+
+
+def test_conduction_matches_dense_assembly():
+    """Variable k, stretched z: the array operator equals the matrix assembled
+    entry by entry from the stencil definition."""
+    nx, ny, nz = 6, 5, 7
+    g = _grid(nx, ny, nz, 1.0, 0.8, 0.6, beta=1.5)
+    rng = np.random.default_rng(30)
+    kc = rng.uniform(0.5, 3.0, g.shape)
+    T = rng.standard_normal(g.shape)
+    A = dr.assemble_conduction(nx, ny, nz, 1.0, 0.8, g.zf, kc)
+    assert _rel(orc.conduction(g, kc, T).ravel(), A @ T.ravel()) < 1e-13
+
+
+def test_heat_is_conserved_in_a_closed_gas_box():
+    """Adiabatic walls, periodic x/y: sum of div(k grad T) dV vanishes, so a
+    box full of gas (Phi = 1) with no net dilatation has dp0/dt = 0."""
+    g, us, vs, ws, rho, S = _small_case(12, 10, 9, beta=1.5)
+    rng = np.random.default_rng(31)
+    kc = rng.uniform(0.2, 2.0, g.shape)
+    T = rng.uniform(0.5, 2.0, g.shape)
+    cond = orc.conduction(g, kc, T)
+    dv = g.cell_volume()
+    assert abs(np.sum(cond * dv)) <= 1e-13 * np.sum(np.abs(cond) * dv)
+    rp = orc.p0_rate(g, np.ones(g.shape), kc, T, us, vs, ws, p0=1.3, gamma=1.4)
+    scale = (1.4 / orc.gas_volume(g, np.ones(g.shape))) * np.sum(np.abs(cond) * dv)
+    assert abs(rp) <= 1e-13 * scale
+
+
+def test_p0_rate_is_the_heat_flux_through_the_interface():
+    """Gas below a flat interface (Phi = 1 for k < m, 0 above), u = 0: Eq. 30
+    gives (gamma - 1)/V_g times the heat flowing into the gas through the
+    interface faces, summed here face by face (discrete Gauss theorem)."""
+    nx, ny, nz, m = 8, 6, 10, 4
+    g = _grid(nx, ny, nz, 1.0, 0.75, 1.0, beta=1.5)
+    rng = np.random.default_rng(32)
+    kc = rng.uniform(0.5, 2.0, g.shape)
+    T = rng.uniform(0.5, 2.0, g.shape)
+    phi = np.zeros(g.shape); phi[:m] = 1.0
+    zero = np.zeros(g.shape)
+    gamma, p0 = 1.4, 0.9
+    flux = 0.0
+    for j in range(ny):
+        for i in range(nx):
+            kf = 0.5 * (kc[m, j, i] + kc[m - 1, j, i])
+            flux += kf * (T[m, j, i] - T[m - 1, j, i]) / (g.zc[m] - g.zc[m - 1]) * g.dx * g.dy
+    vg = float(np.sum(g.dzf[:m])) * g.lx * g.ly
+    assert abs(orc.gas_volume(g, phi) - vg) <= 1e-14 * vg
+    rp = orc.p0_rate(g, phi, kc, T, zero, zero, np.zeros((nz + 1, ny, nx)), p0, gamma)
+    assert rp == pytest.approx((gamma - 1.0) / vg * flux, rel=1e-12)
+
+
+def test_dp0dt_extrapolation_is_exact_for_a_linear_history():
+    """The extrapolation of Sec. 3.3 reproduces a rate linear in time."""
+    a, b, t, dt_old, dt_new = 0.3, -1.7, 2.0, 0.01, 0.013
+    rp_n, rp_nm1 = a + b * t, a + b * (t - dt_old)
+    assert orc.dp0dt_extrapolate(rp_n, rp_nm1, dt_new, dt_old) == pytest.approx(a + b * (t + dt_new), rel=1e-13)
+    assert orc.dp0dt_extrapolate(0.25, 0.25, dt_new, dt_old) == pytest.approx(0.25, rel=1e-15)
+
+
+def test_divergence_source_special_cases():
+    """Eq. 34: zero in the liquid; a uniform temperature leaves only the
+    pressure-rate term; the conduction term enters with (gamma - 1)/gamma."""
+    g = _grid(8, 8, 8)
+    rng = np.random.default_rng(33)
+    phi = rng.uniform(0, 1, g.shape); phi[0] = 0.0
+    kc = rng.uniform(0.5, 2.0, g.shape)
+    gamma, p0, r = 1.4, 1.1, 0.02
+    S = orc.divergence_source(g, phi, kc, np.full(g.shape, 1.7), p0, gamma, r)
+    assert np.all(S[0] == 0.0)
+    assert _rel(S, -phi * r / (gamma * p0)) < 1e-14
+    T = rng.uniform(0.5, 2.0, g.shape)
+    S0 = orc.divergence_source(g, phi, kc, T, p0, gamma, 0.0)
+    assert _rel(S0 * p0, (gamma - 1) / gamma * phi * (dr.assemble_conduction(8, 8, 8, 1.0, 1.0, g.zf, kc)
+                                                        @ T.ravel()).reshape(g.shape)) < 1e-12
