@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--compare-steps", type=int, default=1)
+    ap.add_argument("--no-thermo", action="store_true",
+                    help="skip timing the divergence-source kernels (Eqs. 30, 34)")
     ap.add_argument("--workload", default="bubbles512", choices=["bubbles512", "batch96"],
                     help="bubbles512: the 512^3 projection (default); batch96: 96 grids of mixed sizes "
                          "solved in one graph launch")
@@ -295,6 +297,44 @@ def run_ours(args, rank, world, local_rank):
         out["speedup_mixed_vs_fp64"] = round(ms64 / ms, 3)
         plan64.close()
         plan = make_plan(args.precision)
+
+    # the divergence source from the thermodynamics (Eqs. 30, 34) on the same
+    # grid: a temperature and a conductivity field, CUDA events over 20 calls
+    if not args.no_thermo:
+        rng = np.random.Generator(np.random.PCG64(1003 + 40))
+        Tf = T(1.0 + 0.3 * w.phi + 0.05 * rng.standard_normal(w.shape))
+        kf = T(0.02 + 0.5 * (1.0 - w.phi))
+        Sf = torch.empty_like(Tf)
+        reps = 20
+        out["thermo"] = {}
+        # FP64 operations per cell (add, multiply and FMA each one FP64-pipe
+        # slot): the conduction stencil 27, Eq. 34's scaling 3; the rate adds
+        # the velocity divergence (8) and three weighted sums (6)
+        fp64_slots = 152 * 2 * 2.070e9  # FP64 pipe: 2 lanes per clock per SM
+        for label, call, nbytes, ops in (
+                ("divergence_source", lambda: pp.pressure_divergence_source(plan.handle, phi, kf, Tf, 1.0, 1.4,
+                                                                             1e-2, Sf), 32 * npts, 30),
+                ("p0_rate", lambda: pp.pressure_p0_rate(plan.handle, phi, kf, Tf, us, vs, ws, 1.0, 1.4),
+                 40 * npts + 8 * (w.nz + 1) * w.ny * w.nx, 41)):
+            for _ in range(3):
+                call()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            tms = e0.elapsed_time(e1) / reps
+            gbs = nbytes / (tms / 1e3) / 1e9
+            rate = ops * npts / (tms / 1e3)
+            out["thermo"][label] = {"ms": round(tms, 4), "bound": "alu (FP64 pipe)",
+                                    "fp64_ops_per_cell": ops, "achieved_fp64_gops": round(rate / 1e9, 1),
+                                    "frac_of_fp64_peak": round(rate / fp64_slots, 4),
+                                    "algorithmic_bytes": int(nbytes), "achieved_gbs": round(gbs, 1),
+                                    "frac_of_measured_hbm": round(gbs / hbm_peak, 4)}
+        out["thermo"]["note"] = ("Eq. 34 source and Eq. 30 rate at the benchmark grid (fields larger than L2); "
+                                 "p0_rate includes its device-to-host read of the rate")
 
     # end to end through the C ABI with host (pinned) buffers
     if not args.no_e2e:

@@ -127,6 +127,41 @@ pp_status pressure_solve(pp_plan plan, const double* f, double* p, pp_info* info
 pp_status pressure_mixture_density(pp_plan plan, const double* phi, double rho_g, double rho_l,
                                    double* rho);
 
+/* ---- the divergence source from the thermodynamics --------------------
+ * div(k grad T) is evaluated as D(k_f G T) on the MAC grid (second-order
+ * central, Sec. 3.2): k_f is the arithmetic mean of the two cells of a face,
+ * the z walls are adiabatic (no heat flux), x and y periodic.
+ *
+ * Rate of the thermodynamic pressure, Eq. 30 (the discrete form of Eq.
+ * final_p0):
+ *   RP = (gamma / V_g) [ (gamma - 1)/gamma sum Phi div(k grad T) dV
+ *                        - p0 sum Phi div(u) dV ],
+ * with V_g = sum Phi dV (Eq. v_gas) and dV = dx dy dzf_k.
+ * In: phi (gas volume fraction), kc (conductivity), T (temperature): cell
+ * fields; u, v, w: faces (w wall planes are taken as zero); p0 and gamma.
+ * Out: *rp, on the host; the call waits for the GPU.  PP_ERR_NUMERIC when
+ * there is no gas (V_g = 0); PP_ERR_INVALID_ARG for gamma <= 0 or a
+ * non-finite p0. */
+pp_status pressure_p0_rate(pp_plan plan, const double* phi, const double* kc, const double* T,
+                           const double* u, const double* v, const double* w, double p0,
+                           double gamma, double* rp);
+
+/* Sec. 3.3: (dp0/dt)^{n+1} extrapolated in time from RP^n and RP^{n-1},
+ *   (1 + dt_new/dt_old) rp_n - (dt_new/dt_old) rp_nm1,
+ * into *out (host arithmetic only).  PP_ERR_INVALID_ARG for non-positive
+ * time steps. */
+pp_status pressure_dp0dt_extrapolate(double rp_n, double rp_nm1, double dt_new, double dt_old,
+                                     double* out);
+
+/* Divergence source, Eq. 34:
+ *   S = (1/p0) [ (gamma - 1)/gamma div(k grad T) - dp0dt / gamma ] Phi,
+ * the S that pressure_correct takes.  In: phi, kc, T (cell fields), p0 != 0,
+ * gamma > 0, dp0dt (the extrapolated rate).  Out: S (cell field).  Enqueued
+ * on the plan's stream (waits only when S is a host pointer). */
+pp_status pressure_divergence_source(pp_plan plan, const double* phi, const double* kc,
+                                     const double* T, double p0, double gamma, double dp0dt,
+                                     double* S);
+
 /* Method III projection (Algorithm 1, Sec. 3.3.1; Eqs. new_poisson, corr),
  * or Method I or II when pressure_plan_set_method selected one.
  * In: us, vs, ws (u*, faces; ws wall planes are taken as zero), rho (cell

@@ -15,12 +15,13 @@ using namespace pp;
 
 namespace {
 enum KId { K_RESID, K_CHECK, K_FFTY_F, K_TRI, K_FFTY_I, K_FFTX_I, K_INIT, K_PREP, K_MEANS, K_RHSB,
-           K_RMEAN, K_CORR, K_MIX, K_ADJ_RHS, K_ADJ_FIN, K_ADJ_GRHO, K_RHOT, K_FOLD, K_COUNT };
+           K_RMEAN, K_CORR, K_MIX, K_ADJ_RHS, K_ADJ_FIN, K_ADJ_GRHO, K_RHOT, K_FOLD, K_THERMO, K_SOURCE,
+           K_COUNT };
 const char* const kNames[K_COUNT] = {
     "resid_fftx", "check", "ffty_fwd", "tridiag_z", "ffty_inv", "fftx_inv_update", "init_status",
     "prep_faces", "mean_S", "rhs_b", "remove_mean", "correct", "mixture_density", "adj_rhs",
-    "adj_finish", "adj_grho", "rho_tilde", "fold_pending"};
-const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1, 2, 1};
+    "adj_finish", "adj_grho", "rho_tilde", "fold_pending", "p0_rate", "divergence_source"};
+const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1, 2, 1, 2, 1};
 struct Rec { int kid; cudaEvent_t a, b; };
 struct Prof {
   bool on = false;
@@ -64,6 +65,7 @@ struct pp_plan_s {
   bool use_tri32 = false;
   double* d_rho_tilde = nullptr;
   double* d_delta64 = nullptr;
+  double* d_thermo = nullptr;  // [4] sums and rate of Eq. 30
   double* d_red = nullptr;
   size_t red_len = 0;
   DevStatus* d_st = nullptr;
@@ -340,7 +342,7 @@ void free_plan(pp_plan_s* P) {
   if (!P) return;
   double* dptrs[] = {P->d_inv_dzf, P->d_inv_dzc, P->d_dzf, P->d_za, P->d_zc, P->d_lamx, P->d_lamy,
                      P->d_invd, P->d_mtab, P->d_b, P->d_red, P->faces.cx, P->faces.cy, P->faces.cz,
-                     P->faces.diag, P->d_rho_tilde, P->d_delta64};
+                     P->faces.diag, P->d_rho_tilde, P->d_delta64, P->d_thermo};
   if (P->faces.rhof) cudaFree(P->faces.rhof);
   if (P->d_low) cudaFree(P->d_low);
   float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta, P->d_sdelta,
@@ -492,7 +494,8 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       (st = dalloc(&P->faces.diag, nc * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->faces.rhof, nc * sizeof(float))) != PP_OK ||
       (st = dalloc(&P->d_inv_dzf_f, (size_t)nz * sizeof(float))) != PP_OK ||
-      (st = dalloc(&P->d_st, sizeof(DevStatus))) != PP_OK) {
+      (st = dalloc(&P->d_st, sizeof(DevStatus))) != PP_OK ||
+      (st = dalloc(&P->d_thermo, 4 * sizeof(double))) != PP_OK) {
     free_plan(P);
     return st;
   }
@@ -603,6 +606,54 @@ pp_status pressure_plan_set_method(pp_plan P, int method) {
   }
   P->method = method;
   P->faces.rho_tilde = (method == PP_METHOD_III) ? nullptr : P->d_rho_tilde;
+  return PP_OK;
+}
+
+pp_status pressure_p0_rate(pp_plan P, const double* phi, const double* kc, const double* T, const double* u,
+                           const double* v, const double* w, double p0, double gamma, double* rp) {
+  if (check_plan(P) != PP_OK || !phi || !kc || !T || !u || !v || !w || !rp) return PP_ERR_INVALID_ARG;
+  if (!(gamma > 0.0) || !std::isfinite(p0)) return PP_ERR_INVALID_ARG;
+  const size_t nc = ncell(P), nw = nwface(P);
+  const double *dphi, *dk, *dT, *du, *dv, *dw;
+  pp_status s;
+  if ((s = stage_in(P, phi, nc, 0, &dphi)) != PP_OK || (s = stage_in(P, kc, nc, 1, &dk)) != PP_OK ||
+      (s = stage_in(P, T, nc, 2, &dT)) != PP_OK || (s = stage_in(P, u, nc, 3, &du)) != PP_OK ||
+      (s = stage_in(P, v, nc, 4, &dv)) != PP_OK || (s = stage_in(P, w, nw, 5, &dw)) != PP_OK)
+    return s;
+  PP_K(P, K_THERMO, launch_thermo_rate(P->geo, dphi, dk, dT, du, dv, dw, p0, gamma, P->d_red, P->d_thermo,
+                                       P->stream));
+  double out[4];
+  PP_CK(cudaMemcpyAsync(out, P->d_thermo, sizeof(out), cudaMemcpyDeviceToHost, P->stream));
+  PP_CK(cudaStreamSynchronize(P->stream));
+  if (!(out[2] > 0.0) || !std::isfinite(out[3])) return PP_ERR_NUMERIC;
+  *rp = out[3];
+  return PP_OK;
+}
+
+pp_status pressure_dp0dt_extrapolate(double rp_n, double rp_nm1, double dt_new, double dt_old, double* out) {
+  if (!out || !(dt_old > 0.0) || !(dt_new > 0.0)) return PP_ERR_INVALID_ARG;
+  const double r = dt_new / dt_old;
+  *out = (1.0 + r) * rp_n - r * rp_nm1;
+  return PP_OK;
+}
+
+pp_status pressure_divergence_source(pp_plan P, const double* phi, const double* kc, const double* T, double p0,
+                                     double gamma, double dp0dt, double* S) {
+  if (check_plan(P) != PP_OK || !phi || !kc || !T || !S) return PP_ERR_INVALID_ARG;
+  if (!(gamma > 0.0) || p0 == 0.0 || !std::isfinite(p0) || !std::isfinite(dp0dt)) return PP_ERR_INVALID_ARG;
+  const size_t nc = ncell(P);
+  const double *dphi, *dk, *dT;
+  double* dS;
+  bool staged;
+  pp_status s;
+  if ((s = stage_in(P, phi, nc, 0, &dphi)) != PP_OK || (s = stage_in(P, kc, nc, 1, &dk)) != PP_OK ||
+      (s = stage_in(P, T, nc, 2, &dT)) != PP_OK || (s = stage_out(P, S, 3, &dS, &staged)) != PP_OK)
+    return s;
+  PP_K(P, K_SOURCE, launch_divergence_source(P->geo, dphi, dk, dT, p0, gamma, dp0dt, dS, P->stream));
+  if (staged) {
+    if ((s = copy_back(P, S, dS, nc)) != PP_OK) return s;
+    PP_CK(cudaStreamSynchronize(P->stream));
+  }
   return PP_OK;
 }
 

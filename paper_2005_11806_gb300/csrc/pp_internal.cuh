@@ -221,6 +221,14 @@ cudaError_t launch_adj_finish(const Geo& g, const double* rho, const double* p, 
                               double dt, const double* gu, const double* gv, const double* gw,
                               double* gus, double* gvs, double* gws, double* tx, double* ty,
                               double* tz, cudaStream_t s);
+// Eq. 30: out[0..3] = {sum Phi div(k grad T) dV, sum Phi div(u) dV, V_g, RP}
+// (RP = NaN when V_g = 0); red holds at least reduce_blocks() values.
+cudaError_t launch_thermo_rate(const Geo& g, const double* phi, const double* kc, const double* T,
+                               const double* u, const double* v, const double* w, double p0, double gamma,
+                               double* red, double* out, cudaStream_t s);
+// Eq. 34: S = (1/p0) [ (gamma - 1)/gamma div(k grad T) - dp0dt / gamma ] Phi.
+cudaError_t launch_divergence_source(const Geo& g, const double* phi, const double* kc, const double* T,
+                                     double p0, double gamma, double dp0dt, double* S, cudaStream_t s);
 cudaError_t launch_adj_grho(const Geo& g, const double* tx, const double* ty, const double* tz,
                             double* grho, cudaStream_t s);
 

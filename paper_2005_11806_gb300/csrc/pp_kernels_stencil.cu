@@ -196,6 +196,70 @@ __global__ void k_correct_method1(Geo g, Faces fc, const double* __restrict__ us
   }
 }
 
+// ---- divergence source from the thermodynamics (Eqs. 30, 34, v_gas) ----------
+
+// Block partial sums of Phi div(k grad T) dV, Phi div(u) dV and Phi dV into
+// red[3 b + {0, 1, 2}] (wall values of w taken as zero).
+__global__ void k_thermo_partial(Geo g, const double* __restrict__ phi, const double* __restrict__ kc,
+                                 const double* __restrict__ T, const double* __restrict__ u,
+                                 const double* __restrict__ v, const double* __restrict__ w,
+                                 double* __restrict__ red) {
+  __shared__ double sh[32];
+  const size_t plane = (size_t)g.nx * g.ny, n = plane * g.nz;
+  const double dxdy = g.dx * g.dy;
+  double a = 0.0, b = 0.0, vg = 0.0;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const CellIdx x = cell_index(g, c);
+    const double f = phi[c];
+    const double dv = dxdy * g.dzf[x.k];
+    const double wlo = (x.k == 0) ? 0.0 : w[c];
+    const double whi = (x.k == g.nz - 1) ? 0.0 : w[c + plane];
+    const double div = (u[x.cip] - u[c]) / g.dx + (v[x.cjp] - v[c]) / g.dy + (whi - wlo) * g.inv_dzf[x.k];
+    a += f * cell_conduction(g, kc, T, c) * dv;
+    b += f * div * dv;
+    vg += f * dv;
+  }
+  a = block_sum<double>(a, sh);
+  __syncthreads();
+  b = block_sum<double>(b, sh);
+  __syncthreads();
+  vg = block_sum<double>(vg, sh);
+  if (threadIdx.x == 0) {
+    red[3 * (size_t)blockIdx.x] = a;
+    red[3 * (size_t)blockIdx.x + 1] = b;
+    red[3 * (size_t)blockIdx.x + 2] = vg;
+  }
+}
+
+// out = {sum a, sum b, V_g, RP} with RP of Eq. 30 (RP = NaN when V_g = 0).
+__global__ void k_thermo_rate(const double* __restrict__ red, int nblk, double p0, double gamma,
+                              double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s[3];
+  for (int q = 0; q < 3; ++q) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) t += red[3 * (size_t)b + q];
+    s[q] = block_sum<double>(t, sh);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s[0];
+    out[1] = s[1];
+    out[2] = s[2];
+    out[3] = (s[2] > 0.0) ? gamma / s[2] * ((gamma - 1.0) / gamma * s[0] - p0 * s[1]) : NAN;
+  }
+}
+
+// S = (1/p0) [ (gamma - 1)/gamma div(k grad T) - dp0dt / gamma ] Phi  (Eq. 34).
+__global__ void k_divergence_source(Geo g, const double* __restrict__ phi, const double* __restrict__ kc,
+                                    const double* __restrict__ T, double p0, double gamma, double dp0dt,
+                                    double* __restrict__ S) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  const double a = (gamma - 1.0) / gamma, b = dp0dt / gamma, ip0 = 1.0 / p0;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    S[c] = (a * cell_conduction(g, kc, T, c) - b) * phi[c] * ip0;
+}
+
 // ---- adjoint ---------------------------------------------------------------
 // y = -dt * beta * W_f^{-1} g  (W_f = dzf of the layer on x/y faces, dzc on
 // interior z faces; wall z-faces zero).
@@ -338,6 +402,21 @@ template cudaError_t launch_correct_method1<double>(const Geo&, const Faces&, co
 template cudaError_t launch_correct_method1<float>(const Geo&, const Faces&, const double*, const double*,
                                                    const double*, const double*, const float*, double,
                                                    double*, double*, double*, cudaStream_t);
+
+cudaError_t launch_thermo_rate(const Geo& g, const double* phi, const double* kc, const double* T,
+                               const double* u, const double* v, const double* w, double p0, double gamma,
+                               double* red, double* out, cudaStream_t s) {
+  constexpr int kThermoBlocks = kRedBlocks / 3;  // three partial sums per block fit the buffer
+  k_thermo_partial<<<kThermoBlocks, kThreads, 0, s>>>(g, phi, kc, T, u, v, w, red);
+  k_thermo_rate<<<1, 1024, 0, s>>>(red, kThermoBlocks, p0, gamma, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_divergence_source(const Geo& g, const double* phi, const double* kc, const double* T,
+                                     double p0, double gamma, double dp0dt, double* S, cudaStream_t s) {
+  k_divergence_source<<<grid_for((size_t)g.nx * g.ny * g.nz), kThreads, 0, s>>>(g, phi, kc, T, p0, gamma, dp0dt, S);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_remove_mean(const Geo& g, double* p, double* red, DevStatus* st, cudaStream_t s) {
   cudaError_t e = launch_weighted_mean(g, p, red, &st->pmean, s);

@@ -58,6 +58,7 @@ EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_plan_set_m
            "pressure_last_info", "pressure_profile_enable", "pressure_profile_read",
            "pressure_solve_noalloc", "pressure_batch_create", "pressure_batch_layout",
            "pressure_batch_correct", "pressure_batch_destroy", "pressure_batch_mixture_density",
+           "pressure_p0_rate", "pressure_dp0dt_extrapolate", "pressure_divergence_source",
            "pressure_status_string")
 
 
@@ -91,6 +92,9 @@ def lib():
     L.pressure_batch_correct.argtypes = [vp, vp, vp, vp, vp, vp, d, vp, vp, vp, vp, d, i, pinfo]
     L.pressure_batch_destroy.argtypes = [vp]
     L.pressure_batch_mixture_density.argtypes = [vp, vp, d, d, vp]
+    L.pressure_p0_rate.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, ctypes.POINTER(d)]
+    L.pressure_dp0dt_extrapolate.argtypes = [d, d, d, d, ctypes.POINTER(d)]
+    L.pressure_divergence_source.argtypes = [vp, vp, vp, vp, d, d, d, vp]
     L.pressure_status_string.argtypes = [i]
     L.pressure_status_string.restype = ctypes.c_char_p
     for name in EXPORTS[:-1]:
@@ -212,6 +216,27 @@ def pressure_correct(plan, us, vs, ws, rho, S, dt, p, u, v, w, rtol=1e-10, maxit
     allow = (PP_ERR_NOT_CONVERGED,) if allow_not_converged else ()
     _check(code, "pressure_correct", allow)
     return info.as_dict() if sync else None
+
+
+def pressure_p0_rate(plan, phi, kc, T, u, v, w, p0, gamma):
+    """Eq. 30: the rate of the thermodynamic pressure (host float)."""
+    out = ctypes.c_double()
+    _check(lib().pressure_p0_rate(plan, _ptr(phi), _ptr(kc), _ptr(T), _ptr(u), _ptr(v), _ptr(w), float(p0),
+                                  float(gamma), ctypes.byref(out)), "pressure_p0_rate")
+    return out.value
+
+
+def pressure_dp0dt_extrapolate(rp_n, rp_nm1, dt_new, dt_old):
+    out = ctypes.c_double()
+    _check(lib().pressure_dp0dt_extrapolate(float(rp_n), float(rp_nm1), float(dt_new), float(dt_old),
+                                            ctypes.byref(out)), "pressure_dp0dt_extrapolate")
+    return out.value
+
+
+def pressure_divergence_source(plan, phi, kc, T, p0, gamma, dp0dt, S):
+    """Eq. 34: the divergence source S written into S (cell field)."""
+    _check(lib().pressure_divergence_source(plan, _ptr(phi), _ptr(kc), _ptr(T), float(p0), float(gamma),
+                                            float(dp0dt), _ptr(S)), "pressure_divergence_source")
 
 
 def pressure_last_info(plan):
