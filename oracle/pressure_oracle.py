@@ -34,7 +34,13 @@ Readings of points the paper leaves open:
   ``D u^{s+1} - S_c`` (the paper's L1 sum is reported too);
 * the conduction term ``div(k grad T)`` of Eqs. 30 and 34 is ``D(k_f G T)``
   with the arithmetic face mean of k (the same operator as the pressure's);
-  the z walls are adiabatic (zero heat flux), x and y periodic.
+  the z walls are adiabatic (zero heat flux), x and y periodic;
+* the momentum predictor (Eqs. 29, 32) has no-slip z walls; the density on
+  a face and the viscosity on an edge are arithmetic means of the cells
+  around them; a velocity is carried to an edge by the mean of its two
+  values in x, y or z;
+  the surface-tension force of the VOF model is out of scope (a caller
+  force may stand in for it); the first step is forward Euler.
 
 Pins (tests/test_oracle_pins.py): the single-mode closed form, dense LU
 solves of systems assembled entry by entry, exact-linear-field identities of
@@ -54,6 +60,7 @@ __all__ = [
     "volume_mean", "laplacian", "solve_constant", "method3", "projection_direct",
     "correct_velocity", "adjoint_direct", "adjoint_method3", "method1", "method2",
     "conduction", "gas_volume", "p0_rate", "dp0dt_extrapolate", "divergence_source",
+    "convection", "viscous", "predictor_rhs", "predictor",
 ]
 
 
@@ -547,3 +554,123 @@ def dp0dt_extrapolate(rp_n, rp_nm1, dt_new, dt_old):
 def divergence_source(g, phi, kc, T, p0, gamma, dp0dt):
     """Eq. 34: S = (1/p0) [ (gamma - 1)/gamma div(k grad T) - (1/gamma) dp0/dt ] Phi."""
     return ((gamma - 1.0) / gamma * conduction(g, kc, T) - dp0dt / gamma) * phi / p0
+
+
+# ---------------------------------------------------------------------------
+# Momentum predictor (Sec. 3.3, Eqs. 29 and 32): u* = u^n + dt [(1 + r/2) RU^n
+# - (r/2) RU^{n-1}], RU = -C(u) + (1/rho_f)[div tau(mu, u) + f] + g, with the
+# Newton-Stokes stress tau = mu [(grad u + grad u^T) - (2/3)(div u) I] (Sec. 2)
+# and the convection in divergence form C(u) = div(u u) - u div(u).  Central
+# second-order differences on the MAC grid; z walls are no-slip.
+
+def _zinterp(g, a):
+    """Layered a (nz layers) carried to the interior z-faces 1..nz-1 by the
+    mean of the two layers (returned with nz + 1 planes, wall planes zero).
+    On the paper's uniform grid this is the central interpolation and keeps
+    the convection term energy-conserving; on a stretched z it stays second
+    order for smooth stretching."""
+    out = np.zeros((g.nz + 1,) + a.shape[1:])
+    out[1:-1] = 0.5 * (a[1:] + a[:-1])
+    return out
+
+
+def convection(g, u, v, w):
+    """C(u) = div(u u) - u div(u) at the u, v and w points (w: interior faces;
+    the wall planes are zero).  Products live at cell centres (normal terms)
+    and at cell edges (cross terms); a velocity is carried to an edge by the
+    mean of its two values in x, y or z."""
+    D = divergence(g, u, v, w)
+    # normal fluxes at cell centres
+    fxx = (0.5 * (u + np.roll(u, -1, axis=2))) ** 2
+    fyy = (0.5 * (v + np.roll(v, -1, axis=1))) ** 2
+    wc = 0.5 * (w[1:] + w[:-1])
+    fzz = wc ** 2
+    # cross fluxes at edges: xy edge (i-1/2, j-1/2), xz edge (i-1/2, k-1/2), yz edge (j-1/2, k-1/2)
+    fxy = 0.5 * (u + np.roll(u, 1, axis=1)) * 0.5 * (v + np.roll(v, 1, axis=2))
+    fxz = _zinterp(g, u) * 0.5 * (w + np.roll(w, 1, axis=2))
+    fyz = _zinterp(g, v) * 0.5 * (w + np.roll(w, 1, axis=1))
+    dzf = g.dzf[:, None, None]
+    cx = ((fxx - np.roll(fxx, 1, axis=2)) / g.dx + (np.roll(fxy, -1, axis=1) - fxy) / g.dy
+          + (fxz[1:] - fxz[:-1]) / dzf - u * 0.5 * (D + np.roll(D, 1, axis=2)))
+    cy = ((np.roll(fxy, -1, axis=2) - fxy) / g.dx + (fyy - np.roll(fyy, 1, axis=1)) / g.dy
+          + (fyz[1:] - fyz[:-1]) / dzf - v * 0.5 * (D + np.roll(D, 1, axis=1)))
+    cz = np.zeros((g.nz + 1, g.ny, g.nx))
+    dzc = g.dzc[1:-1, None, None]
+    cz[1:-1] = ((np.roll(fxz[1:-1], -1, axis=2) - fxz[1:-1]) / g.dx
+                + (np.roll(fyz[1:-1], -1, axis=1) - fyz[1:-1]) / g.dy
+                + (fzz[1:] - fzz[:-1]) / dzc - w[1:-1] * _zinterp(g, D)[1:-1])
+    return cx, cy, cz
+
+
+def viscous(g, mu, u, v, w):
+    """div tau at the u, v and w points, tau = mu [(grad u + grad u^T) -
+    (2/3)(div u) I].  Normal stresses at cell centres with mu of the cell;
+    shear stresses at edges with the mean mu of the (up to) four cells
+    around the edge.  No-slip z walls: the wall velocity is zero, so the
+    wall shear uses the half-cell distance to the wall."""
+    D = divergence(g, u, v, w)
+    dzf = g.dzf[:, None, None]
+    txx = mu * (2.0 * (np.roll(u, -1, axis=2) - u) / g.dx - 2.0 / 3.0 * D)
+    tyy = mu * (2.0 * (np.roll(v, -1, axis=1) - v) / g.dy - 2.0 / 3.0 * D)
+    tzz = mu * (2.0 * (w[1:] - w[:-1]) / dzf - 2.0 / 3.0 * D)
+    mxy = 0.25 * (mu + np.roll(mu, 1, axis=2) + np.roll(mu, 1, axis=1) + np.roll(np.roll(mu, 1, axis=1), 1, axis=2))
+    txy = mxy * ((u - np.roll(u, 1, axis=1)) / g.dy + (v - np.roll(v, 1, axis=2)) / g.dx)
+
+    def edge_z(a, axis):
+        """Shear tau_az at the edges between the a-faces and the z-faces
+        (nz + 1 planes): interior planes from the two layers, wall planes
+        from the first layer and the zero wall velocity."""
+        m2 = 0.5 * (mu + np.roll(mu, 1, axis=axis))          # mean over the two cells in x (or y)
+        t = np.empty((g.nz + 1, g.ny, g.nx))
+        dwd = (w - np.roll(w, 1, axis=axis)) / (g.dx if axis == 2 else g.dy)
+        t[1:-1] = 0.5 * (m2[1:] + m2[:-1]) * ((a[1:] - a[:-1]) / g.dzc[1:-1, None, None] + dwd[1:-1])
+        t[0] = m2[0] * (a[0] - 0.0) / (g.zc[0] - g.zf[0])
+        t[-1] = m2[-1] * (0.0 - a[-1]) / (g.zf[-1] - g.zc[-1])
+        return t
+
+    txz = edge_z(u, 2)
+    tyz = edge_z(v, 1)
+    fx = ((txx - np.roll(txx, 1, axis=2)) / g.dx + (np.roll(txy, -1, axis=1) - txy) / g.dy
+          + (txz[1:] - txz[:-1]) / dzf)
+    fy = ((np.roll(txy, -1, axis=2) - txy) / g.dx + (tyy - np.roll(tyy, 1, axis=1)) / g.dy
+          + (tyz[1:] - tyz[:-1]) / dzf)
+    fz = np.zeros((g.nz + 1, g.ny, g.nx))
+    fz[1:-1] = ((np.roll(txz[1:-1], -1, axis=2) - txz[1:-1]) / g.dx
+                + (np.roll(tyz[1:-1], -1, axis=1) - tyz[1:-1]) / g.dy
+                + (tzz[1:] - tzz[:-1]) / g.dzc[1:-1, None, None])
+    return fx, fy, fz
+
+
+def predictor_rhs(g, u, v, w, rho, mu, grav, force=None):
+    """Eq. 32 without the surface-tension force of the VOF model (out of
+    scope): RU = -C(u) + (1/rho_f)[div tau + f] + g, with f an optional
+    force on the faces (fx, fy, fz) given by the caller.  The w wall planes
+    are zero."""
+    cx, cy, cz = convection(g, u, v, w)
+    vx, vy, vz = viscous(g, mu, u, v, w)
+    rx, ry, rz = face_density(g, rho)
+    if force is not None:
+        vx, vy, vz = vx + force[0], vy + force[1], vz + force[2]
+    ru = -cx + vx / rx + grav[0]
+    rv = -cy + vy / ry + grav[1]
+    rw = -cz + vz / rz + grav[2]
+    rw[0] = 0.0
+    rw[-1] = 0.0
+    return ru, rv, rw
+
+
+def predictor(g, u, v, w, rho, mu, grav, dt_new, dt_old=None, ru_prev=None, force=None):
+    """Eq. 29 (Adams-Bashforth): u* = u^n + dt [(1 + r/2) RU^n - (r/2) RU^{n-1}],
+    r = dt_new/dt_old; the first step (no RU^{n-1}) is forward Euler.
+    Returns (u*, v*, w*) and RU^n."""
+    ru = predictor_rhs(g, u, v, w, rho, mu, grav, force)
+    if ru_prev is None:
+        a, b = 1.0, 0.0
+        ru_prev = (0.0, 0.0, 0.0)
+    else:
+        r = dt_new / dt_old
+        a, b = 1.0 + 0.5 * r, 0.5 * r
+    out = tuple(x + dt_new * (a * q - b * qp) for x, q, qp in zip((u, v, w), ru, ru_prev))
+    out[2][0] = 0.0
+    out[2][-1] = 0.0
+    return out, ru

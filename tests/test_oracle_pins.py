@@ -402,3 +402,106 @@ def test_divergence_source_special_cases():
     S0 = orc.divergence_source(g, phi, kc, T, p0, gamma, 0.0)
     assert _rel(S0 * p0, (gamma - 1) / gamma * phi * (dr.assemble_conduction(8, 8, 8, 1.0, 1.0, g.zf, kc)
                                                         @ T.ravel()).reshape(g.shape)) < 1e-12
+
+
+# --- momentum predictor (Eqs. 29, 32; Newton-Stokes stress) -----------------
+
+def _curl_field(g, seed):
+    """A discretely divergence-free MAC field: the discrete curl of a vector
+    potential on the cell edges, zero on the wall edges so that w = 0 on the
+    walls."""
+    nx, ny, nz = g.nx, g.ny, g.nz
+    rng = np.random.default_rng(seed)
+    Ax = rng.standard_normal((nz + 1, ny, nx)); Ay = rng.standard_normal((nz + 1, ny, nx))
+    Az = rng.standard_normal((nz, ny, nx))
+    Ax[0] = Ax[-1] = 0.0; Ay[0] = Ay[-1] = 0.0
+    dzf = g.dzf[:, None, None]
+    u = (np.roll(Az, -1, axis=1) - Az) / g.dy - (Ay[1:] - Ay[:-1]) / dzf
+    v = (Ax[1:] - Ax[:-1]) / dzf - (np.roll(Az, -1, axis=2) - Az) / g.dx
+    w = (np.roll(Ay, -1, axis=2) - Ay) / g.dx - (np.roll(Ax, -1, axis=1) - Ax) / g.dy
+    return u, v, w
+
+
+def test_convection_conserves_momentum_and_energy():
+    """For a divergence-free field, the central divergence form conserves x
+    and y momentum and the kinetic energy (uniform grid, the paper's)."""
+    g = _grid(12, 10, 9, 1.0, 0.8, 0.6)
+    u, v, w = _curl_field(g, 40)
+    assert np.abs(orc.divergence(g, u, v, w)).max() < 1e-10
+    cx, cy, cz = orc.convection(g, u, v, w)
+    dv = g.cell_volume()
+    dvw = (g.dx * g.dy * g.dzc)[:, None, None]
+    scale = np.sum(np.abs(u * cx) * dv)
+    assert abs(np.sum(cx * dv)) < 1e-13 * np.sum(np.abs(cx) * dv)
+    assert abs(np.sum(cy * dv)) < 1e-13 * np.sum(np.abs(cy) * dv)
+    energy = np.sum(u * cx * dv) + np.sum(v * cy * dv) + np.sum(w * cz * dvw)
+    assert abs(energy) < 1e-13 * scale
+
+
+def test_viscous_term_is_mu_laplacian_for_a_solenoidal_mode():
+    """Constant mu, a divergence-free single Fourier mode in x and y with no
+    z dependence: away from the walls div tau = mu * lambda * u with the
+    modified-wavenumber eigenvalue (the transpose and -2/3 div u parts cancel)."""
+    nx, ny, nz, a, b, mu = 16, 12, 6, 3, 2, 0.7
+    g = _grid(nx, ny, nz, 1.0, 0.75, 0.5)
+    xe = (np.arange(nx) - 0.5) * g.dx; ye = (np.arange(ny) - 0.5) * g.dy     # edge coordinates
+    psi = np.sin(2 * np.pi * a * xe[None, None, :] / g.lx) * np.sin(2 * np.pi * b * ye[None, :, None] / g.ly)
+    psi = np.broadcast_to(psi, (nz, ny, nx)).copy()
+    u = (np.roll(psi, -1, axis=1) - psi) / g.dy
+    v = -(np.roll(psi, -1, axis=2) - psi) / g.dx
+    w = np.zeros((nz + 1, ny, nx))
+    lam = -4 / g.dx ** 2 * np.sin(np.pi * a / nx) ** 2 - 4 / g.dy ** 2 * np.sin(np.pi * b / ny) ** 2
+    fx, fy, fz = orc.viscous(g, np.full(g.shape, mu), u, v, w)
+    assert _rel(fx[1:-1], mu * lam * u[1:-1]) < 1e-12
+    assert _rel(fy[1:-1], mu * lam * v[1:-1]) < 1e-12
+    assert np.abs(fz).max() < 1e-9 * np.abs(fx).max()
+
+
+def test_viscous_shear_flow_is_the_conduction_operator():
+    """u = u(z), v = w = 0, mu = mu(z): away from the walls the x component
+    of div tau is d/dz(mu du/dz), the same operator as the pinned conduction
+    term with k = mu (stretched z)."""
+    nx, ny, nz = 6, 5, 12
+    g = _grid(nx, ny, nz, 1.0, 1.0, 0.8, beta=1.5)
+    rng = np.random.default_rng(41)
+    uz = rng.standard_normal(nz); muz = rng.uniform(0.5, 2.0, nz)
+    u = np.broadcast_to(uz[:, None, None], g.shape).copy()
+    mu = np.broadcast_to(muz[:, None, None], g.shape).copy()
+    zero = np.zeros(g.shape)
+    fx, fy, fz = orc.viscous(g, mu, u, zero, np.zeros((nz + 1, ny, nx)))
+    ref = orc.conduction(g, mu, u)
+    assert _rel(fx[1:-1], ref[1:-1]) < 1e-12
+    assert np.abs(fy).max() < 1e-12 and np.abs(fz).max() < 1e-12
+
+
+def test_poiseuille_profile_gives_constant_viscous_force():
+    """u = z (Lz - z), uniform z, constant mu and rho: no convection, and the
+    viscous force is -2 mu in every layer off the walls (second differences
+    are exact for a quadratic), so RU = -2 mu / rho + g there."""
+    nx, ny, nz, mu, rho, lz = 8, 6, 10, 0.3, 2.0, 1.0
+    g = _grid(nx, ny, nz, 1.0, 1.0, lz)
+    u = np.broadcast_to((g.zc * (lz - g.zc))[:, None, None], g.shape).copy()
+    zero = np.zeros(g.shape); wz = np.zeros((nz + 1, ny, nx))
+    cx, cy, cz = orc.convection(g, u, zero, wz)
+    assert max(np.abs(cx).max(), np.abs(cy).max(), np.abs(cz).max()) < 1e-14
+    ru, rv, rw = orc.predictor_rhs(g, u, zero, wz, np.full(g.shape, rho), np.full(g.shape, mu), (0.1, 0.0, -9.81))
+    assert np.allclose(ru[1:-1], -2 * mu / rho + 0.1, rtol=1e-12, atol=1e-12)
+    assert np.allclose(rv, 0.0, atol=1e-13)
+    assert np.allclose(rw[1:-1], -9.81, rtol=1e-13)
+    assert rw[0].max() == 0.0 and rw[-1].max() == 0.0
+
+
+def test_predictor_time_stepping():
+    """Eq. 29: forward Euler on the first step; Adams-Bashforth with a
+    constant RU history reduces to u + dt RU; a fluid at rest with variable
+    density only feels gravity (rho g / rho = g)."""
+    g = _grid(8, 8, 6, beta=1.5)
+    rng = np.random.default_rng(42)
+    rho = rng.uniform(1.0, 1000.0, g.shape); mu = rng.uniform(1e-3, 1.0, g.shape)
+    zero = np.zeros(g.shape); wz = np.zeros((g.nz + 1, g.ny, g.nx))
+    grav = (0.0, 0.5, -9.81)
+    (us, vs, ws), ru = orc.predictor(g, zero, zero, wz, rho, mu, grav, 1e-3)
+    assert np.allclose(us, 0.0) and np.allclose(vs, 0.5e-3, rtol=1e-14) and np.allclose(ws[1:-1], -9.81e-3, rtol=1e-14)
+    u, v, w = _curl_field(g, 43)
+    (a1, b1, c1), ru1 = orc.predictor(g, u, v, w, rho, mu, grav, 2e-3, 1e-3, ru_prev=orc.predictor_rhs(g, u, v, w, rho, mu, grav))
+    assert _rel(a1, u + 2e-3 * ru1[0]) < 1e-14 and _rel(c1[1:-1], w[1:-1] + 2e-3 * ru1[2][1:-1]) < 1e-14
