@@ -335,6 +335,37 @@ def run_ours(args, rank, world, local_rank):
                                     "frac_of_measured_hbm": round(gbs / hbm_peak, 4)}
         out["thermo"]["note"] = ("Eq. 34 source and Eq. 30 rate at the benchmark grid (fields larger than L2); "
                                  "p0_rate includes its device-to-host read of the rate")
+        # the momentum predictor (Eqs. 29, 32) on the same grid: u^n = u*, a
+        # two-phase viscosity, the previous RU, gravity; FP64 stencil
+        muf = T(1.8e-5 * w.phi + 1e-3 * (1.0 - w.phi))
+        ost = [torch.empty_like(Tf), torch.empty_like(Tf), torch.empty_like(ws)]
+        rus = [torch.empty_like(Tf), torch.empty_like(Tf), torch.empty_like(ws)]
+        prev = [torch.zeros_like(Tf), torch.zeros_like(Tf), torch.zeros_like(ws)]
+
+        def pred():
+            pp.pressure_predictor(plan.handle, us, vs, ws, rho, muf, (0.0, 0.0, -9.81), w.dt, ost,
+                                  dt_old=w.dt, ru_prev=prev, ru_out=rus)
+        for _ in range(3):
+            pred()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            pred()
+        e1.record()
+        torch.cuda.synchronize()
+        tms = e0.elapsed_time(e1) / reps
+        # bytes: u, v, w, rho, mu, 3 previous RU read; u*, 3 RU written; the
+        # divergence scratch written and read (16 fields of a cell each)
+        nbytes = 16 * 8 * npts
+        ops = 260  # FP64 operations per cell, counted from the stencil (both kernels)
+        rate = ops * npts / (tms / 1e3)
+        gbs = nbytes / (tms / 1e3) / 1e9
+        out["predictor"] = {"ms": round(tms, 3), "bound": "alu (FP64 pipe)", "fp64_ops_per_cell": ops,
+                            "achieved_fp64_gops": round(rate / 1e9, 1), "frac_of_fp64_peak": round(rate / fp64_slots, 4),
+                            "algorithmic_bytes": int(nbytes), "achieved_gbs": round(gbs, 1),
+                            "frac_of_measured_hbm": round(gbs / hbm_peak, 4),
+                            "note": "Eqs. 29, 32 at the benchmark grid, Adams-Bashforth step, FP64"}
 
     # end to end through the C ABI with host (pinned) buffers
     if not args.no_e2e:

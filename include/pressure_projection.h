@@ -162,6 +162,33 @@ pp_status pressure_divergence_source(pp_plan plan, const double* phi, const doub
                                      const double* T, double p0, double gamma, double dp0dt,
                                      double* S);
 
+/* ---- momentum predictor ------------------------------------------------
+ * Eq. 29 (Adams-Bashforth):
+ *   u* = u^n + dt_new [ (1 + r/2) RU^n - (r/2) RU^{n-1} ],  r = dt_new / dt_old,
+ * forward Euler when ru_prev is NULL (the first step), with Eq. 32
+ *   RU = -C(u) + (1/rho_f) [ div tau(mu, u) + f ] + g,
+ * C(u) = div(u u) - u div(u) (central divergence form) and the
+ * Newton-Stokes stress tau = mu [(grad u + grad u^T) - (2/3)(div u) I]
+ * (Sec. 2).  Central second-order MAC differences: products and normal
+ * stresses at cell centres, cross products and shear stresses at cell edges
+ * (a velocity carried to an edge by the mean of its two values, mu by the
+ * mean of the cells around the edge, rho_f by the mean of the face's two
+ * cells); periodic x and y, no-slip z walls.  The surface-tension force of
+ * the VOF model is out of scope: force (three face fields, or NULL) may
+ * carry any body force, added to div tau.
+ * In: u, v, w (faces of u^n; w wall planes zero), rho, mu (cell fields),
+ * gravity[3], dt_new > 0, dt_old (> 0 with ru_prev), ru_prev[3] (RU^{n-1}
+ * on the faces, or NULL).  Out: u_star[3] (u*, v*, w*; w wall planes zero),
+ * ru_out[3] (RU^n for the next step, or NULL).  Device pointers only
+ * (PP_ERR_INVALID_ARG otherwise); enqueued on the plan's stream.  Uses the
+ * plan's workspace, so it must not overlap a pressure_correct on the same
+ * plan. */
+pp_status pressure_predictor(pp_plan plan, const double* u, const double* v, const double* w,
+                             const double* rho, const double* mu, const double* const force[3],
+                             const double gravity[3], double dt_new, double dt_old,
+                             const double* const ru_prev[3], double* const u_star[3],
+                             double* const ru_out[3]);
+
 /* Method III projection (Algorithm 1, Sec. 3.3.1; Eqs. new_poisson, corr),
  * or Method I or II when pressure_plan_set_method selected one.
  * In: us, vs, ws (u*, faces; ws wall planes are taken as zero), rho (cell

@@ -16,12 +16,12 @@ using namespace pp;
 namespace {
 enum KId { K_RESID, K_CHECK, K_FFTY_F, K_TRI, K_FFTY_I, K_FFTX_I, K_INIT, K_PREP, K_MEANS, K_RHSB,
            K_RMEAN, K_CORR, K_MIX, K_ADJ_RHS, K_ADJ_FIN, K_ADJ_GRHO, K_RHOT, K_FOLD, K_THERMO, K_SOURCE,
-           K_COUNT };
+           K_PRED, K_COUNT };
 const char* const kNames[K_COUNT] = {
     "resid_fftx", "check", "ffty_fwd", "tridiag_z", "ffty_inv", "fftx_inv_update", "init_status",
     "prep_faces", "mean_S", "rhs_b", "remove_mean", "correct", "mixture_density", "adj_rhs",
-    "adj_finish", "adj_grho", "rho_tilde", "fold_pending", "p0_rate", "divergence_source"};
-const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1, 2, 1, 2, 1};
+    "adj_finish", "adj_grho", "rho_tilde", "fold_pending", "p0_rate", "divergence_source", "predictor"};
+const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1, 2, 1, 2, 1, 2};
 struct Rec { int kid; cudaEvent_t a, b; };
 struct Prof {
   bool on = false;
@@ -627,6 +627,36 @@ pp_status pressure_p0_rate(pp_plan P, const double* phi, const double* kc, const
   PP_CK(cudaStreamSynchronize(P->stream));
   if (!(out[2] > 0.0) || !std::isfinite(out[3])) return PP_ERR_NUMERIC;
   *rp = out[3];
+  return PP_OK;
+}
+
+pp_status pressure_predictor(pp_plan P, const double* u, const double* v, const double* w, const double* rho,
+                             const double* mu, const double* const force[3], const double gravity[3], double dt_new,
+                             double dt_old, const double* const ru_prev[3], double* const u_star[3],
+                             double* const ru_out[3]) {
+  if (check_plan(P) != PP_OK || !u || !v || !w || !rho || !mu || !gravity || !u_star) return PP_ERR_INVALID_ARG;
+  if (!u_star[0] || !u_star[1] || !u_star[2] || !(dt_new > 0.0)) return PP_ERR_INVALID_ARG;
+  const double* f[3] = {nullptr, nullptr, nullptr};
+  const double* prev[3] = {nullptr, nullptr, nullptr};
+  double* ru[3] = {nullptr, nullptr, nullptr};
+  for (int q = 0; q < 3; ++q) {
+    if (force) f[q] = force[q];
+    if (ru_prev) prev[q] = ru_prev[q];
+    if (ru_out) ru[q] = ru_out[q];
+  }
+  const bool ab2 = prev[0] || prev[1] || prev[2];
+  if (ab2 && (!prev[0] || !prev[1] || !prev[2] || !(dt_old > 0.0))) return PP_ERR_INVALID_ARG;
+  // device pointers only: the call takes up to 17 fields
+  const void* all[] = {u, v, w, rho, mu, f[0], f[1], f[2], prev[0], prev[1], prev[2],
+                       u_star[0], u_star[1], u_star[2], ru[0], ru[1], ru[2]};
+  for (const void* q : all)
+    if (q != nullptr && !is_device_ptr(q)) return PP_ERR_INVALID_ARG;
+  const double r = ab2 ? dt_new / dt_old : 0.0;
+  const double a = ab2 ? 1.0 + 0.5 * r : 1.0, b = ab2 ? 0.5 * r : 0.0;
+  // the cell divergence goes to the plan's right-hand-side workspace (free
+  // between projections)
+  PP_K(P, K_PRED, launch_predictor(P->geo, u, v, w, rho, mu, f, prev, gravity, dt_new, a, b, P->d_b, u_star, ru,
+                                   P->stream));
   return PP_OK;
 }
 

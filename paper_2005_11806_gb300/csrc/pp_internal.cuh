@@ -229,6 +229,13 @@ cudaError_t launch_thermo_rate(const Geo& g, const double* phi, const double* kc
 // Eq. 34: S = (1/p0) [ (gamma - 1)/gamma div(k grad T) - dp0dt / gamma ] Phi.
 cudaError_t launch_divergence_source(const Geo& g, const double* phi, const double* kc, const double* T,
                                      double p0, double gamma, double dp0dt, double* S, cudaStream_t s);
+// Momentum predictor (Eqs. 29, 32): out = u + dt (a RU - b prev) on the u, v
+// and w faces (w wall planes zero); ru (entries may be null) receives RU;
+// f and prev entries may be null.  D: a cell-field scratch (the divergence).
+cudaError_t launch_predictor(const Geo& g, const double* u, const double* v, const double* w, const double* rho,
+                             const double* mu, const double* const f[3], const double* const prev[3],
+                             const double grav[3], double dt, double a, double b, double* D, double* const out[3],
+                             double* const ru[3], cudaStream_t s);
 cudaError_t launch_adj_grho(const Geo& g, const double* tx, const double* ty, const double* tz,
                             double* grho, cudaStream_t s);
 

@@ -260,6 +260,148 @@ __global__ void k_divergence_source(Geo g, const double* __restrict__ phi, const
     S[c] = (a * cell_conduction(g, kc, T, c) - b) * phi[c] * ip0;
 }
 
+// ---- momentum predictor (Eqs. 29, 32) ---------------------------------------
+
+__global__ void k_cell_divergence(Geo g, const double* __restrict__ u, const double* __restrict__ v,
+                                  const double* __restrict__ w, double* __restrict__ D) {
+  const size_t plane = (size_t)g.nx * g.ny, n = plane * g.nz;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const CellIdx x = cell_index(g, c);
+    D[c] = (u[x.cip] - u[c]) / g.dx + (v[x.cjp] - v[c]) / g.dy + (w[c + plane] - w[c]) * g.inv_dzf[x.k];
+  }
+}
+
+// Predicted velocity at the three low faces of cell (i, j, k): the u-face
+// i-1/2, the v-face j-1/2 and (k >= 1) the w-face k-1/2.  RU = -C(u) +
+// (1/rho_f)[div tau + f] + g with C(u) = div(u u) - u div(u) (central
+// divergence form: normal products at cell centres, cross products at edges,
+// a velocity carried to an edge by the mean of its two values) and the
+// Newton-Stokes stress (normal parts at cell centres with the cell's mu,
+// shear parts at edges with the mean mu of the cells around the edge;
+// no-slip z walls: wall velocity zero, half-cell distance to the wall).
+// u* = u + dt (a RU - b RU_prev).  D: cell divergence.
+__global__ void k_predictor(Geo g, const double* __restrict__ u, const double* __restrict__ v,
+                            const double* __restrict__ w, const double* __restrict__ rho,
+                            const double* __restrict__ mu, const double* __restrict__ D,
+                            const double* __restrict__ fx, const double* __restrict__ fy,
+                            const double* __restrict__ fz, const double* __restrict__ pu,
+                            const double* __restrict__ pv, const double* __restrict__ pw, double gx, double gy,
+                            double gz, double dt, double a, double b, double* __restrict__ us,
+                            double* __restrict__ vs, double* __restrict__ ws, double* __restrict__ ru,
+                            double* __restrict__ rv, double* __restrict__ rw) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const size_t plane = (size_t)nx * ny, n = plane * nz;
+  const double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
+  const double two3 = 2.0 / 3.0;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / plane);
+    const int im = i == 0 ? nx - 1 : i - 1, ip = i + 1 == nx ? 0 : i + 1;
+    const int jm = j == 0 ? ny - 1 : j - 1, jp = j + 1 == ny ? 0 : j + 1;
+    auto at = [&](int ii, int jj, int kk) { return ((size_t)kk * ny + jj) * nx + ii; };
+    const double idzf = g.inv_dzf[k];
+    // mean mu over the four cells around an x-y edge (i'-1/2, j'-1/2) of layer kk
+    auto mxy = [&](int ii, int jj, int kk) {
+      const int iim = ii == 0 ? nx - 1 : ii - 1, jjm = jj == 0 ? ny - 1 : jj - 1;
+      return 0.25 * (mu[at(ii, jj, kk)] + mu[at(iim, jj, kk)] + mu[at(ii, jjm, kk)] + mu[at(iim, jjm, kk)]);
+    };
+    // shear stress tau_xy at the edge (i'-1/2, j'-1/2) of layer kk
+    auto txy = [&](int ii, int jj, int kk) {
+      const int iim = ii == 0 ? nx - 1 : ii - 1, jjm = jj == 0 ? ny - 1 : jj - 1;
+      return mxy(ii, jj, kk) * ((u[at(ii, jj, kk)] - u[at(ii, jjm, kk)]) * idy +
+                                (v[at(ii, jj, kk)] - v[at(iim, jj, kk)]) * idx);
+    };
+    // tau_xz at the edge (i'-1/2, kk-1/2), kk in [0, nz]; tau_yz likewise
+    auto txz = [&](int ii, int jj, int kk) {
+      const int iim = ii == 0 ? nx - 1 : ii - 1;
+      if (kk == 0) return 0.5 * (mu[at(ii, jj, 0)] + mu[at(iim, jj, 0)]) * u[at(ii, jj, 0)] * 2.0 * g.inv_dzf[0];
+      if (kk == nz)
+        return -0.5 * (mu[at(ii, jj, nz - 1)] + mu[at(iim, jj, nz - 1)]) * u[at(ii, jj, nz - 1)] * 2.0 *
+               g.inv_dzf[nz - 1];
+      const double m = 0.25 * (mu[at(ii, jj, kk)] + mu[at(iim, jj, kk)] + mu[at(ii, jj, kk - 1)] +
+                               mu[at(iim, jj, kk - 1)]);
+      return m * ((u[at(ii, jj, kk)] - u[at(ii, jj, kk - 1)]) * g.inv_dzc[kk] +
+                  (w[at(ii, jj, kk)] - w[at(iim, jj, kk)]) * idx);
+    };
+    auto tyz = [&](int ii, int jj, int kk) {
+      const int jjm = jj == 0 ? ny - 1 : jj - 1;
+      if (kk == 0) return 0.5 * (mu[at(ii, jj, 0)] + mu[at(ii, jjm, 0)]) * v[at(ii, jj, 0)] * 2.0 * g.inv_dzf[0];
+      if (kk == nz)
+        return -0.5 * (mu[at(ii, jj, nz - 1)] + mu[at(ii, jjm, nz - 1)]) * v[at(ii, jj, nz - 1)] * 2.0 *
+               g.inv_dzf[nz - 1];
+      const double m = 0.25 * (mu[at(ii, jj, kk)] + mu[at(ii, jjm, kk)] + mu[at(ii, jj, kk - 1)] +
+                               mu[at(ii, jjm, kk - 1)]);
+      return m * ((v[at(ii, jj, kk)] - v[at(ii, jj, kk - 1)]) * g.inv_dzc[kk] +
+                  (w[at(ii, jj, kk)] - w[at(ii, jjm, kk)]) * idy);
+    };
+    // convective cross products at edges
+    auto fxy = [&](int ii, int jj, int kk) {  // u v at (i'-1/2, j'-1/2)
+      const int iim = ii == 0 ? nx - 1 : ii - 1, jjm = jj == 0 ? ny - 1 : jj - 1;
+      return 0.25 * (u[at(ii, jj, kk)] + u[at(ii, jjm, kk)]) * (v[at(ii, jj, kk)] + v[at(iim, jj, kk)]);
+    };
+    auto fxz = [&](int ii, int jj, int kk) {  // u w at (i'-1/2, kk-1/2); zero at the walls
+      if (kk == 0 || kk == nz) return 0.0;
+      const int iim = ii == 0 ? nx - 1 : ii - 1;
+      return 0.25 * (u[at(ii, jj, kk)] + u[at(ii, jj, kk - 1)]) * (w[at(ii, jj, kk)] + w[at(iim, jj, kk)]);
+    };
+    auto fyz = [&](int ii, int jj, int kk) {
+      if (kk == 0 || kk == nz) return 0.0;
+      const int jjm = jj == 0 ? ny - 1 : jj - 1;
+      return 0.25 * (v[at(ii, jj, kk)] + v[at(ii, jj, kk - 1)]) * (w[at(ii, jj, kk)] + w[at(ii, jjm, kk)]);
+    };
+    const double Dc = D[c];
+    // ---- x momentum at the u-face (i-1/2, j, k)
+    {
+      const size_t cm = at(im, j, k);
+      const double uc0 = 0.5 * (u[c] + u[at(ip, j, k)]), ucm = 0.5 * (u[cm] + u[c]);
+      const double conv = (uc0 * uc0 - ucm * ucm) * idx + (fxy(i, jp, k) - fxy(i, j, k)) * idy +
+                          (fxz(i, j, k + 1) - fxz(i, j, k)) * idzf - u[c] * 0.5 * (Dc + D[cm]);
+      const double t0 = mu[c] * (2.0 * (u[at(ip, j, k)] - u[c]) * idx - two3 * Dc);
+      const double tm = mu[cm] * (2.0 * (u[c] - u[cm]) * idx - two3 * D[cm]);
+      double visc = (t0 - tm) * idx + (txy(i, jp, k) - txy(i, j, k)) * idy + (txz(i, j, k + 1) - txz(i, j, k)) * idzf;
+      if (fx != nullptr) visc += fx[c];
+      const double r = -conv + visc / (0.5 * (rho[c] + rho[cm])) + gx;
+      us[c] = u[c] + dt * (a * r - (pu != nullptr ? b * pu[c] : 0.0));
+      if (ru != nullptr) ru[c] = r;
+    }
+    // ---- y momentum at the v-face (i, j-1/2, k)
+    {
+      const size_t cm = at(i, jm, k);
+      const double vc0 = 0.5 * (v[c] + v[at(i, jp, k)]), vcm = 0.5 * (v[cm] + v[c]);
+      const double conv = (fxy(ip, j, k) - fxy(i, j, k)) * idx + (vc0 * vc0 - vcm * vcm) * idy +
+                          (fyz(i, j, k + 1) - fyz(i, j, k)) * idzf - v[c] * 0.5 * (Dc + D[cm]);
+      const double t0 = mu[c] * (2.0 * (v[at(i, jp, k)] - v[c]) * idy - two3 * Dc);
+      const double tm = mu[cm] * (2.0 * (v[c] - v[cm]) * idy - two3 * D[cm]);
+      double visc = (txy(ip, j, k) - txy(i, j, k)) * idx + (t0 - tm) * idy + (tyz(i, j, k + 1) - tyz(i, j, k)) * idzf;
+      if (fy != nullptr) visc += fy[c];
+      const double r = -conv + visc / (0.5 * (rho[c] + rho[cm])) + gy;
+      vs[c] = v[c] + dt * (a * r - (pv != nullptr ? b * pv[c] : 0.0));
+      if (rv != nullptr) rv[c] = r;
+    }
+    // ---- z momentum at the w-face (i, j, k-1/2), interior faces only
+    if (k == 0) {
+      ws[c] = 0.0;
+      if (rw != nullptr) rw[c] = 0.0;
+    } else {
+      const size_t cm = c - plane;
+      const double wc0 = 0.5 * (w[c] + w[c + plane]), wcm = 0.5 * (w[cm] + w[c]);
+      const double idzc = g.inv_dzc[k];
+      const double conv = (fxz(ip, j, k) - fxz(i, j, k)) * idx + (fyz(i, jp, k) - fyz(i, j, k)) * idy +
+                          (wc0 * wc0 - wcm * wcm) * idzc - w[c] * 0.5 * (Dc + D[cm]);
+      const double t0 = mu[c] * (2.0 * (w[c + plane] - w[c]) * idzf - two3 * Dc);
+      const double tm = mu[cm] * (2.0 * (w[c] - w[cm]) * g.inv_dzf[k - 1] - two3 * D[cm]);
+      double visc = (txz(ip, j, k) - txz(i, j, k)) * idx + (tyz(i, jp, k) - tyz(i, j, k)) * idy + (t0 - tm) * idzc;
+      if (fz != nullptr) visc += fz[c];
+      const double r = -conv + visc / (0.5 * (rho[c] + rho[cm])) + gz;
+      ws[c] = w[c] + dt * (a * r - (pw != nullptr ? b * pw[c] : 0.0));
+      if (rw != nullptr) rw[c] = r;
+    }
+    if (k == nz - 1) {
+      ws[c + plane] = 0.0;
+      if (rw != nullptr) rw[c + plane] = 0.0;
+    }
+  }
+}
+
 // ---- adjoint ---------------------------------------------------------------
 // y = -dt * beta * W_f^{-1} g  (W_f = dzf of the layer on x/y faces, dzc on
 // interior z faces; wall z-faces zero).
@@ -415,6 +557,18 @@ cudaError_t launch_thermo_rate(const Geo& g, const double* phi, const double* kc
 cudaError_t launch_divergence_source(const Geo& g, const double* phi, const double* kc, const double* T,
                                      double p0, double gamma, double dp0dt, double* S, cudaStream_t s) {
   k_divergence_source<<<grid_for((size_t)g.nx * g.ny * g.nz), kThreads, 0, s>>>(g, phi, kc, T, p0, gamma, dp0dt, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_predictor(const Geo& g, const double* u, const double* v, const double* w, const double* rho,
+                             const double* mu, const double* const f[3], const double* const prev[3],
+                             const double grav[3], double dt, double a, double b, double* D, double* const out[3],
+                             double* const ru[3], cudaStream_t s) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  k_cell_divergence<<<grid_for(n), kThreads, 0, s>>>(g, u, v, w, D);
+  k_predictor<<<grid_for(n), kThreads, 0, s>>>(g, u, v, w, rho, mu, D, f[0], f[1], f[2], prev[0], prev[1], prev[2],
+                                               grav[0], grav[1], grav[2], dt, a, b, out[0], out[1], out[2], ru[0],
+                                               ru[1], ru[2]);
   return cudaGetLastError();
 }
 

@@ -59,6 +59,7 @@ EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_plan_set_m
            "pressure_solve_noalloc", "pressure_batch_create", "pressure_batch_layout",
            "pressure_batch_correct", "pressure_batch_destroy", "pressure_batch_mixture_density",
            "pressure_p0_rate", "pressure_dp0dt_extrapolate", "pressure_divergence_source",
+           "pressure_predictor",
            "pressure_status_string")
 
 
@@ -95,6 +96,8 @@ def lib():
     L.pressure_p0_rate.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, ctypes.POINTER(d)]
     L.pressure_dp0dt_extrapolate.argtypes = [d, d, d, d, ctypes.POINTER(d)]
     L.pressure_divergence_source.argtypes = [vp, vp, vp, vp, d, d, d, vp]
+    L.pressure_predictor.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(d), d, d,
+                                     ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.pressure_status_string.argtypes = [i]
     L.pressure_status_string.restype = ctypes.c_char_p
     for name in EXPORTS[:-1]:
@@ -237,6 +240,17 @@ def pressure_divergence_source(plan, phi, kc, T, p0, gamma, dp0dt, S):
     """Eq. 34: the divergence source S written into S (cell field)."""
     _check(lib().pressure_divergence_source(plan, _ptr(phi), _ptr(kc), _ptr(T), float(p0), float(gamma),
                                             float(dp0dt), _ptr(S)), "pressure_divergence_source")
+
+
+def pressure_predictor(plan, u, v, w, rho, mu, gravity, dt_new, u_star, dt_old=0.0, ru_prev=None,
+                       ru_out=None, force=None):
+    """Eqs. 29, 32: u_star = (u*, v*, w*) written in place; ru_out receives
+    RU^n; ru_prev = RU^{n-1} (None: forward Euler).  Device tensors only."""
+    trio = lambda ts: None if ts is None else (ctypes.c_void_p * 3)(*[_ptr(t) for t in ts])  # noqa: E731
+    grav = (ctypes.c_double * 3)(*[float(x) for x in gravity])
+    _check(lib().pressure_predictor(plan, _ptr(u), _ptr(v), _ptr(w), _ptr(rho), _ptr(mu), trio(force), grav,
+                                    float(dt_new), float(dt_old), trio(ru_prev), trio(u_star), trio(ru_out)),
+           "pressure_predictor")
 
 
 def pressure_last_info(plan):
