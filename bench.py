@@ -134,9 +134,9 @@ class ClockSampler:
 def algorithmic(kernel, w, precision):
     """Algorithmic bytes and FP64 flops of one launch of each kernel (what
     the step must move: every field read or written once per launch).  Mixed
-    plans recompute the residual exactly every 20th pass and update it in the
+    plans recompute the residual exactly every 40th pass and update it in the
     others, and bring p up to date only before an exact residual, so the
-    residual and inverse-x figures are averages over that 20-pass cycle."""
+    residual and inverse-x figures are averages over that 40-pass cycle."""
     npts = w.nx * w.ny * w.nz
     nsp = (w.nx // 2 + 1) * w.ny * w.nz
     cs = 16 if precision == "fp64" else 8  # bytes per spectral complex value
@@ -146,7 +146,7 @@ def algorithmic(kernel, w, precision):
             return {"bytes": 56 * npts + cs * nsp, "fp64_flops": 19 * npts + 45 * npts}
         exact = 56 * npts     # b, p, cx, cy, cz, diag (FP64), rhof; E written (FP32)
         update = 28 * npts    # E read + write, delta, cxf, cyf, czf, rhof (FP32)
-        return {"bytes": int(0.05 * exact + 0.95 * update) + cs * nsp, "fp64_flops": int(0.05 * 15 * npts)}
+        return {"bytes": int(0.025 * exact + 0.975 * update) + cs * nsp, "fp64_flops": int(0.025 * 15 * npts)}
     if kernel in ("ffty_fwd", "ffty_inv"):
         return {"bytes": 2 * cs * nsp, "fp64_flops": 0 if precision != "fp64" else 45 * npts}
     if kernel == "tridiag_z":
@@ -163,8 +163,8 @@ def algorithmic(kernel, w, precision):
         fold = 24 * npts      # p read + write (FP64), sum of increments read, increment written
         fresh = 8 * npts      # sum of increments written, increment written
         accum = 12 * npts     # sum of increments read + written, increment written
-        return {"bytes": int(0.05 * fold + 0.05 * fresh + 0.9 * accum) + cs * nsp,
-                "fp64_flops": int(0.05 * 2 * npts)}
+        return {"bytes": int(0.025 * fold + 0.025 * fresh + 0.95 * accum) + cs * nsp,
+                "fp64_flops": int(0.025 * 2 * npts)}
     return None
 
 
@@ -172,7 +172,7 @@ def algorithmic(kernel, w, precision):
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 512 x 512 x 128 case:
 # the same kernel, block shape and grid per plane as at 512^3, so the bytes
 # scale with the cells processed.  One updated-residual pass and one exact
-# pass; the launch average follows the 20-pass cycle.  Captured with
+# pass; the launch average follows the 40-pass exact/update cycle.  Captured with
 #   ncu --set full --clock-control none -k regex:"k_resid_fftx|k_ffty|k_tridiag_mixed|k_fftx_inv" -s 20 -c 5
 #   ncu --set full --clock-control none -k regex:"k_resid_fftx" -s 20 -c 1
 # on  python bench.py --n 512 --nz 128 --steps 1 --warmup 0 --maxit 21 --no-cpu-baseline --no-e2e --no-compare
@@ -267,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
                 "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": name,
                 "avg_launch_ms": round(avg_s * 1e3, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     if name == "resid_fftx" and args.precision == "mixed":
-        per_cell = 0.95 * RESID_DRAM_B_PER_CELL["update"] + 0.05 * RESID_DRAM_B_PER_CELL["exact"]
+        per_cell = 0.975 * RESID_DRAM_B_PER_CELL["update"] + 0.025 * RESID_DRAM_B_PER_CELL["exact"]
         roof["traffic"] = int(per_cell * npts)
         roof["traffic_source"] = "ncu DRAM bytes per cell at 512x512x128, scaled to the launch's cells"
     kernels = {k: {"launches": n, "total_ms": round(t, 3), "avg_ms": round(t / n, 4),

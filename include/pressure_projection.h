@@ -57,7 +57,7 @@ typedef enum { PP_BC_PERIODIC = 0, PP_BC_WALL = 1 } pp_bc;
 typedef enum {
     PP_FP64 = 0,       /* every step in FP64 */
     PP_MIXED_FP32 = 1, /* x/y transforms in FP32; the residual is recomputed exactly in
-                          FP64 every 20th pass and updated in FP32 in between (convergence
+                          FP64 every 40th pass and updated in FP32 in between (convergence
                           is only accepted on an exact residual); p is kept in FP64; the z
                           tridiagonal solve runs in FP32 on the well-conditioned (kx, ky)
                           columns (condition number <= 513) and in FP64 on the others,

@@ -152,7 +152,7 @@ cudaError_t timed(pp_plan_s* P, int kid, F&& f) {
 
 // Mixed plans recompute the FP64 residual from p every kExactEvery passes and
 // update it by the FP32 stencil of the last correction in between.
-constexpr int kExactEvery = 20;
+constexpr int kExactEvery = 40;
 
 template <typename X>
 pp_status dalloc(X** p, size_t bytes) {

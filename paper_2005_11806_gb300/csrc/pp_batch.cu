@@ -21,7 +21,7 @@ namespace {
 
 constexpr int kChunk = 2048;  // cells per block of the elementwise grouped kernels
 constexpr int kTriThreads = 128;
-constexpr int kExactEveryBatch = 20;
+constexpr int kExactEveryBatch = 40;
 
 struct GridDev {
   Geo g;

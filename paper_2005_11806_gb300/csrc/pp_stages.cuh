@@ -877,7 +877,7 @@ __device__ __forceinline__ void stage_fftx_inv_m(const Geo& g, const FftDesc& fx
   const bool need_p = !p_zero && MODE <= kInvFoldFresh;            // p is read
   constexpr bool need_s = MODE == kInvFold || MODE == kInvAccum;  // sdelta is read
   // p is prefetched in the plain mode of FP64 plans (every pass); the fold
-  // passes of mixed plans (one in twenty) read it where it is used, which keeps
+  // passes of mixed plans (one in forty) read it where it is used, which keeps
   // their registers within the other modes' budget
   const bool pre_p = need_p && MODE == kInvPlain && sizeof(T) == sizeof(double);
   constexpr bool F32 = std::is_same<T, float>::value;
