@@ -18,15 +18,20 @@ grid, velocities on faces, scalar fields at cell centres):
   nz are the no-penetration walls;
 * z may be stretched: ``zf`` holds the nz + 1 face coordinates, the cell
   centre is the midpoint of its faces, ``dzf[k]`` is the width of cell k and
-  ``dzc[k]`` the distance between the centres that share the z-face k.
+  ``dzc[k]`` the distance between the centres that share the z-face k;
+* with ``ywalls`` the y direction is bounded by two no-penetration walls
+  instead of being periodic.  ``v`` keeps its ``[nz][ny][nx]`` shape: row j
+  is still the face at ``j - 1/2``, and row 0 stands for both walls
+  (``y = 0`` and ``y = ly``), whose normal velocity is zero.
 
 Readings of points the paper leaves open:
 
 * the density on a face is the arithmetic mean of its two cells, so the
   centred form of ``u . grad(rho)`` used by Method III is
   ``D(rho_f u) - rho_c D u``;
-* the pressure satisfies homogeneous Neumann conditions at the z walls and is
-  periodic in x and y; it is fixed to zero volume-weighted mean;
+* the pressure satisfies homogeneous Neumann conditions at the z walls (and
+  at the y walls when y is bounded) and is periodic in the other directions;
+  it is fixed to zero volume-weighted mean;
 * the divergence target ``S`` (Eq. 34) is made compatible with the closed box
   by removing its volume-weighted mean;
 * Algorithm 1 is read as: iteration s uses ``u^s`` (``u^0 = u*``) to produce
@@ -45,13 +50,16 @@ Readings of points the paper leaves open:
 Pins (tests/test_oracle_pins.py): the single-mode closed form, dense LU
 solves of systems assembled entry by entry, exact-linear-field identities of
 D and G, the projection invariants, the constant-density reduction and the
-agreement of Algorithm 1 with the direct sparse solve.  ``adjoint_*`` is
+agreement of Algorithm 1 with the direct sparse solve.  With y walls: the
+cosine eigenmode in y, the even extension to a periodic problem of twice the
+width, dense LU with closed walls and the y-independent reduction.  ``adjoint_*`` is
 pinned by central finite differences of ``projection_direct`` and by the
 dot-product identity.
 """
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft as sfft
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
@@ -67,10 +75,12 @@ __all__ = [
 class Grid:
     """MAC grid: nx x ny cells of uniform width in x and y, nz cells in z with
     face coordinates ``zf`` (length nz + 1, increasing).  Sec. 3 uses uniform
-    spacing; a stretched ``zf`` is allowed."""
+    spacing; a stretched ``zf`` is allowed.  x is periodic, z has walls, y is
+    periodic unless ``ywalls``."""
 
-    def __init__(self, nx, ny, nz, lx, ly, zf):
+    def __init__(self, nx, ny, nz, lx, ly, zf, ywalls=False):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.ywalls = bool(ywalls)
         self.lx, self.ly = float(lx), float(ly)
         zf = np.asarray(zf, dtype=np.float64)
         if zf.shape != (self.nz + 1,) or np.any(np.diff(zf) <= 0):
@@ -101,17 +111,23 @@ def mixture_density(phi, rho_g, rho_l):
 
 
 def divergence(g, u, v, w):
-    """Discrete divergence D: faces -> cell centres (Sec. 3, MAC grid)."""
+    """Discrete divergence D: faces -> cell centres (Sec. 3, MAC grid).  With
+    y walls no flux crosses them: the wall row of v counts as zero."""
+    if g.ywalls:
+        v = np.array(v, dtype=np.float64, copy=True)
+        v[:, 0, :] = 0.0
     return ((np.roll(u, -1, axis=2) - u) / g.dx
             + (np.roll(v, -1, axis=1) - v) / g.dy
             + (w[1:] - w[:-1]) / g.dzf[:, None, None])
 
 
 def gradient(g, p):
-    """Discrete gradient G: cell centres -> faces.  The wall z-faces carry a
+    """Discrete gradient G: cell centres -> faces.  The wall faces carry a
     zero gradient (homogeneous Neumann pressure at no-penetration walls)."""
     gx = (p - np.roll(p, 1, axis=2)) / g.dx
     gy = (p - np.roll(p, 1, axis=1)) / g.dy
+    if g.ywalls:
+        gy[:, 0, :] = 0.0
     gz = np.zeros((g.nz + 1, g.ny, g.nx))
     gz[1:-1] = (p[1:] - p[:-1]) / g.dzc[1:-1, None, None]
     return gx, gy, gz
@@ -161,14 +177,24 @@ def solve_constant(g, f):
     z with the eigenvalues of the periodic second difference on its diagonal
     (Thomas algorithm), the singular (0, 0) column by a bordered dense solve
     that fixes its zero weighted mean, then the inverse DFTs.
+
+    With y walls the y step is the eigenbasis of the Neumann second
+    difference on cell centres, cos(pi m (j + 1/2) / ny), m = 0 .. ny - 1,
+    with eigenvalues -(4 / dy^2) sin^2(pi m / (2 ny)): scipy's DCT-II and its
+    inverse.
     """
     nx, ny, nz = g.nx, g.ny, g.nz
     fc = f - volume_mean(g, f)
-    fh = np.fft.rfft2(fc, axes=(1, 2))                  # [nz, ny, nx//2 + 1]
     kx = np.arange(nx // 2 + 1)
     ky = np.arange(ny)
-    lam = (-4.0 / g.dx ** 2 * np.sin(np.pi * kx / nx) ** 2)[None, :] \
-        + (-4.0 / g.dy ** 2 * np.sin(np.pi * ky / ny) ** 2)[:, None]
+    if g.ywalls:
+        fh = np.fft.rfft(fc, axis=2)
+        fh = sfft.dct(fh.real, type=2, axis=1) + 1j * sfft.dct(fh.imag, type=2, axis=1)
+        lam_y = -4.0 / g.dy ** 2 * np.sin(np.pi * ky / (2 * ny)) ** 2
+    else:
+        fh = np.fft.rfft2(fc, axes=(1, 2))              # [nz, ny, nx//2 + 1]
+        lam_y = -4.0 / g.dy ** 2 * np.sin(np.pi * ky / ny) ** 2
+    lam = (-4.0 / g.dx ** 2 * np.sin(np.pi * kx / nx) ** 2)[None, :] + lam_y[:, None]
     a, c = _z_coefficients(g)
     lam_safe = lam.copy()
     lam_safe[0, 0] = -1.0                               # replaced below
@@ -198,15 +224,23 @@ def solve_constant(g, f):
     rhs = np.zeros(nz + 1, dtype=np.complex128)
     rhs[:nz] = fh[:, 0, 0]
     ph[:, 0, 0] = np.linalg.solve(lz, rhs)[:nz]
-    p = np.fft.irfft2(ph, s=(ny, nx), axes=(1, 2))
+    if g.ywalls:
+        ph = sfft.idct(ph.real, type=2, axis=1) + 1j * sfft.idct(ph.imag, type=2, axis=1)
+        p = np.fft.irfft(ph, n=nx, axis=2)
+    else:
+        p = np.fft.irfft2(ph, s=(ny, nx), axes=(1, 2))
     return p - volume_mean(g, p)
 
 
 def correct_velocity(g, us, vs, ws, rho, p, dt):
-    """Correction step, Eq. (eqn:corr): u = u* - (dt / rho_f) G p."""
+    """Correction step, Eq. (eqn:corr): u = u* - (dt / rho_f) G p.  Wall
+    faces carry zero normal velocity."""
     rx, ry, rz = face_density(g, rho)
     gx, gy, gz = gradient(g, p)
-    return us - dt * gx / rx, vs - dt * gy / ry, ws - dt * gz / rz
+    v = vs - dt * gy / ry
+    if g.ywalls:
+        v[:, 0, :] = 0.0
+    return us - dt * gx / rx, v, ws - dt * gz / rz
 
 
 def method3(g, us, vs, ws, rho, S, dt, rtol=1e-13, maxit=1000):
@@ -341,11 +375,15 @@ def _sparse_operators(g):
         rows.append(r.ravel()); cols.append(cidx.ravel())
         vals.append(np.broadcast_to(val, r.shape).ravel())
 
-    # D: (u_{i+1} - u_i)/dx + (v_{j+1} - v_j)/dy + (w_{k+1} - w_k)/dzf_k
+    # D: (u_{i+1} - u_i)/dx + (v_{j+1} - v_j)/dy + (w_{k+1} - w_k)/dzf_k;
+    # with y walls the wall row of v (row 0, both walls) gets no entries.
+    vopen = np.ones(g.shape)
+    if g.ywalls:
+        vopen[:, 0, :] = 0.0
     add(cid, np.roll(fid_u, -1, axis=2), 1.0 / g.dx)
     add(cid, fid_u, -1.0 / g.dx)
-    add(cid, np.roll(fid_v, -1, axis=1), 1.0 / g.dy)
-    add(cid, fid_v, -1.0 / g.dy)
+    add(cid, np.roll(fid_v, -1, axis=1), np.roll(vopen, -1, axis=1) / g.dy)
+    add(cid, fid_v, -vopen / g.dy)
     inv_dzf = np.broadcast_to((1.0 / g.dzf)[:, None, None], g.shape)
     add(cid, fid_w[1:], inv_dzf)
     add(cid, fid_w[:-1], -inv_dzf)
@@ -356,8 +394,8 @@ def _sparse_operators(g):
     # (p_k - p_{k-1})/dzc_k; wall z-faces: no rows (zero gradient).
     add(fid_u, cid, 1.0 / g.dx)
     add(fid_u, np.roll(cid, 1, axis=2), -1.0 / g.dx)
-    add(fid_v, cid, 1.0 / g.dy)
-    add(fid_v, np.roll(cid, 1, axis=1), -1.0 / g.dy)
+    add(fid_v, cid, vopen / g.dy)
+    add(fid_v, np.roll(cid, 1, axis=1), -vopen / g.dy)
     inv_dzc = np.broadcast_to((1.0 / g.dzc[1:-1])[:, None, None], (nz - 1, ny, nx))
     add(fid_w[1:-1], cid[1:], inv_dzc)
     add(fid_w[1:-1], cid[:-1], -inv_dzc)
@@ -464,6 +502,8 @@ def adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv, gw):
     differentiation of the plain definition (``projection_direct``), with
     literal sparse transposes.  Small grids only.  Returns
     ``(g_us, g_vs, g_ws, g_rho)``; wall entries of ``g_ws`` are zero."""
+    if g.ywalls:
+        raise NotImplementedError("adjoint_direct: periodic y only")
     D, G = _sparse_operators(g)
     beta = _beta_vector(g, rho)
     A = (D @ sp.diags(beta) @ G).tocsr()
@@ -493,6 +533,8 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
     ``p`` is the converged pressure of the forward projection (computed
     here with the same tolerance when not given).
     """
+    if g.ywalls:
+        raise NotImplementedError("adjoint_method3: periodic y only")
     gw = _zero_walls(gw)
     rx, ry, rz = face_density(g, rho)
     wlay = g.dzf[:, None, None]
@@ -579,6 +621,8 @@ def convection(g, u, v, w):
     the wall planes are zero).  Products live at cell centres (normal terms)
     and at cell edges (cross terms); a velocity is carried to an edge by the
     mean of its two values in x, y or z."""
+    if g.ywalls:
+        raise NotImplementedError("convection: periodic y only")
     D = divergence(g, u, v, w)
     # normal fluxes at cell centres
     fxx = (0.5 * (u + np.roll(u, -1, axis=2))) ** 2
@@ -608,6 +652,8 @@ def viscous(g, mu, u, v, w):
     shear stresses at edges with the mean mu of the (up to) four cells
     around the edge.  No-slip z walls: the wall velocity is zero, so the
     wall shear uses the half-cell distance to the wall."""
+    if g.ywalls:
+        raise NotImplementedError("viscous: periodic y only")
     D = divergence(g, u, v, w)
     dzf = g.dzf[:, None, None]
     txx = mu * (2.0 * (np.roll(u, -1, axis=2) - u) / g.dx - 2.0 / 3.0 * D)

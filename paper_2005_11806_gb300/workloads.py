@@ -55,6 +55,7 @@ class Workload:
     rho_l: float = 1.0
     S: np.ndarray | None = None
     extra: dict = field(default_factory=dict)
+    ywalls: bool = False      # walls at y = 0 and y = ly (v row 0 is the wall face)
 
     @property
     def shape(self):
@@ -65,10 +66,10 @@ class Workload:
         return self.nx * self.ny * self.nz
 
 
-def random_faces(nx, ny, nz, sigma, seed, remove_mean=False, dtype=np.float64):
-    """Face velocities drawn i.i.d. N(0, sigma^2); wall z-faces set to zero.
-    With ``remove_mean`` each component's mean over its non-wall faces is
-    subtracted."""
+def random_faces(nx, ny, nz, sigma, seed, remove_mean=False, dtype=np.float64, ywalls=False):
+    """Face velocities drawn i.i.d. N(0, sigma^2); wall z-faces set to zero
+    (and, with ``ywalls``, the wall row 0 of v).  With ``remove_mean`` each
+    component's mean over its non-wall faces is subtracted."""
     out = []
     for comp, shape in ((1, (nz, ny, nx)), (2, (nz, ny, nx)), (3, (nz + 1, ny, nx))):
         rng = np.random.Generator(np.random.PCG64(seed + comp))
@@ -78,6 +79,10 @@ def random_faces(nx, ny, nz, sigma, seed, remove_mean=False, dtype=np.float64):
             a[-1] = 0.0
             if remove_mean:
                 a[1:-1] -= a[1:-1].mean()
+        elif comp == 2 and ywalls:
+            a[:, 0, :] = 0.0
+            if remove_mean:
+                a[:, 1:, :] -= a[:, 1:, :].mean()
         elif remove_mean:
             a -= a.mean()
         out.append(a.astype(dtype, copy=False))
@@ -173,9 +178,10 @@ def single_sphere_case(n=256, seed=1002, dt=1e-3, radius=0.15, centre=(0.5, 0.5,
 
 
 def place_bubbles(count, lx, ly, lz, nx, nz_min_cell, rmin, rmax, rng, gap_cells=2.0,
-                  max_tries=200000):
+                  max_tries=200000, ywalls=False):
     """Non-overlapping bubbles, centres uniform with rejection: at least
-    ``gap_cells`` cells apart (periodic in x/y) and r + gap from the walls."""
+    ``gap_cells`` cells apart (periodic in x/y) and r + gap from the walls
+    (the z walls, and the y walls with ``ywalls``)."""
     h = lx / nx
     out = []
     tries = 0
@@ -185,10 +191,14 @@ def place_bubbles(count, lx, ly, lz, nx, nz_min_cell, rmin, rmax, rng, gap_cells
         c = (rng.uniform(0, lx), rng.uniform(0, ly), rng.uniform(0, lz))
         if c[2] - r < gap_cells * nz_min_cell or c[2] + r > lz - gap_cells * nz_min_cell:
             continue
+        if ywalls and (c[1] - r < gap_cells * h or c[1] + r > ly - gap_cells * h):
+            continue
         ok = True
         for (ox, oy, oz, orr) in out:
             ddx = abs(c[0] - ox); ddx = min(ddx, lx - ddx)
-            ddy = abs(c[1] - oy); ddy = min(ddy, ly - ddy)
+            ddy = abs(c[1] - oy)
+            if not ywalls:
+                ddy = min(ddy, ly - ddy)
             if math.sqrt(ddx * ddx + ddy * ddy + (c[2] - oz) ** 2) < r + orr + gap_cells * h:
                 ok = False
                 break
@@ -247,3 +257,21 @@ def small_bubble_case(n=32, seed=1102, rho_ratio=1000.0, stretched=False, nz=Non
     us, vs, ws = random_faces(nx, ny, nz, 0.1, seed)
     return Workload(f"{nbubbles} bubbles {nx}x{ny}x{nz}", nx, ny, nz, 1.0, ny / nx, zf, dt,
                     us, vs, ws, phi, 1.0, rho_ratio, gas_source(phi))
+
+
+def channel_bubble_case(nx=32, ny=None, nz=None, seed=1202, rho_ratio=1000.0, stretched=False,
+                        nbubbles=3, dt=1e-3):
+    """Bubbles in a duct: periodic in x, walls in y and z.  The bubbles keep
+    a cell's gap from every wall; v* is zero on the y walls (row 0) as w* is
+    on the z walls."""
+    ny = ny or nx
+    nz = nz or nx
+    ly = ny / nx
+    zf = tanh_zfaces(nz, 1.0, 1.5) if stretched else uniform_zfaces(nz, 1.0)
+    rng = np.random.Generator(np.random.PCG64(seed + 10))
+    spheres = place_bubbles(nbubbles, 1.0, ly, 1.0, nx, float(np.min(np.diff(zf))),
+                            0.08, 0.16, rng, gap_cells=1.0, ywalls=True)
+    phi = spheres_phi(nx, ny, nz, 1.0, ly, zf, spheres)
+    us, vs, ws = random_faces(nx, ny, nz, 0.1, seed, ywalls=True)
+    return Workload(f"{nbubbles} bubbles in a duct {nx}x{ny}x{nz}", nx, ny, nz, 1.0, ly, zf, dt,
+                    us, vs, ws, phi, 1.0, rho_ratio, gas_source(phi), ywalls=True)

@@ -10,9 +10,10 @@ def metrics(nz, zf):
     return dzf, zc
 
 
-def assemble_variable(nx, ny, nz, lx, ly, zf, rho):
+def assemble_variable(nx, ny, nz, lx, ly, zf, rho, ywalls=False):
     """Matrix of p -> D(beta G p) with beta = 2/(rho_a + rho_b) on each face,
-    zero flux through the z walls, periodic x and y.  rho=None means beta=1."""
+    zero flux through the z walls, periodic x, and y periodic or (ywalls)
+    bounded by walls with zero flux.  rho=None means beta=1."""
     dx, dy = lx / nx, ly / ny
     dzf, zc = metrics(nz, zf)
     n = nx * ny * nz
@@ -38,6 +39,8 @@ def assemble_variable(nx, ny, nz, lx, ly, zf, rho):
                     A[r, idx(i + di, j, k)] += b
                     A[r, r] -= b
                 for dj in (+1, -1):
+                    if ywalls and not 0 <= j + dj < ny:
+                        continue  # y wall: no flux
                     nb = (k, (j + dj) % ny, i)
                     b = beta(cell, nb) / (dy * dy)
                     A[r, idx(i, j + dj, k)] += b
@@ -70,15 +73,19 @@ def cell_weights(nx, ny, nz, zf):
     return np.repeat(np.array(dzf), nx * ny)
 
 
-def divergence_loops(nx, ny, nz, lx, ly, zf, u, v, w):
+def divergence_loops(nx, ny, nz, lx, ly, zf, u, v, w, ywalls=False):
+    """With ywalls, v[k, j, i] is the face below cell j and both wall faces
+    (below cell 0, above cell ny - 1) carry no flux."""
     dx, dy = lx / nx, ly / ny
     dzf, _ = metrics(nz, zf)
     out = np.zeros((nz, ny, nx))
     for k in range(nz):
         for j in range(ny):
             for i in range(nx):
+                vlo = 0.0 if (ywalls and j == 0) else v[k, j, i]
+                vhi = 0.0 if (ywalls and j == ny - 1) else v[k, (j + 1) % ny, i]
                 out[k, j, i] = ((u[k, j, (i + 1) % nx] - u[k, j, i]) / dx
-                                + (v[k, (j + 1) % ny, i] - v[k, j, i]) / dy
+                                + (vhi - vlo) / dy
                                 + (w[k + 1, j, i] - w[k, j, i]) / dzf[k])
     return out
 

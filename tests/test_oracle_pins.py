@@ -505,3 +505,142 @@ def test_predictor_time_stepping():
     u, v, w = _curl_field(g, 43)
     (a1, b1, c1), ru1 = orc.predictor(g, u, v, w, rho, mu, grav, 2e-3, 1e-3, ru_prev=orc.predictor_rhs(g, u, v, w, rho, mu, grav))
     assert _rel(a1, u + 2e-3 * ru1[0]) < 1e-14 and _rel(c1[1:-1], w[1:-1] + 2e-3 * ru1[2][1:-1]) < 1e-14
+
+
+# --- walls in y ------------------------------------------------------------
+
+def _ygrid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, beta=None):
+    zf = wl.uniform_zfaces(nz, lz) if beta is None else wl.tanh_zfaces(nz, lz, beta)
+    return orc.Grid(nx, ny, nz, lx, ly, zf, ywalls=True)
+
+
+@pytest.mark.parametrize("dims,mode", [((16, 12, 10), (3, 5, 2)), ((10, 7, 6), (2, 6, 5)),
+                                       ((8, 16, 8), (0, 1, 0))])
+def test_ywalls_single_mode_closed_form(dims, mode):
+    """cos(pi b (j + 1/2) / ny) is an eigenvector of the y second difference
+    with Neumann ends, eigenvalue -(4/dy^2) sin^2(pi b / (2 ny)).  Catches the
+    periodic wavenumber left in place, a DCT of the wrong type or scale, and
+    the wall flux left open."""
+    nx, ny, nz = dims
+    lx, ly, lz = 1.0, 1.3, 0.6
+    g = _ygrid(nx, ny, nz, lx, ly, lz)
+    a, b, c = mode
+    i = np.arange(nx)[None, None, :]
+    j = np.arange(ny)[None, :, None]
+    k = np.arange(nz)[:, None, None]
+    f = np.cos(2 * np.pi * a * i / nx + 0.4) * np.cos(np.pi * b * (j + 0.5) / ny) * np.cos(np.pi * c * (k + 0.5) / nz)
+    dx, dy, dz = lx / nx, ly / ny, lz / nz
+    lam = -(4 / dx ** 2 * math.sin(math.pi * a / nx) ** 2 + 4 / dy ** 2 * math.sin(math.pi * b / (2 * ny)) ** 2
+            + 4 / dz ** 2 * math.sin(math.pi * c / (2 * nz)) ** 2)
+    assert _rel(orc.laplacian(g, f), lam * f) < 1e-12
+    assert _rel(orc.solve_constant(g, f), f / lam) < 1e-12
+
+
+@pytest.mark.parametrize("beta", [None, 1.5])
+def test_ywalls_solve_is_the_even_extension_of_a_periodic_solve(beta):
+    """Neumann walls in y are the mirror symmetry of a periodic problem of
+    twice the width: reflect f about y = ly, solve periodically on 2 ny rows,
+    keep the first ny.  No cosine transform on the right-hand side, so this
+    pins the wall solve through the periodic one."""
+    nx, ny, nz = 12, 10, 9
+    g = _ygrid(nx, ny, nz, 1.0, 0.9, 1.0, beta)
+    gp = orc.Grid(nx, 2 * ny, nz, 1.0, 1.8, g.zf)
+    f = np.random.default_rng(21).standard_normal(g.shape)
+    fe = np.concatenate([f, f[:, ::-1, :]], axis=1)
+    assert _rel(orc.solve_constant(g, f), orc.solve_constant(gp, fe)[:, :ny, :]) < 1e-12
+
+
+@pytest.mark.parametrize("dims,beta", [((6, 5, 4), None), ((4, 6, 5), 2.0)])
+def test_ywalls_constant_solve_vs_dense_lu(dims, beta):
+    """Dense LU of the 7-point matrix with no flux through the y walls,
+    assembled entry by entry."""
+    nx, ny, nz = dims
+    lx, ly, lz = 1.0, 0.8, 1.3
+    g = _ygrid(nx, ny, nz, lx, ly, lz, beta)
+    f = np.random.default_rng(8).standard_normal(g.shape)
+    A = dr.assemble_variable(nx, ny, nz, lx, ly, g.zf, None, ywalls=True)
+    wts = dr.cell_weights(nx, ny, nz, g.zf)
+    fc = f.ravel() - np.dot(wts, f.ravel()) / wts.sum()
+    p = orc.solve_constant(g, f)
+    assert _rel(p, dr.bordered_solve(A, fc, wts).reshape(g.shape)) < 1e-12
+
+
+def _ywall_case(nx, ny, nz, beta=None, ratio=1000.0, seed=5):
+    g, us, vs, ws, rho, S = _small_case(nx, ny, nz, beta, ratio, seed)
+    g = orc.Grid(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, ywalls=True)
+    vs[:, 0, :] = 0.0
+    return g, us, vs, ws, rho, S
+
+
+@pytest.mark.parametrize("beta", [None, 1.5])
+def test_ywalls_projection_direct_vs_dense(beta):
+    """The variable-density definition with y walls against a dense LU of
+    D(beta G) assembled entry by entry; the corrected field has no flux
+    through the y walls and meets the divergence target."""
+    g, us, vs, ws, rho, S = _ywall_case(5, 6, 4, beta)
+    dt = 1e-3
+    p, u, v, w = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    A = dr.assemble_variable(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, rho, ywalls=True)
+    wts = dr.cell_weights(g.nx, g.ny, g.nz, g.zf)
+    Sc = S.ravel() - np.dot(wts, S.ravel()) / wts.sum()
+    div = dr.divergence_loops(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, us, vs, ws, ywalls=True).ravel()
+    assert _rel(p, dr.bordered_solve(A, (div - Sc) / dt, wts).reshape(g.shape)) < 1e-11
+    assert np.all(v[:, 0, :] == 0.0)
+    dnew = dr.divergence_loops(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, u, v, w, ywalls=True).ravel()
+    assert np.max(np.abs(dnew - Sc)) < 1e-11 * np.max(np.abs(div))
+
+
+@pytest.mark.parametrize("beta,ratio", [(None, 1000.0), (1.5, 100.0)])
+def test_ywalls_method3_reaches_direct_solution(beta, ratio):
+    """Algorithm 1 with the wall eigenbasis in y converges to the plain
+    definition."""
+    g, us, vs, ws, rho, S = _ywall_case(12, 10, 14, beta, ratio)
+    dt = 1e-3
+    p, u, v, w, info = orc.method3(g, us, vs, ws, rho, S, dt, rtol=1e-13, maxit=3000)
+    assert info["res_hist"][-1] <= 1e-13
+    pd, ud, vd, wd = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    assert _rel(p, pd) < 1e-10
+    for a, b in ((u, ud), (v, vd), (w, wd)):
+        assert _rel(a, b) < 1e-11
+
+
+@pytest.mark.parametrize("method", ["method1", "method2"])
+def test_ywalls_methods_1_2_reach_direct_solution(method):
+    """Methods I and II with y walls reach the same discrete solution."""
+    g, us, vs, ws, rho, S = _ywall_case(12, 10, 14, 1.5, 10.0)
+    dt = 1e-3
+    p, u, v, w, info = getattr(orc, method)(g, us, vs, ws, rho, S, dt, rtol=1e-13)
+    assert info["res_hist"][-1] <= 1e-13
+    pd, ud, vd, wd = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    assert _rel(p, pd) < 1e-10
+    for a, b in ((u, ud), (v, vd), (w, wd)):
+        assert _rel(a, b) < 1e-10
+
+
+def test_ywalls_y_independent_field_matches_periodic():
+    """A right-hand side constant in y meets both the periodic and the wall
+    conditions, so the two solves agree."""
+    g = _ygrid(10, 8, 7, beta=1.5)
+    gp = orc.Grid(10, 8, 7, 1.0, 1.0, g.zf)
+    f = np.broadcast_to(np.random.default_rng(4).standard_normal((7, 1, 10)), g.shape).copy()
+    assert _rel(orc.solve_constant(g, f), orc.solve_constant(gp, f)) < 1e-12
+
+
+
+def test_ywalls_operator_identities():
+    """D against the loop definition with a nonzero wall row in v (no flux
+    crosses a wall whatever the array holds); G of p = y_centre is exactly 1
+    on the interior y faces and 0 on the wall row.  Catches an open wall in
+    D or G and an off-by-one wall row."""
+    g = _ygrid(6, 7, 5, ly=0.7, beta=1.5)
+    rng = np.random.default_rng(12)
+    u, v = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    w = rng.standard_normal((g.nz + 1, g.ny, g.nx))
+    w[0] = w[-1] = 0
+    ref = dr.divergence_loops(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, u, v, w, ywalls=True)
+    assert np.allclose(orc.divergence(g, u, v, w), ref, rtol=0, atol=1e-10)
+    yc = (np.arange(g.ny) + 0.5) * g.dy
+    p = np.broadcast_to(yc[None, :, None], g.shape).copy()
+    gx, gy, gz = orc.gradient(g, p)
+    assert np.allclose(gy[:, 1:, :], 1.0, rtol=0, atol=1e-12) and np.all(gy[:, 0, :] == 0)
+    assert np.allclose(gx, 0) and np.allclose(gz, 0)
