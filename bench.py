@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--compare-steps", type=int, default=1)
     ap.add_argument("--no-thermo", action="store_true",
                     help="skip timing the divergence-source kernels (Eqs. 30, 34)")
+    ap.add_argument("--no-ywalls", action="store_true",
+                    help="skip timing the passes of a plan with walls in y (cosine y transform)")
     ap.add_argument("--workload", default="bubbles512", choices=["bubbles512", "batch96"],
                     help="bubbles512: the 512^3 projection (default); batch96: 96 grids of mixed sizes "
                          "solved in one graph launch")
@@ -366,6 +368,50 @@ def run_ours(args, rank, world, local_rank):
                             "algorithmic_bytes": int(nbytes), "achieved_gbs": round(gbs, 1),
                             "frac_of_measured_hbm": round(gbs / hbm_peak, 4),
                             "note": "Eqs. 29, 32 at the benchmark grid, Adams-Bashforth step, FP64"}
+
+    # walls in y: the same fields in a duct (y boundary closed, v* = 0 on the
+    # wall row), a fixed number of Method III passes with the per-kernel
+    # CUDA-event profile; the y transforms are the cosine transform here
+    if not args.no_ywalls:
+        plan.close()
+        vsy = vs.clone()
+        vsy[:, 0, :] = 0.0
+        plany = pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, lz, zfaces=w.zf, precision=args.precision,
+                        method=args.method, ywalls=True)
+        passes = 80
+
+        def ystep():
+            pp.pressure_mixture_density(plany.handle, phi, w.rho_g, w.rho_l, rho)
+            return pp.pressure_correct(plany.handle, us, vsy, ws, rho, S, w.dt, p, u, v, wo,
+                                       rtol=0.0, maxit=passes, allow_not_converged=True)
+        for _ in range(3):
+            ystep()
+        torch.cuda.synchronize()
+        pp.pressure_profile_enable(plany.handle, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        yinfo = ystep()
+        e1.record()
+        torch.cuda.synchronize()
+        yms = e0.elapsed_time(e1)
+        ykern, _ = pp.pressure_profile_read(plany.handle)
+        pp.pressure_profile_enable(plany.handle, False)
+        plany.close()
+        ybytes = algorithmic("ffty_fwd", w, args.precision)["bytes"]
+        yk = {}
+        for k in ("ffty_fwd", "ffty_inv"):
+            n_, t_ = ykern[k]
+            avg = t_ / n_
+            gbs = ybytes / (avg / 1e3) / 1e9
+            yk[k] = {"avg_ms": round(avg, 4), "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm_peak, 4),
+                     "periodic_avg_ms": kernels[k]["avg_ms"]}
+        out["ywalls"] = {"passes": yinfo["iters"], "ms_per_pass": round(yms / max(yinfo["iters"], 1), 4),
+                         "periodic_ms_per_pass": round(ms / max(info["iters"], 1), 4),
+                         "res_after": yinfo["res_final"], "y_transforms": yk,
+                         "note": ("the benchmark's fields with walls at y = 0 and y = 2 pi, one projection of "
+                                  f"{passes} Method III passes; cosine y transforms (one complex FFT of length ny "
+                                  "per column plus the pairwise twiddles), algorithmic bytes = spectrum read + write")}
+        plan = make_plan(args.precision)
 
     # end to end through the C ABI with host (pinned) buffers
     if not args.no_e2e:

@@ -13,13 +13,16 @@
  * constant-coefficient recast solved iteratively, each pass calling the
  * eigenexpansion (FFT in x and y, tridiagonal in z) Poisson solver.
  *
- * Grid (Sec. 3): marker-and-cell, x and y periodic with uniform spacing,
- * z bounded by no-penetration walls (homogeneous Neumann pressure), uniform
- * or stretched.  Arrays are contiguous, x fastest:
+ * Grid (Sec. 3): marker-and-cell, x periodic and y periodic or walled
+ * (uniform spacing), z bounded by no-penetration walls (homogeneous Neumann
+ * pressure), uniform or stretched.  Arrays are contiguous, x fastest:
  *   cell fields  (p, rho, S, phi)  [nz][ny][nx]
  *   u            [nz][ny][nx]      u[k][j][i] on the x-face at i - 1/2
  *   v            [nz][ny][nx]      v[k][j][i] on the y-face at j - 1/2
  *   w            [nz+1][ny][nx]    w[k][j][i] on the z-face k (0 and nz: walls)
+ * With walls in y (bc[1] = PP_BC_WALL) v keeps its [nz][ny][nx] shape: row
+ * j = 0 stands for both walls (y = 0 and y = ly); its input values are taken
+ * as zero and it is returned as zero, like the wall planes of w.
  * The face density is the arithmetic mean of the two adjacent cells.  The
  * divergence target S is made compatible with the closed box by removing its
  * volume-weighted mean (S_c = S - <S>_V); p is returned with zero
@@ -44,7 +47,8 @@ extern "C" {
 typedef enum {
     PP_OK = 0,
     PP_ERR_INVALID_ARG = 1,   /* bad pointer, size, tolerance or dt */
-    PP_ERR_UNSUPPORTED = 2,   /* grid size with a prime factor > 5, bad bc */
+    PP_ERR_UNSUPPORTED = 2,   /* grid size with a prime factor > 5, bad bc, or a call not
+                                 built for walls in y */
     PP_ERR_NOT_CONVERGED = 3, /* maxit reached before the tolerance */
     PP_ERR_NUMERIC = 4,       /* NaN/Inf in the residual */
     PP_ERR_CUDA = 5,          /* a CUDA runtime call failed */
@@ -85,10 +89,20 @@ typedef enum {
 typedef enum { PP_METHOD_III = 0, PP_METHOD_I = 1, PP_METHOD_II = 2 } pp_method;
 
 typedef struct {
-    int nx, ny, nz;        /* cells; nx, ny have prime factors in {2,3,5}; nx even */
+    int nx, ny, nz;        /* cells; nx, ny have prime factors in {2,3,5}; nx even;
+                              ny even with walls in y */
     double lx, ly, lz;     /* domain lengths */
     const double* zfaces;  /* host, nz+1 increasing face coordinates, or NULL (uniform) */
-    int bc[3];             /* must be {PP_BC_PERIODIC, PP_BC_PERIODIC, PP_BC_WALL} */
+    int bc[3];             /* {PP_BC_PERIODIC, PP_BC_PERIODIC, PP_BC_WALL}, or walls in y:
+                              {PP_BC_PERIODIC, PP_BC_WALL, PP_BC_WALL}.  With walls in y the
+                              y transform is the cosine eigenbasis of the Neumann second
+                              difference, cos(pi m (j + 1/2) / ny), eigenvalues
+                              -(4/dy^2) sin^2(pi m / (2 ny)), computed by one complex FFT
+                              of length ny; pressure_solve, pressure_correct (Methods I, II
+                              and III) and pressure_mixture_density take them, the adjoint,
+                              the thermodynamic source and the predictor return
+                              PP_ERR_UNSUPPORTED, and the batched and no-allocation entry
+                              points take periodic y only */
 } pp_grid;
 
 typedef struct {

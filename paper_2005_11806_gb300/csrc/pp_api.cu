@@ -47,6 +47,7 @@ struct pp_plan_s {
   double *d_lamx = nullptr, *d_lamy = nullptr, *d_invd = nullptr, *d_mtab = nullptr;
   float* d_inv_dzf_f = nullptr;
   void *d_twx = nullptr, *d_twy = nullptr;
+  void* d_dcty = nullptr;  // walls in y: exp(-i pi m / (2 ny)), m < ny (C2 of the plan's FFT type)
   // workspaces
   void* d_spec = nullptr;
   double2* d_ybuf = nullptr;
@@ -111,6 +112,20 @@ std::vector<C2<T>> twiddles(int n) {
     const double a = two_pi * (double)m / (double)n;
     t[m].x = (T)std::cos(a);
     t[m].y = (T)std::sin(a);
+  }
+  return t;
+}
+
+// Twiddles of the cosine transform along a walled direction of n cells:
+// exp(-i pi m / (2 n)), m = 0 .. n - 1 (FP64 on the host).
+template <typename T>
+std::vector<C2<T>> dct_twiddles(int n) {
+  std::vector<C2<T>> t(n);
+  const double pi = 3.14159265358979323846264338327950288;
+  for (int m = 0; m < n; ++m) {
+    const double a = pi * (double)m / (2.0 * (double)n);
+    t[m].x = (T)std::cos(a);
+    t[m].y = (T)(-std::sin(a));
   }
   return t;
 }
@@ -235,14 +250,15 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr, fl
   // the split solve (mtab present) keeps its intermediate in the spectrum
   double2* ybuf = (double2*)P->d_spec;
   const double scale = 1.0 / ((double)P->nx * (double)P->ny);
-  PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream));
+  const C2<T>* dct = (const C2<T>*)P->d_dcty;  // null: periodic y
+  PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream, dct));
   if (P->z_tc) {
     PP_K(P, K_TRI, launch_zgemm(g, P->ze, reinterpret_cast<float2*>(spec), P->d_st, P->stream));
   } else {
     PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab,
                                      P->use_tri32 ? &P->tri32 : nullptr));
   }
-  PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream));
+  PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream, dct));
   PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream, delta,
                                        sdelta));
   return PP_OK;
@@ -356,6 +372,7 @@ void free_plan(pp_plan_s* P) {
   for (double* d : dptrs) if (d) cudaFree(d);
   if (P->d_twx) cudaFree(P->d_twx);
   if (P->d_twy) cudaFree(P->d_twy);
+  if (P->d_dcty) cudaFree(P->d_dcty);
   if (P->d_spec) cudaFree(P->d_spec);
   if (P->d_ybuf) cudaFree(P->d_ybuf);
   if (P->d_st) cudaFree(P->d_st);
@@ -395,9 +412,12 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   if (prec != PP_FP64 && prec != PP_MIXED_FP32 && prec != PP_MIXED_TC && prec != PP_MIXED_Z64)
     return PP_ERR_INVALID_ARG;
   if (prec == PP_MIXED_TC && G.nz > 512) return PP_ERR_UNSUPPORTED;
-  if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL)
+  if (G.bc[0] != PP_BC_PERIODIC || (G.bc[1] != PP_BC_PERIODIC && G.bc[1] != PP_BC_WALL) ||
+      G.bc[2] != PP_BC_WALL)
     return PP_ERR_UNSUPPORTED;
+  const bool ywall = (G.bc[1] == PP_BC_WALL);
   if ((G.nx & 1) != 0) return PP_ERR_UNSUPPORTED;
+  if (ywall && (G.ny < 2 || (G.ny & 1) != 0)) return PP_ERR_UNSUPPORTED;  // cosine transform by an FFT of even length
   if (G.nx > 2048 || G.ny > 2048) return PP_ERR_UNSUPPORTED;  // one line per block in the FFTs
   if ((long)G.nx * G.ny * (G.nz + 1) > (1L << 31)) return PP_ERR_UNSUPPORTED;
   pp_plan_s* P = new (std::nothrow) pp_plan_s();
@@ -437,8 +457,10 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
     const double s = std::sin(pi * (double)k / (double)G.nx);
     lamx[k] = -4.0 / (P->dx * P->dx) * s * s;
   }
+  // walls in y: eigenvalues of the Neumann second difference on cell
+  // centres, for the cosine modes cos(pi k (j + 1/2) / ny)
   for (int k = 0; k < G.ny; ++k) {
-    const double s = std::sin(pi * (double)k / (double)G.ny);
+    const double s = std::sin(pi * (double)k / (ywall ? 2.0 * (double)G.ny : (double)G.ny));
     lamy[k] = -4.0 / (P->dy * P->dy) * s * s;
   }
 
@@ -466,12 +488,22 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
         (st = dalloc(&P->d_twy, ty.size() * sizeof(double2))) != PP_OK) { free_plan(P); return st; }
     cudaMemcpy(P->d_twx, tx.data(), tx.size() * sizeof(double2), cudaMemcpyHostToDevice);
     cudaMemcpy(P->d_twy, ty.data(), ty.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    if (ywall) {
+      auto tc = dct_twiddles<double>(G.ny);
+      if ((st = dalloc(&P->d_dcty, tc.size() * sizeof(double2))) != PP_OK) { free_plan(P); return st; }
+      cudaMemcpy(P->d_dcty, tc.data(), tc.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    }
   } else {
     auto tx = twiddles<float>(G.nx), ty = twiddles<float>(G.ny);
     if ((st = dalloc(&P->d_twx, tx.size() * sizeof(float2))) != PP_OK ||
         (st = dalloc(&P->d_twy, ty.size() * sizeof(float2))) != PP_OK) { free_plan(P); return st; }
     cudaMemcpy(P->d_twx, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice);
     cudaMemcpy(P->d_twy, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (ywall) {
+      auto tc = dct_twiddles<float>(G.ny);
+      if ((st = dalloc(&P->d_dcty, tc.size() * sizeof(float2))) != PP_OK) { free_plan(P); return st; }
+      cudaMemcpy(P->d_dcty, tc.data(), tc.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    }
   }
   // residual partial sums: 2 per residual block, or the reduction grid
   const size_t rpb_min = 2;
@@ -521,6 +553,7 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   g.inv_dy2 = 1.0 / (P->dy * P->dy);
   g.inv_dzf = P->d_inv_dzf; g.inv_dzc = P->d_inv_dzc; g.dzf = P->d_dzf;
   g.za = P->d_za; g.zc = P->d_zc; g.lz = lz_sum;
+  g.ywall = (G.bc[1] == PP_BC_WALL) ? 1 : 0;
   if (prec == PP_MIXED_TC) {
     int nzp = 0, zm = 0;
     std::vector<float> mu;
@@ -612,6 +645,7 @@ pp_status pressure_plan_set_method(pp_plan P, int method) {
 pp_status pressure_p0_rate(pp_plan P, const double* phi, const double* kc, const double* T, const double* u,
                            const double* v, const double* w, double p0, double gamma, double* rp) {
   if (check_plan(P) != PP_OK || !phi || !kc || !T || !u || !v || !w || !rp) return PP_ERR_INVALID_ARG;
+  if (P->geo.ywall) return PP_ERR_UNSUPPORTED;
   if (!(gamma > 0.0) || !std::isfinite(p0)) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P), nw = nwface(P);
   const double *dphi, *dk, *dT, *du, *dv, *dw;
@@ -635,6 +669,7 @@ pp_status pressure_predictor(pp_plan P, const double* u, const double* v, const 
                              double dt_old, const double* const ru_prev[3], double* const u_star[3],
                              double* const ru_out[3]) {
   if (check_plan(P) != PP_OK || !u || !v || !w || !rho || !mu || !gravity || !u_star) return PP_ERR_INVALID_ARG;
+  if (P->geo.ywall) return PP_ERR_UNSUPPORTED;
   if (!u_star[0] || !u_star[1] || !u_star[2] || !(dt_new > 0.0)) return PP_ERR_INVALID_ARG;
   const double* f[3] = {nullptr, nullptr, nullptr};
   const double* prev[3] = {nullptr, nullptr, nullptr};
@@ -670,6 +705,7 @@ pp_status pressure_dp0dt_extrapolate(double rp_n, double rp_nm1, double dt_new, 
 pp_status pressure_divergence_source(pp_plan P, const double* phi, const double* kc, const double* T, double p0,
                                      double gamma, double dp0dt, double* S) {
   if (check_plan(P) != PP_OK || !phi || !kc || !T || !S) return PP_ERR_INVALID_ARG;
+  if (P->geo.ywall) return PP_ERR_UNSUPPORTED;
   if (!(gamma > 0.0) || p0 == 0.0 || !std::isfinite(p0) || !std::isfinite(dp0dt)) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P);
   const double *dphi, *dk, *dT;
@@ -789,6 +825,7 @@ pp_status pressure_solve_adjoint(pp_plan P, const double* rho, const double* p, 
                                  pp_info* info) {
   if (check_plan(P) != PP_OK || !rho || !p || !gu || !gv || !gw || !gus || !gvs || !gws || !grho)
     return PP_ERR_INVALID_ARG;
+  if (P->geo.ywall) return PP_ERR_UNSUPPORTED;
   if (!(dt > 0.0) || !(rtol >= 0.0) || maxit < 0) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P), nw = nwface(P);
   pp_status s;

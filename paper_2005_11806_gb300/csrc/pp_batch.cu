@@ -560,6 +560,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     g.inv_dzf = (const double*)(P + o.idzf); g.inv_dzc = (const double*)(P + o.idzc);
     g.dzf = (const double*)(P + o.dzf); g.za = (const double*)(P + o.za); g.zc = (const double*)(P + o.zc);
     g.inv_dzf_f = (const float*)(P + o.idzff); g.lz = zf[nz] - zf[0];
+    g.ywall = 0;
     d.fc.cx = (double*)(P + o.cx); d.fc.cy = (double*)(P + o.cy); d.fc.cz = (double*)(P + o.cz);
     d.fc.diag = (double*)(P + o.diag); d.fc.rhof = (float*)(P + o.rhof); d.fc.cxf = (float*)(P + o.cxf);
     d.fc.cyf = (float*)(P + o.cyf); d.fc.czf = (float*)(P + o.czf);

@@ -25,7 +25,9 @@ __device__ __forceinline__ CellIdx cell_index(const Geo& g, size_t c) {
 }
 
 // Face coefficients of cell c (beta = 2/(rho_a + rho_b) on its x-, y- and
-// z-face "below", x/y coefficients scaled by the layer width dzf_k).
+// z-face "below", x/y coefficients scaled by the layer width dzf_k).  Wall
+// faces get 0: the z walls, and with walls in y the y-face below row 0,
+// which the periodic indexing also reaches as the face above row ny - 1.
 __device__ __forceinline__ void cell_prep_faces(const Geo& g, const double* __restrict__ rho,
                                                 const Faces& fc, size_t c) {
   const CellIdx x = cell_index(g, c);
@@ -33,7 +35,7 @@ __device__ __forceinline__ void cell_prep_faces(const Geo& g, const double* __re
   const double r = rho[c];
   const double w = g.dzf[x.k];
   fc.cx[c] = 2.0 / (r + rho[x.cim]) * g.inv_dx2 * w;
-  fc.cy[c] = 2.0 / (r + rho[x.cjm]) * g.inv_dy2 * w;
+  fc.cy[c] = (g.ywall && x.j == 0) ? 0.0 : 2.0 / (r + rho[x.cjm]) * g.inv_dy2 * w;
   fc.cz[c] = (x.k == 0) ? 0.0 : 2.0 / (r + rho[c - plane]) * g.inv_dzc[x.k];
   if (x.k == g.nz - 1) fc.cz[c + plane] = 0.0;
   fc.rhof[c] = (float)r;
@@ -53,8 +55,9 @@ __device__ __forceinline__ void cell_prep_diag(const Geo& g, const Faces& fc, si
   if (fc.diagf != nullptr) fc.diagf[c] = (float)fc.diag[c];
 }
 
-// d = D u* - (S - meanS) at cell c (wall values of w* taken as zero); stores
-// the row-scaled b_s = dzf_k d / dt and returns d.
+// d = D u* - (S - meanS) at cell c (wall values of w*, and of v* with walls
+// in y, taken as zero); stores the row-scaled b_s = dzf_k d / dt and
+// returns d.
 __device__ __forceinline__ double cell_rhs_b(const Geo& g, const double* __restrict__ us,
                                              const double* __restrict__ vs,
                                              const double* __restrict__ ws,
@@ -64,7 +67,9 @@ __device__ __forceinline__ double cell_rhs_b(const Geo& g, const double* __restr
   const size_t plane = (size_t)g.nx * g.ny;
   const double wlo = (x.k == 0) ? 0.0 : ws[c];
   const double whi = (x.k == g.nz - 1) ? 0.0 : ws[c + plane];
-  double d = (us[x.cip] - us[c]) / g.dx + (vs[x.cjp] - vs[c]) / g.dy + (whi - wlo) * g.inv_dzf[x.k];
+  const double vlo = (g.ywall && x.j == 0) ? 0.0 : vs[c];
+  const double vhi = (g.ywall && x.j == g.ny - 1) ? 0.0 : vs[x.cjp];
+  double d = (us[x.cip] - us[c]) / g.dx + (vhi - vlo) / g.dy + (whi - wlo) * g.inv_dzf[x.k];
   if (S != nullptr) d -= (S[c] - meanS);
   b[c] = d * g.dzf[x.k] * inv_dt;
   return d;
@@ -85,7 +90,8 @@ __device__ __forceinline__ double cell_conduction(const Geo& g, const double* __
   return sx * g.inv_dx2 + sy * g.inv_dy2 + sz * g.inv_dzf[x.k];
 }
 
-// u = u* - dt beta G p at the faces of cell c (Eq. corr); w walls = 0.
+// u = u* - dt beta G p at the faces of cell c (Eq. corr); w walls = 0, and
+// with walls in y the wall row 0 of v = 0.
 __device__ __forceinline__ void cell_correct(const Geo& g, const Faces& fc,
                                              const double* __restrict__ us,
                                              const double* __restrict__ vs,
@@ -99,7 +105,7 @@ __device__ __forceinline__ void cell_correct(const Geo& g, const Faces& fc,
   // dt beta_x / dx = dt dx cx / dzf_k (cx carries dzf_k)
   const double ax = dt * g.dx * g.inv_dzf[x.k], ay = dt * g.dy * g.inv_dzf[x.k];
   u[c] = us[c] - ax * fc.cx[c] * (pc - p[x.cim]);
-  v[c] = vs[c] - ay * fc.cy[c] * (pc - p[x.cjm]);
+  v[c] = (g.ywall && x.j == 0) ? 0.0 : vs[c] - ay * fc.cy[c] * (pc - p[x.cjm]);
   w[c] = (x.k == 0) ? 0.0 : ws[c] - dt * fc.cz[c] * (pc - p[c - plane]);
   if (x.k == g.nz - 1) w[c + plane] = 0.0;
 }

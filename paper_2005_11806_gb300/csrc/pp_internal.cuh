@@ -54,6 +54,7 @@ struct Geo {
   const double* zc;       // [nz]   super-diagonal of L_z
   const float* inv_dzf_f; // [nz]   1 / cell width (FP32 copy)
   double lz;
+  int ywall;              // 1: walls at y = 0 and y = ly (v row 0 is the wall face); 0: periodic y
 };
 
 // Coefficients of D(beta G .) with each cell's row multiplied by its width
@@ -122,8 +123,10 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
                               const DevStatus* st, cudaStream_t s, float* E = nullptr,
                               const float* delta = nullptr);
 template <typename T>
+// dct: the cosine-transform twiddles exp(-i pi m / (2 ny)) for walls in y,
+// or null for the periodic DFT.
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
-                        const DevStatus* st, cudaStream_t s);
+                        const DevStatus* st, cudaStream_t s, const C2<T>* dct = nullptr);
 // FP32 Thomas tables for the well-conditioned z columns of mixed plans.  A
 // column (kx, ky) has the shift lambda = lambda_x(kx) + lambda_y(ky) <= 0;
 // the eigenvalues of its system lie in [lambda - 2 Dmax, lambda] with

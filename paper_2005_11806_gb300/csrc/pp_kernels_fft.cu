@@ -24,15 +24,17 @@ __global__ void __launch_bounds__(256, 4) k_resid_fftx(Geo g, Faces fc, FftDesc 
                       need_exact, E, delta, smem_raw);
 }
 
-template <typename T, int DIR>
+// DCT: the cosine transform of walls in y instead of the periodic DFT.
+template <typename T, int DIR, bool DCT>
 // Three blocks per SM (FP32: 52 KB of buffers each at ny = 512) measured
 // faster than four; the bound also keeps the register count from deciding it.
 __global__ void __launch_bounds__(256, sizeof(T) == sizeof(float) ? 3 : 2) k_ffty(Geo g, FftDesc fy, const C2<T>* __restrict__ twy,
                                               C2<T>* __restrict__ spec, int tx, long long ntiles,
-                                              const DevStatus* __restrict__ st) {
+                                              const DevStatus* __restrict__ st,
+                                              const C2<T>* __restrict__ dct) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_ffty_persistent<T, DIR>(g, fy, twy, spec, tx, ntiles, blockIdx.x, gridDim.x, smem_raw);
+  stage_ffty_persistent<T, DIR, DCT>(g, fy, twy, spec, tx, ntiles, blockIdx.x, gridDim.x, smem_raw, dct);
 }
 
 template <typename T>
@@ -124,7 +126,7 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
 
 template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
-                        const DevStatus* st, cudaStream_t s) {
+                        const DevStatus* st, cudaStream_t s, const C2<T>* dct) {
   const int tx = ffty_tile(g.ny, sizeof(C2<T>), kEpt);
   const int tsz = g.ny * tx;
   const size_t smem = (sizeof(T) == sizeof(float))
@@ -133,7 +135,8 @@ cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>
   const long long ntiles = (long long)((g.nxh + tx - 1) / tx) * g.nz;
   // persistent grid: exactly the blocks that are resident at once (shared
   // memory and registers both counted), so no block waits for a second wave
-  auto kern = inverse ? k_ffty<T, 1> : k_ffty<T, -1>;
+  auto kern = dct ? (inverse ? k_ffty<T, 1, true> : k_ffty<T, -1, true>)
+                  : (inverse ? k_ffty<T, 1, false> : k_ffty<T, -1, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0, dev = 0, nsm = 0;
@@ -143,7 +146,7 @@ cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>
   if (per_sm < 1) per_sm = 1;
   long long nblk = (long long)nsm * per_sm;
   if (nblk > ntiles) nblk = ntiles;
-  kern<<<(int)nblk, kThreads, smem, s>>>(g, fy, twy, spec, tx, ntiles, st);
+  kern<<<(int)nblk, kThreads, smem, s>>>(g, fy, twy, spec, tx, ntiles, st, dct);
   return cudaGetLastError();
 }
 
@@ -215,7 +218,7 @@ cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, c
                                             int, int, C2<T>*, double*, int*, const DevStatus*,       \
                                             cudaStream_t, float*, const float*);                    \
   template cudaError_t launch_ffty<T>(const Geo&, const FftDesc&, const C2<T>*, C2<T>*, int,         \
-                                      const DevStatus*, cudaStream_t);                               \
+                                      const DevStatus*, cudaStream_t, const C2<T>*);                 \
   template cudaError_t launch_tridiag<T>(const Geo&, const double*, C2<T>*, double2*,                \
                                          const DevStatus*, cudaStream_t, const double*,              \
                                          const TriF32*);                                             \

@@ -191,7 +191,7 @@ __global__ void k_correct_method1(Geo g, Faces fc, const double* __restrict__ us
     const double dc = (double)delta[c];
     const double bx = fc.cx[c] * idzf / g.inv_dx2, by = fc.cy[c] * idzf / g.inv_dy2;
     u[c] += dt * (bx - ir0) * (dc - (double)delta[x.cim]) / g.dx;
-    v[c] += dt * (by - ir0) * (dc - (double)delta[x.cjm]) / g.dy;
+    if (!(g.ywall && x.j == 0)) v[c] += dt * (by - ir0) * (dc - (double)delta[x.cjm]) / g.dy;
     if (x.k > 0) w[c] += dt * (fc.cz[c] - ir0 * g.inv_dzc[x.k]) * (dc - (double)delta[c - plane]);
   }
 }

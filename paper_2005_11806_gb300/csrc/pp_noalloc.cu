@@ -173,6 +173,7 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   g.za = (const double*)(S + o_za);
   g.zc = (const double*)(S + o_zc);
   g.lz = zf[nz] - zf[0];
+  g.ywall = 0;
   double2* spec = (double2*)(S + o_spec);
   double* invd = (double*)(S + o_invd);
   const double2* dtwx = (const double2*)(S + o_twx);

@@ -399,7 +399,13 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <typename T>
+// Row order of the cosine transform through a complex FFT (Makhoul): the
+// sequence v_r = x_{2r} (r < n/2), v_r = x_{2(n-1-r)+1} (r >= n/2), n even.
+__device__ __forceinline__ int dct_row(int r, int n) { return (r < (n >> 1)) ? 2 * r : 2 * (n - 1 - r) + 1; }
+
+// REORDER: shared row r receives global row dct_row(r) (forward cosine
+// transform); otherwise row r receives row r.
+template <typename T, bool REORDER = false>
 __device__ __forceinline__ void ffty_issue_tile(const Geo& g, const C2<T>* __restrict__ spec, int tx, int ntx,
                                                 long long tile, C2<T>* buf) {
   const int ny = g.ny, nxh = g.nxh;
@@ -408,7 +414,8 @@ __device__ __forceinline__ void ffty_issue_tile(const Geo& g, const C2<T>* __res
   const size_t base = (size_t)bz * ny * nxh;
   const int lg_tx = 31 - __clz(tx);  // tx is a power of two (ffty_tile)
   for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
-    const int y = t >> lg_tx, x = t & (tx - 1);
+    const int r = t >> lg_tx, x = t & (tx - 1);
+    const int y = REORDER ? dct_row(r, ny) : r;
     if (kx0 + x < nxh) {
       if (sizeof(C2<T>) == 8) cp_async8(&buf[t], &spec[base + (size_t)y * nxh + kx0 + x]);
       else {
@@ -424,11 +431,33 @@ __device__ __forceinline__ void ffty_issue_tile(const Geo& g, const C2<T>* __res
   cp_async_commit();
 }
 
-template <typename T, int DIR>
+template <typename T> __device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {  // a * conj(b)
+  C2<T> r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.y * b.x - a.x * b.y;
+  return r;
+}
+
+// Persistent y transform.  DCT = false: complex DFT along y (periodic y).
+// DCT = true (walls in y): the eigenbasis of the Neumann second difference
+// on cell centres, X_m = sum_j x_j cos(pi m (2j + 1) / (2 ny)), computed
+// with one complex FFT of length ny (Makhoul's reordering) and the twiddles
+// w_m = exp(-i pi m / (2 ny)) of `dct`:
+//   forward:  Z = FFT(x reordered by dct_row);
+//             X_m = (w_m Z_m + conj(w_m) Z_{ny-m}) / 2   (Z_ny = Z_0);
+//   inverse:  V_m = conj(w_m) (Y_m - i Y_{ny-m})          (Y_ny = 0);
+//             x_{dct_row(r)} = (IFFT(V))_r, unnormalised like the periodic
+//             inverse (the caller's 1/(nx ny) completes both).
+// The transform acts on real and imaginary parts alike, so the complex
+// x-spectrum goes through unchanged.
+template <typename T, int DIR, bool DCT = false>
 __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDesc& fy,
                                                       const C2<T>* __restrict__ twy, C2<T>* spec, int tx,
                                                       long long ntiles, long long first, long long stride,
-                                                      unsigned char* smem_raw) {
+                                                      unsigned char* smem_raw,
+                                                      const C2<T>* __restrict__ dct = nullptr) {
+  constexpr bool REORDER_IN = DCT && DIR < 0;
+  constexpr bool REORDER_OUT = DCT && DIR > 0;
   const int ny = g.ny, nxh = g.nxh;
   const int ntx = (nxh + tx - 1) / tx;
   const int tsz = ny * tx;
@@ -448,12 +477,32 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
   if constexpr (F32) {
     if (fast) load_twiddles_smem(twy, ny, twb);
   }
-  if (first < ntiles) ffty_issue_tile<T>(g, spec, tx, ntx, first, X0 + L);
+  if (first < ntiles) ffty_issue_tile<T, REORDER_IN>(g, spec, tx, ntx, first, X0 + L);
   for (long long tile = first; tile < ntiles; tile += stride) {
     cp_async_wait_all();
     __syncthreads();
     const long long next = tile + stride;
-    if (next < ntiles) ffty_issue_tile<T>(g, spec, tx, ntx, next, X0 + F);
+    if (next < ntiles) ffty_issue_tile<T, REORDER_IN>(g, spec, tx, ntx, next, X0 + F);
+    if constexpr (REORDER_OUT) {
+      // V_m and V_{ny-m} from the pair (Y_m, Y_{ny-m}), in place; V_0 = Y_0.
+      C2<T>* Y = X0 + L;
+      const int half = ny >> 1;
+      for (int t = threadIdx.x; t < half * tx; t += blockDim.x) {
+        const int m = 1 + (t >> lg_tx), x = t & (tx - 1);
+        const C2<T> w = dct[m];
+        const C2<T> a = Y[m * tx + x], b = Y[(ny - m) * tx + x];
+        C2<T> d, e;  // a - i b, a + i b
+        d.x = a.x + b.y; d.y = a.y - b.x;
+        e.x = a.x - b.y; e.y = a.y + b.x;
+        if (m == ny - m) {
+          Y[m * tx + x] = cmulc<T>(d, w);
+        } else {
+          Y[m * tx + x] = cmulc<T>(d, w);
+          Y[(ny - m) * tx + x] = cmul<T>(e, w);
+        }
+      }
+      __syncthreads();
+    }
     const C2<T>* res = nullptr;
     if constexpr (F32) {
       if (fast) res = smem_f2() + fft_dispatch_smem<DIR, true>(L, Q, twb, fy, tx, tx, 1, threadIdx.x, blockDim.x);
@@ -463,8 +512,21 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
     const int kx0 = bx * tx;
     const size_t base = (size_t)bz * ny * nxh;
     for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
-      const int y = t >> lg_tx, x = t & (tx - 1);
-      if (kx0 + x < nxh) spec[base + (size_t)y * nxh + kx0 + x] = res[t];
+      const int r = t >> lg_tx, x = t & (tx - 1);
+      if (kx0 + x >= nxh) continue;
+      if constexpr (REORDER_IN) {
+        // X_r = (w_r Z_r + conj(w_r) Z_{ny-r}) / 2
+        const C2<T> w = dct[r];
+        const C2<T> a = cmul<T>(res[t], w);
+        const C2<T> b = cmulc<T>(res[(r == 0 ? 0 : ny - r) * tx + x], w);
+        C2<T> o;
+        o.x = (T)0.5 * (a.x + b.x);
+        o.y = (T)0.5 * (a.y + b.y);
+        spec[base + (size_t)r * nxh + kx0 + x] = o;
+      } else {
+        const int y = REORDER_OUT ? dct_row(r, ny) : r;
+        spec[base + (size_t)y * nxh + kx0 + x] = res[t];
+      }
     }
     __syncthreads();
     // rotate: the prefetched buffer holds the next tile; the other two are free

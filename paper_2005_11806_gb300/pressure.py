@@ -144,9 +144,11 @@ def _check(code, what, allow=()):
     return code
 
 
-def pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None):
+def pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None,
+                         ywalls=False):
     """Create a plan; returns an opaque handle (int).  ``zfaces``: None for a
-    uniform z grid, else nz + 1 increasing face coordinates (host array)."""
+    uniform z grid, else nz + 1 increasing face coordinates (host array).
+    ``ywalls``: walls at y = 0 and y = ly instead of periodic y."""
     g = pp_grid()
     g.nx, g.ny, g.nz = int(nx), int(ny), int(nz)
     g.lx, g.ly, g.lz = float(lx), float(ly), float(lz)
@@ -156,7 +158,7 @@ def pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", 
         if keep.shape != (int(nz) + 1,):
             raise ValueError("zfaces must hold nz + 1 values")
         g.zfaces = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    g.bc[0], g.bc[1], g.bc[2] = PP_BC_PERIODIC, PP_BC_PERIODIC, PP_BC_WALL
+    g.bc[0], g.bc[1], g.bc[2] = PP_BC_PERIODIC, PP_BC_WALL if ywalls else PP_BC_PERIODIC, PP_BC_WALL
     out = ctypes.c_void_p()
     _check(lib().pressure_plan_create(ctypes.byref(g), PRECISIONS[precision], _stream(stream),
                                       ctypes.byref(out)), "pressure_plan_create")
@@ -342,10 +344,10 @@ class Plan:
     """Owning wrapper of a plan handle."""
 
     def __init__(self, nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None,
-                 method="III"):
+                 method="III", ywalls=False):
         self.shape = (int(nz), int(ny), int(nx))
         self.wshape = (int(nz) + 1, int(ny), int(nx))
-        self.handle = pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces, precision, stream)
+        self.handle = pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces, precision, stream, ywalls)
         if method != "III":
             pressure_plan_set_method(self.handle, method)
 
