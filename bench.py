@@ -72,6 +72,8 @@ def parse():
                     help="skip timing the divergence-source kernels (Eqs. 30, 34)")
     ap.add_argument("--no-ywalls", action="store_true",
                     help="skip timing the passes of a plan with walls in y (cosine y transform)")
+    ap.add_argument("--no-zcosine", action="store_true",
+                    help="skip timing the cosine z solve against the tridiagonal one (FP64, uniform z)")
     ap.add_argument("--workload", default="bubbles512", choices=["bubbles512", "batch96"],
                     help="bubbles512: the 512^3 projection (default); batch96: 96 grids of mixed sizes "
                          "solved in one graph launch")
@@ -411,6 +413,43 @@ def run_ours(args, rank, world, local_rank):
                          "note": ("the benchmark's fields with walls at y = 0 and y = 2 pi, one projection of "
                                   f"{passes} Method III passes; cosine y transforms (one complex FFT of length ny "
                                   "per column plus the pairwise twiddles), algorithmic bytes = spectrum read + write")}
+        plan = make_plan(args.precision)
+
+    # the z solve by the cosine basis against the tridiagonal solve: FP64
+    # plans on the same fields with uniform z faces, a fixed pass count each
+    if not args.no_zcosine:
+        plan.close()
+        zc_out = {}
+        for zs in ("tridiag", "cosine"):
+            planz = pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, lz, precision="fp64", method=args.method, zsolve=zs)
+            zpasses = 20
+
+            def zstep():
+                pp.pressure_mixture_density(planz.handle, phi, w.rho_g, w.rho_l, rho)
+                return pp.pressure_correct(planz.handle, us, vs, ws, rho, S, w.dt, p, u, v, wo,
+                                           rtol=0.0, maxit=zpasses, allow_not_converged=True)
+            zstep()
+            torch.cuda.synchronize()
+            pp.pressure_profile_enable(planz.handle, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            zinfo = zstep()
+            e1.record()
+            torch.cuda.synchronize()
+            zk, _ = pp.pressure_profile_read(planz.handle)
+            planz.close()
+            names = ("tridiag_z",) if zs == "tridiag" else ("zdct_fwd", "zdct_inv")
+            zc_out[zs] = {"ms_per_pass": round(e0.elapsed_time(e1) / max(zinfo["iters"], 1), 4),
+                          "z_solve_ms_per_pass": round(sum(zk[k][1] / zk[k][0] for k in names), 4),
+                          "kernels": {k: round(zk[k][1] / zk[k][0], 4) for k in names}}
+        nsp = (w.nx // 2 + 1) * w.ny * w.nz
+        for k in ("zdct_fwd", "zdct_inv"):
+            gbs = 2 * 16 * nsp / (zc_out["cosine"]["kernels"][k] / 1e3) / 1e9
+            zc_out["cosine"][k + "_gbs"] = round(gbs, 1)
+        zc_out["note"] = ("FP64 plans, the benchmark's fields on uniform z faces, 20 Method III passes each; "
+                          "the cosine z solve is two FFT-sized passes over the spectrum (FP64-pipe bound), "
+                          "the tridiagonal one a single sweep")
+        out["zcosine"] = zc_out
         plan = make_plan(args.precision)
 
     # end to end through the C ABI with host (pinned) buffers

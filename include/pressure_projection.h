@@ -88,6 +88,18 @@ typedef enum {
  * their pass counts compare. */
 typedef enum { PP_METHOD_III = 0, PP_METHOD_I = 1, PP_METHOD_II = 2 } pp_method;
 
+/* Solver of the z direction inside each constant-coefficient solve.
+ *   PP_ZSOLVE_TRIDIAG: one tridiagonal (Thomas) solve per (kx, ky) column;
+ *                      any z spacing (the default).
+ *   PP_ZSOLVE_COSINE:  uniform z only: the z eigenbasis of the Neumann
+ *                      second difference is cos(pi m (k + 1/2) / nz), so the
+ *                      solve is a cosine transform along z (one complex FFT
+ *                      of length nz per column), a divide by
+ *                      lambda_x + lambda_y - (4/dz^2) sin^2(pi m / (2 nz))
+ *                      with the (0, 0, 0) mode set to zero, and the inverse
+ *                      transform.  FP64 plans, nz even. */
+typedef enum { PP_ZSOLVE_TRIDIAG = 0, PP_ZSOLVE_COSINE = 1 } pp_zsolve;
+
 typedef struct {
     int nx, ny, nz;        /* cells; nx, ny have prime factors in {2,3,5}; nx even;
                               ny even with walls in y */
@@ -131,6 +143,15 @@ pp_status pressure_plan_destroy(pp_plan plan);
  * Returns PP_ERR_INVALID_ARG for an unknown method, PP_ERR_OOM when that
  * allocation fails. */
 pp_status pressure_plan_set_method(pp_plan plan, int method);
+
+/* Select the z solve (pp_zsolve; plans start with PP_ZSOLVE_TRIDIAG) of
+ * every later solve on this plan.  PP_ZSOLVE_COSINE allocates its tables
+ * (twiddles and eigenvalues of length nz) on first use.  Returns
+ * PP_ERR_INVALID_ARG for an unknown value, PP_ERR_UNSUPPORTED unless the
+ * plan is FP64 with uniform z faces (within 1e-12 relative) and even
+ * nz <= 2048, PP_ERR_OOM when an allocation fails.  Both solves reach the
+ * same discrete solution (Sec. 3.3.1: the eigenexpansion solve is exact). */
+pp_status pressure_plan_set_zsolve(pp_plan plan, int zsolve);
 
 /* Constant-coefficient solve by the eigenexpansion method (Sec. 3.3.1):
  * the zero-mean p with D G p = f - <f>_V.  f, p: cell fields. */

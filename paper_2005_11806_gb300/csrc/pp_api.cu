@@ -16,12 +16,13 @@ using namespace pp;
 namespace {
 enum KId { K_RESID, K_CHECK, K_FFTY_F, K_TRI, K_FFTY_I, K_FFTX_I, K_INIT, K_PREP, K_MEANS, K_RHSB,
            K_RMEAN, K_CORR, K_MIX, K_ADJ_RHS, K_ADJ_FIN, K_ADJ_GRHO, K_RHOT, K_FOLD, K_THERMO, K_SOURCE,
-           K_PRED, K_COUNT };
+           K_PRED, K_ZDCT_F, K_ZDCT_I, K_COUNT };
 const char* const kNames[K_COUNT] = {
     "resid_fftx", "check", "ffty_fwd", "tridiag_z", "ffty_inv", "fftx_inv_update", "init_status",
     "prep_faces", "mean_S", "rhs_b", "remove_mean", "correct", "mixture_density", "adj_rhs",
-    "adj_finish", "adj_grho", "rho_tilde", "fold_pending", "p0_rate", "divergence_source", "predictor"};
-const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1, 2, 1, 2, 1, 2};
+    "adj_finish", "adj_grho", "rho_tilde", "fold_pending", "p0_rate", "divergence_source", "predictor",
+    "zdct_fwd", "zdct_inv"};
+const int kLaunches[K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 1, 1, 1, 1, 1, 2, 1, 2, 1, 2, 1, 1};
 struct Rec { int kid; cudaEvent_t a, b; };
 struct Prof {
   bool on = false;
@@ -48,6 +49,14 @@ struct pp_plan_s {
   float* d_inv_dzf_f = nullptr;
   void *d_twx = nullptr, *d_twy = nullptr;
   void* d_dcty = nullptr;  // walls in y: exp(-i pi m / (2 ny)), m < ny (C2 of the plan's FFT type)
+  // z solve by the cosine basis (uniform z, FP64 plans; pressure_plan_set_zsolve)
+  int zsolve = PP_ZSOLVE_TRIDIAG;
+  bool z_uniform = false;
+  double dz = 0.0;
+  FftDesc fz{};
+  double2* d_twz = nullptr;
+  double2* d_dctz = nullptr;
+  double* d_lamz = nullptr;
   // workspaces
   void* d_spec = nullptr;
   double2* d_ybuf = nullptr;
@@ -254,6 +263,14 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr, fl
   PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream, dct));
   if (P->z_tc) {
     PP_K(P, K_TRI, launch_zgemm(g, P->ze, reinterpret_cast<float2*>(spec), P->d_st, P->stream));
+  } else if (P->zsolve == PP_ZSOLVE_COSINE) {
+    if constexpr (std::is_same<T, double>::value) {
+      const ZDivide zd{P->d_lamx, P->d_lamy, P->d_lamz};
+      PP_K(P, K_ZDCT_F, launch_zdct<double>(g, P->fz, P->d_twz, spec, 0, P->d_st, P->stream, P->d_dctz, zd));
+      PP_K(P, K_ZDCT_I, launch_zdct<double>(g, P->fz, P->d_twz, spec, 1, P->d_st, P->stream, P->d_dctz, zd));
+    } else {
+      return PP_ERR_UNSUPPORTED;
+    }
   } else {
     PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab,
                                      P->use_tri32 ? &P->tri32 : nullptr));
@@ -373,6 +390,9 @@ void free_plan(pp_plan_s* P) {
   if (P->d_twx) cudaFree(P->d_twx);
   if (P->d_twy) cudaFree(P->d_twy);
   if (P->d_dcty) cudaFree(P->d_dcty);
+  if (P->d_twz) cudaFree(P->d_twz);
+  if (P->d_dctz) cudaFree(P->d_dctz);
+  if (P->d_lamz) cudaFree(P->d_lamz);
   if (P->d_spec) cudaFree(P->d_spec);
   if (P->d_ybuf) cudaFree(P->d_ybuf);
   if (P->d_st) cudaFree(P->d_st);
@@ -450,6 +470,13 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   for (int k = 1; k < nz; ++k) za[k] = inv_dzc[k] * inv_dzf[k];
   for (int k = 0; k < nz - 1; ++k) zc[k] = inv_dzc[k + 1] * inv_dzf[k];
   const double lz_sum = zf[nz] - zf[0];
+  {
+    const double h = lz_sum / nz;
+    double dev = 0.0;
+    for (int k = 0; k < nz; ++k) dev = std::max(dev, std::fabs(dzf[k] - h));
+    P->z_uniform = dev <= 1e-12 * h;
+    P->dz = h;
+  }
   // modified wavenumbers of the periodic second difference
   std::vector<double> lamx(P->nxh), lamy(G.ny);
   const double pi = 3.14159265358979323846264338327950288;
@@ -623,6 +650,35 @@ pp_status pressure_plan_destroy(pp_plan P) {
   if (!P) return PP_ERR_INVALID_ARG;
   cudaStreamSynchronize(P->stream);
   free_plan(P);
+  return PP_OK;
+}
+
+pp_status pressure_plan_set_zsolve(pp_plan P, int zsolve) {
+  if (check_plan(P) != PP_OK) return PP_ERR_INVALID_ARG;
+  if (zsolve == PP_ZSOLVE_TRIDIAG) { P->zsolve = zsolve; return PP_OK; }
+  if (zsolve != PP_ZSOLVE_COSINE) return PP_ERR_INVALID_ARG;
+  if (P->prec != PP_FP64 || !P->z_uniform || (P->nz & 1) != 0 || P->nz > 2048) return PP_ERR_UNSUPPORTED;
+  if (P->d_lamz == nullptr) {  // tables made on first use; d_lamz is allocated last
+    if (!factor_len(P->nz, &P->fz)) return PP_ERR_UNSUPPORTED;
+    const int nz = P->nz;
+    auto tw = twiddles<double>(nz);
+    auto tc = dct_twiddles<double>(nz);
+    std::vector<double> lamz(nz);
+    const double pi = 3.14159265358979323846264338327950288;
+    for (int m = 0; m < nz; ++m) {
+      const double sn = std::sin(pi * (double)m / (2.0 * (double)nz));
+      lamz[m] = -4.0 / (P->dz * P->dz) * sn * sn;
+    }
+    pp_status st;
+    if ((!P->d_twz && (st = dalloc(&P->d_twz, nz * sizeof(double2))) != PP_OK) ||
+        (!P->d_dctz && (st = dalloc(&P->d_dctz, nz * sizeof(double2))) != PP_OK) ||
+        (st = dalloc(&P->d_lamz, nz * sizeof(double))) != PP_OK)
+      return st;
+    PP_CK(cudaMemcpy(P->d_twz, tw.data(), nz * sizeof(double2), cudaMemcpyHostToDevice));
+    PP_CK(cudaMemcpy(P->d_dctz, tc.data(), nz * sizeof(double2), cudaMemcpyHostToDevice));
+    PP_CK(cudaMemcpy(P->d_lamz, lamz.data(), nz * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  P->zsolve = zsolve;
   return PP_OK;
 }
 

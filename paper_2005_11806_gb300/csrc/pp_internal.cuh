@@ -122,9 +122,21 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
                               int p_zero, int scale_rho, C2<T>* spec, double* red, int* nblk_out,
                               const DevStatus* st, cudaStream_t s, float* E = nullptr,
                               const float* delta = nullptr);
+// z solve of a uniform walled z by the cosine basis (FP64 plans): forward
+// transform with the eigenvalue divide (inverse = 0), then the inverse
+// transform (inverse = 1).  dct: exp(-i pi m / (2 nz)); zd: the eigenvalues.
+struct ZDivide {
+  const double* lamx;  // [nxh]
+  const double* lamy;  // [ny]
+  const double* lamz;  // [nz] -(4/dz^2) sin^2(pi m / (2 nz))
+};
 template <typename T>
+cudaError_t launch_zdct(const Geo& g, const FftDesc& fz, const C2<T>* twz, C2<T>* spec, int inverse,
+                        const DevStatus* st, cudaStream_t s, const C2<T>* dct, const ZDivide& zd);
+
 // dct: the cosine-transform twiddles exp(-i pi m / (2 ny)) for walls in y,
 // or null for the periodic DFT.
+template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
                         const DevStatus* st, cudaStream_t s, const C2<T>* dct = nullptr);
 // FP32 Thomas tables for the well-conditioned z columns of mixed plans.  A

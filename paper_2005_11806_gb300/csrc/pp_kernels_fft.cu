@@ -37,6 +37,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == sizeof(float) ? 3 : 2) k_fft
   stage_ffty_persistent<T, DIR, DCT>(g, fy, twy, spec, tx, ntiles, blockIdx.x, gridDim.x, smem_raw, dct);
 }
 
+// z solve for uniform walls in z: cosine transform along z with the
+// eigenvalue divide (DIR = -1), then the inverse cosine transform (DIR = +1).
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256, 2) k_fftz(Geo g, FftDesc fz, const C2<T>* __restrict__ twz,
+                                                 C2<T>* __restrict__ spec, int tx, long long ntiles,
+                                                 const DevStatus* __restrict__ st,
+                                                 const C2<T>* __restrict__ dct, ZDivide zd) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage_ffty_persistent<T, DIR, true, 1>(g, fz, twz, spec, tx, ntiles, blockIdx.x, gridDim.x, smem_raw, dct, zd);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_tridiag(Geo g, const double* __restrict__ invd,
                                                  C2<T>* spec, double2* ybuf,  // ybuf may alias spec
@@ -149,6 +161,31 @@ cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>
   kern<<<(int)nblk, kThreads, smem, s>>>(g, fy, twy, spec, tx, ntiles, st, dct);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_zdct(const Geo& g, const FftDesc& fz, const C2<T>* twz, C2<T>* spec, int inverse,
+                        const DevStatus* st, cudaStream_t s, const C2<T>* dct, const ZDivide& zd) {
+  const int tx = ffty_tile(g.nz, sizeof(C2<T>), kEpt);
+  const int tsz = g.nz * tx;
+  const size_t smem = (sizeof(T) == sizeof(float))
+                          ? ((size_t)2 * tsz + fft_pad_elems(tsz) + g.nz) * sizeof(float2)
+                          : (size_t)3 * tsz * sizeof(C2<T>);
+  const long long ntiles = (long long)((g.nxh + tx - 1) / tx) * g.ny;
+  auto kern = inverse ? k_fftz<T, 1> : k_fftz<T, -1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, nsm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem)) != cudaSuccess) return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  long long nblk = (long long)nsm * per_sm;
+  if (nblk > ntiles) nblk = ntiles;
+  kern<<<(int)nblk, kThreads, smem, s>>>(g, fz, twz, spec, tx, ntiles, st, dct, zd);
+  return cudaGetLastError();
+}
+template cudaError_t launch_zdct<double>(const Geo&, const FftDesc&, const double2*, double2*, int,
+                                         const DevStatus*, cudaStream_t, const double2*, const ZDivide&);
 
 template <typename T>
 cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,

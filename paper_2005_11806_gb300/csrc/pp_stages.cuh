@@ -403,25 +403,39 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // sequence v_r = x_{2r} (r < n/2), v_r = x_{2(n-1-r)+1} (r >= n/2), n even.
 __device__ __forceinline__ int dct_row(int r, int n) { return (r < (n >> 1)) ? 2 * r : 2 * (n - 1 - r) + 1; }
 
+// Lines of the spectrum [nz][ny][nxh] that a persistent transform walks.
+// AXIS = 0: along y (length ny, element stride nxh), one tile per (z plane,
+// kx tile).  AXIS = 1: along z (length nz, stride ny nxh), one tile per
+// (ky, kx tile).
+template <int AXIS> struct Lines {
+  int n;             // transform length
+  size_t rstride;    // elements between consecutive entries of a line
+  size_t ostride;    // elements between consecutive outer indices
+  __device__ __forceinline__ explicit Lines(const Geo& g)
+      : n(AXIS ? g.nz : g.ny), rstride(AXIS ? (size_t)g.ny * g.nxh : (size_t)g.nxh),
+        ostride(AXIS ? (size_t)g.nxh : (size_t)g.ny * g.nxh) {}
+};
+
 // REORDER: shared row r receives global row dct_row(r) (forward cosine
 // transform); otherwise row r receives row r.
-template <typename T, bool REORDER = false>
+template <typename T, bool REORDER = false, int AXIS = 0>
 __device__ __forceinline__ void ffty_issue_tile(const Geo& g, const C2<T>* __restrict__ spec, int tx, int ntx,
                                                 long long tile, C2<T>* buf) {
-  const int ny = g.ny, nxh = g.nxh;
+  const Lines<AXIS> ln(g);
+  const int n = ln.n, nxh = g.nxh;
   const int bz = (int)(tile / ntx), bx = (int)(tile - (long long)bz * ntx);
   const int kx0 = bx * tx;
-  const size_t base = (size_t)bz * ny * nxh;
+  const size_t base = (size_t)bz * ln.ostride;
   const int lg_tx = 31 - __clz(tx);  // tx is a power of two (ffty_tile)
-  for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
+  for (int t = threadIdx.x; t < n * tx; t += blockDim.x) {
     const int r = t >> lg_tx, x = t & (tx - 1);
-    const int y = REORDER ? dct_row(r, ny) : r;
+    const int y = REORDER ? dct_row(r, n) : r;
     if (kx0 + x < nxh) {
-      if (sizeof(C2<T>) == 8) cp_async8(&buf[t], &spec[base + (size_t)y * nxh + kx0 + x]);
+      const size_t at = base + (size_t)y * ln.rstride + kx0 + x;
+      if (sizeof(C2<T>) == 8) cp_async8(&buf[t], &spec[at]);
       else {
-        cp_async8(&buf[t], &spec[base + (size_t)y * nxh + kx0 + x]);
-        cp_async8(reinterpret_cast<char*>(&buf[t]) + 8,
-                  reinterpret_cast<const char*>(&spec[base + (size_t)y * nxh + kx0 + x]) + 8);
+        cp_async8(&buf[t], &spec[at]);
+        cp_async8(reinterpret_cast<char*>(&buf[t]) + 8, reinterpret_cast<const char*>(&spec[at]) + 8);
       }
     } else {
       buf[t].x = (T)0;
@@ -450,15 +464,22 @@ template <typename T> __device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {
 //             inverse (the caller's 1/(nx ny) completes both).
 // The transform acts on real and imaginary parts alike, so the complex
 // x-spectrum goes through unchanged.
-template <typename T, int DIR, bool DCT = false>
+// AXIS = 1 runs the same transforms along z (uniform walls in z: the z
+// eigenbasis is the same cosine basis).  Its forward pass also divides by
+// the eigenvalue: X / (nz (lambda_x + lambda_y + lambda_z)), with the
+// singular (0, 0, 0) mode set to 0 (zero mean), so forward + inverse is the
+// whole z solve.
+template <typename T, int DIR, bool DCT = false, int AXIS = 0>
 __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDesc& fy,
                                                       const C2<T>* __restrict__ twy, C2<T>* spec, int tx,
                                                       long long ntiles, long long first, long long stride,
                                                       unsigned char* smem_raw,
-                                                      const C2<T>* __restrict__ dct = nullptr) {
+                                                      const C2<T>* __restrict__ dct = nullptr,
+                                                      ZDivide zd = ZDivide{}) {
   constexpr bool REORDER_IN = DCT && DIR < 0;
   constexpr bool REORDER_OUT = DCT && DIR > 0;
-  const int ny = g.ny, nxh = g.nxh;
+  const Lines<AXIS> ln(g);
+  const int ny = ln.n, nxh = g.nxh;  // ny: the transform length (ny, or nz for AXIS = 1)
   const int ntx = (nxh + tx - 1) / tx;
   const int tsz = ny * tx;
   const int lg_tx = 31 - __clz(tx);  // tx is a power of two (ffty_tile)
@@ -477,12 +498,12 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
   if constexpr (F32) {
     if (fast) load_twiddles_smem(twy, ny, twb);
   }
-  if (first < ntiles) ffty_issue_tile<T, REORDER_IN>(g, spec, tx, ntx, first, X0 + L);
+  if (first < ntiles) ffty_issue_tile<T, REORDER_IN, AXIS>(g, spec, tx, ntx, first, X0 + L);
   for (long long tile = first; tile < ntiles; tile += stride) {
     cp_async_wait_all();
     __syncthreads();
     const long long next = tile + stride;
-    if (next < ntiles) ffty_issue_tile<T, REORDER_IN>(g, spec, tx, ntx, next, X0 + F);
+    if (next < ntiles) ffty_issue_tile<T, REORDER_IN, AXIS>(g, spec, tx, ntx, next, X0 + F);
     if constexpr (REORDER_OUT) {
       // V_m and V_{ny-m} from the pair (Y_m, Y_{ny-m}), in place; V_0 = Y_0.
       C2<T>* Y = X0 + L;
@@ -510,7 +531,7 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
     if (!fast) res = fft_dispatch<T, DIR, true>(X0 + L, X0 + Q, fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
     const int bz = (int)(tile / ntx), bx = (int)(tile - (long long)bz * ntx);
     const int kx0 = bx * tx;
-    const size_t base = (size_t)bz * ny * nxh;
+    const size_t base = (size_t)bz * ln.ostride;
     for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
       const int r = t >> lg_tx, x = t & (tx - 1);
       if (kx0 + x >= nxh) continue;
@@ -519,13 +540,19 @@ __device__ __forceinline__ void stage_ffty_persistent(const Geo& g, const FftDes
         const C2<T> w = dct[r];
         const C2<T> a = cmul<T>(res[t], w);
         const C2<T> b = cmulc<T>(res[(r == 0 ? 0 : ny - r) * tx + x], w);
+        T h = (T)0.5;
+        if constexpr (AXIS == 1) {
+          // bz is ky here; the (0, 0, 0) mode is the pinned mean
+          const double lam = zd.lamx[kx0 + x] + zd.lamy[bz] + zd.lamz[r];
+          h = (kx0 + x == 0 && bz == 0 && r == 0) ? (T)0 : (T)(0.5 / ((double)ny * lam));
+        }
         C2<T> o;
-        o.x = (T)0.5 * (a.x + b.x);
-        o.y = (T)0.5 * (a.y + b.y);
-        spec[base + (size_t)r * nxh + kx0 + x] = o;
+        o.x = h * (a.x + b.x);
+        o.y = h * (a.y + b.y);
+        spec[base + (size_t)r * ln.rstride + kx0 + x] = o;
       } else {
         const int y = REORDER_OUT ? dct_row(r, ny) : r;
-        spec[base + (size_t)y * nxh + kx0 + x] = res[t];
+        spec[base + (size_t)y * ln.rstride + kx0 + x] = res[t];
       }
     }
     __syncthreads();

@@ -53,8 +53,8 @@ class PressureError(RuntimeError):
 
 _lib = None
 
-EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_plan_set_method", "pressure_solve",
-           "pressure_mixture_density", "pressure_correct", "pressure_solve_adjoint",
+EXPORTS = ("pressure_plan_create", "pressure_plan_destroy", "pressure_plan_set_method",
+           "pressure_plan_set_zsolve", "pressure_solve", "pressure_mixture_density", "pressure_correct", "pressure_solve_adjoint",
            "pressure_last_info", "pressure_profile_enable", "pressure_profile_read",
            "pressure_solve_noalloc", "pressure_batch_create", "pressure_batch_layout",
            "pressure_batch_correct", "pressure_batch_destroy", "pressure_batch_mixture_density",
@@ -77,6 +77,7 @@ def lib():
     L.pressure_plan_create.argtypes = [ctypes.POINTER(pp_grid), i, vp, ctypes.POINTER(vp)]
     L.pressure_plan_destroy.argtypes = [vp]
     L.pressure_plan_set_method.argtypes = [vp, i]
+    L.pressure_plan_set_zsolve.argtypes = [vp, i]
     L.pressure_solve.argtypes = [vp, vp, vp, pinfo]
     L.pressure_mixture_density.argtypes = [vp, vp, d, d, vp]
     L.pressure_correct.argtypes = [vp, vp, vp, vp, vp, vp, d, vp, i, vp, vp, vp, d, i, pinfo]
@@ -190,6 +191,15 @@ def pressure_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, zfaces=None, stream=Non
 
 def pressure_plan_destroy(plan):
     _check(lib().pressure_plan_destroy(plan), "pressure_plan_destroy")
+
+
+ZSOLVES = {"tridiag": 0, "cosine": 1}
+
+
+def pressure_plan_set_zsolve(plan, zsolve):
+    """zsolve: "tridiag" (default) or "cosine" (uniform z, FP64 plans)."""
+    code = ZSOLVES[zsolve] if isinstance(zsolve, str) else int(zsolve)
+    _check(lib().pressure_plan_set_zsolve(plan, code), "pressure_plan_set_zsolve")
 
 
 def pressure_plan_set_method(plan, method):
@@ -344,12 +354,14 @@ class Plan:
     """Owning wrapper of a plan handle."""
 
     def __init__(self, nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None,
-                 method="III", ywalls=False):
+                 method="III", ywalls=False, zsolve="tridiag"):
         self.shape = (int(nz), int(ny), int(nx))
         self.wshape = (int(nz) + 1, int(ny), int(nx))
         self.handle = pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces, precision, stream, ywalls)
         if method != "III":
             pressure_plan_set_method(self.handle, method)
+        if zsolve != "tridiag":
+            pressure_plan_set_zsolve(self.handle, zsolve)
 
     def close(self):
         if getattr(self, "handle", None):
