@@ -11,7 +11,10 @@
  *
  * with Method III (Sec. 3.3.1, Eq. new_poisson, Algorithm 1): a
  * constant-coefficient recast solved iteratively, each pass calling the
- * eigenexpansion (FFT in x and y, tridiagonal in z) Poisson solver.
+ * eigenexpansion Poisson solver: a real FFT in x, a complex FFT in y (a
+ * cosine transform with walls in y), and in z a tridiagonal solve per
+ * (kx, ky) column (or the tensor-core eigenvector products of PP_MIXED_TC,
+ * or the cosine transform of PP_ZSOLVE_COSINE for uniform z).
  *
  * Grid (Sec. 3): marker-and-cell, x periodic and y periodic or walled
  * (uniform spacing), z bounded by no-penetration walls (homogeneous Neumann
