@@ -51,6 +51,8 @@ def _plan(pp, nx, ny, nz, lx, ly, zf, precision="fp64"):
     ((24, 20, 17), 1.5, "fp64"),        # ragged: radix 3/5, odd nz, stretched z
     ((96, 30, 9), 2.0, "fp64"),
     ((64, 48, 40), 1.5, "mixed"),
+    ((64, 16, 512), None, "mixed"),     # nz = 512 with well-conditioned FP32 z columns
+    ((48, 30, 100), 1.5, "mixed"),      # radices 2, 3, 5 in y, stretched z
 ])
 def test_constant_solve_vs_oracle(pp, dims, stretch, precision):
     nx, ny, nz = dims
