@@ -145,6 +145,27 @@ def _check(code, what, allow=()):
     return code
 
 
+# Cell and z-face counts of the plans this module created.  Fields are
+# checked against them before a call: the library sees raw pointers, and a
+# short buffer would be read or written past its end on the device.
+_PLAN_SIZES = {}
+
+
+def _sized(plan, *fields):
+    """fields: (array or None, kind) pairs, kind "c" for a cell field
+    ([nz][ny][nx]) and "w" for a z-face field ([nz+1][ny][nx])."""
+    dims = _PLAN_SIZES.get(plan)
+    if dims is None:
+        return
+    for x, kind in fields:
+        if x is None:
+            continue
+        n = x.size if isinstance(x, np.ndarray) else getattr(x, "numel", lambda: None)()
+        need = dims[0] if kind == "c" else dims[1]
+        if n is not None and n < need:
+            raise ValueError(f"a {'cell' if kind == 'c' else 'z-face'} field needs {need} elements, got {n}")
+
+
 def pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None,
                          ywalls=False):
     """Create a plan; returns an opaque handle (int).  ``zfaces``: None for a
@@ -163,6 +184,7 @@ def pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", 
     out = ctypes.c_void_p()
     _check(lib().pressure_plan_create(ctypes.byref(g), PRECISIONS[precision], _stream(stream),
                                       ctypes.byref(out)), "pressure_plan_create")
+    _PLAN_SIZES[out.value] = (g.nx * g.ny * g.nz, g.nx * g.ny * (g.nz + 1))
     return out.value
 
 
@@ -190,6 +212,7 @@ def pressure_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, zfaces=None, stream=Non
 
 
 def pressure_plan_destroy(plan):
+    _PLAN_SIZES.pop(plan, None)
     _check(lib().pressure_plan_destroy(plan), "pressure_plan_destroy")
 
 
@@ -209,12 +232,14 @@ def pressure_plan_set_method(plan, method):
 
 
 def pressure_solve(plan, f, p):
+    _sized(plan, (f, "c"), (p, "c"))
     info = pp_info()
     _check(lib().pressure_solve(plan, _ptr(f), _ptr(p), ctypes.byref(info)), "pressure_solve")
     return info.as_dict()
 
 
 def pressure_mixture_density(plan, phi, rho_g, rho_l, rho):
+    _sized(plan, (phi, "c"), (rho, "c"))
     _check(lib().pressure_mixture_density(plan, _ptr(phi), float(rho_g), float(rho_l), _ptr(rho)),
            "pressure_mixture_density")
 
@@ -223,6 +248,7 @@ def pressure_correct(plan, us, vs, ws, rho, S, dt, p, u, v, w, rtol=1e-10, maxit
                      warm_start=False, sync=True, allow_not_converged=False):
     """Method III projection.  With ``sync=False`` the call only enqueues the
     work (read the status later with ``pressure_last_info``)."""
+    _sized(plan, (us, "c"), (vs, "c"), (ws, "w"), (rho, "c"), (S, "c"), (p, "c"), (u, "c"), (v, "c"), (w, "w"))
     info = pp_info()
     code = lib().pressure_correct(plan, _ptr(us), _ptr(vs), _ptr(ws), _ptr(rho), _ptr(S),
                                   float(dt), _ptr(p), int(bool(warm_start)), _ptr(u), _ptr(v),
@@ -235,6 +261,7 @@ def pressure_correct(plan, us, vs, ws, rho, S, dt, p, u, v, w, rtol=1e-10, maxit
 
 def pressure_p0_rate(plan, phi, kc, T, u, v, w, p0, gamma):
     """Eq. 30: the rate of the thermodynamic pressure (host float)."""
+    _sized(plan, (phi, "c"), (kc, "c"), (T, "c"), (u, "c"), (v, "c"), (w, "w"))
     out = ctypes.c_double()
     _check(lib().pressure_p0_rate(plan, _ptr(phi), _ptr(kc), _ptr(T), _ptr(u), _ptr(v), _ptr(w), float(p0),
                                   float(gamma), ctypes.byref(out)), "pressure_p0_rate")
@@ -250,6 +277,7 @@ def pressure_dp0dt_extrapolate(rp_n, rp_nm1, dt_new, dt_old):
 
 def pressure_divergence_source(plan, phi, kc, T, p0, gamma, dp0dt, S):
     """Eq. 34: the divergence source S written into S (cell field)."""
+    _sized(plan, (phi, "c"), (kc, "c"), (T, "c"), (S, "c"))
     _check(lib().pressure_divergence_source(plan, _ptr(phi), _ptr(kc), _ptr(T), float(p0), float(gamma),
                                             float(dp0dt), _ptr(S)), "pressure_divergence_source")
 
@@ -258,6 +286,10 @@ def pressure_predictor(plan, u, v, w, rho, mu, gravity, dt_new, u_star, dt_old=0
                        ru_out=None, force=None):
     """Eqs. 29, 32: u_star = (u*, v*, w*) written in place; ru_out receives
     RU^n; ru_prev = RU^{n-1} (None: forward Euler).  Device tensors only."""
+    _sized(plan, (u, "c"), (v, "c"), (w, "w"), (rho, "c"), (mu, "c"))
+    for ts in (force, ru_prev, u_star, ru_out):
+        if ts is not None:
+            _sized(plan, *zip(ts, ("c", "c", "w")))
     trio = lambda ts: None if ts is None else (ctypes.c_void_p * 3)(*[_ptr(t) for t in ts])  # noqa: E731
     grav = (ctypes.c_double * 3)(*[float(x) for x in gravity])
     _check(lib().pressure_predictor(plan, _ptr(u), _ptr(v), _ptr(w), _ptr(rho), _ptr(mu), trio(force), grav,
@@ -273,6 +305,8 @@ def pressure_last_info(plan):
 
 def pressure_solve_adjoint(plan, rho, p, dt, gu, gv, gw, gus, gvs, gws, grho, rtol=1e-10, maxit=500,
                            allow_not_converged=False):
+    _sized(plan, (rho, "c"), (p, "c"), (gu, "c"), (gv, "c"), (gw, "w"), (gus, "c"), (gvs, "c"), (gws, "w"),
+           (grho, "c"))
     info = pp_info()
     code = lib().pressure_solve_adjoint(plan, _ptr(rho), _ptr(p), float(dt), _ptr(gu), _ptr(gv),
                                         _ptr(gw), _ptr(gus), _ptr(gvs), _ptr(gws), _ptr(grho),
