@@ -644,3 +644,37 @@ def test_ywalls_operator_identities():
     gx, gy, gz = orc.gradient(g, p)
     assert np.allclose(gy[:, 1:, :], 1.0, rtol=0, atol=1e-12) and np.all(gy[:, 0, :] == 0)
     assert np.allclose(gx, 0) and np.allclose(gz, 0)
+
+
+@pytest.mark.parametrize("n,beta,ratio,ywalls", [(32, 1.5, 1000.0, False), (32, None, 10.0, False),
+                                                 (48, 1.5, 1000.0, False), (32, 1.5, 1000.0, True)])
+def test_method3_matches_preconditioned_cg(n, beta, ratio, ywalls):
+    """Beyond the reach of the direct solve: W_c D(beta G) is symmetric
+    (D^T = -W_f G W_c^-1), so the variable-density equation is solved
+    independently by Jacobi-preconditioned conjugate gradients on
+    -W_c A p = -W_c rhs, and Algorithm 1's converged p and u must match it.
+    Catches a fixed point that differs from Eq. lap_p by a small term (a
+    wrong face average, a dropped u . grad rho part) that the tiny-grid
+    pins might not resolve."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    g, us, vs, ws, rho, S = (_ywall_case if ywalls else _small_case)(n, n, n, beta, ratio)
+    dt = 1e-3
+    D, G = orc._sparse_operators(g)
+    rx, ry, rz = orc.face_density(g, rho)
+    bf = 1.0 / np.concatenate([rx.ravel(), ry.ravel(), rz.ravel()])
+    A = (D @ sp.diags(bf) @ G).tocsr()
+    Sc = S - orc.volume_mean(g, S)
+    rhs = (D @ np.concatenate([us.ravel(), vs.ravel(), ws.ravel()]) - Sc.ravel()) / dt
+    wc = np.broadcast_to(g.cell_volume(), g.shape).ravel()
+    K = -(sp.diags(wc) @ A).tocsr()
+    assert abs(K - K.T).max() <= 1e-12 * abs(K).max()
+    x, info = spla.cg(K, -(wc * rhs), rtol=1e-14, maxiter=20000, M=sp.diags(1.0 / K.diagonal()))
+    assert info == 0
+    x = x.reshape(g.shape)
+    x -= orc.volume_mean(g, x)
+    p, u, v, w, oinfo = orc.method3(g, us, vs, ws, rho, S, dt, rtol=1e-13, maxit=20000)
+    assert oinfo["res_hist"][-1] <= 1e-13
+    assert _rel(p, x) < 1e-10
+    for a, b in zip((u, v, w), orc.correct_velocity(g, us, vs, ws, rho, x, dt)):
+        assert _rel(a, b) < 1e-11
