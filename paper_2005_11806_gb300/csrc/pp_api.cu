@@ -513,23 +513,35 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
     auto tx = twiddles<double>(G.nx), ty = twiddles<double>(G.ny);
     if ((st = dalloc(&P->d_twx, tx.size() * sizeof(double2))) != PP_OK ||
         (st = dalloc(&P->d_twy, ty.size() * sizeof(double2))) != PP_OK) { free_plan(P); return st; }
-    cudaMemcpy(P->d_twx, tx.data(), tx.size() * sizeof(double2), cudaMemcpyHostToDevice);
-    cudaMemcpy(P->d_twy, ty.data(), ty.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(P->d_twx, tx.data(), tx.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P->d_twy, ty.data(), ty.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_plan(P);
+      return PP_ERR_CUDA;
+    }
     if (ywall) {
       auto tc = dct_twiddles<double>(G.ny);
       if ((st = dalloc(&P->d_dcty, tc.size() * sizeof(double2))) != PP_OK) { free_plan(P); return st; }
-      cudaMemcpy(P->d_dcty, tc.data(), tc.size() * sizeof(double2), cudaMemcpyHostToDevice);
+      if (cudaMemcpy(P->d_dcty, tc.data(), tc.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        free_plan(P);
+        return PP_ERR_CUDA;
+      }
     }
   } else {
     auto tx = twiddles<float>(G.nx), ty = twiddles<float>(G.ny);
     if ((st = dalloc(&P->d_twx, tx.size() * sizeof(float2))) != PP_OK ||
         (st = dalloc(&P->d_twy, ty.size() * sizeof(float2))) != PP_OK) { free_plan(P); return st; }
-    cudaMemcpy(P->d_twx, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    cudaMemcpy(P->d_twy, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(P->d_twx, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P->d_twy, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_plan(P);
+      return PP_ERR_CUDA;
+    }
     if (ywall) {
       auto tc = dct_twiddles<float>(G.ny);
       if ((st = dalloc(&P->d_dcty, tc.size() * sizeof(float2))) != PP_OK) { free_plan(P); return st; }
-      cudaMemcpy(P->d_dcty, tc.data(), tc.size() * sizeof(float2), cudaMemcpyHostToDevice);
+      if (cudaMemcpy(P->d_dcty, tc.data(), tc.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        free_plan(P);
+        return PP_ERR_CUDA;
+      }
     }
   }
   // residual partial sums: 2 per residual block, or the reduction grid
