@@ -40,3 +40,48 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(pressure, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         pressure.lib()
+
+
+def _lib_or_build():
+    from paper_2005_11806_gb300 import pressure
+    if not os.path.exists(pressure.LIB_PATH):
+        from paper_2005_11806_gb300 import build_ext
+        build_ext.build()
+    return pressure
+
+
+@pytest.mark.parametrize("dims,lens,prec,bc,code", [
+    ((0, 8, 8), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),      # empty grid
+    ((8, 8, 0), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),
+    ((8, 8, 8), (1, -1, 1), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),     # negative length
+    ((7, 8, 8), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_UNSUPPORTED"),      # odd nx (two real rows per complex FFT)
+    ((8, 7, 8), (1, 1, 1), "fp64", (0, 1, 1), "PP_ERR_UNSUPPORTED"),      # odd ny with walls in y
+    ((8, 8, 8), (1, 1, 1), "fp64", (1, 0, 1), "PP_ERR_UNSUPPORTED"),      # walls in x
+    ((8, 8, 8), (1, 1, 1), "fp64", (0, 0, 0), "PP_ERR_UNSUPPORTED"),      # periodic z
+    ((4096, 8, 8), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_UNSUPPORTED"),   # longer than one FFT block
+    ((14, 8, 8), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_UNSUPPORTED"),     # prime factor 7
+    ((8, 8, 1024), (1, 1, 1), "mixed_tc", (0, 0, 1), "PP_ERR_UNSUPPORTED"),  # tensor-core z beyond 512
+])
+def test_plan_create_rejects_bad_descriptors(dims, lens, prec, bc, code):
+    """Descriptor checks come before any CUDA call, so they run here."""
+    import ctypes
+    pressure = _lib_or_build()
+    g = pressure.pp_grid()
+    g.nx, g.ny, g.nz = dims
+    g.lx, g.ly, g.lz = lens
+    g.bc[0], g.bc[1], g.bc[2] = bc
+    out = ctypes.c_void_p()
+    got = pressure.lib().pressure_plan_create(ctypes.byref(g), pressure.PRECISIONS[prec], None, ctypes.byref(out))
+    assert got == getattr(pressure, code)
+    assert out.value is None
+
+
+def test_host_only_entry_points():
+    pressure = _lib_or_build()
+    # dp0/dt at t^{n+1} from two rates, linear in time (Sec. 3.3)
+    assert pressure.pressure_dp0dt_extrapolate(2.0, 1.0, 1e-3, 2e-3) == pytest.approx(2.5)
+    with pytest.raises(pressure.PressureError) as e:
+        pressure.pressure_dp0dt_extrapolate(2.0, 1.0, 1e-3, 0.0)
+    assert e.value.code == pressure.PP_ERR_INVALID_ARG
+    assert pressure.status_string(pressure.PP_OK)
+    assert pressure.status_string(pressure.PP_ERR_UNSUPPORTED) != pressure.status_string(pressure.PP_OK)
