@@ -543,9 +543,11 @@ def run_batch(args, rank, world, local_rank):
     return out
 
 
-def cpu_baseline(w, iters, passes=1):
+def cpu_baseline(w, iters, passes=1, iters_source="the GPU run's pass count"):
     """The oracle as it stands, timed on this host: `passes` Method III
-    passes on the full workload, scaled to one projection of `iters` passes."""
+    passes on the full workload, scaled to one projection of `iters` passes.
+    `cores` is the CPU time over the wall time of the sample (numpy's own
+    threads), capped at the host's thread count."""
     import numpy as np
 
     import oracle.pressure_oracle as orc
@@ -559,9 +561,9 @@ def cpu_baseline(w, iters, passes=1):
     npts = w.nx * w.ny * w.nz
     per_pass = wall / passes
     return {"value": npts / (per_pass * max(iters, 1)) / 1e9, "unit": "Gpts/s",
-            "cores": max(1, int(round(cpu / wall))), "kind": "oracle",
-            "sample": f"{passes} of {iters} Method III passes of the same 512^3 workload "
-                      f"({per_pass:.1f} s per pass), scaled to the full projection",
+            "cores": max(1, min(os.cpu_count() or 1, int(round(cpu / wall)))), "kind": "oracle",
+            "sample": f"{passes} of {iters} Method III passes ({iters_source}) of the same "
+                      f"{w.nx}x{w.ny}x{w.nz} workload ({per_pass:.3g} s per pass), scaled to the full projection",
             "host_threads_available": os.cpu_count(), "seconds_per_pass": round(per_pass, 2)}
 
 
@@ -574,10 +576,13 @@ def main():
         if rank != 0:
             return 0
         w = workload(args)
-        iters = int(os.environ.get("PP_REF_ITERS", "0")) or REF_ITERS_DEFAULT
+        iters = int(os.environ.get("PP_REF_ITERS", "0"))
+        src = "PP_REF_ITERS"
+        if not iters:
+            iters, src = REF_ITERS_DEFAULT, "the 512^3 benchmark's FP64 pass count"
         samples = []
         for _ in range(args.warmup + args.steps):
-            samples.append(cpu_baseline(w, iters))
+            samples.append(cpu_baseline(w, iters, iters_source=src))
         vals = [s["value"] for s in samples[args.warmup:]]
         v = statistics.median(vals)
         cb = dict(samples[-1])

@@ -65,3 +65,25 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference"])
     monkeypatch.setattr(bench, "workload", lambda args: pytest.fail("rank 1 must not build the workload"))
     assert bench.main() == 0
+
+
+def test_reference_arm_json_line(monkeypatch, capsys):
+    """The reference arm (the oracle timed on the host) prints one JSON line
+    with the contract's keys; a small grid keeps it to a second."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--n", "16", "--bubbles", "1",
+                                      "--steps", "1", "--warmup", "3"])
+    assert bench.main() == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["warmup"] >= 3 and line["value"] > 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and 1 <= cb["cores"] <= (os.cpu_count() or 1)
+    assert "16x16x16" in cb["sample"] and cb["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
