@@ -87,3 +87,24 @@ def test_reference_arm_json_line(monkeypatch, capsys):
     assert cb["kind"] == "oracle" and 1 <= cb["cores"] <= (os.cpu_count() or 1)
     assert "16x16x16" in cb["sample"] and cb["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_algorithmic_bytes_per_cell_at_512():
+    """The roofline's numerators: algorithmic bytes per cell of each pass
+    kernel of the 512^3 mixed benchmark (residual 32.7 averaged over the
+    40-pass exact/update cycle, y transforms 8.0, z solve 20.1, inverse x
+    16.2)."""
+    sys.path.insert(0, ROOT)
+    import types
+    import bench
+    w = types.SimpleNamespace(nx=512, ny=512, nz=512)
+    npts = 512 ** 3
+    per_cell = {k: bench.algorithmic(k, w, "mixed")["bytes"] / npts
+                for k in ("resid_fftx", "ffty_fwd", "tridiag_z", "fftx_inv_update")}
+    assert per_cell["resid_fftx"] == pytest.approx(32.7, abs=0.05)
+    assert per_cell["ffty_fwd"] == pytest.approx(8.03, abs=0.05)
+    assert per_cell["tridiag_z"] == pytest.approx(20.1, abs=0.05)
+    assert per_cell["fftx_inv_update"] == pytest.approx(16.2, abs=0.05)
+    # the residual's DRAM traffic per launch: 39 update passes to 1 exact
+    traffic = 0.975 * bench.RESID_DRAM_B_PER_CELL["update"] + 0.025 * bench.RESID_DRAM_B_PER_CELL["exact"]
+    assert traffic * npts == pytest.approx(4.83e9, rel=2e-3)
