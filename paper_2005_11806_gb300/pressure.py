@@ -358,13 +358,17 @@ class Batch:
         self.wface_offset = list(wo)
         self.ncell, self.nwface = tot[0], tot[1]
         self.tiles = (tiles[0], tiles[1])
+        _PLAN_SIZES[self.handle] = (self.ncell, self.nwface)   # packed buffers are checked like a plan's
 
     def mixture_density(self, phi, rho_g, rho_l, rho):
+        _sized(self.handle, (phi, "c"), (rho, "c"))
         _check(lib().pressure_batch_mixture_density(self.handle, _ptr(phi), float(rho_g), float(rho_l),
                                                     _ptr(rho)), "pressure_batch_mixture_density")
 
     def correct(self, us, vs, ws, rho, S, dt, p, u, v, w, rtol=1e-10, maxit=500,
                 allow_not_converged=False):
+        _sized(self.handle, (us, "c"), (vs, "c"), (ws, "w"), (rho, "c"), (S, "c"), (p, "c"), (u, "c"),
+               (v, "c"), (w, "w"))
         infos = (pp_info * self.n)()
         code = lib().pressure_batch_correct(self.handle, _ptr(us), _ptr(vs), _ptr(ws), _ptr(rho), _ptr(S),
                                             float(dt), _ptr(p), _ptr(u), _ptr(v), _ptr(w), float(rtol),
@@ -374,6 +378,7 @@ class Batch:
 
     def close(self):
         if getattr(self, "handle", None):
+            _PLAN_SIZES.pop(self.handle, None)
             _check(lib().pressure_batch_destroy(self.handle), "pressure_batch_destroy")
             self.handle = None
 

@@ -75,3 +75,22 @@ def test_destroy_forgets_the_plan(fake):
     pressure.pressure_plan_destroy(h)
     assert h not in pressure._PLAN_SIZES
     assert f.calls == ["pressure_plan_destroy"]
+
+
+def test_batch_buffers_are_checked(monkeypatch):
+    """The packed buffers of a batch are checked against its total cell and
+    z-face counts."""
+    f = _FakeLib()
+    monkeypatch.setattr(pressure, "_lib", f)
+    b = pressure.Batch.__new__(pressure.Batch)
+    b.handle, b.n, b.ncell, b.nwface = 0xBA7C, 2, 100, 120
+    monkeypatch.setitem(pressure._PLAN_SIZES, b.handle, (b.ncell, b.nwface))
+    c, w = np.zeros(100), np.zeros(120)
+    b.correct(c, c, w, c, c, 1e-3, c, c, c, w)
+    with pytest.raises(ValueError, match="z-face"):
+        b.correct(c, c, c, c, c, 1e-3, c, c, c, w)
+    with pytest.raises(ValueError, match="cell"):
+        b.mixture_density(np.zeros(99), 1.0, 1000.0, c)
+    assert f.calls == ["pressure_batch_correct"]
+    b.close()
+    assert b.handle is None and 0xBA7C not in pressure._PLAN_SIZES
