@@ -206,6 +206,11 @@ def pressure_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, zfaces=None, stream=Non
     """FP64 constant-coefficient solve that allocates no device memory (see
     the header).  f, p: CUDA float64 tensors.  Returns after enqueueing."""
     g, keep = _grid(nx, ny, nz, lx, ly, lz, zfaces)
+    n = int(nx) * int(ny) * int(nz)
+    for x in (f, p):
+        got = x.size if isinstance(x, np.ndarray) else getattr(x, "numel", lambda: None)()
+        if got is not None and got < n:
+            raise ValueError(f"a cell field needs {n} elements, got {got}")
     _check(lib().pressure_solve_noalloc(ctypes.byref(g), _ptr(f), _ptr(p), _stream(stream)),
            "pressure_solve_noalloc")
     del keep

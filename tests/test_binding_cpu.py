@@ -94,3 +94,12 @@ def test_batch_buffers_are_checked(monkeypatch):
     assert f.calls == ["pressure_batch_correct"]
     b.close()
     assert b.handle is None and 0xBA7C not in pressure._PLAN_SIZES
+
+
+def test_noalloc_fields_are_checked(monkeypatch):
+    f = _FakeLib()
+    monkeypatch.setattr(pressure, "_lib", f)
+    pressure.pressure_solve_noalloc(4, 4, 4, 1.0, 1.0, 1.0, np.zeros(64), np.zeros(64))
+    with pytest.raises(ValueError, match="cell"):
+        pressure.pressure_solve_noalloc(4, 4, 4, 1.0, 1.0, 1.0, np.zeros(64), np.zeros(63))
+    assert f.calls == ["pressure_solve_noalloc"]
