@@ -678,3 +678,34 @@ def test_method3_matches_preconditioned_cg(n, beta, ratio, ywalls):
     assert _rel(p, x) < 1e-10
     for a, b in zip((u, v, w), orc.correct_velocity(g, us, vs, ws, rho, x, dt)):
         assert _rel(a, b) < 1e-11
+
+
+def test_degenerate_divergence_free_input_takes_no_pass():
+    """u* that already meets the target exactly (a uniform flow along the
+    periodic directions: D u* = S_c = 0 with no round-off): Algorithm 1
+    stops before its first pass with p = 0 and u = u*.  (A field that is
+    divergence-free only to round-off is iterated on that noise, as the
+    relative stopping rule defines.)"""
+    g = _grid(8, 6, 5, beta=1.5)
+    rng = np.random.default_rng(31)
+    us = np.full(g.shape, 0.37)
+    vs = np.full(g.shape, -1.25)
+    ws = np.zeros((g.nz + 1, g.ny, g.nx))
+    assert np.all(orc.divergence(g, us, vs, ws) == 0.0)
+    rho = orc.mixture_density(rng.uniform(0, 1, g.shape), 1.0, 1000.0)
+    p, u, v, w, info = orc.method3(g, us, vs, ws, rho, np.zeros(g.shape), 1e-3)
+    assert info["iters"] == 0 and info["res0"] == 0.0
+    assert np.all(p == 0.0) and np.array_equal(u, us) and np.array_equal(v, vs) and np.array_equal(w, ws)
+
+
+def test_single_layer_is_the_two_dimensional_problem():
+    """nz = 1: no z coupling, so a mode cos(2 pi a i/nx) cos(2 pi b j/ny) has
+    the 2-D eigenvalue, and the (0, 0) mode is the pinned mean."""
+    nx, ny = 16, 12
+    g = _grid(nx, ny, 1, 1.0, 0.8, 0.3)
+    i = np.arange(nx)[None, None, :]
+    j = np.arange(ny)[None, :, None]
+    f = np.cos(2 * np.pi * 3 * i / nx) * np.cos(2 * np.pi * 2 * j / ny + 0.5)
+    lam = -(4 * (nx / 1.0) ** 2 * math.sin(math.pi * 3 / nx) ** 2 + 4 * (ny / 0.8) ** 2 * math.sin(math.pi * 2 / ny) ** 2)
+    assert _rel(orc.solve_constant(g, f), f / lam) < 1e-12
+    assert np.max(np.abs(orc.solve_constant(g, np.ones(g.shape)))) < 1e-14
