@@ -58,6 +58,8 @@ dot-product identity.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import scipy.fft as sfft
 import scipy.sparse as sp
@@ -68,8 +70,15 @@ __all__ = [
     "volume_mean", "laplacian", "solve_constant", "method3", "projection_direct",
     "correct_velocity", "adjoint_direct", "adjoint_method3", "method1", "method2",
     "conduction", "gas_volume", "p0_rate", "dp0dt_extrapolate", "divergence_source",
-    "convection", "viscous", "predictor_rhs", "predictor",
+    "convection", "viscous", "predictor_rhs", "predictor", "method1_rho_tilde",
+    "method1_correction", "method2_rho_tilde", "ab2_weights",
 ]
+
+
+# Threads of scipy's FFTs (the batch of 1-D transforms is split among them;
+# the arithmetic of each transform does not depend on it).  The rest of the
+# oracle is plain single-threaded numpy.
+WORKERS = os.cpu_count() or 1
 
 
 class Grid:
@@ -173,7 +182,7 @@ def solve_constant(g, f):
     (Sec. 3.3.1: homogeneous pressure boundary conditions, solved exactly).
 
     Returns the zero-mean p with ``D G p = f - <f>_V``.  Steps: real DFT in x,
-    complex DFT in y (numpy's FFT), one tridiagonal system per (kx, ky) along
+    complex DFT in y (scipy's FFT), one tridiagonal system per (kx, ky) along
     z with the eigenvalues of the periodic second difference on its diagonal
     (Thomas algorithm), the singular (0, 0) column by a bordered dense solve
     that fixes its zero weighted mean, then the inverse DFTs.
@@ -188,11 +197,12 @@ def solve_constant(g, f):
     kx = np.arange(nx // 2 + 1)
     ky = np.arange(ny)
     if g.ywalls:
-        fh = np.fft.rfft(fc, axis=2)
-        fh = sfft.dct(fh.real, type=2, axis=1) + 1j * sfft.dct(fh.imag, type=2, axis=1)
+        fh = sfft.rfft(fc, axis=2, workers=WORKERS)
+        fh = (sfft.dct(fh.real, type=2, axis=1, workers=WORKERS)
+              + 1j * sfft.dct(fh.imag, type=2, axis=1, workers=WORKERS))
         lam_y = -4.0 / g.dy ** 2 * np.sin(np.pi * ky / (2 * ny)) ** 2
     else:
-        fh = np.fft.rfft2(fc, axes=(1, 2))              # [nz, ny, nx//2 + 1]
+        fh = sfft.rfft2(fc, axes=(1, 2), workers=WORKERS)   # [nz, ny, nx//2 + 1]
         lam_y = -4.0 / g.dy ** 2 * np.sin(np.pi * ky / ny) ** 2
     lam = (-4.0 / g.dx ** 2 * np.sin(np.pi * kx / nx) ** 2)[None, :] + lam_y[:, None]
     a, c = _z_coefficients(g)
@@ -225,10 +235,11 @@ def solve_constant(g, f):
     rhs[:nz] = fh[:, 0, 0]
     ph[:, 0, 0] = np.linalg.solve(lz, rhs)[:nz]
     if g.ywalls:
-        ph = sfft.idct(ph.real, type=2, axis=1) + 1j * sfft.idct(ph.imag, type=2, axis=1)
-        p = np.fft.irfft(ph, n=nx, axis=2)
+        ph = (sfft.idct(ph.real, type=2, axis=1, workers=WORKERS)
+              + 1j * sfft.idct(ph.imag, type=2, axis=1, workers=WORKERS))
+        p = sfft.irfft(ph, n=nx, axis=2, workers=WORKERS)
     else:
-        p = np.fft.irfft2(ph, s=(ny, nx), axes=(1, 2))
+        p = sfft.irfft2(ph, s=(ny, nx), axes=(1, 2), workers=WORKERS)
     return p - volume_mean(g, p)
 
 
@@ -296,7 +307,7 @@ def method1(g, us, vs, ws, rho, S, dt, rtol=1e-13, maxit=5000):
     measure ||p^{s+1} - p^s|| is reported in the history."""
     Sc = S - volume_mean(g, S)
     rx, ry, rz = face_density(g, rho)
-    rho0 = float(np.min(rho))
+    rho0 = method1_rho_tilde(rho)
     pre = (rho0 / dt) * (divergence(g, us, vs, ws) - Sc)
     res0 = np.linalg.norm((divergence(g, us, vs, ws) - Sc).ravel())
     p = np.zeros(g.shape)
@@ -313,12 +324,34 @@ def method1(g, us, vs, ws, rho, S, dt, rtol=1e-13, maxit=5000):
         s += 1
         if hist[-1] <= rtol:
             break
+    u, v, w = method1_correction(g, us, vs, ws, rho, rho0, p, p_prev, dt)
+    return p, u, v, w, {"iters": s, "res_hist": hist, "dp_hist": dp_hist, "rho_tilde": rho0}
+
+
+def method1_rho_tilde(rho):
+    """Eq. poisson_me1: the constant density of Method I is the smallest
+    density in the domain."""
+    return float(np.min(rho))
+
+
+def method1_correction(g, us, vs, ws, rho, rho0, p, p_q, dt):
+    """Eq. poisson_me2, Method I's modified correction:
+    u = u* - dt [ (1/rho0) G p + (1/rho_f - 1/rho0) G p^q ], with p the last
+    iterate and p^q the one before it."""
+    rx, ry, rz = face_density(g, rho)
     gx, gy, gz = gradient(g, p)
-    qx, qy, qz = gradient(g, p_prev)
+    qx, qy, qz = gradient(g, p_q)
     u = us - dt * (gx / rho0 + (1.0 / rx - 1.0 / rho0) * qx)
     v = vs - dt * (gy / rho0 + (1.0 / ry - 1.0 / rho0) * qy)
     w = ws - dt * (gz / rho0 + (1.0 / rz - 1.0 / rho0) * qz)
-    return p, u, v, w, {"iters": s, "res_hist": hist, "dp_hist": dp_hist, "rho_tilde": rho0}
+    return u, v, w
+
+
+def method2_rho_tilde(rho):
+    """Eq. poisson_laizet: the harmonic mean of the two phase densities,
+    taken as the smallest and largest density in the domain (reading R17)."""
+    rmin, rmax = float(np.min(rho)), float(np.max(rho))
+    return 2.0 * rmin * rmax / (rmin + rmax)
 
 
 def method2(g, us, vs, ws, rho, S, dt, rtol=1e-13, maxit=5000):
@@ -330,8 +363,7 @@ def method2(g, us, vs, ws, rho, S, dt, rtol=1e-13, maxit=5000):
     method3."""
     Sc = S - volume_mean(g, S)
     rx, ry, rz = face_density(g, rho)
-    rmin, rmax = float(np.min(rho)), float(np.max(rho))
-    rt = 2.0 * rmin * rmax / (rmin + rmax)
+    rt = method2_rho_tilde(rho)
     b = (divergence(g, us, vs, ws) - Sc) / dt
     res0 = np.linalg.norm((b * dt).ravel())
     p = np.zeros(g.shape)
@@ -714,9 +746,16 @@ def predictor(g, u, v, w, rho, mu, grav, dt_new, dt_old=None, ru_prev=None, forc
         a, b = 1.0, 0.0
         ru_prev = (0.0, 0.0, 0.0)
     else:
-        r = dt_new / dt_old
-        a, b = 1.0 + 0.5 * r, 0.5 * r
+        a, b = ab2_weights(dt_new, dt_old)
     out = tuple(x + dt_new * (a * q - b * qp) for x, q, qp in zip((u, v, w), ru, ru_prev))
     out[2][0] = 0.0
     out[2][-1] = 0.0
     return out, ru
+
+
+def ab2_weights(dt_new, dt_old):
+    """Eq. 29's Adams-Bashforth weights for a step dt_new after a step dt_old:
+    u* = u^n + dt_new [a RU^n - b RU^{n-1}], a = 1 + r/2, b = r/2,
+    r = dt_new / dt_old."""
+    r = dt_new / dt_old
+    return 1.0 + 0.5 * r, 0.5 * r

@@ -123,3 +123,54 @@ def assemble_conduction(nx, ny, nz, lx, ly, zf, kc):
                     A[r, idx(i, j, kk)] += b
                     A[r, r] -= b
     return A
+
+
+def gradient_loops(nx, ny, nz, lx, ly, zf, p, ywalls=False):
+    """G p on the faces, cell by cell: x faces (i - 1/2), y faces (j - 1/2),
+    z faces k = 0 .. nz (the wall faces 0 and nz carry no gradient); with
+    ywalls the wall row j = 0 of the y faces carries none either."""
+    dx, dy = lx / nx, ly / ny
+    _, zc = metrics(nz, zf)
+    gx = np.zeros((nz, ny, nx))
+    gy = np.zeros((nz, ny, nx))
+    gz = np.zeros((nz + 1, ny, nx))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                gx[k, j, i] = (p[k, j, i] - p[k, j, (i - 1) % nx]) / dx
+                if not (ywalls and j == 0):
+                    gy[k, j, i] = (p[k, j, i] - p[k, (j - 1) % ny, i]) / dy
+                if k > 0:
+                    gz[k, j, i] = (p[k, j, i] - p[k - 1, j, i]) / (zc[k] - zc[k - 1])
+    return gx, gy, gz
+
+
+def face_beta_loops(nx, ny, nz, rho):
+    """1 / rho_f on the faces with rho_f the arithmetic mean of the two cells
+    of a face (x, y faces periodic; z faces 1 .. nz - 1; the wall planes of z
+    hold 0, where the gradient vanishes anyway)."""
+    bx = np.zeros((nz, ny, nx))
+    by = np.zeros((nz, ny, nx))
+    bz = np.zeros((nz + 1, ny, nx))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                bx[k, j, i] = 2.0 / (rho[k, j, i] + rho[k, j, (i - 1) % nx])
+                by[k, j, i] = 2.0 / (rho[k, j, i] + rho[k, (j - 1) % ny, i])
+                if k > 0:
+                    bz[k, j, i] = 2.0 / (rho[k, j, i] + rho[k - 1, j, i])
+    return bx, by, bz
+
+
+def pseudo_inverse_laplacian(nx, ny, nz, lx, ly, zf):
+    """Dense matrix of f -> the zero-mean p with L p = f - <f>_V (L = D G, the
+    constant-coefficient operator), one bordered LU solve per unit vector."""
+    L = assemble_variable(nx, ny, nz, lx, ly, zf, None)
+    wts = cell_weights(nx, ny, nz, zf)
+    n = L.shape[0]
+    out = np.zeros((n, n))
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = 1.0
+        out[:, c] = bordered_solve(L, e - (wts @ e) / wts.sum(), wts)
+    return out

@@ -1,0 +1,360 @@
+"""Pins of the oracle's convection term, the Adams-Bashforth weights of the
+predictor (Eqs. 29, 32), Method I's modified correction (Eq. poisson_me2)
+and the constant densities of Methods I and II (Eqs. poisson_me1,
+poisson_laizet), each against something other than the oracle itself:
+closed forms of the discrete stencils worked out by hand for special
+fields, the exactness of a second-order multistep formula, and dense
+matrices assembled entry by entry (tests/dense_reference.py).  The last
+section plants a mistake in each and checks that a pin fails.  CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.pressure_oracle as orc
+from paper_2005_11806_gb300 import workloads as wl
+from tests import dense_reference as dr
+
+
+def _grid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, beta=None):
+    zf = wl.uniform_zfaces(nz, lz) if beta is None else wl.tanh_zfaces(nz, lz, beta)
+    return orc.Grid(nx, ny, nz, lx, ly, zf)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _bcast(a, shape):
+    return np.broadcast_to(a, shape).copy()
+
+
+# --- convection C(u) = div(u u) - u div(u) -----------------------------------
+
+def test_convection_shear_by_a_uniform_cross_velocity():
+    """u = sin(kappa y) on the x faces (y of the face centre (j + 1/2) dy) is
+    carried by a uniform v = V0: div u = 0, and the only term left is the xy
+    edge flux, whose centred difference is the closed form
+    C_x = V0 cos(kappa y_j) sin(kappa dy) / dy (a sine's central difference).
+    The same with the roles of x and y exchanged for C_y.  Fixes the sign and
+    scale of the cross terms (the conservation pins are blind to both)."""
+    nx, ny, nz, lx, ly, V0 = 6, 16, 5, 0.7, 1.3, 0.37
+    g = _grid(nx, ny, nz, lx, ly, 0.9, beta=1.5)
+    kap = 2 * math.pi / ly
+    yj = (np.arange(ny) + 0.5) * g.dy
+    u = _bcast(np.sin(kap * yj)[None, :, None], g.shape)
+    v = np.full(g.shape, V0)
+    w = np.zeros((nz + 1, ny, nx))
+    cx, cy, cz = orc.convection(g, u, v, w)
+    ref = _bcast((V0 * np.cos(kap * yj) * math.sin(kap * g.dy) / g.dy)[None, :, None], g.shape)
+    assert _rel(cx, ref) < 1e-13
+    assert np.abs(cy).max() < 1e-13 and np.abs(cz).max() < 1e-13
+
+    nx, ny = 18, 4
+    g = _grid(nx, ny, nz, lx, ly, 0.9)
+    kap = 2 * math.pi / lx
+    xi = (np.arange(nx) + 0.5) * g.dx
+    U0 = -0.81
+    v = _bcast(np.sin(kap * xi)[None, None, :], g.shape)
+    u = np.full(g.shape, U0)
+    cx, cy, cz = orc.convection(g, u, v, np.zeros((nz + 1, ny, nx)))
+    ref = _bcast((U0 * np.cos(kap * xi) * math.sin(kap * g.dx) / g.dx)[None, None, :], g.shape)
+    assert _rel(cy, ref) < 1e-13
+    assert np.abs(cx).max() < 1e-13 and np.abs(cz).max() < 1e-13
+
+
+def _compressive_closed_form(n, d):
+    """A single sine u_i = sin(theta_i) on the faces of one direction,
+    theta_i = 2 h i (h = half the phase step), nothing else moving.  With
+    a_i = (u_i + u_{i+1})/2 = cos h sin(theta_i + h) and the divergence
+    D_i = 2 sin h cos(theta_i + h) / d, the centred
+    (a_i^2 - a_{i-1}^2)/d - u_i (D_i + D_{i-1})/2 reduces to
+    sin(4h) sin(2 theta_i) / (4 d); the continuous limit is u u' = k sin(2kx)/2."""
+    return lambda theta, h: math.sin(4 * h) * np.sin(2 * theta) / (4 * d)
+
+
+def test_convection_compressive_single_modes():
+    """Compressive single modes along x, y and z (uniform z, w zero on the
+    walls): the closed form above fixes the normal flux and the -u div(u)
+    term, which vanishes on every divergence-free field the conservation
+    pins use."""
+    nx, ny, nz, lx, ly, lz = 12, 10, 8, 1.1, 0.8, 0.6
+    g = _grid(nx, ny, nz, lx, ly, lz)
+    z3 = np.zeros((nz + 1, ny, nx))
+    zc = np.zeros(g.shape)
+    # x: faces at x = i dx
+    th = 2 * math.pi * np.arange(nx) / nx
+    u = _bcast(np.sin(th)[None, None, :], g.shape)
+    cx, cy, cz = orc.convection(g, u, zc, z3)
+    ref = _bcast(_compressive_closed_form(nx, g.dx)(th, math.pi / nx)[None, None, :], g.shape)
+    assert _rel(cx, ref) < 1e-12
+    assert np.abs(cy).max() < 1e-13 and np.abs(cz).max() < 1e-13
+    # y: faces at y = j dy
+    th = 2 * math.pi * np.arange(ny) / ny
+    v = _bcast(np.sin(th)[None, :, None], g.shape)
+    cx, cy, cz = orc.convection(g, zc, v, z3)
+    ref = _bcast(_compressive_closed_form(ny, g.dy)(th, math.pi / ny)[None, :, None], g.shape)
+    assert _rel(cy, ref) < 1e-12
+    assert np.abs(cx).max() < 1e-13 and np.abs(cz).max() < 1e-13
+    # z: faces at z = k dz, k = 0 .. nz, w = sin(pi k / nz) vanishes on both walls
+    dz = lz / nz
+    th = math.pi * np.arange(nz + 1) / nz
+    w = _bcast(np.sin(th)[:, None, None], (nz + 1, ny, nx))
+    cx, cy, cz = orc.convection(g, zc, zc, w)
+    ref = _bcast(_compressive_closed_form(nz, dz)(th, math.pi / (2 * nz))[:, None, None], (nz + 1, ny, nx))
+    ref[0] = ref[-1] = 0.0
+    assert _rel(cz, ref) < 1e-12
+    assert np.abs(cx).max() < 1e-13 and np.abs(cy).max() < 1e-13
+
+
+def test_convection_by_a_uniform_wall_normal_velocity_stretched():
+    """u = u(z) arbitrary on a stretched z, w = W0 on every interior z face
+    (0 on the walls), v = 0.  Worked out by hand from the stencil: the xz
+    edge flux is W0 times the face mean of u, so in the interior layers
+    C_x = W0 (u_{k+1} - u_{k-1}) / (2 dzf_k); in the two wall layers the
+    divergence is +-W0/dzf and the -u div(u) term turns the one-sided flux
+    into W0 (u_1 - u_0) / (2 dzf_0) and W0 (u_{n-1} - u_{n-2}) / (2 dzf_{n-1}).
+    For w itself: the centre values of w are W0/2 in the wall layers and W0
+    inside, so C_z on face 1 is W0^2 (3/(4 dzc_1) - 1/(2 dzf_0)), on face
+    nz - 1 it is W0^2 (1/(2 dzf_{n-1}) - 3/(4 dzc_{n-1})), and 0 between.
+    Fixes the xz edge term, the z interpolation of div(u) and their signs."""
+    nx, ny, nz, W0 = 4, 3, 9, 0.6
+    g = _grid(nx, ny, nz, 1.0, 1.0, 0.8, beta=2.0)
+    rng = np.random.default_rng(77)
+    uz = rng.standard_normal(nz)
+    u = _bcast(uz[:, None, None], g.shape)
+    w = np.full((nz + 1, ny, nx), W0)
+    w[0] = w[-1] = 0.0
+    cx, cy, cz = orc.convection(g, u, np.zeros(g.shape), w)
+    dzf = g.dzf
+    ref = np.empty(nz)
+    ref[1:-1] = W0 * (uz[2:] - uz[:-2]) / (2 * dzf[1:-1])
+    ref[0] = W0 * (uz[1] - uz[0]) / (2 * dzf[0])
+    ref[-1] = W0 * (uz[-1] - uz[-2]) / (2 * dzf[-1])
+    assert _rel(cx, _bcast(ref[:, None, None], g.shape)) < 1e-13
+    assert np.abs(cy).max() < 1e-13
+    refz = np.zeros(nz + 1)
+    refz[1] = W0 ** 2 * (3 / (4 * g.dzc[1]) - 1 / (2 * dzf[0]))
+    refz[nz - 1] = W0 ** 2 * (1 / (2 * dzf[-1]) - 3 / (4 * g.dzc[nz - 1]))
+    assert _rel(cz, _bcast(refz[:, None, None], (nz + 1, ny, nx))) < 1e-13
+
+
+# --- Adams-Bashforth weights (Eq. 29) ----------------------------------------
+
+def test_adams_bashforth_is_exact_for_a_linear_history():
+    """A second-order two-step formula integrates a right-hand side that is
+    linear in time exactly, for any step ratio r: with RU(t) = RU^n + beta
+    (t - t_n), int_{t_n}^{t_n + dt_new} RU = dt_new (RU^n + beta dt_new / 2).
+    Feeding RU^{n-1} = RU^n - beta dt_old must give that increment.  The
+    history differs from RU^n and r = 2.5 != 1, so any weights other than
+    Eq. 29's (1 + r/2, r/2) fail, e.g. (1 + r, r) or a - b = 1 pairs."""
+    g = _grid(8, 6, 7, beta=1.5)
+    rng = np.random.default_rng(91)
+    rho = rng.uniform(1.0, 50.0, g.shape)
+    mu = rng.uniform(1e-3, 0.1, g.shape)
+    u, v = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    w = rng.standard_normal((g.nz + 1, g.ny, g.nx)); w[0] = w[-1] = 0.0
+    grav = (0.1, 0.0, -9.81)
+    dt_old, dt_new = 1e-3, 2.5e-3
+    ru = orc.predictor_rhs(g, u, v, w, rho, mu, grav)
+    beta = (rng.standard_normal(g.shape), rng.standard_normal(g.shape),
+            rng.standard_normal((g.nz + 1, g.ny, g.nx)))
+    prev = tuple(q - b * dt_old for q, b in zip(ru, beta))
+    (a1, b1, c1), ru_out = orc.predictor(g, u, v, w, rho, mu, grav, dt_new, dt_old, ru_prev=prev)
+    for out, x, q, b in zip((a1, b1, c1), (u, v, w), ru, beta):
+        ref = x + dt_new * (q + 0.5 * b * dt_new)
+        if out.shape[0] == g.nz + 1:
+            ref = ref.copy(); ref[0] = ref[-1] = 0.0
+        assert _rel(out, ref) < 1e-14
+
+
+# --- Methods I and II: dense restatements on a tiny grid ----------------------
+
+def _case(ratio=10.0):
+    """5 x 4 x 6 cells, stretched z, a gas block with pure gas and pure
+    liquid cells (so min rho = rho_g and max rho = rho_l), a thin interface
+    layer, a random u* and a gas source."""
+    nx, ny, nz = 5, 4, 6
+    zf = wl.tanh_zfaces(nz, 0.8, 1.5)
+    g = orc.Grid(nx, ny, nz, 1.0, 0.9, zf)
+    phi = np.zeros(g.shape)
+    phi[1:4, 1:3, 1:3] = 1.0
+    phi[4, 1:3, 1:3] = 0.35
+    rho_g, rho_l = 1.0, ratio
+    rho = orc.mixture_density(phi, rho_g, rho_l)
+    rng = np.random.default_rng(23)
+    us, vs = rng.standard_normal(g.shape) * 0.1, rng.standard_normal(g.shape) * 0.1
+    ws = rng.standard_normal((nz + 1, ny, nx)) * 0.1; ws[0] = ws[-1] = 0.0
+    S = wl.gas_source(phi)
+    return g, zf, us, vs, ws, rho, S, rho_g, rho_l
+
+
+def _dense(g, zf, rho):
+    A = dr.assemble_variable(g.nx, g.ny, g.nz, g.lx, g.ly, zf, rho)
+    Lp = dr.pseudo_inverse_laplacian(g.nx, g.ny, g.nz, g.lx, g.ly, zf)
+    wts = dr.cell_weights(g.nx, g.ny, g.nz, zf)
+    return A, Lp, wts
+
+
+def _b(g, zf, us, vs, ws, S, wts, dt):
+    d = dr.divergence_loops(g.nx, g.ny, g.nz, g.lx, g.ly, zf, us, vs, ws).ravel()
+    Sc = S.ravel() - (wts @ S.ravel()) / wts.sum()
+    return (d - Sc) / dt
+
+
+def test_method1_modified_correction_after_two_passes():
+    """Stop Method I after two passes and rebuild both iterates and
+    Eq. poisson_me2 from the dense operators: p1 = L+ (rho0 b),
+    p2 = L+ [D((1 - rho0 beta) G p1) + rho0 b] (Eq. poisson_me1, L+ the
+    zero-mean inverse of D G), then
+    u = u* - dt [ (1/rho0) G p2 + (beta - 1/rho0) G p1 ].
+    Two passes, so p2 != p1 and a correction that swaps p and p^q (or uses
+    Eq. corr) differs by dt (2/rho0 - beta) G (p1 - p2)."""
+    g, zf, us, vs, ws, rho, S, rho_g, _ = _case(10.0)
+    dt = 1e-3
+    A, Lp, wts = _dense(g, zf, rho)
+    b = _b(g, zf, us, vs, ws, S, wts, dt)
+    rho0 = rho_g                      # Eq. poisson_me1: the smallest density
+    sh = g.shape
+    p1 = Lp @ (rho0 * b)
+    bx, by, bz = dr.face_beta_loops(g.nx, g.ny, g.nz, rho)
+    gx, gy, gz = dr.gradient_loops(g.nx, g.ny, g.nz, g.lx, g.ly, zf, p1.reshape(sh))
+    dflux = dr.divergence_loops(g.nx, g.ny, g.nz, g.lx, g.ly, zf, (1 - rho0 * bx) * gx,
+                                (1 - rho0 * by) * gy, (1 - rho0 * bz) * gz).ravel()
+    p2 = Lp @ (dflux + rho0 * b)
+    g2 = dr.gradient_loops(g.nx, g.ny, g.nz, g.lx, g.ly, zf, p2.reshape(sh))
+    g1 = (gx, gy, gz)
+    ref = [x - dt * (q2 / rho0 + (bb - 1 / rho0) * q1) for x, q2, q1, bb in
+           zip((us, vs, ws), g2, g1, (bx, by, bz))]
+    ref[2][0] = ref[2][-1] = 0.0
+    p, u, v, w, info = orc.method1(g, us, vs, ws, rho, S, dt, rtol=0.0, maxit=2)
+    assert info["iters"] == 2
+    assert _rel(p.ravel(), p2) < 1e-12
+    for a, r in zip((u, v, w), ref):
+        assert _rel(a, r) < 1e-12
+    # the swap is not a rounding-level change here
+    swapped = us - dt * (g1[0] / rho0 + (bx - 1 / rho0) * g2[0])
+    assert _rel(swapped, ref[0]) > 1e-3
+
+
+def _dense_residuals(A, Lp, scale, b, npass):
+    """Relative residual norms of the defect-correction iteration
+    r^{s+1} = (I - A L+ diag(scale)) r^s, r^0 = b (Sec. 3.3.1: each method
+    adds L+ (rho~ times the residual) to p; A = D(beta G))."""
+    M = np.eye(len(b)) - A @ Lp @ np.diag(scale)
+    r, out = b.copy(), []
+    for _ in range(npass):
+        r = M @ r
+        out.append(float(np.linalg.norm(r) / np.linalg.norm(b)))
+    return np.array(out), M
+
+
+def _spectral_radius_on_compatible(M, wts):
+    """Largest |eigenvalue| of M on the residuals with zero weighted sum
+    (the space it maps into itself); orthonormal basis Q of that space."""
+    n = len(wts)
+    Q, _ = np.linalg.qr(np.column_stack([wts, np.eye(n)[:, :n - 1]]))
+    Q = Q[:, 1:]
+    return float(np.max(np.abs(np.linalg.eigvals(Q.T @ M @ Q))))
+
+
+@pytest.mark.parametrize("method", ["method1", "method2", "method3"])
+def test_residual_history_is_the_dense_iteration(method):
+    """The constant density decides how fast each method contracts, so it is
+    pinned through the residual history.  The dense iteration uses the
+    paper's definitions directly: Method I's smallest density
+    (Eq. poisson_me1), Method II's harmonic mean of the two phase
+    densities (Eq. poisson_laizet), Method III's cell density
+    (Eq. new_poisson).  The oracle's relative residuals after each pass must
+    equal the dense iteration's, and the late contraction per pass must
+    approach the spectral radius of the error-propagation matrix."""
+    g, zf, us, vs, ws, rho, S, rho_g, rho_l = _case(10.0)
+    dt = 1e-3
+    A, Lp, wts = _dense(g, zf, rho)
+    b = _b(g, zf, us, vs, ws, S, wts, dt)
+    n = len(b)
+    scale = {"method1": np.full(n, rho_g),
+             "method2": np.full(n, 2.0 / (1.0 / rho_g + 1.0 / rho_l)),
+             "method3": rho.ravel()}[method]
+    npass = 60
+    ref, M = _dense_residuals(A, Lp, scale, b, npass)
+    _, _, _, _, info = getattr(orc, method)(g, us, vs, ws, rho, S, dt, rtol=0.0, maxit=npass)
+    hist = np.array(info["res_hist"])
+    assert len(hist) == npass
+    # pass by pass while the residual is far above the rounding floor
+    k = int(np.searchsorted(-ref, -1e-6))
+    assert k >= 8
+    assert np.max(np.abs(hist[:k] / ref[:k] - 1.0)) < 1e-8
+    # late contraction, measured down to 1e-11, against the spectral radius
+    kl = int(np.searchsorted(-ref, -1e-11))
+    rad = _spectral_radius_on_compatible(M, wts)
+    assert rad < 1.0
+    late = (hist[kl - 1] / hist[kl - 7]) ** (1.0 / 6.0)
+    assert abs(late - rad) < 0.03 * rad, (late, rad)
+
+
+# --- planted mistakes: each must make a pin above fail ------------------------
+
+def test_planted_convection_sign_is_caught(monkeypatch):
+    orig = orc.convection
+    monkeypatch.setattr(orc, "convection", lambda g, u, v, w: tuple(-c for c in orig(g, u, v, w)))
+    with pytest.raises(AssertionError):
+        test_convection_shear_by_a_uniform_cross_velocity()
+    with pytest.raises(AssertionError):
+        test_convection_compressive_single_modes()
+
+
+def test_planted_convection_scale_is_caught(monkeypatch):
+    orig = orc.convection
+    monkeypatch.setattr(orc, "convection", lambda g, u, v, w: tuple(0.5 * c for c in orig(g, u, v, w)))
+    with pytest.raises(AssertionError):
+        test_convection_shear_by_a_uniform_cross_velocity()
+
+
+def test_planted_dropped_u_div_u_is_caught(monkeypatch):
+    """C without its -u div(u) part (divergence form only)."""
+    orig = orc.convection
+
+    def planted(g, u, v, w):
+        cx, cy, cz = orig(g, u, v, w)
+        D = orc.divergence(g, u, v, w)
+        Dz = np.zeros((g.nz + 1, g.ny, g.nx))
+        Dz[1:-1] = 0.5 * (D[1:] + D[:-1])
+        return (cx + u * 0.5 * (D + np.roll(D, 1, axis=2)), cy + v * 0.5 * (D + np.roll(D, 1, axis=1)),
+                cz + w * Dz)
+    monkeypatch.setattr(orc, "convection", planted)
+    # the divergence-free conservation pins cannot see it ...
+    from tests.test_oracle_pins import test_convection_conserves_momentum_and_energy
+    test_convection_conserves_momentum_and_energy()
+    # ... the compressive closed forms do
+    with pytest.raises(AssertionError):
+        test_convection_compressive_single_modes()
+    with pytest.raises(AssertionError):
+        test_convection_by_a_uniform_wall_normal_velocity_stretched()
+
+
+def test_planted_adams_bashforth_weights_are_caught(monkeypatch):
+    """The dp0/dt extrapolation's weights (1 + r, r) in place of Eq. 29's."""
+    monkeypatch.setattr(orc, "ab2_weights", lambda dn, do: (1.0 + dn / do, dn / do))
+    with pytest.raises(AssertionError):
+        test_adams_bashforth_is_exact_for_a_linear_history()
+
+
+def test_planted_swapped_method1_iterates_are_caught(monkeypatch):
+    orig = orc.method1_correction
+    monkeypatch.setattr(orc, "method1_correction",
+                        lambda g, us, vs, ws, rho, rho0, p, p_q, dt: orig(g, us, vs, ws, rho, rho0, p_q, p, dt))
+    with pytest.raises(AssertionError):
+        test_method1_modified_correction_after_two_passes()
+
+
+@pytest.mark.parametrize("name,method,planted", [
+    ("method2_rho_tilde", "method2", lambda rho: 0.5 * (float(np.min(rho)) + float(np.max(rho)))),
+    ("method2_rho_tilde", "method2", lambda rho: float(np.min(rho))),
+    ("method1_rho_tilde", "method1", lambda rho: 2.0 / (1.0 / float(np.min(rho)) + 1.0 / float(np.max(rho)))),
+])
+def test_planted_constant_density_is_caught(monkeypatch, name, method, planted):
+    monkeypatch.setattr(orc, name, planted)
+    with pytest.raises(AssertionError):
+        test_residual_history_is_the_dense_iteration(method)
