@@ -255,20 +255,27 @@ pp_status pressure_solve_adjoint(pp_plan plan, const double* rho, const double* 
 
 /* Constant-coefficient FP64 solve (same result as pressure_solve on an FP64
  * plan) that allocates no device memory.  The paper has no counterpart: this
- * entry point serves callers that cannot call cudaMalloc, e.g. code running
- * while a stream is being captured, hosts whose device memory belongs to an
- * external pool or budget, or loops that must not enter an allocator.
- * Working memory is one fixed 16 MiB device array inside the library, held by
- * every GPU that loads the library until the process exits; grids whose
- * spectral array, pivots and tables do not fit return PP_ERR_TOO_LARGE
- * (about 128 x 128 x 64 cells fit).  f and p must be device pointers (host
- * pointers return PP_ERR_INVALID_ARG); the caller owns them.  Work is
- * enqueued on `stream` (a cudaStream_t) and the call returns without waiting.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
- * share the array and each overwrites what the previous one left: calls that
- * may overlap on the GPU (different streams or devices sharing nothing else)
- * race and must be ordered by the caller. */
+ * entry point serves callers that cannot call cudaMalloc, e.g. hosts whose
+ * device memory belongs to an external pool or budget, or loops that must
+ * not enter an allocator.  Working memory is one fixed 16 MiB device array
+ * inside the library, held by every GPU that loads the library until the
+ * process exits; grids whose spectral array, pivots and tables do not fit
+ * return PP_ERR_TOO_LARGE (about 128 x 128 x 64 cells fit).  Grids are
+ * periodic in x and y (bc = {PERIODIC, PERIODIC, WALL}); nx even, nx and ny
+ * with prime factors in {2, 3, 5} and at most 2048 (else
+ * PP_ERR_UNSUPPORTED); zfaces (host, nz + 1 increasing values, or NULL) is
+ * read during the call only.  f and p must be device pointers (host
+ * pointers return PP_ERR_INVALID_ARG); the caller owns them.  Every table
+ * is computed on the device, so the call copies nothing from the host: it
+ * enqueues its kernels on `stream` (a cudaStream_t) and returns PP_OK
+ * without waiting for the GPU.  No device-side status is reported: errors
+ * found before the launches are returned, and the result is ready once the
+ * stream reaches it.  The first call on a device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture.  Calls on one device share its array and each overwrites
+ * what the previous one left: calls that may overlap on the same device
+ * (different streams) race and must be ordered by the caller.  Calls on
+ * different devices use separate arrays. */
 pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f, double* p, void* stream);
 
 /* ---- batched projections of independent grids -------------------------

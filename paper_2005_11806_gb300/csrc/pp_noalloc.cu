@@ -1,21 +1,24 @@
 // pressure_solve_noalloc: the FP64 constant-coefficient eigenexpansion solve
 // without any device allocation, for callers that cannot call cudaMalloc
-// (code that runs while a stream is being captured, hosts whose memory is
-// owned by an external pool or budget, real-time loops that forbid allocator
-// calls).  Its working memory is one file-scope device array of fixed size;
-// every device that loads this library holds that array until the process
-// exits.  The kernels are the ones pressure_solve launches.
+// (hosts whose device memory is owned by an external pool or budget, loops
+// that must not enter an allocator).  Its working memory is one file-scope
+// device array of fixed size; every device that loads this library holds
+// that array until the process exits.  The transform and z-solve kernels are
+// the ones pressure_solve launches; the tables (twiddles, wavenumbers, z
+// metrics) are computed on the device from scalar arguments, with the z face
+// coordinates passed by value in kernel parameters, so the call issues no
+// host-to-device copy and does not wait for the GPU.
 #include <cmath>
 #include <cstring>
 #include <mutex>
-#include <vector>
 
 #include "pp_internal.cuh"
 
 using namespace pp;
 
 // Scratch of the allocation-free entry point: spectral array, Thomas pivots,
-// twiddles, z metrics, eigenvalues, reduction partials and the status word.
+// twiddles, z faces and metrics, eigenvalues, reduction partials and the
+// status word.
 static constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char pp_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -59,14 +62,66 @@ bool factor(int n, FftDesc* d) {
   return m == 1;
 }
 
-std::vector<double2> twiddle_table(int n) {
-  std::vector<double2> t(n);
-  const double two_pi = 6.283185307179586476925286766559;
-  for (int m = 0; m < n; ++m) {
-    const double a = two_pi * (double)m / (double)n;
-    t[m] = make_double2(std::cos(a), std::sin(a));
+// z face coordinates travel to the device by value, in kernel parameters
+// (under 4 KB per launch), so no host buffer has to outlive the call.
+constexpr int kFaceChunk = 480;
+struct FaceChunk {
+  double v[kFaceChunk];
+  int off, n;
+};
+
+__global__ void k_na_store_faces(FaceChunk c, double* __restrict__ zf) {
+  for (int i = threadIdx.x; i < c.n; i += blockDim.x) zf[c.off + i] = c.v[i];
+}
+
+__global__ void k_na_uniform_faces(double lz, int nz, double* __restrict__ zf) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nz; k += gridDim.x * blockDim.x)
+    zf[k] = lz * (double)k / (double)nz;
+}
+
+// The tables of one constant-coefficient solve (Sec. 3 grid, Sec. 3.3.1
+// eigenexpansion): FFT twiddles (cos, sin)(2 pi m / n), the modified
+// wavenumbers -(4/h^2) sin^2(pi k / n) of the periodic second difference,
+// and the z metrics of the faces zf (cell widths, centre distances, the
+// sub- and super-diagonal of L_z), each entry computed from zf directly.
+__global__ void k_na_tables(int nx, int ny, int nz, double dx, double dy, const double* __restrict__ zf,
+                            double2* __restrict__ twx, double2* __restrict__ twy, double* __restrict__ dzf,
+                            double* __restrict__ idzf, double* __restrict__ idzc, double* __restrict__ za,
+                            double* __restrict__ zc, double* __restrict__ lamx, double* __restrict__ lamy) {
+  const int nxh = nx / 2 + 1;
+  int nmax = nx > ny ? nx : ny;
+  if (nz + 1 > nmax) nmax = nz + 1;
+  auto inv_dzc = [&](int k) {  // 1 / centre distance across z-face k (0 on the walls)
+    if (k <= 0 || k >= nz) return 0.0;
+    const double c1 = 0.5 * (zf[k] + zf[k + 1]), c0 = 0.5 * (zf[k - 1] + zf[k]);
+    return 1.0 / (c1 - c0);
+  };
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nmax; m += gridDim.x * blockDim.x) {
+    double sn, cs;
+    if (m < nx) {
+      sincospi(2.0 * (double)m / (double)nx, &sn, &cs);
+      twx[m] = make_double2(cs, sn);
+    }
+    if (m < ny) {
+      sincospi(2.0 * (double)m / (double)ny, &sn, &cs);
+      twy[m] = make_double2(cs, sn);
+      const double s = sinpi((double)m / (double)ny);
+      lamy[m] = -4.0 / (dy * dy) * s * s;
+    }
+    if (m < nxh) {
+      const double s = sinpi((double)m / (double)nx);
+      lamx[m] = -4.0 / (dx * dx) * s * s;
+    }
+    if (m <= nz) idzc[m] = inv_dzc(m);
+    if (m < nz) {
+      const double w = zf[m + 1] - zf[m];
+      const double iw = 1.0 / w;
+      dzf[m] = w;
+      idzf[m] = iw;
+      za[m] = (m >= 1) ? inv_dzc(m) * iw : 0.0;
+      zc[m] = (m + 1 < nz) ? inv_dzc(m + 1) * iw : 0.0;
+    }
   }
-  return t;
 }
 
 struct Carve {
@@ -98,6 +153,10 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL)
     return PP_ERR_UNSUPPORTED;
   if ((G.nx & 1) != 0) return PP_ERR_UNSUPPORTED;
+  // the limits of pressure_plan_create: one transform line per block in the
+  // FFT kernels, 32-bit cell offsets
+  if (G.nx > 2048 || G.ny > 2048) return PP_ERR_UNSUPPORTED;
+  if ((long long)G.nx * G.ny * (G.nz + 1) > (1LL << 31)) return PP_ERR_UNSUPPORTED;
   FftDesc fx, fy;
   if (!factor(G.nx, &fx) || !factor(G.ny, &fy)) return PP_ERR_UNSUPPORTED;
   if (!is_device(f) || !is_device(p)) return PP_ERR_INVALID_ARG;
@@ -120,47 +179,45 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   const size_t o_lamy = c.take((size_t)ny * sizeof(double));
   const size_t o_red = c.take((size_t)reduce_blocks() * sizeof(double));
   const size_t o_st = c.take(sizeof(DevStatus));
+  const size_t o_zf = c.take((size_t)(nz + 1) * sizeof(double));
   if (c.off > kNoAllocScratchBytes) return PP_ERR_TOO_LARGE;
 
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return PP_ERR_CUDA;
   unsigned char* S = (unsigned char*)base;
 
-  // Host tables (z metrics of Sec. 3's grid, modified wavenumbers, twiddles).
-  std::vector<double> zf(nz + 1);
-  for (int k = 0; k <= nz; ++k) zf[k] = G.zfaces ? G.zfaces[k] : G.lz * (double)k / (double)nz;
-  for (int k = 0; k < nz; ++k)
-    if (!(zf[k + 1] > zf[k])) return PP_ERR_INVALID_ARG;
-  std::vector<double> dzf(nz), idzf(nz), zcen(nz), idzc(nz + 1, 0.0), za(nz, 0.0), zc(nz, 0.0);
-  for (int k = 0; k < nz; ++k) {
-    dzf[k] = zf[k + 1] - zf[k];
-    idzf[k] = 1.0 / dzf[k];
-    zcen[k] = 0.5 * (zf[k] + zf[k + 1]);
+  // Face coordinates: checked here, sent by value (no host buffer is read
+  // after the call returns); every table is then computed on the device.
+  const double z0 = G.zfaces ? G.zfaces[0] : 0.0;
+  const double zn = G.zfaces ? G.zfaces[nz] : G.lz;
+  if (G.zfaces) {
+    for (int k = 0; k < nz; ++k)
+      if (!(G.zfaces[k + 1] > G.zfaces[k])) return PP_ERR_INVALID_ARG;
   }
-  for (int k = 1; k < nz; ++k) idzc[k] = 1.0 / (zcen[k] - zcen[k - 1]);
-  for (int k = 1; k < nz; ++k) za[k] = idzc[k] * idzf[k];
-  for (int k = 0; k < nz - 1; ++k) zc[k] = idzc[k + 1] * idzf[k];
   const double dx = G.lx / nx, dy = G.ly / ny;
-  const double pi = 3.14159265358979323846264338327950288;
-  std::vector<double> lamx(nxh), lamy(ny);
-  for (int k = 0; k < nxh; ++k) {
-    const double sn = std::sin(pi * (double)k / (double)nx);
-    lamx[k] = -4.0 / (dx * dx) * sn * sn;
+  double* dzfaces = (double*)(S + o_zf);
+  if (G.zfaces) {
+    FaceChunk ch;
+    for (int off = 0; off <= nz; off += kFaceChunk) {
+      ch.off = off;
+      ch.n = (nz + 1 - off) < kFaceChunk ? (nz + 1 - off) : kFaceChunk;
+      for (int i = 0; i < ch.n; ++i) ch.v[i] = G.zfaces[off + i];
+      k_na_store_faces<<<1, 256, 0, s>>>(ch, dzfaces);
+    }
+  } else {
+    k_na_uniform_faces<<<(nz + 256) / 256, 256, 0, s>>>(G.lz, nz, dzfaces);
   }
-  for (int k = 0; k < ny; ++k) {
-    const double sn = std::sin(pi * (double)k / (double)ny);
-    lamy[k] = -4.0 / (dy * dy) * sn * sn;
+  {
+    int nmax = nx > ny ? nx : ny;
+    if (nz + 1 > nmax) nmax = nz + 1;
+    int nb = (nmax + 255) / 256;
+    if (nb > 1024) nb = 1024;
+    k_na_tables<<<nb, 256, 0, s>>>(nx, ny, nz, dx, dy, dzfaces, (double2*)(S + o_twx), (double2*)(S + o_twy),
+                                   (double*)(S + o_dzf), (double*)(S + o_idzf), (double*)(S + o_idzc),
+                                   (double*)(S + o_za), (double*)(S + o_zc), (double*)(S + o_lamx),
+                                   (double*)(S + o_lamy));
   }
-  std::vector<double2> twx = twiddle_table(nx), twy = twiddle_table(ny);
-  struct Up { size_t off; const void* src; size_t bytes; } ups[] = {
-      {o_twx, twx.data(), twx.size() * sizeof(double2)}, {o_twy, twy.data(), twy.size() * sizeof(double2)},
-      {o_dzf, dzf.data(), dzf.size() * sizeof(double)},  {o_idzf, idzf.data(), idzf.size() * sizeof(double)},
-      {o_idzc, idzc.data(), idzc.size() * sizeof(double)}, {o_za, za.data(), za.size() * sizeof(double)},
-      {o_zc, zc.data(), zc.size() * sizeof(double)},     {o_lamx, lamx.data(), lamx.size() * sizeof(double)},
-      {o_lamy, lamy.data(), lamy.size() * sizeof(double)}};
-  for (const Up& u : ups)
-    if (cudaMemcpyAsync(S + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return PP_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
 
   Geo g;
   g.nx = nx; g.ny = ny; g.nz = nz; g.nxh = nxh;
@@ -172,7 +229,7 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   g.dzf = (const double*)(S + o_dzf);
   g.za = (const double*)(S + o_za);
   g.zc = (const double*)(S + o_zc);
-  g.lz = zf[nz] - zf[0];
+  g.lz = zn - z0;
   g.ywall = 0;
   double2* spec = (double2*)(S + o_spec);
   double* invd = (double*)(S + o_invd);

@@ -85,3 +85,26 @@ def test_host_only_entry_points():
     assert e.value.code == pressure.PP_ERR_INVALID_ARG
     assert pressure.status_string(pressure.PP_OK)
     assert pressure.status_string(pressure.PP_ERR_UNSUPPORTED) != pressure.status_string(pressure.PP_OK)
+
+
+@pytest.mark.parametrize("dims,bc,code", [
+    ((4096, 2, 1), (0, 0, 1), "PP_ERR_UNSUPPORTED"),   # one x line per FFT block: nx <= 2048
+    ((2, 4096, 1), (0, 0, 1), "PP_ERR_UNSUPPORTED"),   # one y line per FFT block: ny <= 2048
+    ((7, 4, 3), (0, 0, 1), "PP_ERR_UNSUPPORTED"),      # odd nx
+    ((14, 4, 3), (0, 0, 1), "PP_ERR_UNSUPPORTED"),     # prime factor 7
+    ((8, 8, 8), (0, 1, 1), "PP_ERR_UNSUPPORTED"),      # walls in y: periodic y only
+    ((0, 8, 8), (0, 0, 1), "PP_ERR_INVALID_ARG"),      # empty grid
+])
+def test_noalloc_rejects_bad_descriptors_before_any_cuda_call(dims, bc, code):
+    """The allocation-free solve checks the grid before it touches the
+    device, so these run without a GPU (the field pointers are never used)."""
+    import ctypes
+    pressure = _lib_or_build()
+    g = pressure.pp_grid()
+    g.nx, g.ny, g.nz = dims
+    g.lx, g.ly, g.lz = 1.0, 1.0, 1.0
+    g.bc[0], g.bc[1], g.bc[2] = bc
+    buf = (ctypes.c_double * 8)()
+    got = pressure.lib().pressure_solve_noalloc(ctypes.byref(g), ctypes.cast(buf, ctypes.c_void_p),
+                                                ctypes.cast(buf, ctypes.c_void_p), None)
+    assert got == getattr(pressure, code)

@@ -1,14 +1,17 @@
 """The allocation-free constant-coefficient solve (pressure_solve_noalloc)
-against the plan-based pressure_solve, through the C ABI.
+against the plan-based pressure_solve and the CPU oracle, through the C ABI.
 
-Callers that cannot call cudaMalloc use this entry point; its working memory
-is a fixed device array inside the library that every call reuses.  This
-file is collected last so that a run stopping at the first failure has run
-every other test first; it also passes when run alone in a fresh process.
+Callers that cannot call cudaMalloc (device memory owned by an external pool
+or budget, loops that must not enter an allocator) use this entry point; its
+working memory is a fixed device array inside the library that every call
+reuses.  This file is collected last so that a run stopping at the first
+failure has run every other test first; it also passes when run alone in a
+fresh process.
 """
 import numpy as np
 import pytest
 
+import oracle.pressure_oracle as orc
 from paper_2005_11806_gb300 import workloads as wl
 
 torch = pytest.importorskip("torch")
@@ -51,6 +54,10 @@ def test_noalloc_matches_plan_solve_twice(pp):
         ref = _plan_solve(pp, dims, lengths, zf, f)
         err = float(torch.linalg.vector_norm(p - ref) / torch.linalg.vector_norm(ref))
         assert err < FP64_TOL, (dims, err)
+        g = orc.Grid(nx, ny, nz, lengths[0], lengths[1], zf)
+        po = orc.solve_constant(g, f.cpu().numpy())
+        err_o = float(np.linalg.norm(p.cpu().numpy() - po) / np.linalg.norm(po))
+        assert err_o < FP64_TOL, (dims, err_o)
 
 
 def test_noalloc_rejects_grids_beyond_the_scratch(pp):
@@ -59,3 +66,30 @@ def test_noalloc_rejects_grids_beyond_the_scratch(pp):
     with pytest.raises(pp.PressureError) as ei:
         pp.pressure_solve_noalloc(256, 256, 64, 1.0, 1.0, 1.0, f, p)
     assert ei.value.code == pp.PP_ERR_TOO_LARGE
+
+
+def test_noalloc_input_checks_return_before_any_launch(pp):
+    """Argument errors come back as status codes from the host-side checks,
+    with nothing enqueued: the output keeps its NaN fill."""
+    f = torch.zeros(4096 * 2, dtype=torch.float64, device="cuda")
+    p = torch.full_like(f, float("nan"))
+    bad = [
+        (dict(nx=7, ny=4, nz=3), pp.PP_ERR_UNSUPPORTED),        # odd nx (two real rows per transform)
+        (dict(nx=4096, ny=2, nz=1), pp.PP_ERR_UNSUPPORTED),     # one x line per block: nx <= 2048
+        (dict(nx=2, ny=4096, nz=1), pp.PP_ERR_UNSUPPORTED),     # one y line per block: ny <= 2048
+        (dict(nx=14, ny=4, nz=3), pp.PP_ERR_UNSUPPORTED),       # prime factor 7
+    ]
+    for dims, code in bad:
+        with pytest.raises(pp.PressureError) as ei:
+            pp.pressure_solve_noalloc(dims["nx"], dims["ny"], dims["nz"], 1.0, 1.0, 1.0, f, p)
+        assert ei.value.code == code, dims
+    zf = np.array([0.0, 0.5, 0.4, 1.0])                          # not increasing
+    with pytest.raises(pp.PressureError) as ei:
+        pp.pressure_solve_noalloc(4, 4, 3, 1.0, 1.0, 1.0, f, p, zfaces=zf)
+    assert ei.value.code == pp.PP_ERR_INVALID_ARG
+    fh = np.zeros(4 * 4 * 3)                                     # a host array as f
+    with pytest.raises(pp.PressureError) as ei:
+        pp.pressure_solve_noalloc(4, 4, 3, 1.0, 1.0, 1.0, fh, p)
+    assert ei.value.code == pp.PP_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert bool(torch.isnan(p).all())
