@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_tc", "mixed_z64"])
+    ap.add_argument("--precision", default="mixed_z64", choices=["mixed_z64", "mixed", "fp64", "mixed_tc"],
+                    help="mixed_z64 (default): FP32 transforms, FP64 residual and FP64 z recurrences in every "
+                         "column; mixed: the hybrid z solve (FP32 on well-conditioned columns)")
     ap.add_argument("--method", default="III", choices=["III", "II", "I"],
                     help="iteration of Sec. 3.3.1 (Method III is the measured one; I and II compare)")
     ap.add_argument("--n", type=int, default=512)
@@ -74,6 +76,12 @@ def parse():
                     help="skip timing the passes of a plan with walls in y (cosine y transform)")
     ap.add_argument("--no-zcosine", action="store_true",
                     help="skip timing the cosine z solve against the tridiagonal one (FP64, uniform z)")
+    ap.add_argument("--no-hybrid", action="store_true",
+                    help="skip the leg that times the hybrid-z mixed plan beside the headline")
+    ap.add_argument("--no-sphere256", action="store_true",
+                    help="skip the 256^3 gas-sphere projections (FP64 and the headline plan)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 96-grid batch line timed after the headline")
     ap.add_argument("--workload", default="bubbles512", choices=["bubbles512", "batch96"],
                     help="bubbles512: the 512^3 projection (default); batch96: 96 grids of mixed sizes "
                          "solved in one graph launch")
@@ -156,9 +164,14 @@ def algorithmic(kernel, w, precision):
     if kernel == "tridiag_z":
         if precision == "mixed_tc":
             return {"bytes": 2 * cs * nsp, "fp64_flops": 0, "tensor_flops": 3 * 2 * 2 * w.nz * 2 * nsp}
-        if precision in ("fp64", "mixed_z64"):
+        if precision == "fp64":
             # f in, forward values out and back in, x out; multipliers and inverse pivots (FP64)
             return {"bytes": (4 * cs + 16) * nsp, "fp64_flops": 6 * nsp}
+        if precision == "mixed_z64":
+            # FP32 spectrum: f in, s out and back in, x out; tables m, e (FP64) and 1/d (FP32) on
+            # (ny/2 + 1) nxh columns (ky and ny - ky share one); one FP64 FMA per scalar per sweep
+            ntab = (w.nx // 2 + 1) * (w.ny // 2 + 1) * w.nz
+            return {"bytes": 4 * cs * nsp + 20 * ntab, "fp64_flops": 2 * 4 * nsp}
         # same traffic with FP32 values and FP32 tables (well-conditioned columns)
         return {"bytes": (4 * cs + 8) * nsp, "fp64_flops": 0}
     if kernel == "fftx_inv_update":
@@ -270,7 +283,7 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": name,
                 "avg_launch_ms": round(avg_s * 1e3, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    if name == "resid_fftx" and args.precision == "mixed":
+    if name == "resid_fftx" and args.precision in ("mixed", "mixed_z64"):
         per_cell = 0.975 * RESID_DRAM_B_PER_CELL["update"] + 0.025 * RESID_DRAM_B_PER_CELL["exact"]
         roof["traffic"] = int(per_cell * npts)
         roof["traffic_source"] = "ncu DRAM bytes per cell at 512x512x128, scaled to the launch's cells"
@@ -290,7 +303,7 @@ def run_ours(args, rank, world, local_rank):
            "input_gen_s": round(gen_s, 1)}
 
     # FP64 comparison leg (same input, same tolerance)
-    if not args.no_compare and args.precision == "mixed":
+    if not args.no_compare and args.precision in ("mixed", "mixed_z64"):
         plan.close()
         plan64 = make_plan("fp64")
         ms64, infos64, kern64, _, clocks64 = timed(plan64, args.compare_steps, 1, True)
@@ -300,6 +313,21 @@ def run_ours(args, rank, world, local_rank):
                        "kernels": {k: {"launches": n, "total_ms": round(t, 3)} for k, (n, t) in kern64.items()}}
         out["speedup_mixed_vs_fp64"] = round(ms64 / ms, 3)
         plan64.close()
+        plan = make_plan(args.precision)
+
+    # the hybrid z solve (FP32 recurrences on the well-conditioned columns,
+    # FP64 on the rest) beside the headline plan: same input and tolerance
+    if not args.no_hybrid and args.precision == "mixed_z64":
+        plan.close()
+        planh = make_plan("mixed")
+        msh, infosh, kernh, _, clocksh = timed(planh, args.compare_steps, 1, True)
+        out["mixed_hybrid_z"] = {
+            "value": round(whole_job_gpts(npts, world, msh), 5), "ms_per_step": round(msh, 3),
+            "iterations": infosh[-1]["iters"], "res_final": infosh[-1]["res_final"],
+            "steps": args.compare_steps, "warmup": 1, "clocks": clocksh,
+            "tridiag_z_avg_ms": round(kernh["tridiag_z"][1] / kernh["tridiag_z"][0], 4),
+            "note": "PP_MIXED_FP32: z recurrences in FP32 on columns of condition number <= 513, FP64 on the others"}
+        planh.close()
         plan = make_plan(args.precision)
 
     # the divergence source from the thermodynamics (Eqs. 30, 34) on the same
@@ -452,6 +480,41 @@ def run_ours(args, rank, world, local_rank):
         out["zcosine"] = zc_out
         plan = make_plan(args.precision)
 
+    # the gas sphere at 256^3 (the smaller variable-density configuration):
+    # FP64 and the headline plan to the same tolerance; its FP64 pass count
+    # also scales the oracle's timed pass there
+    if not args.no_sphere256:
+        from paper_2005_11806_gb300 import workloads as wl
+        plan.close()
+        w2 = wl.single_sphere_case(n=256)
+        T2 = {k: T(getattr(w2, k)) for k in ("us", "vs", "ws", "phi", "S")}
+        r2 = torch.empty(w2.shape, dtype=torch.float64, device=dev)
+        p2, u2, v2 = torch.empty_like(r2), torch.empty_like(r2), torch.empty_like(r2)
+        ww2 = torch.empty((w2.nz + 1, w2.ny, w2.nx), dtype=torch.float64, device=dev)
+        n2 = w2.nx * w2.ny * w2.nz
+        out["sphere256"] = {"workload": w2.name + ", uniform z, Method III to rel. residual <= %g" % args.rtol}
+        for prec in ("fp64", args.precision):
+            pl = pp.Plan(w2.nx, w2.ny, w2.nz, w2.lx, w2.ly, float(w2.zf[-1]), zfaces=w2.zf, precision=prec,
+                         method=args.method)
+
+            def s2():
+                pp.pressure_mixture_density(pl.handle, T2["phi"], w2.rho_g, w2.rho_l, r2)
+                return pp.pressure_correct(pl.handle, T2["us"], T2["vs"], T2["ws"], r2, T2["S"], w2.dt, p2, u2, v2,
+                                           ww2, rtol=args.rtol, maxit=args.maxit, allow_not_converged=True)
+            s2()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            i2 = s2()
+            e1.record()
+            torch.cuda.synchronize()
+            t2 = e0.elapsed_time(e1)
+            out["sphere256"][prec] = {"value": round(n2 / (t2 / 1e3) / 1e9, 5), "unit": "Gpts/s",
+                                      "ms": round(t2, 3), "iterations": i2["iters"], "res_final": i2["res_final"]}
+            pl.close()
+        del T2, r2, p2, u2, v2, ww2
+        plan = make_plan(args.precision)
+
     # end to end through the C ABI with host (pinned) buffers
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
@@ -478,10 +541,15 @@ def run_ours(args, rank, world, local_rank):
                       "h2d_bytes_per_step": 5 * nc + nw, "d2h_bytes_per_step": 4 * nc + nw,
                       "steps": 1, "warmup": 1}
     plan.close()
+    if not args.no_batch:
+        b = run_batch(args, rank, world, local_rank, steps=1, warmup=1)
+        out["batch96"] = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "warmup",
+                                            "iterations", "all_converged", "worst_res_final", "config",
+                                            "clocks", "create_s")}
     return out, w
 
 
-def run_batch(args, rank, world, local_rank):
+def run_batch(args, rank, world, local_rank, steps=None, warmup=None):
     """96 independent projections of mixed sizes (N in {64, 96, 128, 160, 192},
     z aspect U[1, 2], one droplet each, ratio 1000:1) in one graph launch per
     step, mixed precision, each grid to rel. residual <= rtol."""
@@ -511,7 +579,9 @@ def run_batch(args, rank, world, local_rank):
         B.mixture_density(phi, cases[0].rho_g, cases[0].rho_l, rho)  # Eq. 22, one launch over all grids
         return B.correct(us, vs, ws, rho, S, cases[0].dt, p, u, v, w, rtol=args.rtol, maxit=args.maxit,
                          allow_not_converged=True)
-    for _ in range(args.warmup):
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    for _ in range(warmup):
         step()
     if world > 1:
         torch.distributed.barrier()
@@ -519,16 +589,16 @@ def run_batch(args, rank, world, local_rank):
     sampler = ClockSampler(local_rank)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         infos = step()
     e1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, torch.device("cuda", local_rank))
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, torch.device("cuda", local_rank))
     its = [i["iters"] for i in infos]
     out = {"metric": "batched pressure-solve Gpts/s: 96 mixed-size grids, rel. residual <=1e-10",
            "value": round(whole_job_gpts(B.ncell, world, ms), 5), "unit": "Gpts/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+           "steps": steps, "warmup": warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
            "config": {"workload": "96 grids N in {64,96,128,160,192}, z aspect U[1,2], one droplet each, "
                                   f"ratio {args.ratio:g}:1, random-divergence u*, one graph launch per step",
@@ -546,10 +616,9 @@ def run_batch(args, rank, world, local_rank):
 def cpu_baseline(w, iters, passes=1, iters_source="the GPU run's pass count"):
     """The oracle as it stands, timed on this host: `passes` Method III
     passes on the full workload, scaled to one projection of `iters` passes.
-    `cores` is the CPU time over the wall time of the sample (numpy's own
-    threads), capped at the host's thread count."""
-    import numpy as np
-
+    The oracle's FFTs run on all host threads (scipy.fft workers); `cores`
+    is that thread count and `cpu_utilisation` the CPU time over the wall
+    time of the sample (the rest of the oracle is single-threaded numpy)."""
     import oracle.pressure_oracle as orc
     rho = orc.mixture_density(w.phi, w.rho_g, w.rho_l)
     g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf)
@@ -561,10 +630,58 @@ def cpu_baseline(w, iters, passes=1, iters_source="the GPU run's pass count"):
     npts = w.nx * w.ny * w.nz
     per_pass = wall / passes
     return {"value": npts / (per_pass * max(iters, 1)) / 1e9, "unit": "Gpts/s",
-            "cores": max(1, min(os.cpu_count() or 1, int(round(cpu / wall)))), "kind": "oracle",
+            "cores": int(orc.WORKERS), "kind": "oracle",
             "sample": f"{passes} of {iters} Method III passes ({iters_source}) of the same "
                       f"{w.nx}x{w.ny}x{w.nz} workload ({per_pass:.3g} s per pass), scaled to the full projection",
+            "cpu_utilisation": round(cpu / wall, 2),
             "host_threads_available": os.cpu_count(), "seconds_per_pass": round(per_pass, 2)}
+
+
+def oracle_configs(iters_sphere256):
+    """The oracle on the smaller configurations (host cores, FFTs on every
+    thread): the 32^3 random-divergence case (rho = 1: one constant solve is
+    the whole projection), the gas sphere at 32^3 run to rel. residual 1e-10,
+    and the gas sphere at 256^3: one constant solve and one Method III pass,
+    the projection extrapolated by the pass count the GPU's FP64 plan needs
+    (its iterates equal the oracle's)."""
+    import numpy as np
+
+    import oracle.pressure_oracle as orc
+    from paper_2005_11806_gb300 import workloads as wl
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        r = fn()
+        return time.perf_counter() - t0, r
+
+    out = {}
+    w = wl.random_divergence_case(n=32)
+    g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf)
+    f = orc.divergence(g, w.us, w.vs, w.ws) / w.dt
+    t_solve, _ = timed(lambda: orc.solve_constant(g, f))
+    t_proj, r = timed(lambda: orc.method3(g, w.us, w.vs, w.ws, np.ones(g.shape), w.S, w.dt, rtol=1e-10))
+    n = 32 ** 3
+    out["random_divergence_32"] = {"solve_s": round(t_solve, 5), "solve_gpts": n / t_solve / 1e9,
+                                   "projection_s": round(t_proj, 5), "projection_gpts": n / t_proj / 1e9,
+                                   "passes": r[4]["iters"]}
+    w = wl.single_sphere_case(n=32)
+    g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf)
+    rho = orc.mixture_density(w.phi, w.rho_g, w.rho_l)
+    t_proj, r = timed(lambda: orc.method3(g, w.us, w.vs, w.ws, rho, w.S, w.dt, rtol=1e-10, maxit=5000))
+    out["sphere_32"] = {"projection_s": round(t_proj, 3), "projection_gpts": n / t_proj / 1e9,
+                        "passes": r[4]["iters"], "res_final": r[4]["res_hist"][-1]}
+    w = wl.single_sphere_case(n=256)
+    g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf)
+    rho = orc.mixture_density(w.phi, w.rho_g, w.rho_l)
+    f = orc.divergence(g, w.us, w.vs, w.ws) / w.dt
+    t_solve, _ = timed(lambda: orc.solve_constant(g, f))
+    t_pass, _ = timed(lambda: orc.method3(g, w.us, w.vs, w.ws, rho, w.S, w.dt, rtol=0.0, maxit=1))
+    n = 256 ** 3
+    out["sphere_256"] = {"solve_s": round(t_solve, 3), "solve_gpts": n / t_solve / 1e9,
+                         "pass_s": round(t_pass, 3), "passes": iters_sphere256,
+                         "projection_gpts_extrapolated": n / (t_pass * max(iters_sphere256, 1)) / 1e9}
+    out["threads"] = int(orc.WORKERS)
+    return out
 
 
 def main():
@@ -610,6 +727,8 @@ def main():
     out, w = run_ours(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, out["iterations"])
+        if "sphere256" in out:
+            out["cpu_baseline"]["configs"] = oracle_configs(out["sphere256"]["fp64"]["iterations"])
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -114,8 +114,8 @@ typedef struct {
                               difference, cos(pi m (j + 1/2) / ny), eigenvalues
                               -(4/dy^2) sin^2(pi m / (2 ny)), computed by one complex FFT
                               of length ny; pressure_solve, pressure_correct (Methods I, II
-                              and III) and pressure_mixture_density take them, the adjoint,
-                              the thermodynamic source and the predictor return
+                              and III), pressure_solve_adjoint and pressure_mixture_density
+                              take them, the thermodynamic source and the predictor return
                               PP_ERR_UNSUPPORTED, and the batched and no-allocation entry
                               points take periodic y only */
 } pp_grid;
@@ -246,8 +246,9 @@ pp_status pressure_correct(pp_plan plan, const double* us, const double* vs, con
  * the fixed point of Algorithm 1).  In: rho, p (the converged pressure of
  * the forward call with the same rho and dt), gu, gv, gw = dL/du^{n+1}.
  * Out: gus, gvs, gws = dL/du*, grho = dL/drho (cell field).  The transposed
- * system is solved by the same Method III loop.  Wall entries of gw are
- * ignored and those of gws are written as zero. */
+ * system is solved by the same Method III loop.  Wall entries of gw (and,
+ * with walls in y, the wall row j = 0 of gv) are ignored and those of gws
+ * (and of gvs) are written as zero: they are not unknowns. */
 pp_status pressure_solve_adjoint(pp_plan plan, const double* rho, const double* p, double dt,
                                  const double* gu, const double* gv, const double* gw,
                                  double* gus, double* gvs, double* gws, double* grho,

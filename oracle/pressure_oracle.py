@@ -502,6 +502,15 @@ def _zero_walls(gw):
     return gw
 
 
+def _zero_ywall_row(g, gv):
+    """With y walls the wall row of v (row 0, both walls) is not an unknown
+    either: its gradient is defined as zero, like the wall planes of w."""
+    gv = np.array(gv, dtype=np.float64, copy=True)
+    if g.ywalls:
+        gv[:, 0, :] = 0.0
+    return gv
+
+
 def _bordered_solve_transposed(g, A, rhs):
     """Solve A^T x = rhs with sum(x) = 0.  A^T has the volume vector as null
     vector and the constant vector as left null vector, so a compatible rhs
@@ -533,20 +542,20 @@ def adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv, gw):
     """Gradients of L(u^{n+1}) w.r.t. u* and rho_c by implicit
     differentiation of the plain definition (``projection_direct``), with
     literal sparse transposes.  Small grids only.  Returns
-    ``(g_us, g_vs, g_ws, g_rho)``; wall entries of ``g_ws`` are zero."""
-    if g.ywalls:
-        raise NotImplementedError("adjoint_direct: periodic y only")
+    ``(g_us, g_vs, g_ws, g_rho)``; wall entries of ``g_ws`` (and, with y
+    walls, the wall row of ``g_vs``) are zero."""
     D, G = _sparse_operators(g)
     beta = _beta_vector(g, rho)
     A = (D @ sp.diags(beta) @ G).tocsr()
     Sc = S - volume_mean(g, S)
     rhs = (D @ _face_vector(us, vs, ws) - Sc.ravel()) / dt
     p = _bordered_solve(g, A, rhs)
-    gvec = _face_vector(gu, gv, _zero_walls(gw))
+    gvec = _face_vector(gu, _zero_ywall_row(g, gv), _zero_walls(gw))
     lam = _bordered_solve_transposed(g, A, G.T @ (beta * gvec))
     gus = gvec - D.T @ lam
     u, v, w = _split_faces(g, gus)
     w = _zero_walls(w)
+    v = _zero_ywall_row(g, v)
     gus = _face_vector(u, v, w)
     grho = _beta_to_rho(g, beta, -dt * (G @ p) * gus)
     return u, v, w, grho
@@ -565,9 +574,8 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
     ``p`` is the converged pressure of the forward projection (computed
     here with the same tolerance when not given).
     """
-    if g.ywalls:
-        raise NotImplementedError("adjoint_method3: periodic y only")
     gw = _zero_walls(gw)
+    gv = _zero_ywall_row(g, gv)
     rx, ry, rz = face_density(g, rho)
     wlay = g.dzf[:, None, None]
     wz = np.ones(g.nz + 1)
@@ -580,6 +588,7 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
     gx, gy, gz = gradient(g, mu)
     gus, gvs, gws = gu + wlay * gx, gv + wlay * gy, gw + wz * gz
     gws = _zero_walls(gws)
+    gvs = _zero_ywall_row(g, gvs)
     info_fwd = None
     if p is None:
         p, _, _, _, info_fwd = method3(g, us, vs, ws, rho, S, dt, rtol=rtol, maxit=maxit)

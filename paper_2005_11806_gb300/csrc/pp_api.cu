@@ -47,6 +47,7 @@ struct pp_plan_s {
   double *d_inv_dzf = nullptr, *d_inv_dzc = nullptr, *d_dzf = nullptr, *d_za = nullptr, *d_zc = nullptr;
   double *d_lamx = nullptr, *d_lamy = nullptr, *d_invd = nullptr, *d_mtab = nullptr;
   float* d_inv_dzf_f = nullptr;
+  float* d_cw_f = nullptr;  // [3][nz + 1] FP32 layer factors of the face coefficients
   void *d_twx = nullptr, *d_twy = nullptr;
   void* d_dcty = nullptr;  // walls in y: exp(-i pi m / (2 ny)), m < ny (C2 of the plan's FFT type)
   // z solve by the cosine basis (uniform z, FP64 plans; pressure_plan_set_zsolve)
@@ -73,6 +74,11 @@ struct pp_plan_s {
   int* d_low = nullptr;
   TriF32 tri32{};
   bool use_tri32 = false;
+  // PP_MIXED_Z64: tables of the FP64-recurrence z solve (TriZ64)
+  double *d_z64m = nullptr, *d_z64e = nullptr;
+  float* d_z64d = nullptr;
+  TriZ64 z64{};
+  bool use_z64 = false;
   double* d_rho_tilde = nullptr;
   double* d_delta64 = nullptr;
   double* d_thermo = nullptr;  // [4] sums and rate of Eq. 30
@@ -271,6 +277,8 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr, fl
     } else {
       return PP_ERR_UNSUPPORTED;
     }
+  } else if (std::is_same<T, float>::value && P->use_z64) {
+    PP_K(P, K_TRI, launch_tridiag_z64(g, P->z64, reinterpret_cast<float2*>(spec), P->d_st, P->stream));
   } else {
     PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab,
                                      P->use_tri32 ? &P->tri32 : nullptr));
@@ -378,8 +386,10 @@ void free_plan(pp_plan_s* P) {
                      P->faces.diag, P->d_rho_tilde, P->d_delta64, P->d_thermo};
   if (P->faces.rhof) cudaFree(P->faces.rhof);
   if (P->d_low) cudaFree(P->d_low);
-  float* fptrs[] = {P->faces.cxf, P->faces.cyf, P->faces.czf, P->faces.diagf, P->d_delta, P->d_sdelta,
-                    P->d_mtab_f, P->d_invd_f, P->d_zc_f};
+  float* fptrs[] = {P->faces.diagf, P->d_delta, P->d_sdelta, P->d_mtab_f, P->d_invd_f, P->d_zc_f,
+                    P->d_z64d, P->d_cw_f};
+  if (P->d_z64m) cudaFree(P->d_z64m);
+  if (P->d_z64e) cudaFree(P->d_z64e);
   for (float* f : fptrs) if (f) cudaFree(f);
   if (P->d_E) cudaFree(P->d_E);
   if (P->d_mu) cudaFree(P->d_mu);
@@ -554,9 +564,6 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       (prec != PP_FP64 && (st = dalloc(&P->d_E, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->d_delta, nc * sizeof(float))) != PP_OK) ||
       (prec != PP_FP64 && (st = dalloc(&P->d_sdelta, nc * sizeof(float))) != PP_OK) ||
-      (prec != PP_FP64 && (st = dalloc(&P->faces.cxf, nc * sizeof(float))) != PP_OK) ||
-      (prec != PP_FP64 && (st = dalloc(&P->faces.cyf, nc * sizeof(float))) != PP_OK) ||
-      (prec != PP_FP64 && (st = dalloc(&P->faces.czf, nw * sizeof(float))) != PP_OK) ||
       (st = dalloc(&P->d_b, nc * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->d_red, P->red_len * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->faces.cx, nc * sizeof(double))) != PP_OK ||
@@ -565,6 +572,7 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       (st = dalloc(&P->faces.diag, nc * sizeof(double))) != PP_OK ||
       (st = dalloc(&P->faces.rhof, nc * sizeof(float))) != PP_OK ||
       (st = dalloc(&P->d_inv_dzf_f, (size_t)nz * sizeof(float))) != PP_OK ||
+      (st = dalloc(&P->d_cw_f, 3 * (size_t)(nz + 1) * sizeof(float))) != PP_OK ||
       (st = dalloc(&P->d_st, sizeof(DevStatus))) != PP_OK ||
       (st = dalloc(&P->d_thermo, 4 * sizeof(double))) != PP_OK) {
     free_plan(P);
@@ -579,7 +587,9 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   {
     std::vector<float> f32(nz);
     for (int k = 0; k < nz; ++k) f32[k] = (float)inv_dzf[k];
-    if (cudaMemcpy(P->d_inv_dzf_f, f32.data(), nz * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+    const std::vector<float> cw = layer_factors_f32(nz, dzf, inv_dzc, 1.0 / (P->dx * P->dx), 1.0 / (P->dy * P->dy));
+    if (cudaMemcpy(P->d_inv_dzf_f, f32.data(), nz * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P->d_cw_f, cw.data(), cw.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
       free_plan(P);
       return PP_ERR_CUDA;
     }
@@ -587,6 +597,7 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   Geo& g = P->geo;
   g.nx = G.nx; g.ny = G.ny; g.nz = nz; g.nxh = P->nxh;
   g.inv_dzf_f = P->d_inv_dzf_f;
+  g.cw_f = P->d_cw_f;
   g.dx = P->dx; g.dy = P->dy;
   g.inv_dx2 = 1.0 / (P->dx * P->dx);
   g.inv_dy2 = 1.0 / (P->dy * P->dy);
@@ -653,6 +664,27 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
     P->tri32.low = P->d_low;
     P->tri32.nlow = (int)low.size();
     P->use_tri32 = true;
+  }
+  if (prec == PP_MIXED_Z64) {
+    // periodic y: lambda_y(ky) = lambda_y(ny - ky), one table column for both
+    const int ysym = ywall ? 0 : 1;
+    const int nyt = ysym ? G.ny / 2 + 1 : G.ny;
+    const size_t ntab = (size_t)nz * nyt * P->nxh;
+    if ((st = dalloc(&P->d_z64m, ntab * sizeof(double))) != PP_OK ||
+        (st = dalloc(&P->d_z64e, ntab * sizeof(double))) != PP_OK ||
+        (st = dalloc(&P->d_z64d, ntab * sizeof(float))) != PP_OK ||
+        launch_setup_z64(g, P->d_lamx, P->d_lamy, nyt, ysym, P->d_z64m, P->d_z64e, P->d_z64d, P->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess) {
+      free_plan(P);
+      return st != PP_OK ? st : PP_ERR_CUDA;
+    }
+    P->z64.m = P->d_z64m;
+    P->z64.e = P->d_z64e;
+    P->z64.d = P->d_z64d;
+    P->z64.nyt = nyt;
+    P->z64.ysym = ysym;
+    P->use_z64 = true;
   }
   *out = P;
   return PP_OK;
@@ -893,7 +925,6 @@ pp_status pressure_solve_adjoint(pp_plan P, const double* rho, const double* p, 
                                  pp_info* info) {
   if (check_plan(P) != PP_OK || !rho || !p || !gu || !gv || !gw || !gus || !gvs || !gws || !grho)
     return PP_ERR_INVALID_ARG;
-  if (P->geo.ywall) return PP_ERR_UNSUPPORTED;
   if (!(dt > 0.0) || !(rtol >= 0.0) || maxit < 0) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P), nw = nwface(P);
   pp_status s;

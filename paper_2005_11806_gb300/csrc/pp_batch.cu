@@ -477,8 +477,8 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
 
   // pool layout: per grid, every buffer and table
   struct Off {
-    size_t spec, E, delta, sdelta, b, red, st, cx, cy, cz, diag, rhof, cxf, cyf, czf, invd, mtab,
-        twx, twy, idzf, idzc, dzf, za, zc, idzff, lamx, lamy, mtabf, invdf, zcf;
+    size_t spec, E, delta, sdelta, b, red, st, cx, cy, cz, diag, rhof, invd, mtab,
+        twx, twy, idzf, idzc, dzf, za, zc, idzff, cwf, lamx, lamy, mtabf, invdf, zcf;
   };
   std::vector<Off> off(ngrids);
   Carve cv;
@@ -500,11 +500,12 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     o.sdelta = cv.take(nc * 4);
     o.b = cv.take(nc * 8); o.red = cv.take(nred * 8); o.st = cv.take(sizeof(DevStatus));
     o.cx = cv.take(nc * 8); o.cy = cv.take(nc * 8); o.cz = cv.take(nw * 8); o.diag = cv.take(nc * 8);
-    o.rhof = cv.take(nc * 4); o.cxf = cv.take(nc * 4); o.cyf = cv.take(nc * 4); o.czf = cv.take(nw * 4);
+    o.rhof = cv.take(nc * 4);
     o.invd = cv.take(nsp * 8); o.mtab = cv.take(nsp * 8);
     o.twx = cv.take((size_t)G.nx * sizeof(float2)); o.twy = cv.take((size_t)G.ny * sizeof(float2));
     o.idzf = cv.take((size_t)G.nz * 8); o.idzc = cv.take((size_t)(G.nz + 1) * 8); o.dzf = cv.take((size_t)G.nz * 8);
     o.za = cv.take((size_t)G.nz * 8); o.zc = cv.take((size_t)G.nz * 8); o.idzff = cv.take((size_t)G.nz * 4);
+    o.cwf = cv.take(3 * (size_t)(G.nz + 1) * 4);
     o.lamx = cv.take((size_t)(G.nx / 2 + 1) * 8); o.lamy = cv.take((size_t)G.ny * 8);
     o.mtabf = cv.take(nsp * 4); o.invdf = cv.take(nsp * 4); o.zcf = cv.take((size_t)G.nz * 4);
   }
@@ -543,6 +544,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     std::vector<double> lamx(nxh), lamy(ny);
     for (int k = 0; k < nxh; ++k) { const double sn = std::sin(pi * k / nx); lamx[k] = -4.0 / (dx * dx) * sn * sn; }
     for (int k = 0; k < ny; ++k) { const double sn = std::sin(pi * k / ny); lamy[k] = -4.0 / (dy * dy) * sn * sn; }
+    const std::vector<float> cwf = layer_factors_f32(nz, dzf, idzc, 1.0 / (dx * dx), 1.0 / (dy * dy));
     std::vector<float2> twx(nx), twy(ny);
     for (int m = 0; m < nx; ++m) twx[m] = make_float2((float)std::cos(two_pi * m / nx), (float)std::sin(two_pi * m / nx));
     for (int m = 0; m < ny; ++m) twy[m] = make_float2((float)std::cos(two_pi * m / ny), (float)std::sin(two_pi * m / ny));
@@ -551,7 +553,8 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
         {o.dzf, dzf.data(), dzf.size() * 8}, {o.idzf, idzf.data(), idzf.size() * 8},
         {o.idzc, idzc.data(), idzc.size() * 8}, {o.za, za.data(), za.size() * 8}, {o.zc, zc.data(), zc.size() * 8},
         {o.idzff, idzff.data(), idzff.size() * 4}, {o.lamx, lamx.data(), lamx.size() * 8},
-        {o.lamy, lamy.data(), lamy.size() * 8}, {o.zcf, zcf.data(), zcf.size() * 4}};
+        {o.lamy, lamy.data(), lamy.size() * 8}, {o.zcf, zcf.data(), zcf.size() * 4},
+        {o.cwf, cwf.data(), cwf.size() * 4}};
     for (const Up& u : ups)
       if (cudaMemcpy(P + u.off, u.src, u.bytes, cudaMemcpyHostToDevice) != cudaSuccess) { free_batch(B); return PP_ERR_CUDA; }
     Geo& g = d.g;
@@ -559,11 +562,10 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     g.inv_dx2 = 1.0 / (dx * dx); g.inv_dy2 = 1.0 / (dy * dy);
     g.inv_dzf = (const double*)(P + o.idzf); g.inv_dzc = (const double*)(P + o.idzc);
     g.dzf = (const double*)(P + o.dzf); g.za = (const double*)(P + o.za); g.zc = (const double*)(P + o.zc);
-    g.inv_dzf_f = (const float*)(P + o.idzff); g.lz = zf[nz] - zf[0];
+    g.inv_dzf_f = (const float*)(P + o.idzff); g.cw_f = (const float*)(P + o.cwf); g.lz = zf[nz] - zf[0];
     g.ywall = 0;
     d.fc.cx = (double*)(P + o.cx); d.fc.cy = (double*)(P + o.cy); d.fc.cz = (double*)(P + o.cz);
-    d.fc.diag = (double*)(P + o.diag); d.fc.rhof = (float*)(P + o.rhof); d.fc.cxf = (float*)(P + o.cxf);
-    d.fc.cyf = (float*)(P + o.cyf); d.fc.czf = (float*)(P + o.czf);
+    d.fc.diag = (double*)(P + o.diag); d.fc.rhof = (float*)(P + o.rhof);
     factor(nx, &d.fx);
     factor(ny, &d.fy);
     d.twx = (const float2*)(P + o.twx); d.twy = (const float2*)(P + o.twy);

@@ -39,12 +39,6 @@ __device__ __forceinline__ void cell_prep_faces(const Geo& g, const double* __re
   fc.cz[c] = (x.k == 0) ? 0.0 : 2.0 / (r + rho[c - plane]) * g.inv_dzc[x.k];
   if (x.k == g.nz - 1) fc.cz[c + plane] = 0.0;
   fc.rhof[c] = (float)r;
-  if (fc.cxf != nullptr) {
-    fc.cxf[c] = (float)fc.cx[c];
-    fc.cyf[c] = (float)fc.cy[c];
-    fc.czf[c] = (float)fc.cz[c];
-    if (x.k == g.nz - 1) fc.czf[c + plane] = 0.0f;
-  }
 }
 
 // diag = sum of the six (row-scaled) coefficients of cell c.

@@ -53,6 +53,11 @@ struct Geo {
   const double* za;       // [nz]   sub-diagonal of L_z
   const double* zc;       // [nz]   super-diagonal of L_z
   const float* inv_dzf_f; // [nz]   1 / cell width (FP32 copy)
+  // FP32 layer factors of the face coefficients, [3][nz + 1]: dzf_k / dx^2,
+  // dzf_k / dy^2 (k < nz) and 1 / dzc_k (z faces k = 0 .. nz, 0 on the walls).
+  // The mixed residual update forms its FP32 coefficients from these and the
+  // FP32 density instead of reading stored coefficient fields.
+  const float* cw_f;
   double lz;
   int ywall;              // 1: walls at y = 0 and y = ly (v row 0 is the wall face); 0: periodic y
 };
@@ -61,10 +66,10 @@ struct Geo {
 // dzf_k (so the z coefficients need no per-cell scaling):
 //   cx = dzf_k beta_x / dx^2, cy = dzf_k beta_y / dy^2 (faces of layer k),
 //   cz = beta_z / dzc (z faces, 0 on the walls),
-//   diag = sum of the six coefficients of the cell, rhof = rho_c in FP32.
-//   cxf, cyf, czf: FP32 copies for the residual update of the mixed path
-//   (null on FP64 plans); diagf: FP32 diagonal when not null (unused by the
-//   solver's own kernels).
+//   diag = sum of the six coefficients of the cell, rhof = rho_c in FP32
+//   (the mixed residual update recomputes its FP32 coefficients from rhof:
+//   face_beta_f); diagf: FP32 diagonal when not null (unused by the solver's
+//   own kernels).
 //   rho_tilde: device scalar that replaces rho_c as the scaling of the
 //   residual (Methods I and II of Sec. 3.3.1); null selects Method III.
 struct Faces {
@@ -73,9 +78,6 @@ struct Faces {
   double* cz;    // [nz+1][ny][nx]
   double* diag;  // [nz][ny][nx]
   float* rhof;   // [nz][ny][nx]
-  float* cxf;
-  float* cyf;
-  float* czf;
   float* diagf;
   const double* rho_tilde;
 };
@@ -92,6 +94,22 @@ __device__ __forceinline__ double widen_f32(float f) {
   if (e == 0u) { hi = sign; lo = 0u; }
   if (e == 0xFFu) hi = sign | 0x7FF00000u | (m >> 3);
   return __hiloint2double((int)hi, (int)lo);
+}
+
+// 1 / rho_f of a face from its two cells' FP32 densities (arithmetic face
+// density, as the FP64 coefficients): 2 / (a + b), fast FP32 division.
+__device__ __forceinline__ float face_beta_f(float a, float b) { return __fdividef(2.f, a + b); }
+
+// Host: the [3][nz + 1] FP32 layer factors of Geo::cw_f.
+inline std::vector<float> layer_factors_f32(int nz, const std::vector<double>& dzf,
+                                            const std::vector<double>& inv_dzc, double inv_dx2, double inv_dy2) {
+  std::vector<float> cw(3 * (size_t)(nz + 1), 0.f);
+  for (int k = 0; k < nz; ++k) {
+    cw[k] = (float)(inv_dx2 * dzf[k]);
+    cw[(nz + 1) + k] = (float)(inv_dy2 * dzf[k]);
+  }
+  for (int k = 0; k <= nz; ++k) cw[2 * (nz + 1) + k] = (float)inv_dzc[k];
+  return cw;
 }
 
 // FP64 -> FP32 narrowing on the integer pipe: round half away from zero on
@@ -139,6 +157,10 @@ cudaError_t launch_zdct(const Geo& g, const FftDesc& fz, const C2<T>* twz, C2<T>
 template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
                         const DevStatus* st, cudaStream_t s, const C2<T>* dct = nullptr);
+// FP32 y transform of length 512 (periodic y) with the data in registers
+// (pp_kernels_ffty512.cu); launch_ffty routes such plans to it.
+cudaError_t launch_ffty512(const Geo& g, const float2* twy, float2* spec, int inverse, const DevStatus* st,
+                           cudaStream_t s);
 // FP32 Thomas tables for the well-conditioned z columns of mixed plans.  A
 // column (kx, ky) has the shift lambda = lambda_x(kx) + lambda_y(ky) <= 0;
 // the eigenvalues of its system lie in [lambda - 2 Dmax, lambda] with
@@ -168,6 +190,28 @@ template <typename T>
 cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double2* ybuf,
                            const DevStatus* st, cudaStream_t s, const double* mtab = nullptr,
                            const TriF32* f32 = nullptr);
+// FP64 z solve of PP_MIXED_Z64 plans: FP64 recurrences in every (kx, ky)
+// column, values stored in FP32.  Thomas elimination in the form
+//   forward   y_k = f_k - m_k y_{k-1},            m_k = a_k / d_{k-1}
+//             s_k = (1/d_k) y_k                   (stored, FP32)
+//   backward  x_k = s_k - e_k x_{k+1},            e_k = c_k / d_k,
+// so each sweep costs one FP64 FMA per scalar.  The tables depend on the
+// column only through lambda = lambda_x(kx) + lambda_y(ky); with periodic y
+// lambda_y(ky) = lambda_y(ny - ky), so ky and ny - ky share one table column
+// (ysym: nyt = ny/2 + 1 table rows of nxh columns per layer, ky' = min(ky,
+// ny - ky)); with walls in y nyt = ny.  Table column 0 is the singular
+// (0, 0) system: its last inverse pivot is 0 (pinned unknown).
+struct TriZ64 {
+  const double* m;  // [nz][nyt][nxh]
+  const double* e;  // [nz][nyt][nxh]
+  const float* d;   // [nz][nyt][nxh] 1 / d_k
+  int nyt;
+  int ysym;
+};
+cudaError_t launch_setup_z64(const Geo& g, const double* lamx, const double* lamy, int nyt, int ysym,
+                             double* m, double* e, float* d, cudaStream_t s);
+cudaError_t launch_tridiag_z64(const Geo& g, const TriZ64& t, float2* spec, const DevStatus* st,
+                               cudaStream_t s);
 // dst[i] = (float) src[i], i < n.
 cudaError_t launch_narrow(const double* src, float* dst, size_t n, cudaStream_t s);
 // Inverse x-transform; p = scale * z (p_zero) or p += scale * z; when delta

@@ -75,6 +75,40 @@ __global__ void __launch_bounds__(128, 16) k_tridiag_split(Geo g, const double* 
   stage_tridiag_split<T>(g, mtab, invd, spec, (size_t)blockIdx.x * blockDim.x + threadIdx.x, m0);
 }
 
+// PP_MIXED_Z64 z solve: one thread per (kx, ky) column, all FP64
+// recurrences (stage_tridiag_z64).  The grid is persistent-sized (every
+// block resident at once) and the columns are dealt out a warp at a time,
+// round robin over the blocks (work warp = warp-in-block x gridDim +
+// block), so every SM gets the same number of FP64 chains whatever the
+// block scheduler's placement; a warp still takes 32 consecutive columns.
+// Work warp 0 (warp 0 of block 0) holds the singular column 0 alone, so no
+// warp runs both variants of the sweep one after the other; work warp w > 0
+// holds columns 1 + 32 (w - 1) + lane.  Block 0 first reduces column 0's
+// dzf-weighted z means.
+__global__ void __launch_bounds__(128, 8) k_tridiag_z64(Geo g, TriZ64 t, float2* spec,
+                                                        const DevStatus* __restrict__ st) {
+  if (stopped(st)) return;
+  __shared__ double shm[34];
+  const unsigned ncol = (unsigned)g.ny * g.nxh;
+  const unsigned ntc = (unsigned)t.nyt * g.nxh;
+  if (blockIdx.x == 0) zero_column_means<float>(g, reinterpret_cast<const float*>(spec), 2 * (size_t)ncol, shm);
+  const unsigned wstride = (blockDim.x >> 5) * gridDim.x;
+  const unsigned lane = threadIdx.x & 31u;
+  for (unsigned wq = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; wq == 0 || (wq - 1) * 32u + 1u < ncol;
+       wq += wstride) {
+    if (wq == 0) {  // warp 0 of block 0: column 0 on lane 0
+      if (lane == 0) stage_tridiag_z64<true>(g, t, spec, 0, ncol, 0, ntc, shm[32], shm[33]);
+      continue;
+    }
+    const unsigned col = 1u + (wq - 1) * 32u + lane;
+    if (col >= ncol) continue;
+    const int ky = (int)(col / (unsigned)g.nxh);
+    const int kx = (int)(col - (unsigned)ky * g.nxh);
+    const int kyt = (t.ysym && 2 * ky > g.ny) ? g.ny - ky : ky;
+    stage_tridiag_z64<false>(g, t, spec, col, ncol, (unsigned)kyt * g.nxh + kx, ntc, 0.0, 0.0);
+  }
+}
+
 __global__ void __launch_bounds__(128, 8) k_tridiag_mixed(Geo g, const double* __restrict__ mtab,
                                                          const double* __restrict__ invd, TriF32 f,
                                                          float2* spec, const DevStatus* __restrict__ st) {
@@ -139,6 +173,10 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
 template <typename T>
 cudaError_t launch_ffty(const Geo& g, const FftDesc& fy, const C2<T>* twy, C2<T>* spec, int inverse,
                         const DevStatus* st, cudaStream_t s, const C2<T>* dct) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (g.ny == 512 && dct == nullptr)
+      return launch_ffty512(g, reinterpret_cast<const float2*>(twy), reinterpret_cast<float2*>(spec), inverse, st, s);
+  }
   const int tx = ffty_tile(g.ny, sizeof(C2<T>), kEpt);
   const int tsz = g.ny * tx;
   const size_t smem = (sizeof(T) == sizeof(float))
@@ -201,6 +239,25 @@ cudaError_t launch_tridiag(const Geo& g, const double* invd, C2<T>* spec, double
     const int nblk = (int)((ncol + 127) / 128);
     k_tridiag<T><<<nblk, 128, 0, s>>>(g, invd, spec, ybuf, st);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_z64(const Geo& g, const TriZ64& t, float2* spec, const DevStatus* st,
+                               cudaStream_t s) {
+  const size_t ncol = (size_t)g.ny * g.nxh;
+  const long long nwarps = 1 + (long long)((ncol - 1 + 31) / 32);  // column 0 alone, then 32 per warp
+  int per_sm = 0, dev = 0, nsm = 0;
+  cudaError_t e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_z64, 128, 0)) != cudaSuccess) return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  // all blocks resident at once; no more blocks than warps of work (each
+  // block then still holds at least one column in its first warp)
+  long long nblk = (long long)nsm * per_sm;
+  if (nblk > nwarps) nblk = nwarps;
+  if (nblk < 1) nblk = 1;
+  k_tridiag_z64<<<(int)nblk, 128, 0, s>>>(g, t, spec, st);
   return cudaGetLastError();
 }
 

@@ -135,6 +135,32 @@ __global__ void k_setup_pivots(Geo g, const double* __restrict__ lamx, const dou
   }
 }
 
+// Tables of the PP_MIXED_Z64 z solve (TriZ64), one thread per table column
+// tc = ky' nxh + kx with lambda = lambda_x(kx) + lambda_y(ky'): the same
+// pivot recurrence as k_setup_pivots, stored as m_k = a_k / d_{k-1},
+// e_k = c_k / d_k (FP64) and 1 / d_k (FP32).  Column 0 is the singular
+// (0, 0) system: its last inverse pivot is 0.
+__global__ void k_setup_z64(Geo g, const double* __restrict__ lamx, const double* __restrict__ lamy, int nyt,
+                            double* __restrict__ m, double* __restrict__ e, float* __restrict__ dinv) {
+  const size_t ntc = (size_t)nyt * g.nxh;
+  const size_t tc = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tc >= ntc) return;
+  const int j = (int)(tc / g.nxh), kx = (int)(tc % g.nxh);
+  const double lam = lamx[kx] + lamy[j];
+  double d = -(g.za[0] + g.zc[0]) + lam;
+  double inv_prev = 0.0;
+  for (int k = 0; k < g.nz; ++k) {
+    if (k > 0) d = (-(g.za[k] + g.zc[k]) + lam) - g.za[k] * g.zc[k - 1] / d;
+    const bool pin = (tc == 0 && k == g.nz - 1);  // singular (0, 0) column: pin the last unknown
+    const double inv = pin ? 0.0 : 1.0 / d;
+    const size_t o = (size_t)k * ntc + tc;
+    m[o] = (k == 0) ? 0.0 : g.za[k] * inv_prev;
+    e[o] = (k + 1 < g.nz) ? g.zc[k] * inv : 0.0;
+    dinv[o] = (float)inv;
+    inv_prev = inv;
+  }
+}
+
 // ---- Methods I and II (Sec. 3.3.1) -------------------------------------------
 constexpr int kExtBlocks = kRedBlocks / 2;  // (min, max) pairs fit the partial-sum buffer
 
@@ -419,7 +445,8 @@ __global__ void k_adj_rhs(Geo g, const double* __restrict__ rho, const double* _
     const double r = rho[c];
     const double idzf = g.inv_dzf[k];
     yu[c] = -dt * (2.0 / (r + rho[cim])) * gu[c] * idzf;
-    yv[c] = -dt * (2.0 / (r + rho[cjm])) * gv[c] * idzf;
+    // with walls in y the wall row of v is not an unknown: no gradient enters there
+    yv[c] = (g.ywall && j == 0) ? 0.0 : -dt * (2.0 / (r + rho[cjm])) * gv[c] * idzf;
     yw[c] = (k == 0) ? 0.0 : -dt * (2.0 / (r + rho[c - plane])) * gw[c] * g.inv_dzc[k];
     if (k == nz - 1) yw[c + plane] = 0.0;
   }
@@ -443,12 +470,13 @@ __global__ void k_adj_finish(Geo g, const double* __restrict__ rho, const double
     const double dzf = g.dzf[k];
     const double r = rho[c];
     const double a = gu[c] + dzf * (mu[c] - mu[cim]) * idx;
-    const double bb = gv[c] + dzf * (mu[c] - mu[cjm]) * idy;
+    const bool vwall = g.ywall && j == 0;  // wall row of v: zero gradient, no density dependence
+    const double bb = vwall ? 0.0 : gv[c] + dzf * (mu[c] - mu[cjm]) * idy;
     gus[c] = a;
     gvs[c] = bb;
     const double bx = 2.0 / (r + rho[cim]), by = 2.0 / (r + rho[cjm]);
     tx[c] = -0.5 * bx * bx * (-dt * (p[c] - p[cim]) * idx * a);
-    ty[c] = -0.5 * by * by * (-dt * (p[c] - p[cjm]) * idy * bb);
+    ty[c] = vwall ? 0.0 : -0.5 * by * by * (-dt * (p[c] - p[cjm]) * idy * bb);
     if (k == 0) {
       gws[c] = 0.0;
       tz[c] = 0.0;
@@ -584,6 +612,14 @@ cudaError_t launch_setup_pivots(const Geo& g, const double* lamx, const double* 
                                 cudaStream_t s, double* mtab) {
   const size_t ncol = (size_t)g.ny * g.nxh;
   k_setup_pivots<<<(int)((ncol + 127) / 128), 128, 0, s>>>(g, lamx, lamy, invd, mtab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_z64(const Geo& g, const double* lamx, const double* lamy, int nyt, int ysym,
+                             double* m, double* e, float* d, cudaStream_t s) {
+  (void)ysym;  // the table rows are ky' = 0 .. nyt - 1 either way
+  const size_t ntc = (size_t)nyt * g.nxh;
+  k_setup_z64<<<(int)((ntc + 127) / 128), 128, 0, s>>>(g, lamx, lamy, nyt, m, e, d);
   return cudaGetLastError();
 }
 

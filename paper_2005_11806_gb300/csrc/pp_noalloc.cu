@@ -219,7 +219,7 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   }
   if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
 
-  Geo g;
+  Geo g{};
   g.nx = nx; g.ny = ny; g.nz = nz; g.nxh = nxh;
   g.dx = dx; g.dy = dy;
   g.inv_dx2 = 1.0 / (dx * dx);

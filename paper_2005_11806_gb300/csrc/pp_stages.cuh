@@ -156,16 +156,38 @@ __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc,
         const int il = (i == 0) ? nx - 1 : i - 1, ir = (i + 4 == nx) ? 0 : i + 4;
         const float4 d = ld4(delta + c);
         const float dl = delta[rowoff + il], dr = delta[rowoff + ir];
-        const float4 cx = ld4(fc.cxf + c);
-        const float cxr = fc.cxf[rowoff + ir];
         const float4 dyp = ld4(delta + cyp), dym = ld4(delta + cym);
-        const float4 cyp4 = ld4(fc.cyf + cyp), cym4 = ld4(fc.cyf + c);
         const bool up = k + 1 < nz, dn = k > 0;
-        float4 dzp = d, czp = make_float4(0.f, 0.f, 0.f, 0.f), dzm = d, czm = czp;
-        if (up) { dzp = ld4(delta + c + plane); czp = ld4(fc.czf + c + plane); }
-        if (dn) { dzm = ld4(delta + c - plane); czm = ld4(fc.czf + c); }
+        float4 dzp = d, dzm = d;
+        if (up) dzp = ld4(delta + c + plane);
+        if (dn) dzm = ld4(delta + c - plane);
+        // FP32 face coefficients from the FP32 density of the cell and its
+        // six neighbours and the layer factors (z walls: factor 0; y walls:
+        // the wall faces of rows 0 and ny - 1 are 0)
+        const float4 rc = ld4(fc.rhof + c);
+        const float rl = fc.rhof[rowoff + il], rr = fc.rhof[rowoff + ir];
+        const float4 ryp = ld4(fc.rhof + cyp), rym = ld4(fc.rhof + cym);
+        float4 rzp = rc, rzm = rc;
+        if (up) rzp = ld4(fc.rhof + c + plane);
+        if (dn) rzm = ld4(fc.rhof + c - plane);
+        const int nz1 = nz + 1;
+        const float wx = g.cw_f[k];
+        const float wyl = (g.ywall && j == 0) ? 0.f : g.cw_f[nz1 + k];
+        const float wyh = (g.ywall && j + 1 == ny) ? 0.f : g.cw_f[nz1 + k];
+        const float wzp = g.cw_f[2 * nz1 + k + 1], wzm = g.cw_f[2 * nz1 + k];
+        const float4 cx = make_float4(wx * face_beta_f(rl, rc.x), wx * face_beta_f(rc.x, rc.y),
+                                      wx * face_beta_f(rc.y, rc.z), wx * face_beta_f(rc.z, rc.w));
+        const float cxr = wx * face_beta_f(rc.w, rr);
+        const float4 cyp4 = make_float4(wyh * face_beta_f(rc.x, ryp.x), wyh * face_beta_f(rc.y, ryp.y),
+                                        wyh * face_beta_f(rc.z, ryp.z), wyh * face_beta_f(rc.w, ryp.w));
+        const float4 cym4 = make_float4(wyl * face_beta_f(rc.x, rym.x), wyl * face_beta_f(rc.y, rym.y),
+                                        wyl * face_beta_f(rc.z, rym.z), wyl * face_beta_f(rc.w, rym.w));
+        const float4 czp = make_float4(wzp * face_beta_f(rc.x, rzp.x), wzp * face_beta_f(rc.y, rzp.y),
+                                       wzp * face_beta_f(rc.z, rzp.z), wzp * face_beta_f(rc.w, rzp.w));
+        const float4 czm = make_float4(wzm * face_beta_f(rc.x, rzm.x), wzm * face_beta_f(rc.y, rzm.y),
+                                       wzm * face_beta_f(rc.z, rzm.z), wzm * face_beta_f(rc.w, rzm.w));
         float4 e = ld4(E + c);
-        const float4 rh = scale_rho && !const_scale ? ld4(fc.rhof + c) : make_float4(rt_f, rt_f, rt_f, rt_f);
+        const float4 rh = scale_rho && !const_scale ? rc : make_float4(rt_f, rt_f, rt_f, rt_f);
         const float idzf = g.inv_dzf_f[k];
         auto cell = [&](float dc, float dxm, float dxp, float cxm, float cxp, float dypv, float cypv,
                         float dymv, float cymv, float dzpv, float czpv, float dzmv, float czmv, float& ev,
@@ -274,14 +296,20 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
           double ep = 0.0;
           float ev = 0.f;  // FP32 dzf_k e of the mixed path
           if (update) {
-            // E^s = E^{s-1} - A delta, A delta in FP32
+            // E^s = E^{s-1} - A delta, A delta in FP32 with the FP32
+            // coefficients formed from rhof (as in resid_update_vec4)
             const float dc = delta[c];
-            float t = fc.cxf[rowoff + ip] * (delta[rowoff + ip] - dc);
-            t = fmaf(fc.cxf[c], delta[rowoff + im] - dc, t);
-            t = fmaf(fc.cyf[rowp + i], delta[rowp + i] - dc, t);
-            t = fmaf(fc.cyf[c], delta[rowm + i] - dc, t);
-            if (k + 1 < nz) t = fmaf(fc.czf[c + plane], delta[c + plane] - dc, t);
-            if (k > 0) t = fmaf(fc.czf[c], delta[c - plane] - dc, t);
+            const float rcc = fc.rhof[c];
+            const int nz1 = nz + 1;
+            const float wx = g.cw_f[k], wy = g.cw_f[nz1 + k];
+            const float wyl = (g.ywall && j == 0) ? 0.f : wy, wyh = (g.ywall && j + 1 == ny) ? 0.f : wy;
+            float t = wx * face_beta_f(rcc, fc.rhof[rowoff + ip]) * (delta[rowoff + ip] - dc);
+            t = fmaf(wx * face_beta_f(fc.rhof[rowoff + im], rcc), delta[rowoff + im] - dc, t);
+            t = fmaf(wyh * face_beta_f(rcc, fc.rhof[rowp + i]), delta[rowp + i] - dc, t);
+            t = fmaf(wyl * face_beta_f(rcc, fc.rhof[rowm + i]), delta[rowm + i] - dc, t);
+            if (k + 1 < nz)
+              t = fmaf(g.cw_f[2 * nz1 + k + 1] * face_beta_f(rcc, fc.rhof[c + plane]), delta[c + plane] - dc, t);
+            if (k > 0) t = fmaf(g.cw_f[2 * nz1 + k] * face_beta_f(rcc, fc.rhof[c - plane]), delta[c - plane] - dc, t);
             ev = E[c] - t;
             E[c] = ev;
           } else {
@@ -742,6 +770,83 @@ __device__ __forceinline__ void stage_tridiag_split(const Geo& g, const double* 
         dq[u] = invd[(size_t)kn * ncol + col];
         x = fma(-g.zc[k], x, yy) * d;
         stv((size_t)k * stride + sid, x);
+      }
+    }
+  }
+}
+
+// One column of a PP_MIXED_Z64 plan (TriZ64), both components in one thread
+// (two independent FP64 chains sharing the table loads): both sweeps are
+// FP64 recurrences with one FMA per row and component; the spectrum keeps
+// its FP32 storage, so the forward values are stored as s_k = (1/d_k) y_k,
+// rounded to FP32 and multiplied by the FP32 inverse pivot (the same 2^-24
+// relative perturbation per value as storing y_k itself).  ZERO: the
+// singular column 0, whose right-hand side first loses its dzf-weighted z
+// mean (m0x, m0y).  Loads run PF rows ahead.  32-bit offsets: the plan keeps
+// nx ny (nz + 1) below 2^31.
+template <bool ZERO>
+__device__ __forceinline__ void stage_tridiag_z64(const Geo& g, const TriZ64& t, float2* __restrict__ spec,
+                                                  unsigned col, unsigned ncol, unsigned tc, unsigned ntc,
+                                                  double m0x, double m0y) {
+  constexpr int PF = 4;
+  const int nz = g.nz;
+  const double* __restrict__ tm = t.m;
+  const double* __restrict__ te = t.e;
+  const float* __restrict__ td = t.d;
+  float2 fq[PF];
+  float dq[PF];
+  double mq[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const unsigned k = u < nz ? u : nz - 1;
+    fq[u] = spec[k * ncol + col];
+    mq[u] = tm[k * ntc + tc];
+    dq[u] = td[k * ntc + tc];
+  }
+  double yx = 0.0, yy = 0.0;
+  float2 s = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < nz; k0 += PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 + u;
+      if (k < nz) {
+        const double fx = widen_f32(fq[u].x), fy = widen_f32(fq[u].y);
+        const double m = mq[u];
+        const float dk = dq[u];
+        const unsigned kn = k + PF < nz ? k + PF : nz - 1;
+        fq[u] = spec[kn * ncol + col];
+        mq[u] = tm[kn * ntc + tc];
+        dq[u] = td[kn * ntc + tc];
+        yx = fma(-m, yx, ZERO ? fx - m0x : fx);
+        yy = fma(-m, yy, ZERO ? fy - m0y : fy);
+        s = make_float2(narrow_f64(yx) * dk, narrow_f64(yy) * dk);
+        spec[(unsigned)k * ncol + col] = s;
+      }
+    }
+  }
+  // x_{nz-1} = s_{nz-1} (already stored); backward from row nz - 2
+  double xx = widen_f32(s.x), xy = widen_f32(s.y);
+  float2 sq[PF];
+  double eq[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const unsigned k = nz - 2 - u >= 0 ? nz - 2 - u : 0;
+    sq[u] = spec[k * ncol + col];
+    eq[u] = te[k * ntc + tc];
+  }
+  for (int k0 = nz - 2; k0 >= 0; k0 -= PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 - u;
+      if (k >= 0) {
+        const double sx = widen_f32(sq[u].x), sy = widen_f32(sq[u].y);
+        const double e = eq[u];
+        const unsigned kn = k - PF >= 0 ? k - PF : 0;
+        sq[u] = spec[kn * ncol + col];
+        eq[u] = te[kn * ntc + tc];
+        xx = fma(-e, xx, sx);
+        xy = fma(-e, xy, sy);
+        spec[(unsigned)k * ncol + col] = make_float2(narrow_f64(xx), narrow_f64(xy));
       }
     }
   }

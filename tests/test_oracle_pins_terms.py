@@ -358,3 +358,90 @@ def test_planted_constant_density_is_caught(monkeypatch, name, method, planted):
     monkeypatch.setattr(orc, name, planted)
     with pytest.raises(AssertionError):
         test_residual_history_is_the_dense_iteration(method)
+
+
+# --- adjoint with walls in y -------------------------------------------------
+
+def _duct_case():
+    """6 x 4 x 5 duct (walls in y and z), stretched z, a gas block at ratio
+    100, v* zero on the wall row."""
+    nx, ny, nz = 6, 4, 5
+    zf = wl.tanh_zfaces(nz, 0.5, 2.0)
+    g = orc.Grid(nx, ny, nz, 1.0, 0.8, zf, ywalls=True)
+    phi = np.zeros(g.shape)
+    phi[1:3, 1:3, 2:4] = 1.0
+    phi[3, 1:3, 2:4] = 0.5
+    rho = orc.mixture_density(phi, 1.0, 100.0)
+    rng = np.random.default_rng(61)
+    us, vs = rng.standard_normal(g.shape) * 0.1, rng.standard_normal(g.shape) * 0.1
+    ws = rng.standard_normal((nz + 1, ny, nx)) * 0.1
+    vs[:, 0, :] = 0.0
+    ws[0] = ws[-1] = 0.0
+    tgt = (rng.standard_normal(g.shape) * 0.1, rng.standard_normal(g.shape) * 0.1,
+           rng.standard_normal((nz + 1, ny, nx)) * 0.1)
+    return g, us, vs, ws, rho, wl.gas_source(phi), tgt
+
+
+def _duct_loss(g, us, vs, ws, rho, S, dt, tgt):
+    """L = ||u^{n+1} - target||^2 over the unknowns: the wall planes of w and
+    the wall row of v are not unknowns (zero by the walls)."""
+    _, u, v, w = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    return float(np.sum((u - tgt[0]) ** 2) + np.sum((v[:, 1:] - tgt[1][:, 1:]) ** 2)
+                 + np.sum((w[1:-1] - tgt[2][1:-1]) ** 2))
+
+
+def test_ywalls_adjoint_central_differences_and_dot_product():
+    """With walls in y: adjoint_direct against central differences of the
+    projection (eps = 1e-6 relative) on entries of u*, v* (off the wall row),
+    w* and rho; the dot-product identity <P d, g> = <d, P^T g> with d and g
+    zero on the wall faces; and the Algorithm-1 form of the adjoint against
+    the literal sparse transpose."""
+    g, us, vs, ws, rho, S, tgt = _duct_case()
+    dt = 1e-3
+    _, u, v, w = orc.projection_direct(g, us, vs, ws, rho, S, dt)
+    gu, gv, gw = 2 * (u - tgt[0]), 2 * (v - tgt[1]), 2 * (w - tgt[2])
+    gv[:, 0, :] = 0.0
+    gus, gvs, gws, grho = orc.adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv, gw)
+    assert np.all(gvs[:, 0, :] == 0.0) and np.all(gws[0] == 0.0) and np.all(gws[-1] == 0.0)
+    arrs = {"us": us, "vs": vs, "ws": ws, "rho": rho}
+    grads = {"us": gus, "vs": gvs, "ws": gws, "rho": grho}
+    for key, idx in (("us", (1, 2, 3)), ("vs", (2, 1, 4)), ("vs", (3, 3, 0)), ("ws", (2, 2, 1)),
+                     ("rho", (2, 1, 2)), ("rho", (3, 2, 3)), ("rho", (0, 0, 5))):
+        base = arrs[key]
+        h = 1e-6 * max(1.0, abs(base[idx]))
+        plus, minus = dict(arrs), dict(arrs)
+        plus[key] = base.copy(); plus[key][idx] += h
+        minus[key] = base.copy(); minus[key][idx] -= h
+        fd = (_duct_loss(g, plus["us"], plus["vs"], plus["ws"], plus["rho"], S, dt, tgt)
+              - _duct_loss(g, minus["us"], minus["vs"], minus["ws"], minus["rho"], S, dt, tgt)) / (2 * h)
+        an = grads[key][idx]
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * np.max(np.abs(gus))), (key, idx, fd, an)
+    rng = np.random.default_rng(62)
+    du, dv = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    dw = rng.standard_normal((g.nz + 1, g.ny, g.nx))
+    dv[:, 0, :] = 0.0
+    dw[0] = dw[-1] = 0.0
+    zero = np.zeros(g.shape)
+    _, pu, pv, pw = orc.projection_direct(g, du, dv, dw, rho, zero, dt)
+    pv[:, 0, :] = 0.0
+    a1, a2, a3, _ = orc.adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv, gw)
+    lhs = np.sum(pu * gu) + np.sum(pv * gv) + np.sum(pw[1:-1] * gw[1:-1])
+    rhs = np.sum(du * a1) + np.sum(dv * a2) + np.sum(dw * a3)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    b1, b2, b3, brho, _ = orc.adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13)
+    for x, y in ((b1, gus), (b2, gvs), (b3, gws), (brho, grho)):
+        assert _rel(x, y) < 1e-9
+    # an upstream gradient on the wall row (not an unknown) is ignored
+    gv_wall = gv.copy()
+    gv_wall[:, 0, :] = rng.standard_normal((g.nz, g.nx))
+    for fn in (lambda: orc.adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv_wall, gw),
+               lambda: orc.adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv_wall, gw, rtol=1e-13)[:4]):
+        for x, y in zip(fn(), (gus, gvs, gws, grho)):
+            assert _rel(x, y) < 1e-9
+
+
+def test_planted_ywall_gradient_kept_is_caught(monkeypatch):
+    """The wall row of v treated as an unknown (its upstream gradient kept)."""
+    monkeypatch.setattr(orc, "_zero_ywall_row", lambda g, gv: np.array(gv, dtype=np.float64, copy=True))
+    with pytest.raises(AssertionError):
+        test_ywalls_adjoint_central_differences_and_dot_product()
