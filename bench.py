@@ -156,8 +156,8 @@ def algorithmic(kernel, w, precision):
         if precision == "fp64":
             # b, p, cx, cy, cz, diag, rho (FP64) + FP64 half spectrum; stencil 7 FMA + 5, x-FFT
             return {"bytes": 56 * npts + cs * nsp, "fp64_flops": 19 * npts + 45 * npts}
-        exact = 56 * npts     # b, p, cx, cy, cz, diag (FP64), rhof; E written (FP32)
-        update = 28 * npts    # E read + write, delta, cxf, cyf, czf, rhof (FP32)
+        exact = 60 * npts     # b, p, cx, cy, cz, diag (FP64), rhof; E written (FP32)
+        update = 16 * npts    # E read + write, delta, rhof (FP32; coefficients formed from rhof)
         return {"bytes": int(0.025 * exact + 0.975 * update) + cs * nsp, "fp64_flops": int(0.025 * 15 * npts)}
     if kernel in ("ffty_fwd", "ffty_inv"):
         return {"bytes": 2 * cs * nsp, "fp64_flops": 0 if precision != "fp64" else 45 * npts}
@@ -185,16 +185,22 @@ def algorithmic(kernel, w, precision):
     return None
 
 
-# DRAM bytes per cell of k_resid_fftx on mixed plans, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the 512 x 512 x 128 case:
-# the same kernel, block shape and grid per plane as at 512^3, so the bytes
-# scale with the cells processed.  One updated-residual pass and one exact
-# pass; the launch average follows the 40-pass exact/update cycle.  Captured with
-#   ncu --set full --clock-control none -k regex:"k_resid_fftx|k_ffty|k_tridiag_mixed|k_fftx_inv" -s 20 -c 5
-#   ncu --set full --clock-control none -k regex:"k_resid_fftx" -s 20 -c 1
-# on  python bench.py --n 512 --nz 128 --steps 1 --warmup 0 --maxit 21 --no-cpu-baseline --no-e2e --no-compare
-# (summary: profiles/pass_kernels_bubbles512x512x128_full.md).
-RESID_DRAM_B_PER_CELL = {"update": 35.11, "exact": 69.52}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell of a
+# launch of the pass kernels of mixed plans, from ncu captures on the
+# 512 x 512 x 128 case: the same kernels, block shapes and per-plane grids as
+# at 512^3, so the bytes scale with the cells processed (the captures and
+# their commands are summarised under profiles/).  The residual kernel's
+# figure is weighted over the 40-pass exact/update cycle: 20.36 B on an
+# update pass (profiles/pass_kernels_mixed_z64_bubbles512x512x128.md), 69.52 B
+# on an exact pass (the exact branch is unchanged since
+# profiles/pass_kernels_bubbles512x512x128_full.md).  The z solve's is for
+# the PP_MIXED_Z64 kernel (same capture as the update pass).
+# None: not captured for the kernel as it stands.
+RESID_DRAM_B_PER_CELL = {"update": 20.36, "exact": 69.52}
+DRAM_B_PER_CELL = {
+    "resid_fftx": 0.975 * RESID_DRAM_B_PER_CELL["update"] + 0.025 * RESID_DRAM_B_PER_CELL["exact"],
+    "tridiag_z": 17.23,
+}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -283,9 +289,9 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": name,
                 "avg_launch_ms": round(avg_s * 1e3, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    if name == "resid_fftx" and args.precision in ("mixed", "mixed_z64"):
-        per_cell = 0.975 * RESID_DRAM_B_PER_CELL["update"] + 0.025 * RESID_DRAM_B_PER_CELL["exact"]
-        roof["traffic"] = int(per_cell * npts)
+    if (args.precision == "mixed_z64" or (args.precision == "mixed" and name == "resid_fftx")) \
+            and DRAM_B_PER_CELL.get(name) is not None:
+        roof["traffic"] = int(DRAM_B_PER_CELL[name] * npts)
         roof["traffic_source"] = "ncu DRAM bytes per cell at 512x512x128, scaled to the launch's cells"
     kernels = {k: {"launches": n, "total_ms": round(t, 3), "avg_ms": round(t / n, 4),
                    "share": round(t / sum(x[1] for x in kern.values()), 4)} for k, (n, t) in kern.items()}

@@ -224,6 +224,10 @@ template <typename T>
 cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
                             double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s,
                             T* delta = nullptr, float* sdelta = nullptr);
+// The same for FP32 spectra of length nx = 512, with the transform in
+// registers (pp_kernels_fftx512.cu); launch_fftx_inv routes such plans to it.
+cudaError_t launch_fftx512_inv(const Geo& g, const float2* twx, const float2* spec, double scale, double* p,
+                               int p_zero, const DevStatus* st, cudaStream_t s, float* delta, float* sdelta);
 cudaError_t launch_fold_pending(const Geo& g, double* p, const float* sdelta, const DevStatus* st,
                                 cudaStream_t s);
 

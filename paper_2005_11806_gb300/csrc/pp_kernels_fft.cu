@@ -291,6 +291,11 @@ template <typename T>
 cudaError_t launch_fftx_inv(const Geo& g, const FftDesc& fx, const C2<T>* twx, const C2<T>* spec,
                             double scale, double* p, int p_zero, const DevStatus* st, cudaStream_t s,
                             T* delta, float* sdelta) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (g.nx == 512)
+      return launch_fftx512_inv(g, reinterpret_cast<const float2*>(twx), reinterpret_cast<const float2*>(spec),
+                                scale, p, p_zero, st, s, delta, sdelta);
+  }
   const int rpb = rows_per_block(g.nx, kEpt);
   const long nrows = (long)g.nz * g.ny;
   const int nblk = (int)((nrows + rpb - 1) / rpb);

@@ -91,9 +91,9 @@ def test_reference_arm_json_line(monkeypatch, capsys):
 
 def test_algorithmic_bytes_per_cell_at_512():
     """The roofline's numerators: algorithmic bytes per cell of each pass
-    kernel of the 512^3 mixed benchmark (residual 32.7 averaged over the
-    40-pass exact/update cycle, y transforms 8.0, z solve 20.1, inverse x
-    16.2)."""
+    kernel of the 512^3 benchmark (residual 21.1 averaged over the 40-pass
+    exact/update cycle, y transforms 8.0, z solve 20.1 for the hybrid and
+    21.1 for the FP64-recurrence plan, inverse x 16.2)."""
     sys.path.insert(0, ROOT)
     import types
     import bench
@@ -101,10 +101,12 @@ def test_algorithmic_bytes_per_cell_at_512():
     npts = 512 ** 3
     per_cell = {k: bench.algorithmic(k, w, "mixed")["bytes"] / npts
                 for k in ("resid_fftx", "ffty_fwd", "tridiag_z", "fftx_inv_update")}
-    assert per_cell["resid_fftx"] == pytest.approx(32.7, abs=0.05)
+    assert per_cell["resid_fftx"] == pytest.approx(21.1, abs=0.05)
     assert per_cell["ffty_fwd"] == pytest.approx(8.03, abs=0.05)
     assert per_cell["tridiag_z"] == pytest.approx(20.1, abs=0.05)
     assert per_cell["fftx_inv_update"] == pytest.approx(16.2, abs=0.05)
+    z64 = bench.algorithmic("tridiag_z", w, "mixed_z64")
+    assert z64["bytes"] / npts == pytest.approx(21.1, abs=0.05)
+    assert z64["fp64_flops"] == 8 * 257 * 512 * 512
     # the residual's DRAM traffic per launch: 39 update passes to 1 exact
-    traffic = 0.975 * bench.RESID_DRAM_B_PER_CELL["update"] + 0.025 * bench.RESID_DRAM_B_PER_CELL["exact"]
-    assert traffic * npts == pytest.approx(4.83e9, rel=2e-3)
+    assert bench.DRAM_B_PER_CELL["resid_fftx"] * npts == pytest.approx(2.899e9, rel=2e-3)

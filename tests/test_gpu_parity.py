@@ -191,6 +191,72 @@ def test_projection_mixed_vs_oracle(pp, stretched, precision):
     assert max(errs) < 1e-9
 
 
+@pytest.mark.parametrize("dims,precision", [
+    ((512, 15, 7), "mixed_z64"),    # 512-point x lines in registers; odd row count (a half-empty pair)
+    ((16, 512, 6), "mixed"),        # 512-point y lines in registers
+    ((512, 512, 3), "mixed_z64"),   # both, several row groups per block
+])
+def test_register_transforms_vs_oracle(pp, dims, precision):
+    """The 512-point FP32 transforms (residual + forward x, inverse x +
+    update, y) against the oracle: a constant solve within the FP32 bound,
+    then a projection that crosses the exact / updated residual cycle (50
+    passes) and converges to 1e-10 with the oracle's fields."""
+    nx, ny, nz = dims
+    zf = wl.tanh_zfaces(nz, 0.7, 1.5)
+    g = orc.Grid(nx, ny, nz, 1.0, 0.8, zf)
+    f = np.random.default_rng(nx + 3 * ny + nz).standard_normal(g.shape)
+    plan = _plan(pp, nx, ny, nz, 1.0, 0.8, zf, precision)
+    p = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    pp.pressure_solve(plan.handle, dev(f), p)
+    err = _rel(host(p), orc.solve_constant(g, f))
+    bound = mixed_solve_bound(nx, ny)
+    print(f"register transforms {dims} {precision}: constant solve {err:.3e} (bound {bound:.3e})")
+    assert err < bound
+    rng = np.random.default_rng(5)
+    phi = np.zeros(g.shape)
+    phi[:, ny // 4:ny // 2 + 1, nx // 3:nx // 2] = 1.0
+    rho = orc.mixture_density(phi, 1.0, 100.0)
+    us, vs = rng.standard_normal(g.shape) * 0.1, rng.standard_normal(g.shape) * 0.1
+    ws = rng.standard_normal((nz + 1, ny, nx)) * 0.1
+    ws[0] = ws[-1] = 0.0
+    S = wl.gas_source(phi)
+    dt = 1e-3
+    p0, u0, v0, w0, _ = orc.method3(g, us, vs, ws, rho, S, dt, rtol=1e-12, maxit=3000)
+    u, v = torch.empty_like(p), torch.empty_like(p)
+    ww = torch.empty((nz + 1, ny, nx), dtype=torch.float64, device="cuda")
+    info = pp.pressure_correct(plan.handle, dev(us), dev(vs), dev(ws), dev(rho), dev(S), dt, p, u, v, ww,
+                               rtol=1e-10, maxit=3000)
+    assert info["status"] == 0 and info["res_final"] <= 1e-10 and info["iters"] > 45
+    Sc = S - orc.volume_mean(g, S)
+    d0 = orc.divergence(g, us, vs, ws) - Sc
+    assert np.linalg.norm(orc.divergence(g, host(u), host(v), host(ww)) - Sc) <= 1e-10 * np.linalg.norm(d0) * 1.0001
+    errs = [_rel(host(a), b) for a, b in ((u, u0), (v, v0), (ww, w0))]
+    print(f"register transforms {dims} {precision}: converged fields vs oracle {errs}, iters {info['iters']}")
+    assert max(errs) < 1e-8
+
+
+@pytest.mark.parametrize("dims", [(512, 512, 16), (512, 512, 17), (512, 64, 96)])
+def test_register_transforms_many_lines_per_block(pp, dims):
+    """The persistent 512-point kernels with several lines (x) and tiles (y)
+    per block, the next tile's values loaded during the current transform:
+    constant solves against the oracle within the FP32 bound, both mixed
+    plans."""
+    nx, ny, nz = dims
+    zf = wl.tanh_zfaces(nz, 1.0, 1.5)
+    g = orc.Grid(nx, ny, nz, 2.0, 2.0, zf)
+    f = np.random.default_rng(nz).standard_normal(g.shape)
+    ref = orc.solve_constant(g, f)
+    bound = mixed_solve_bound(nx, ny)
+    for precision in ("mixed_z64", "mixed"):
+        plan = _plan(pp, nx, ny, nz, 2.0, 2.0, zf, precision)
+        p = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+        pp.pressure_solve(plan.handle, dev(f), p)
+        err = _rel(host(p), ref)
+        print(f"register transforms {dims} {precision}: constant solve {err:.3e} (bound {bound:.3e})")
+        assert err < bound
+        plan.close()
+
+
 def test_host_pointers_match_device(pp):
     w, rho = _case(24, True, 10.0)
     a = _run_gpu(pp, w, rho, "fp64", rtol=1e-11)
