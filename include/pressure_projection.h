@@ -114,10 +114,10 @@ typedef struct {
                               difference, cos(pi m (j + 1/2) / ny), eigenvalues
                               -(4/dy^2) sin^2(pi m / (2 ny)), computed by one complex FFT
                               of length ny; pressure_solve, pressure_correct (Methods I, II
-                              and III), pressure_solve_adjoint and pressure_mixture_density
-                              take them, the thermodynamic source and the predictor return
-                              PP_ERR_UNSUPPORTED, and the batched and no-allocation entry
-                              points take periodic y only */
+                              and III), pressure_solve_adjoint, pressure_mixture_density, the
+                              thermodynamic source (adiabatic y walls) and the predictor
+                              (no-slip y walls) take them; the batched and no-allocation
+                              entry points take periodic y only */
 } pp_grid;
 
 typedef struct {
@@ -168,7 +168,8 @@ pp_status pressure_mixture_density(pp_plan plan, const double* phi, double rho_g
 /* ---- the divergence source from the thermodynamics --------------------
  * div(k grad T) is evaluated as D(k_f G T) on the MAC grid (second-order
  * central, Sec. 3.2): k_f is the arithmetic mean of the two cells of a face,
- * the z walls are adiabatic (no heat flux), x and y periodic.
+ * the z walls (and the y walls of a plan with walls in y) are adiabatic (no
+ * heat flux), x (and otherwise y) periodic.
  *
  * Rate of the thermodynamic pressure, Eq. 30 (the discrete form of Eq.
  * final_p0):
@@ -211,7 +212,9 @@ pp_status pressure_divergence_source(pp_plan plan, const double* phi, const doub
  * stresses at cell centres, cross products and shear stresses at cell edges
  * (a velocity carried to an edge by the mean of its two values, mu by the
  * mean of the cells around the edge, rho_f by the mean of the face's two
- * cells); periodic x and y, no-slip z walls.  The surface-tension force of
+ * cells); periodic x and y (or no-slip y walls on a plan with walls in y:
+ * the wall row of v is read and written as zero, the wall shear of u and w
+ * is taken over half a cell), no-slip z walls.  The surface-tension force of
  * the VOF model is out of scope: force (three face fields, or NULL) may
  * carry any body force, added to div tau.
  * In: u, v, w (faces of u^n; w wall planes zero), rho, mu (cell fields),

@@ -40,9 +40,9 @@ Readings of points the paper leaves open:
 * the conduction term ``div(k grad T)`` of Eqs. 30 and 34 is ``D(k_f G T)``
   with the arithmetic face mean of k (the same operator as the pressure's);
   the z walls are adiabatic (zero heat flux), x and y periodic;
-* the momentum predictor (Eqs. 29, 32) has no-slip z walls; the density on
-  a face and the viscosity on an edge are arithmetic means of the cells
-  around them; a velocity is carried to an edge by the mean of its two
+* the momentum predictor (Eqs. 29, 32) has no-slip z walls (and no-slip y
+  walls when y is bounded); the density on a face and the viscosity on an
+  edge are arithmetic means of the cells around them; a velocity is carried to an edge by the mean of its two
   values in x, y or z;
   the surface-tension force of the VOF model is out of scope (a caller
   force may stand in for it); the first step is forward Euler.
@@ -661,9 +661,12 @@ def convection(g, u, v, w):
     """C(u) = div(u u) - u div(u) at the u, v and w points (w: interior faces;
     the wall planes are zero).  Products live at cell centres (normal terms)
     and at cell edges (cross terms); a velocity is carried to an edge by the
-    mean of its two values in x, y or z."""
+    mean of its two values in x, y or z.  With y walls the wall row of v is
+    zero (no-penetration), so every product on a y-wall edge vanishes, and
+    the wall row of C_y is zero."""
     if g.ywalls:
-        raise NotImplementedError("convection: periodic y only")
+        v = np.array(v, dtype=np.float64, copy=True)
+        v[:, 0, :] = 0.0
     D = divergence(g, u, v, w)
     # normal fluxes at cell centres
     fxx = (0.5 * (u + np.roll(u, -1, axis=2))) ** 2
@@ -684,6 +687,8 @@ def convection(g, u, v, w):
     cz[1:-1] = ((np.roll(fxz[1:-1], -1, axis=2) - fxz[1:-1]) / g.dx
                 + (np.roll(fyz[1:-1], -1, axis=1) - fyz[1:-1]) / g.dy
                 + (fzz[1:] - fzz[:-1]) / dzc - w[1:-1] * _zinterp(g, D)[1:-1])
+    if g.ywalls:
+        cy[:, 0, :] = 0.0
     return cx, cy, cz
 
 
@@ -692,9 +697,10 @@ def viscous(g, mu, u, v, w):
     (2/3)(div u) I].  Normal stresses at cell centres with mu of the cell;
     shear stresses at edges with the mean mu of the (up to) four cells
     around the edge.  No-slip z walls: the wall velocity is zero, so the
-    wall shear uses the half-cell distance to the wall."""
+    wall shear uses the half-cell distance to the wall.  With y walls the
+    same holds there (``_viscous_ywalls``)."""
     if g.ywalls:
-        raise NotImplementedError("viscous: periodic y only")
+        return _viscous_ywalls(g, mu, u, v, w)
     D = divergence(g, u, v, w)
     dzf = g.dzf[:, None, None]
     txx = mu * (2.0 * (np.roll(u, -1, axis=2) - u) / g.dx - 2.0 / 3.0 * D)
@@ -728,6 +734,60 @@ def viscous(g, mu, u, v, w):
     return fx, fy, fz
 
 
+def _viscous_ywalls(g, mu, u, v, w):
+    """div tau with no-slip walls in y as well as in z.  The wall row of v
+    is zero.  Shear stresses on the y-wall edges use the zero wall velocity
+    and the half-cell distance to the wall (as at the z walls), so the two
+    walls need separate edge rows: tau_xy and tau_yz are kept on ny + 1 edge
+    rows (row 0 the wall y = 0, row ny the wall y = ly, rows 1 .. ny - 1
+    between cells).  The edges where a y wall meets a z wall carry no shear
+    (both velocities vanish there)."""
+    nx, ny, nz = g.nx, g.ny, g.nz
+    v = np.array(v, dtype=np.float64, copy=True)
+    v[:, 0, :] = 0.0
+    D = divergence(g, u, v, w)
+    dzf = g.dzf[:, None, None]
+    txx = mu * (2.0 * (np.roll(u, -1, axis=2) - u) / g.dx - 2.0 / 3.0 * D)
+    vtop = np.concatenate([v, np.zeros((nz, 1, nx))], axis=1)      # v on the ny + 1 y-face rows
+    tyy = mu * (2.0 * (vtop[:, 1:] - vtop[:, :-1]) / g.dy - 2.0 / 3.0 * D)
+    tzz = mu * (2.0 * (w[1:] - w[:-1]) / dzf - 2.0 / 3.0 * D)
+    mux = 0.5 * (mu + np.roll(mu, 1, axis=2))                      # mean over the two cells in x
+    # tau_xy on the (i - 1/2, j - 1/2) edges, j = 0 .. ny
+    txy = np.zeros((nz, ny + 1, nx))
+    mxy = 0.5 * (mux[:, 1:] + mux[:, :-1])
+    txy[:, 1:-1] = mxy * ((u[:, 1:] - u[:, :-1]) / g.dy + (v[:, 1:] - np.roll(v[:, 1:], 1, axis=2)) / g.dx)
+    txy[:, 0] = mux[:, 0] * (u[:, 0] - 0.0) / (0.5 * g.dy)
+    txy[:, -1] = mux[:, -1] * (0.0 - u[:, -1]) / (0.5 * g.dy)
+    # tau_xz on the (i - 1/2, k - 1/2) edges (as in the periodic case)
+    txz = np.empty((nz + 1, ny, nx))
+    dwdx = (w - np.roll(w, 1, axis=2)) / g.dx
+    txz[1:-1] = 0.5 * (mux[1:] + mux[:-1]) * ((u[1:] - u[:-1]) / g.dzc[1:-1, None, None] + dwdx[1:-1])
+    txz[0] = mux[0] * (u[0] - 0.0) / (g.zc[0] - g.zf[0])
+    txz[-1] = mux[-1] * (0.0 - u[-1]) / (g.zf[-1] - g.zc[-1])
+    # tau_yz on the (j - 1/2, k - 1/2) edges, j = 0 .. ny, k = 0 .. nz
+    tyz = np.zeros((nz + 1, ny + 1, nx))
+    muz = np.zeros((nz + 1, ny, nx))                               # mean over the two cells in z
+    muz[1:-1] = 0.5 * (mu[1:] + mu[:-1])
+    myz = 0.5 * (muz[:, 1:] + muz[:, :-1])
+    dvdz = (v[1:] - v[:-1]) / g.dzc[1:-1, None, None]
+    tyz[1:-1, 1:-1] = myz[1:-1] * (dvdz[:, 1:] + (w[1:-1, 1:] - w[1:-1, :-1]) / g.dy)
+    tyz[1:-1, 0] = muz[1:-1, 0] * (w[1:-1, 0] - 0.0) / (0.5 * g.dy)
+    tyz[1:-1, -1] = muz[1:-1, -1] * (0.0 - w[1:-1, -1]) / (0.5 * g.dy)
+    my2 = 0.5 * (mu + np.roll(mu, 1, axis=1))                      # y faces between cells (row 0 unused)
+    tyz[0, 1:-1] = my2[0, 1:] * (v[0, 1:] - 0.0) / (g.zc[0] - g.zf[0])
+    tyz[-1, 1:-1] = my2[-1, 1:] * (0.0 - v[-1, 1:]) / (g.zf[-1] - g.zc[-1])
+    fx = ((txx - np.roll(txx, 1, axis=2)) / g.dx + (txy[:, 1:] - txy[:, :-1]) / g.dy
+          + (txz[1:] - txz[:-1]) / dzf)
+    fy = np.zeros((nz, ny, nx))
+    fy[:, 1:] = ((np.roll(txy[:, 1:-1], -1, axis=2) - txy[:, 1:-1]) / g.dx
+                 + (tyy[:, 1:] - tyy[:, :-1]) / g.dy + (tyz[1:, 1:-1] - tyz[:-1, 1:-1]) / dzf)
+    fz = np.zeros((nz + 1, ny, nx))
+    fz[1:-1] = ((np.roll(txz[1:-1], -1, axis=2) - txz[1:-1]) / g.dx
+                + (tyz[1:-1, 1:] - tyz[1:-1, :-1]) / g.dy
+                + (tzz[1:] - tzz[:-1]) / g.dzc[1:-1, None, None])
+    return fx, fy, fz
+
+
 def predictor_rhs(g, u, v, w, rho, mu, grav, force=None):
     """Eq. 32 without the surface-tension force of the VOF model (out of
     scope): RU = -C(u) + (1/rho_f)[div tau + f] + g, with f an optional
@@ -743,6 +803,8 @@ def predictor_rhs(g, u, v, w, rho, mu, grav, force=None):
     rw = -cz + vz / rz + grav[2]
     rw[0] = 0.0
     rw[-1] = 0.0
+    if g.ywalls:
+        rv[:, 0, :] = 0.0
     return ru, rv, rw
 
 
@@ -759,6 +821,8 @@ def predictor(g, u, v, w, rho, mu, grav, dt_new, dt_old=None, ru_prev=None, forc
     out = tuple(x + dt_new * (a * q - b * qp) for x, q, qp in zip((u, v, w), ru, ru_prev))
     out[2][0] = 0.0
     out[2][-1] = 0.0
+    if g.ywalls:
+        out[1][:, 0, :] = 0.0
     return out, ru
 
 

@@ -70,14 +70,18 @@ __device__ __forceinline__ double cell_rhs_b(const Geo& g, const double* __restr
 }
 
 // div(k grad T) at cell c: D(k_f G T) with k_f the arithmetic mean of the
-// two cells of a face, no flux through the z walls (Eqs. 30 and 34).
+// two cells of a face, no flux through the z walls, nor through the y walls
+// when y is bounded (Eqs. 30 and 34).
 __device__ __forceinline__ double cell_conduction(const Geo& g, const double* __restrict__ kc,
                                                   const double* __restrict__ T, size_t c) {
   const CellIdx x = cell_index(g, c);
   const size_t plane = (size_t)g.nx * g.ny;
   const double k0 = kc[c], t0 = T[c];
   double sx = 0.5 * (k0 + kc[x.cip]) * (T[x.cip] - t0) + 0.5 * (k0 + kc[x.cim]) * (T[x.cim] - t0);
-  double sy = 0.5 * (k0 + kc[x.cjp]) * (T[x.cjp] - t0) + 0.5 * (k0 + kc[x.cjm]) * (T[x.cjm] - t0);
+  // with walls in y no heat crosses the faces below row 0 and above row ny - 1
+  const bool yhi = !(g.ywall && x.j + 1 == g.ny), ylo = !(g.ywall && x.j == 0);
+  double sy = (yhi ? 0.5 * (k0 + kc[x.cjp]) * (T[x.cjp] - t0) : 0.0) +
+              (ylo ? 0.5 * (k0 + kc[x.cjm]) * (T[x.cjm] - t0) : 0.0);
   double sz = 0.0;
   if (x.k + 1 < g.nz) sz += 0.5 * (k0 + kc[c + plane]) * (T[c + plane] - t0) * g.inv_dzc[x.k + 1];
   if (x.k > 0) sz += 0.5 * (k0 + kc[c - plane]) * (T[c - plane] - t0) * g.inv_dzc[x.k];

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(64 * kXLines, 4) k_fftx512_inv(Geo g, const fl
   float2* tw = sm;
   float2* s1 = sm + L::TW;
   float2* s2 = s1 + L::S1;
-  for (int i = threadIdx.x; i < L::N; i += blockDim.x) tw[i] = twx[i];
+  r512_load_twiddles(tw, twx);
   __syncthreads();
   const bool lazy = sdelta != nullptr && st != nullptr;
   const bool fold = lazy && st->need_exact != 0;

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(64 * TX) k_ffty512(Geo g, const float2* __rest
   float2* tw = sm;
   float2* s1 = sm + L::TW;
   float2* s2 = s1 + L::S1;
-  for (int i = threadIdx.x; i < L::N; i += blockDim.x) tw[i] = twy[i];
+  r512_load_twiddles(tw, twy);
   const int nxh = g.nxh;
   const int ntx = (nxh + TX - 1) / TX;
   const int x = threadIdx.x % TX, j = threadIdx.x / TX;  // column in the tile, line thread 0..63

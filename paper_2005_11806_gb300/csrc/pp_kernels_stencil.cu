@@ -240,7 +240,10 @@ __global__ void k_thermo_partial(Geo g, const double* __restrict__ phi, const do
     const double dv = dxdy * g.dzf[x.k];
     const double wlo = (x.k == 0) ? 0.0 : w[c];
     const double whi = (x.k == g.nz - 1) ? 0.0 : w[c + plane];
-    const double div = (u[x.cip] - u[c]) / g.dx + (v[x.cjp] - v[c]) / g.dy + (whi - wlo) * g.inv_dzf[x.k];
+    // the wall row of v (walls in y) carries no flux, like the wall planes of w
+    const double vlo = (g.ywall && x.j == 0) ? 0.0 : v[c];
+    const double vhi = (g.ywall && x.j == g.ny - 1) ? 0.0 : v[x.cjp];
+    const double div = (u[x.cip] - u[c]) / g.dx + (vhi - vlo) / g.dy + (whi - wlo) * g.inv_dzf[x.k];
     a += f * cell_conduction(g, kc, T, c) * dv;
     b += f * div * dv;
     vg += f * dv;
@@ -293,7 +296,10 @@ __global__ void k_cell_divergence(Geo g, const double* __restrict__ u, const dou
   const size_t plane = (size_t)g.nx * g.ny, n = plane * g.nz;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
     const CellIdx x = cell_index(g, c);
-    D[c] = (u[x.cip] - u[c]) / g.dx + (v[x.cjp] - v[c]) / g.dy + (w[c + plane] - w[c]) * g.inv_dzf[x.k];
+    // walls in y: the wall row of v carries no flux
+    const double vlo = (g.ywall && x.j == 0) ? 0.0 : v[c];
+    const double vhi = (g.ywall && x.j == g.ny - 1) ? 0.0 : v[x.cjp];
+    D[c] = (u[x.cip] - u[c]) / g.dx + (vhi - vlo) / g.dy + (w[c + plane] - w[c]) * g.inv_dzf[x.k];
   }
 }
 
@@ -305,7 +311,12 @@ __global__ void k_cell_divergence(Geo g, const double* __restrict__ u, const dou
 // Newton-Stokes stress (normal parts at cell centres with the cell's mu,
 // shear parts at edges with the mean mu of the cells around the edge;
 // no-slip z walls: wall velocity zero, half-cell distance to the wall).
-// u* = u + dt (a RU - b RU_prev).  D: cell divergence.
+// With walls in y the y walls are no-slip too: the wall row of v is zero
+// (read as zero, written as zero), the edges on y = 0 (edge row 0) and
+// y = ly (edge row ny) carry the wall shear of u and w over half a cell and
+// no convective flux, and the edges where a y wall meets a z wall carry
+// nothing.  Edge rows are passed unwrapped (0 .. ny); periodic y wraps ny
+// to 0.  u* = u + dt (a RU - b RU_prev).  D: cell divergence.
 __global__ void k_predictor(Geo g, const double* __restrict__ u, const double* __restrict__ v,
                             const double* __restrict__ w, const double* __restrict__ rho,
                             const double* __restrict__ mu, const double* __restrict__ D,
@@ -316,6 +327,7 @@ __global__ void k_predictor(Geo g, const double* __restrict__ u, const double* _
                             double* __restrict__ vs, double* __restrict__ ws, double* __restrict__ ru,
                             double* __restrict__ rv, double* __restrict__ rw) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const bool ywall = g.ywall != 0;
   const size_t plane = (size_t)nx * ny, n = plane * nz;
   const double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
   const double two3 = 2.0 / 3.0;
@@ -324,17 +336,27 @@ __global__ void k_predictor(Geo g, const double* __restrict__ u, const double* _
     const int im = i == 0 ? nx - 1 : i - 1, ip = i + 1 == nx ? 0 : i + 1;
     const int jm = j == 0 ? ny - 1 : j - 1, jp = j + 1 == ny ? 0 : j + 1;
     auto at = [&](int ii, int jj, int kk) { return ((size_t)kk * ny + jj) * nx + ii; };
+    // v at the face row jj (0 .. ny - 1); the wall row reads as zero
+    auto vv = [&](int ii, int jj, int kk) { return (ywall && jj == 0) ? 0.0 : v[at(ii, jj, kk)]; };
     const double idzf = g.inv_dzf[k];
-    // mean mu over the four cells around an x-y edge (i'-1/2, j'-1/2) of layer kk
+    // is the edge row jj (0 .. ny) a y wall?
+    auto ywall_edge = [&](int jj) { return ywall && (jj == 0 || jj == ny); };
+    // mean mu over the four cells around an x-y edge (i'-1/2, j'-1/2) of layer kk (interior edge row)
     auto mxy = [&](int ii, int jj, int kk) {
       const int iim = ii == 0 ? nx - 1 : ii - 1, jjm = jj == 0 ? ny - 1 : jj - 1;
       return 0.25 * (mu[at(ii, jj, kk)] + mu[at(iim, jj, kk)] + mu[at(ii, jjm, kk)] + mu[at(iim, jjm, kk)]);
     };
-    // shear stress tau_xy at the edge (i'-1/2, j'-1/2) of layer kk
+    // shear stress tau_xy at the edge (i'-1/2, jj-1/2) of layer kk, jj in [0, ny]
     auto txy = [&](int ii, int jj, int kk) {
-      const int iim = ii == 0 ? nx - 1 : ii - 1, jjm = jj == 0 ? ny - 1 : jj - 1;
-      return mxy(ii, jj, kk) * ((u[at(ii, jj, kk)] - u[at(ii, jjm, kk)]) * idy +
-                                (v[at(ii, jj, kk)] - v[at(iim, jj, kk)]) * idx);
+      const int iim = ii == 0 ? nx - 1 : ii - 1;
+      if (ywall_edge(jj)) {  // no-slip y wall: u = 0 half a cell away, v = 0 along it
+        const int jr = jj == 0 ? 0 : ny - 1;
+        const double m = 0.5 * (mu[at(ii, jr, kk)] + mu[at(iim, jr, kk)]);
+        return (jj == 0 ? 2.0 : -2.0) * m * u[at(ii, jr, kk)] * idy;
+      }
+      const int jw = jj == ny ? 0 : jj, jjm = jw == 0 ? ny - 1 : jw - 1;
+      return mxy(ii, jw, kk) * ((u[at(ii, jw, kk)] - u[at(ii, jjm, kk)]) * idy +
+                                (vv(ii, jw, kk) - vv(iim, jw, kk)) * idx);
     };
     // tau_xz at the edge (i'-1/2, kk-1/2), kk in [0, nz]; tau_yz likewise
     auto txz = [&](int ii, int jj, int kk) {
@@ -348,59 +370,74 @@ __global__ void k_predictor(Geo g, const double* __restrict__ u, const double* _
       return m * ((u[at(ii, jj, kk)] - u[at(ii, jj, kk - 1)]) * g.inv_dzc[kk] +
                   (w[at(ii, jj, kk)] - w[at(iim, jj, kk)]) * idx);
     };
+    // tau_yz at the edge (jj-1/2, kk-1/2), jj in [0, ny], kk in [0, nz]
     auto tyz = [&](int ii, int jj, int kk) {
-      const int jjm = jj == 0 ? ny - 1 : jj - 1;
-      if (kk == 0) return 0.5 * (mu[at(ii, jj, 0)] + mu[at(ii, jjm, 0)]) * v[at(ii, jj, 0)] * 2.0 * g.inv_dzf[0];
+      if (ywall_edge(jj)) {  // no-slip y wall: w = 0 half a cell away, v = 0 along it
+        if (kk == 0 || kk == nz) return 0.0;  // a y wall meets a z wall
+        const int jr = jj == 0 ? 0 : ny - 1;
+        const double m = 0.5 * (mu[at(ii, jr, kk)] + mu[at(ii, jr, kk - 1)]);
+        return (jj == 0 ? 2.0 : -2.0) * m * w[at(ii, jr, kk)] * idy;
+      }
+      const int jw = jj == ny ? 0 : jj, jjm = jw == 0 ? ny - 1 : jw - 1;
+      if (kk == 0) return 0.5 * (mu[at(ii, jw, 0)] + mu[at(ii, jjm, 0)]) * vv(ii, jw, 0) * 2.0 * g.inv_dzf[0];
       if (kk == nz)
-        return -0.5 * (mu[at(ii, jj, nz - 1)] + mu[at(ii, jjm, nz - 1)]) * v[at(ii, jj, nz - 1)] * 2.0 *
+        return -0.5 * (mu[at(ii, jw, nz - 1)] + mu[at(ii, jjm, nz - 1)]) * vv(ii, jw, nz - 1) * 2.0 *
                g.inv_dzf[nz - 1];
-      const double m = 0.25 * (mu[at(ii, jj, kk)] + mu[at(ii, jjm, kk)] + mu[at(ii, jj, kk - 1)] +
+      const double m = 0.25 * (mu[at(ii, jw, kk)] + mu[at(ii, jjm, kk)] + mu[at(ii, jw, kk - 1)] +
                                mu[at(ii, jjm, kk - 1)]);
-      return m * ((v[at(ii, jj, kk)] - v[at(ii, jj, kk - 1)]) * g.inv_dzc[kk] +
-                  (w[at(ii, jj, kk)] - w[at(ii, jjm, kk)]) * idy);
+      return m * ((vv(ii, jw, kk) - vv(ii, jw, kk - 1)) * g.inv_dzc[kk] +
+                  (w[at(ii, jw, kk)] - w[at(ii, jjm, kk)]) * idy);
     };
-    // convective cross products at edges
-    auto fxy = [&](int ii, int jj, int kk) {  // u v at (i'-1/2, j'-1/2)
-      const int iim = ii == 0 ? nx - 1 : ii - 1, jjm = jj == 0 ? ny - 1 : jj - 1;
-      return 0.25 * (u[at(ii, jj, kk)] + u[at(ii, jjm, kk)]) * (v[at(ii, jj, kk)] + v[at(iim, jj, kk)]);
+    // convective cross products at edges (zero on the walls, where the
+    // wall-normal velocity vanishes)
+    auto fxy = [&](int ii, int jj, int kk) {  // u v at (i'-1/2, jj-1/2), jj in [0, ny]
+      if (ywall_edge(jj)) return 0.0;
+      const int jw = jj == ny ? 0 : jj;
+      const int iim = ii == 0 ? nx - 1 : ii - 1, jjm = jw == 0 ? ny - 1 : jw - 1;
+      return 0.25 * (u[at(ii, jw, kk)] + u[at(ii, jjm, kk)]) * (vv(ii, jw, kk) + vv(iim, jw, kk));
     };
     auto fxz = [&](int ii, int jj, int kk) {  // u w at (i'-1/2, kk-1/2); zero at the walls
       if (kk == 0 || kk == nz) return 0.0;
       const int iim = ii == 0 ? nx - 1 : ii - 1;
       return 0.25 * (u[at(ii, jj, kk)] + u[at(ii, jj, kk - 1)]) * (w[at(ii, jj, kk)] + w[at(iim, jj, kk)]);
     };
-    auto fyz = [&](int ii, int jj, int kk) {
-      if (kk == 0 || kk == nz) return 0.0;
-      const int jjm = jj == 0 ? ny - 1 : jj - 1;
-      return 0.25 * (v[at(ii, jj, kk)] + v[at(ii, jj, kk - 1)]) * (w[at(ii, jj, kk)] + w[at(ii, jjm, kk)]);
+    auto fyz = [&](int ii, int jj, int kk) {  // v w at (jj-1/2, kk-1/2), jj in [0, ny]
+      if (kk == 0 || kk == nz || ywall_edge(jj)) return 0.0;
+      const int jw = jj == ny ? 0 : jj, jjm = jw == 0 ? ny - 1 : jw - 1;
+      return 0.25 * (vv(ii, jw, kk) + vv(ii, jw, kk - 1)) * (w[at(ii, jw, kk)] + w[at(ii, jjm, kk)]);
     };
     const double Dc = D[c];
     // ---- x momentum at the u-face (i-1/2, j, k)
     {
       const size_t cm = at(im, j, k);
       const double uc0 = 0.5 * (u[c] + u[at(ip, j, k)]), ucm = 0.5 * (u[cm] + u[c]);
-      const double conv = (uc0 * uc0 - ucm * ucm) * idx + (fxy(i, jp, k) - fxy(i, j, k)) * idy +
+      const double conv = (uc0 * uc0 - ucm * ucm) * idx + (fxy(i, j + 1, k) - fxy(i, j, k)) * idy +
                           (fxz(i, j, k + 1) - fxz(i, j, k)) * idzf - u[c] * 0.5 * (Dc + D[cm]);
       const double t0 = mu[c] * (2.0 * (u[at(ip, j, k)] - u[c]) * idx - two3 * Dc);
       const double tm = mu[cm] * (2.0 * (u[c] - u[cm]) * idx - two3 * D[cm]);
-      double visc = (t0 - tm) * idx + (txy(i, jp, k) - txy(i, j, k)) * idy + (txz(i, j, k + 1) - txz(i, j, k)) * idzf;
+      double visc = (t0 - tm) * idx + (txy(i, j + 1, k) - txy(i, j, k)) * idy +
+                    (txz(i, j, k + 1) - txz(i, j, k)) * idzf;
       if (fx != nullptr) visc += fx[c];
       const double r = -conv + visc / (0.5 * (rho[c] + rho[cm])) + gx;
       us[c] = u[c] + dt * (a * r - (pu != nullptr ? b * pu[c] : 0.0));
       if (ru != nullptr) ru[c] = r;
     }
-    // ---- y momentum at the v-face (i, j-1/2, k)
-    {
+    // ---- y momentum at the v-face (i, j-1/2, k); with walls in y the wall row stays zero
+    if (ywall && j == 0) {
+      vs[c] = 0.0;
+      if (rv != nullptr) rv[c] = 0.0;
+    } else {
       const size_t cm = at(i, jm, k);
-      const double vc0 = 0.5 * (v[c] + v[at(i, jp, k)]), vcm = 0.5 * (v[cm] + v[c]);
+      const double vvc = vv(i, j, k), vvp = vv(i, jp, k), vvm = vv(i, jm, k);
+      const double vc0 = 0.5 * (vvc + vvp), vcm = 0.5 * (vvm + vvc);
       const double conv = (fxy(ip, j, k) - fxy(i, j, k)) * idx + (vc0 * vc0 - vcm * vcm) * idy +
-                          (fyz(i, j, k + 1) - fyz(i, j, k)) * idzf - v[c] * 0.5 * (Dc + D[cm]);
-      const double t0 = mu[c] * (2.0 * (v[at(i, jp, k)] - v[c]) * idy - two3 * Dc);
-      const double tm = mu[cm] * (2.0 * (v[c] - v[cm]) * idy - two3 * D[cm]);
+                          (fyz(i, j, k + 1) - fyz(i, j, k)) * idzf - vvc * 0.5 * (Dc + D[cm]);
+      const double t0 = mu[c] * (2.0 * (vvp - vvc) * idy - two3 * Dc);
+      const double tm = mu[cm] * (2.0 * (vvc - vvm) * idy - two3 * D[cm]);
       double visc = (txy(ip, j, k) - txy(i, j, k)) * idx + (t0 - tm) * idy + (tyz(i, j, k + 1) - tyz(i, j, k)) * idzf;
       if (fy != nullptr) visc += fy[c];
       const double r = -conv + visc / (0.5 * (rho[c] + rho[cm])) + gy;
-      vs[c] = v[c] + dt * (a * r - (pv != nullptr ? b * pv[c] : 0.0));
+      vs[c] = vvc + dt * (a * r - (pv != nullptr ? b * pv[c] : 0.0));
       if (rv != nullptr) rv[c] = r;
     }
     // ---- z momentum at the w-face (i, j, k-1/2), interior faces only
@@ -411,11 +448,11 @@ __global__ void k_predictor(Geo g, const double* __restrict__ u, const double* _
       const size_t cm = c - plane;
       const double wc0 = 0.5 * (w[c] + w[c + plane]), wcm = 0.5 * (w[cm] + w[c]);
       const double idzc = g.inv_dzc[k];
-      const double conv = (fxz(ip, j, k) - fxz(i, j, k)) * idx + (fyz(i, jp, k) - fyz(i, j, k)) * idy +
+      const double conv = (fxz(ip, j, k) - fxz(i, j, k)) * idx + (fyz(i, j + 1, k) - fyz(i, j, k)) * idy +
                           (wc0 * wc0 - wcm * wcm) * idzc - w[c] * 0.5 * (Dc + D[cm]);
       const double t0 = mu[c] * (2.0 * (w[c + plane] - w[c]) * idzf - two3 * Dc);
       const double tm = mu[cm] * (2.0 * (w[c] - w[cm]) * g.inv_dzf[k - 1] - two3 * D[cm]);
-      double visc = (txz(ip, j, k) - txz(i, j, k)) * idx + (tyz(i, jp, k) - tyz(i, j, k)) * idy + (t0 - tm) * idzc;
+      double visc = (txz(ip, j, k) - txz(i, j, k)) * idx + (tyz(i, j + 1, k) - tyz(i, j, k)) * idy + (t0 - tm) * idzc;
       if (fz != nullptr) visc += fz[c];
       const double r = -conv + visc / (0.5 * (rho[c] + rho[cm])) + gz;
       ws[c] = w[c] + dt * (a * r - (pw != nullptr ? b * pw[c] : 0.0));

@@ -24,26 +24,30 @@ struct R512 {
   static constexpr int S1 = N * TX;         // first exchange buffer [c][b][x]
   static constexpr int CS2 = 64 * TX + TX;  // second buffer: slab of one c, padded
   static constexpr int S2 = 8 * CS2;        // [c][g][f][x]
-  static constexpr int TW = N;              // twiddle table (cos, sin)(2 pi m / 512)
+  // twiddles, laid out so that a warp's reads are consecutive: T1[c][b] =
+  // w^{b c} (c < 8, b < 64) for the first stage, T2[r][f] = w^{8 f r} for
+  // the second; each entry copied from the (cos, sin)(2 pi m / 512) table
+  static constexpr int TW = 8 * 64 + 64;
   static constexpr size_t smem_bytes() { return (size_t)(TW + S1 + S2) * sizeof(float2); }
 };
 
-// v[r] *= w^{r q} for r = 1..7, with w^q, w^{2q}, w^{4q} read from the
-// table (index in units of 2 pi / 512) and the other powers formed by
-// products.
+// Fills the two twiddle tables of R512 from the 512-entry table `tw512`
+// (global memory); every thread of the block calls it, a barrier follows.
+__device__ __forceinline__ void r512_load_twiddles(float2* tw, const float2* __restrict__ tw512) {
+  for (int i = threadIdx.x; i < 8 * 64 + 64; i += blockDim.x) {
+    int m;
+    if (i < 512) m = (i >> 6) * (i & 63);               // T1[c][b]: b c
+    else m = 8 * ((i - 512) & 7) * ((i - 512) >> 3);    // T2[r][f]: 8 f r
+    tw[i] = tw512[m & 511];
+  }
+}
+
+// v[r] *= tab[r * stride + q] for r = 1..7 (the entry holds w^{r q'}, with
+// the direction's sign applied here).
 template <int DIR>
-__device__ __forceinline__ void r512_twiddle8(float2* v, const float2* __restrict__ tw, int q) {
-  const float2 w1 = tw_dir<DIR>(tw[q & 511]);
-  const float2 w2 = tw_dir<DIR>(tw[(2 * q) & 511]);
-  const float2 w4 = tw_dir<DIR>(tw[(4 * q) & 511]);
-  const float2 w3 = cmul<float>(w1, w2);
-  v[1] = cmul<float>(v[1], w1);
-  v[2] = cmul<float>(v[2], w2);
-  v[3] = cmul<float>(v[3], w3);
-  v[4] = cmul<float>(v[4], w4);
-  v[5] = cmul<float>(v[5], cmul<float>(w1, w4));
-  v[6] = cmul<float>(v[6], cmul<float>(w2, w4));
-  v[7] = cmul<float>(v[7], cmul<float>(w3, w4));
+__device__ __forceinline__ void r512_twiddle8(float2* v, const float2* __restrict__ tab, int stride, int q) {
+#pragma unroll
+  for (int r = 1; r < 8; ++r) v[r] = cmul<float>(v[r], tw_dir<DIR>(tab[r * stride + q]));
 }
 
 // The transform of the thread's line (see above); every thread of the block
@@ -58,7 +62,7 @@ __device__ __forceinline__ void r512_transform(float2 (&v)[8], float2 (&u)[8], f
                                                const float2* __restrict__ tw, int x, int j, F&& after_s1) {
   using L = R512<TX>;
   Dft<float, DIR, 8>::run(v);
-  r512_twiddle8<DIR>(v, tw, j);
+  r512_twiddle8<DIR>(v, tw, 64, j);
 #pragma unroll
   for (int c = 0; c < 8; ++c) s1[(c * 64 + j) * TX + x] = v[c];
   after_s1();
@@ -68,7 +72,7 @@ __device__ __forceinline__ void r512_transform(float2 (&v)[8], float2 (&u)[8], f
 #pragma unroll
     for (int e = 0; e < 8; ++e) u[e] = s1[(c * 64 + 8 * e + f) * TX + x];
     Dft<float, DIR, 8>::run(u);
-    r512_twiddle8<DIR>(u, tw, 8 * f);
+    r512_twiddle8<DIR>(u, tw + 512, 8, f);
 #pragma unroll
     for (int gg = 0; gg < 8; ++gg) s2[c * L::CS2 + (gg * 8 + f) * TX + x] = u[gg];
   }

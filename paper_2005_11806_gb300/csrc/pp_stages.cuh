@@ -131,7 +131,7 @@ __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast
 __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc, float* __restrict__ E,
                                                   const float* __restrict__ delta, int scale_rho,
                                                   bool const_scale, float rt_f, long row0, int rpb,
-                                                  float2* bufA, float& s2, float& s1) {
+                                                  float2* bufA, int seq_stride, float& s2, float& s1) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const long nrows = (long)nz * ny;
   const size_t plane = (size_t)nx * ny;
@@ -212,7 +212,7 @@ __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc,
       }
       rr[h] = r;
     }
-    float4* dst = reinterpret_cast<float4*>(bufA + (size_t)qp * nx + i);
+    float4* dst = reinterpret_cast<float4*>(bufA + (size_t)qp * seq_stride + i);
     dst[0] = make_float4(rr[0].x, rr[1].x, rr[0].y, rr[1].y);
     dst[1] = make_float4(rr[0].z, rr[1].z, rr[0].w, rr[1].w);
   }
@@ -230,27 +230,20 @@ __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc,
 //   FP32 as sum_nb c_nb (delta_nb - delta_c) (no diagonal needed).
 // Two real rows are packed into one complex sequence (re = even row,
 // im = odd row), transformed together and separated afterwards.
+// The rows [row0, row0 + rpb) of the residual (the first step of the stage
+// below) into bufA: complex sequence q = (row - row0) / 2 at element offset
+// q * seq_stride (re = even row, im = odd row); s2, s1 accumulate e^2 and
+// |e| of the thread's cells.  Every thread of the block calls it.
 template <typename T>
-__device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx,
-                                                 const C2<T>* __restrict__ twx,
-                                                 const double* __restrict__ b,
-                                                 const double* __restrict__ rho,
-                                                 const double* __restrict__ p, int mode, int p_zero,
-                                                 int scale_rho, C2<T>* __restrict__ spec,
-                                                 double* __restrict__ red, int rpb, int blk,
-                                                 bool need_exact, float* __restrict__ E,
-                                                 const float* __restrict__ delta,
-                                                 unsigned char* smem_raw) {
-  __shared__ double shred[32];
-  const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
+__device__ __forceinline__ void resid_rows(const Geo& g, const Faces& fc, const double* __restrict__ b,
+                                           const double* __restrict__ rho, const double* __restrict__ p, int mode,
+                                           int p_zero, int scale_rho, long row0, int rpb, bool need_exact,
+                                           float* __restrict__ E, const float* __restrict__ delta, C2<T>* bufA,
+                                           int seq_stride, T& s2, T& s1) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
   const bool update = (E != nullptr) && !p_zero && !need_exact;
-  const int nseq = rpb >> 1;
-  C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
-  C2<T>* bufB = bufA + (size_t)nseq * nx;
   const int nrows = nz * ny;
-  const long row0 = (long)blk * rpb;
   const size_t plane = (size_t)ny * nx;
-  T s2 = (T)0, s1 = (T)0;
   // constant scaling of Methods I and II (one device scalar for all cells)
   const bool const_scale = fc.rho_tilde != nullptr;
   const double rt = (const_scale && mode != 0) ? *fc.rho_tilde : 0.0;
@@ -260,20 +253,12 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
   const int rows_par = blockDim.x / tpr;
   const int qoff = threadIdx.x / tpr, i0 = threadIdx.x - qoff * tpr;
   const bool vec = update && sizeof(T) == sizeof(float) && (nx & 3) == 0;
-  // FP32 fast transform: buffer A, buffer B (written padded by the first
-  // pass: fft_pad_elems), then the twiddle table
-  constexpr bool F32 = std::is_same<T, float>::value;
-  const int twb = nseq * nx + fft_pad_elems(nseq * nx);
-  const bool fast = F32 && fft_smem_shape(nx, nseq, false);
-  if constexpr (F32) {
-    if (fast) load_twiddles_smem(twx, nx, twb);
-  }
   if (vec) {
     float a2 = 0.f, a1 = 0.f;
     resid_update_vec4(g, fc, E, delta, scale_rho, const_scale, rt_f, row0, rpb,
-                      reinterpret_cast<float2*>(bufA), a2, a1);
-    s2 = (T)a2;
-    s1 = (T)a1;
+                      reinterpret_cast<float2*>(bufA), seq_stride, a2, a1);
+    s2 += (T)a2;
+    s1 += (T)a1;
   }
   for (int q = qoff; !vec && q < rpb && qoff < rows_par; q += rows_par) {
     const int row = (int)row0 + q;
@@ -342,10 +327,40 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
           }
         }
       }
-      C2<T>& z = bufA[(size_t)(q >> 1) * nx + i];
+      C2<T>& z = bufA[(size_t)(q >> 1) * seq_stride + i];
       if (q & 1) z.y = r; else z.x = r;
     }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx,
+                                                 const C2<T>* __restrict__ twx,
+                                                 const double* __restrict__ b,
+                                                 const double* __restrict__ rho,
+                                                 const double* __restrict__ p, int mode, int p_zero,
+                                                 int scale_rho, C2<T>* __restrict__ spec,
+                                                 double* __restrict__ red, int rpb, int blk,
+                                                 bool need_exact, float* __restrict__ E,
+                                                 const float* __restrict__ delta,
+                                                 unsigned char* smem_raw) {
+  __shared__ double shred[32];
+  const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
+  const int nseq = rpb >> 1;
+  C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* bufB = bufA + (size_t)nseq * nx;
+  const int nrows = nz * ny;
+  const long row0 = (long)blk * rpb;
+  T s2 = (T)0, s1 = (T)0;
+  // FP32 fast transform: buffer A, buffer B (written padded by the first
+  // pass: fft_pad_elems), then the twiddle table
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const int twb = nseq * nx + fft_pad_elems(nseq * nx);
+  const bool fast = F32 && fft_smem_shape(nx, nseq, false);
+  if constexpr (F32) {
+    if (fast) load_twiddles_smem(twx, nx, twb);
+  }
+  resid_rows<T>(g, fc, b, rho, p, mode, p_zero, scale_rho, row0, rpb, need_exact, E, delta, bufA, nx, s2, s1);
   if (mode != 0) {
     // block partial sums of e^2 and |e|: in the arithmetic's own precision
     // (FP32 shuffles on mixed plans: the FP64 pipe is the scarce one)

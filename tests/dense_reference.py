@@ -90,10 +90,10 @@ def divergence_loops(nx, ny, nz, lx, ly, zf, u, v, w, ywalls=False):
     return out
 
 
-def assemble_conduction(nx, ny, nz, lx, ly, zf, kc):
+def assemble_conduction(nx, ny, nz, lx, ly, zf, kc, ywalls=False):
     """Matrix of T -> D(k_f G T) with k_f the arithmetic mean of the two
     cells of a face (kc indexed [k][j][i]); no flux through the z walls,
-    periodic x and y."""
+    periodic x, and y periodic or (ywalls) bounded by walls with no flux."""
     dx, dy = lx / nx, ly / ny
     dzf, zc = metrics(nz, zf)
     n = nx * ny * nz
@@ -111,6 +111,8 @@ def assemble_conduction(nx, ny, nz, lx, ly, zf, kc):
                     A[r, idx(i + di, j, k)] += kf / (dx * dx)
                     A[r, r] -= kf / (dx * dx)
                 for dj in (+1, -1):
+                    if ywalls and not 0 <= j + dj < ny:
+                        continue  # adiabatic y wall
                     kf = 0.5 * (kc[k][j][i] + kc[k][(j + dj) % ny][i])
                     A[r, idx(i, j + dj, k)] += kf / (dy * dy)
                     A[r, r] -= kf / (dy * dy)

@@ -48,8 +48,8 @@ def _state(w, seed):
     return rho, mu, prev, force
 
 
-def _gpu(pp, w, rho, mu, grav, dt_new, dt_old=0.0, prev=None, force=None):
-    plan = pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, float(w.zf[-1] - w.zf[0]), zfaces=w.zf)
+def _gpu(pp, w, rho, mu, grav, dt_new, dt_old=0.0, prev=None, force=None, ywalls=False):
+    plan = pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, float(w.zf[-1] - w.zf[0]), zfaces=w.zf, ywalls=ywalls)
     out = [torch.empty(w.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
     out.append(torch.empty((w.nz + 1, w.ny, w.nx), dtype=torch.float64, device="cuda"))
     ru = [torch.empty_like(t) for t in out]
@@ -74,6 +74,30 @@ def test_predictor_vs_oracle(pp, dims, stretched, ab2):
     errs = [_rel(a, b) for a, b in zip(out + ru, (ue, ve, we) + tuple(rue))]
     print("predictor vs oracle:", errs)
     assert max(errs) < TOL
+    assert np.all(out[2][0] == 0.0) and np.all(out[2][-1] == 0.0)
+
+
+@pytest.mark.parametrize("dims,ab2", [((24, 16, 18), True), ((40, 30, 25), False)])
+def test_predictor_with_walls_in_y_vs_oracle(pp, dims, ab2):
+    """No-slip walls in y (a duct, stretched z): u*, v*, w* and RU against
+    the oracle's walled-y predictor (itself pinned by Poiseuille profiles
+    and its reduction to the periodic stencil away from the walls).  A
+    nonzero wall row of v^n is read as zero; the wall row of v* and of RU_y
+    is written as zero."""
+    nx, ny, nz = dims
+    w = wl.channel_bubble_case(nx, ny, nz, seed=1206, rho_ratio=1000.0, stretched=True)
+    g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf, ywalls=True)
+    rho, mu, prev, force = _state(w, 1107)
+    w.vs[:, 0, :] = 0.4
+    grav = (0.2, 0.3, -9.81)
+    kw = dict(dt_old=1e-3, prev=prev) if ab2 else {}
+    out, ru = _gpu(pp, w, rho, mu, grav, 1.3e-3, force=force, ywalls=True, **kw)
+    (ue, ve, we), rue = orc.predictor(g, w.us, w.vs, w.ws, rho, mu, grav, 1.3e-3,
+                                      dt_old=1e-3 if ab2 else None, ru_prev=prev if ab2 else None, force=force)
+    errs = [_rel(a, b) for a, b in zip(out + ru, (ue, ve, we) + tuple(rue))]
+    print("walled-y predictor vs oracle:", errs)
+    assert max(errs) < TOL
+    assert np.all(out[1][:, 0, :] == 0.0) and np.all(ru[1][:, 0, :] == 0.0)
     assert np.all(out[2][0] == 0.0) and np.all(out[2][-1] == 0.0)
 
 

@@ -70,6 +70,27 @@ def test_p0_rate_and_source_vs_oracle(pp, dims, stretched):
     assert rph == rp
 
 
+@pytest.mark.parametrize("dims", [(24, 16, 18), (40, 30, 25)])
+def test_p0_rate_and_source_with_walls_in_y(pp, dims):
+    """Walls in y (a duct, stretched z): the rate of p0 and S against the
+    oracle, whose conduction has no flux through the y walls and whose
+    divergence reads the wall row of v as zero (set to 0.7 here, ignored)."""
+    nx, ny, nz = dims
+    w = wl.channel_bubble_case(nx, ny, nz, seed=1204, rho_ratio=1000.0, stretched=True)
+    g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf, ywalls=True)
+    T, kc = _fields(w, 1105)
+    vs = w.vs.copy()
+    vs[:, 0, :] = 0.7
+    plan = pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, float(w.zf[-1] - w.zf[0]), zfaces=w.zf, ywalls=True)
+    gamma, p0 = 1.4, 0.95
+    rp = pp.pressure_p0_rate(plan.handle, dev(w.phi), dev(kc), dev(T), dev(w.us), dev(vs), dev(w.ws), p0, gamma)
+    rp0 = orc.p0_rate(g, w.phi, kc, T, w.us, vs, w.ws, p0, gamma)
+    assert abs(rp - rp0) <= TOL * max(abs(rp0), 1e-300) * 10
+    S = torch.empty(w.shape, dtype=torch.float64, device="cuda")
+    pp.pressure_divergence_source(plan.handle, dev(w.phi), dev(kc), dev(T), p0, gamma, 0.3 * rp, S)
+    assert _rel(host(S), orc.divergence_source(g, w.phi, kc, T, p0, gamma, 0.3 * rp)) < TOL
+
+
 def test_source_feeds_the_projection(pp):
     """S from Eq. 34 is the divergence the projection then imposes:
     D u^{n+1} = S_c to 1e-12 (oracle divergence)."""

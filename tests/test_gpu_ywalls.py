@@ -209,24 +209,9 @@ def test_ywalls_host_pointers_and_wall_input_ignored(pp):
         assert np.array_equal(x, y)
 
 
-def test_ywalls_unsupported_calls(pp):
-    w, rho = _case(16, 12, 10)
-    g = _grid(w)
-    plan = _plan(pp, g)
-    one = dev(np.ones(w.shape))
-    wz = dev(np.zeros((w.nz + 1, w.ny, w.nx)))
-    out = [torch.empty(w.shape, dtype=torch.float64, device="cuda") for _ in range(2)] + [wz.clone()]
-    calls = [
-        lambda: pp.pressure_p0_rate(plan.handle, one, one, one, one, one, wz, 1.0, 1.4),
-        lambda: pp.pressure_divergence_source(plan.handle, one, one, one, 1.0, 1.4, 0.0, out[0]),
-        lambda: pp.pressure_predictor(plan.handle, one, one, wz, one, one, (0, 0, 0), 1e-3, out),
-    ]
-    for call in calls:
-        with pytest.raises(pp.PressureError) as e:
-            call()
-        assert e.value.code == pp.PP_ERR_UNSUPPORTED
+def test_ywalls_odd_ny_is_refused(pp):
     with pytest.raises(pp.PressureError) as e:
-        pp.Plan(16, 9, 8, 1.0, 1.0, 1.0, ywalls=True)   # odd ny
+        pp.Plan(16, 9, 8, 1.0, 1.0, 1.0, ywalls=True)   # odd ny: the cosine transform by an even FFT
     assert e.value.code == pp.PP_ERR_UNSUPPORTED
 
 

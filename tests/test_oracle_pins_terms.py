@@ -445,3 +445,147 @@ def test_planted_ywall_gradient_kept_is_caught(monkeypatch):
     monkeypatch.setattr(orc, "_zero_ywall_row", lambda g, gv: np.array(gv, dtype=np.float64, copy=True))
     with pytest.raises(AssertionError):
         test_ywalls_adjoint_central_differences_and_dot_product()
+
+
+# --- the divergence source with walls in y (Eqs. 30, 34) ---------------------
+
+def test_ywalls_conduction_matches_dense_assembly_and_conserves_heat():
+    """With walls in y the conduction operator D(k_f G T) equals the matrix
+    assembled entry by entry with no flux through the y walls (variable k,
+    stretched z), and a closed duct full of gas loses no heat:
+    sum div(k grad T) dV = 0, so dp0/dt = 0 with no dilatation (Eq. 30)."""
+    nx, ny, nz = 6, 5, 7
+    zf = wl.tanh_zfaces(nz, 0.6, 1.5)
+    g = orc.Grid(nx, ny, nz, 1.0, 0.8, zf, ywalls=True)
+    rng = np.random.default_rng(71)
+    kc = rng.uniform(0.5, 3.0, g.shape)
+    T = rng.standard_normal(g.shape)
+    A = dr.assemble_conduction(nx, ny, nz, 1.0, 0.8, zf, kc, ywalls=True)
+    cond = orc.conduction(g, kc, T)
+    assert _rel(cond.ravel(), A @ T.ravel()) < 1e-13
+    dv = g.cell_volume()
+    assert abs(np.sum(cond * dv)) <= 1e-13 * np.sum(np.abs(cond) * dv)
+    zero = np.zeros(g.shape)
+    rp = orc.p0_rate(g, np.ones(g.shape), kc, T, zero, zero, np.zeros((nz + 1, ny, nx)), 1.0, 1.4)
+    assert abs(rp) <= 1e-13 * (1.4 / orc.gas_volume(g, np.ones(g.shape))) * np.sum(np.abs(cond) * dv)
+
+
+def test_planted_open_y_wall_in_conduction_is_caught(monkeypatch):
+    """Heat flowing through the y walls (the periodic faces used by both G
+    and D, i.e. a periodic y)."""
+    orig_g, orig_d = orc.gradient, orc.divergence
+
+    def periodic(g):
+        return orc.Grid(g.nx, g.ny, g.nz, g.lx, g.ly, g.zf, ywalls=False)
+    monkeypatch.setattr(orc, "gradient", lambda g, p: orig_g(periodic(g), p))
+    monkeypatch.setattr(orc, "divergence", lambda g, u, v, w: orig_d(periodic(g), u, v, w))
+    with pytest.raises(AssertionError):
+        test_ywalls_conduction_matches_dense_assembly_and_conserves_heat()
+
+
+# --- the momentum predictor with walls in y (Eqs. 29, 32) --------------------
+
+def _ygrid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0):
+    return orc.Grid(nx, ny, nz, lx, ly, wl.uniform_zfaces(nz, lz), ywalls=True)
+
+
+def test_ywalls_poiseuille_profiles_give_the_wall_closed_form():
+    """No-slip y walls.  u = y (ly - y) at the cell centres (zero on both
+    walls), constant mu: the second difference is exact for a quadratic, so
+    div tau = -2 mu in every row off the walls; in the two wall rows the
+    shear at the wall is mu u_0 / (dy/2) = mu (ly - dy/2) while the exact
+    slope is ly, and the discrete force is exactly -1.5 mu there (layers
+    off the z walls, whose shear adds to the two layers next to them).  The
+    same for w = y (ly - y) on the z faces away from the z walls.  No convection
+    in either.  Fixes the half-cell wall distance, the wall velocity and
+    both walls' edge rows."""
+    nx, ny, nz, mu, ly = 4, 10, 8, 0.7, 1.3
+    g = _ygrid(nx, ny, nz, 1.0, ly, 0.9)
+    yc = (np.arange(ny) + 0.5) * g.dy
+    prof = yc * (ly - yc)
+    expect = np.full(ny, -2.0 * mu)
+    expect[0] = expect[-1] = -1.5 * mu
+    zero = np.zeros(g.shape)
+    wz = np.zeros((nz + 1, ny, nx))
+    u = _bcast(prof[None, :, None], g.shape)
+    fx, fy, fz = orc.viscous(g, np.full(g.shape, mu), u, zero, wz)
+    # layers next to the z walls also feel the z-wall shear
+    assert np.allclose(fx[1:-1], _bcast(expect[None, :, None], fx[1:-1].shape), rtol=1e-12, atol=1e-12)
+    assert np.abs(fy).max() < 1e-12 and np.abs(fz).max() < 1e-12
+    cx, cy, cz = orc.convection(g, u, zero, wz)
+    assert max(np.abs(cx).max(), np.abs(cy).max(), np.abs(cz).max()) < 1e-13
+    w = np.zeros((nz + 1, ny, nx))
+    w[1:-1] = prof[None, :, None]
+    fx, fy, fz = orc.viscous(g, np.full(g.shape, mu), zero, zero, w)
+    assert np.allclose(fz[2:-2], _bcast(expect[None, :, None], fz[2:-2].shape), rtol=1e-12, atol=1e-12)
+    assert np.abs(fx).max() < 1e-12
+
+
+def test_ywalls_compressive_mode_and_wall_row():
+    """v = sin(pi j / ny) on the y faces (zero on both walls), nothing else
+    moving: C_y off the wall row is the compressive closed form
+    sin(4h) sin(2 theta) / (4 dy), h = pi / (2 ny); the wall row of C_y, of
+    RU_y and of the predicted v is zero."""
+    nx, ny, nz = 4, 12, 5
+    g = _ygrid(nx, ny, nz, 1.0, 0.9, 0.7)
+    th = np.pi * np.arange(ny) / ny
+    v = _bcast(np.sin(th)[None, :, None], g.shape)
+    zero = np.zeros(g.shape)
+    wz = np.zeros((nz + 1, ny, nx))
+    cx, cy, cz = orc.convection(g, zero, v, wz)
+    ref = _bcast(_compressive_closed_form(ny, g.dy)(th, np.pi / (2 * ny))[None, :, None], g.shape)
+    assert _rel(cy[:, 1:], ref[:, 1:]) < 1e-12
+    assert np.all(cy[:, 0] == 0.0) and np.abs(cx).max() < 1e-13 and np.abs(cz).max() < 1e-13
+    rho = np.full(g.shape, 2.0)
+    (us, vs, ws), ru = orc.predictor(g, zero, v, wz, rho, np.full(g.shape, 0.1), (0.0, 1.0, 0.0), 1e-3)
+    assert np.all(vs[:, 0] == 0.0) and np.all(ru[1][:, 0] == 0.0)
+
+
+def test_planted_ywall_shear_mistakes_are_caught(monkeypatch):
+    """A full cell (not half a cell) to the y wall, and free-slip y walls."""
+    orig = orc._viscous_ywalls
+
+    def full_cell(g, mu, u, v, w):
+        fx, fy, fz = orig(g, mu, u, v, w)
+        # the wall rows' shear halved: as if the wall were dy away
+        mux = 0.5 * (mu + np.roll(mu, 1, axis=2))
+        fx = fx.copy()
+        fx[:, 0] -= 0.5 * mux[:, 0] * u[:, 0] / (0.5 * g.dy) / g.dy
+        fx[:, -1] -= 0.5 * mux[:, -1] * u[:, -1] / (0.5 * g.dy) / g.dy
+        return fx, fy, fz
+
+    def free_slip(g, mu, u, v, w):
+        fx, fy, fz = orig(g, mu, u, v, w)
+        mux = 0.5 * (mu + np.roll(mu, 1, axis=2))
+        fx = fx.copy()
+        fx[:, 0] += mux[:, 0] * u[:, 0] / (0.5 * g.dy) / g.dy
+        fx[:, -1] += mux[:, -1] * u[:, -1] / (0.5 * g.dy) / g.dy
+        return fx, fy, fz
+    for planted in (full_cell, free_slip):
+        monkeypatch.setattr(orc, "_viscous_ywalls", planted)
+        with pytest.raises(AssertionError):
+            test_ywalls_poiseuille_profiles_give_the_wall_closed_form()
+
+
+def test_ywalls_predictor_terms_reduce_to_periodic_away_from_the_walls():
+    """Fields that vanish in the two rows next to each y wall never reach the
+    walls: the walled-y convection and viscous terms must then equal the
+    periodic ones everywhere (variable mu, stretched z).  Checks the interior
+    indexing of the walled code (edge rows, means of mu) against the pinned
+    periodic operators."""
+    nx, ny, nz = 5, 10, 6
+    zf = wl.tanh_zfaces(nz, 0.7, 1.5)
+    gw_ = orc.Grid(nx, ny, nz, 1.0, 0.9, zf, ywalls=True)
+    gp = orc.Grid(nx, ny, nz, 1.0, 0.9, zf)
+    rng = np.random.default_rng(81)
+    u, v = rng.standard_normal(gp.shape), rng.standard_normal(gp.shape)
+    w = rng.standard_normal((nz + 1, ny, nx))
+    w[0] = w[-1] = 0.0
+    for a in (u, v, w):
+        a[:, :2] = 0.0
+        a[:, -2:] = 0.0
+    v[:, 2] = 0.0   # the face below row 2 borders row 1
+    mu = rng.uniform(0.1, 1.0, gp.shape)
+    for fn in (lambda g: orc.convection(g, u, v, w), lambda g: orc.viscous(g, mu, u, v, w)):
+        for a, b in zip(fn(gw_), fn(gp)):
+            assert np.allclose(a, b, rtol=1e-13, atol=1e-13 * np.abs(b).max())
