@@ -132,27 +132,33 @@ __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc,
                                                   const float* __restrict__ delta, int scale_rho,
                                                   bool const_scale, float rt_f, long row0, int rpb,
                                                   float2* bufA, int seq_stride, float& s2, float& s1) {
+  // 32-bit cell offsets (grids keep nx ny (nz + 1) below 2^31); the block's
+  // first row is split into (layer, row in layer) once, the others step
+  // from it (no 64-bit division per cell group)
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const long nrows = (long)nz * ny;
-  const size_t plane = (size_t)nx * ny;
+  const int nrows = nz * ny;
+  const unsigned plane = (unsigned)nx * ny;
   const int t4 = nx >> 2;
   const int npairs = rpb >> 1;
   const int lg4 = ((t4 & (t4 - 1)) == 0) ? 31 - __clz(t4) : -1;
+  const int r0 = (int)row0;
+  const int k0 = r0 / ny, j0 = r0 - k0 * ny;
   for (int w = threadIdx.x; w < npairs * t4; w += blockDim.x) {
     const int qp = lg4 >= 0 ? (w >> lg4) : w / t4;
     const int i = (w - qp * t4) << 2;
     float4 rr[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const long row = row0 + 2 * qp + h;
+      const int row = r0 + 2 * qp + h;
       float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
       if (row < nrows) {
-        const int k = (int)(row / ny), j = (int)(row - (long)k * ny);
+        int k = k0, j = j0 + 2 * qp + h;
+        while (j >= ny) { j -= ny; ++k; }
         const int jp = (j + 1 == ny) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
-        const size_t rowoff = (size_t)row * nx;
-        const size_t kp = (size_t)k * plane;
-        const size_t c = rowoff + i;
-        const size_t cyp = kp + (size_t)jp * nx + i, cym = kp + (size_t)jm * nx + i;
+        const unsigned rowoff = (unsigned)row * nx;
+        const unsigned kp = (unsigned)k * plane;
+        const unsigned c = rowoff + i;
+        const unsigned cyp = kp + (unsigned)jp * nx + i, cym = kp + (unsigned)jm * nx + i;
         const int il = (i == 0) ? nx - 1 : i - 1, ir = (i + 4 == nx) ? 0 : i + 4;
         const float4 d = ld4(delta + c);
         const float dl = delta[rowoff + il], dr = delta[rowoff + ir];
@@ -212,7 +218,7 @@ __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc,
       }
       rr[h] = r;
     }
-    float4* dst = reinterpret_cast<float4*>(bufA + (size_t)qp * seq_stride + i);
+    float4* dst = reinterpret_cast<float4*>(bufA + qp * seq_stride + i);
     dst[0] = make_float4(rr[0].x, rr[1].x, rr[0].y, rr[1].y);
     dst[1] = make_float4(rr[0].z, rr[1].z, rr[0].w, rr[1].w);
   }
