@@ -205,25 +205,43 @@ __global__ void __launch_bounds__(kThreadsZ, 1) k_zgemm(float* spec, long long n
       issue_copy(r);
     }
   };
-  auto convert_b = [&](int kc) {  // all threads; every load issued before use
-    constexpr int PER = kTileN * kChunkK / kThreadsZ;
+  // B chunk kc of the first product: levels kc*64 .. +64 of the tile's
+  // columns, split into BF16 hi and lo.  Thread (n, group) takes 8
+  // consecutive levels of column n at a time, so each half of the split is
+  // one 16-byte shared store into the K-major core layout (8 k-values of a
+  // row are contiguous there): a quarter-warp's stores fill one 128-byte
+  // line, free of bank conflicts.  Every load is issued before use.
+  auto convert_b = [&](int kc) {  // all threads
+    constexpr int GROUPS = kChunkK / 8;                 // 8 groups of 8 levels
+    constexpr int GPT = GROUPS * kTileN / kThreadsZ;    // groups per thread: 4
     unsigned char* sB = sB0 + (kc & 1) * kChunkBytesB;
-    const int n = tid & (kTileN - 1), kl0 = tid / kTileN;
+    const int n = tid & (kTileN - 1), g0 = tid / kTileN;
     const long long col = col0 + n;
-    float x[PER];
+    float x[GPT][8];
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int lev = kc * kChunkK + kl0 + u * (kThreadsZ / kTileN);
-      x[u] = (lev < nz && col < ncols) ? spec[(long long)lev * ncols + col] : 0.f;
+    for (int m = 0; m < GPT; ++m) {
+      const int grp = g0 + m * (kThreadsZ / kTileN);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int lev = kc * kChunkK + grp * 8 + e;
+        x[m][e] = (lev < nz && col < ncols) ? spec[(long long)lev * ncols + col] : 0.f;
+      }
     }
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int kl = kl0 + u * (kThreadsZ / kTileN);
-      __nv_bfloat16_raw hi, lo;
-      split_bf16(x[u], hi, lo);
-      const uint32_t o = core_off(n, kl, 1024u);
-      *reinterpret_cast<__nv_bfloat16_raw*>(sB + o) = hi;
-      *reinterpret_cast<__nv_bfloat16_raw*>(sB + kChunkBytesB / 2 + o) = lo;
+    for (int m = 0; m < GPT; ++m) {
+      const int grp = g0 + m * (kThreadsZ / kTileN);
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        __nv_bfloat16_raw h0, l0, h1, l1;
+        split_bf16(x[m][e], h0, l0);
+        split_bf16(x[m][e + 1], h1, l1);
+        hi[e >> 1] = (uint32_t)h0.x | ((uint32_t)h1.x << 16);
+        lo[e >> 1] = (uint32_t)l0.x | ((uint32_t)l1.x << 16);
+      }
+      const uint32_t o = core_off(n, grp * 8, 1024u);
+      *reinterpret_cast<uint4*>(sB + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(sB + kChunkBytesB / 2 + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     fence_async_smem();
   };
