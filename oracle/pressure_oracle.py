@@ -22,7 +22,13 @@ grid, velocities on faces, scalar fields at cell centres):
 * with ``ywalls`` the y direction is bounded by two no-penetration walls
   instead of being periodic.  ``v`` keeps its ``[nz][ny][nx]`` shape: row j
   is still the face at ``j - 1/2``, and row 0 stands for both walls
-  (``y = 0`` and ``y = ly``), whose normal velocity is zero.
+  (``y = 0`` and ``y = ly``), whose normal velocity is zero;
+* a bounded y may be stretched: ``yf`` holds the ny + 1 face coordinates,
+  ``dyf[j]`` is the width of row j and ``dyc[j]`` the distance between the
+  centres that share the y-face j (j = 1 .. ny - 1).  The y step of the
+  eigenexpansion solve is then the eigenbasis of the y part of L, found
+  numerically (Sec. 3.3.1 needs only homogeneous conditions, not uniform
+  spacing).
 
 Readings of points the paper leaves open:
 
@@ -62,6 +68,7 @@ import os
 
 import numpy as np
 import scipy.fft as sfft
+import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
@@ -85,9 +92,10 @@ class Grid:
     """MAC grid: nx x ny cells of uniform width in x and y, nz cells in z with
     face coordinates ``zf`` (length nz + 1, increasing).  Sec. 3 uses uniform
     spacing; a stretched ``zf`` is allowed.  x is periodic, z has walls, y is
-    periodic unless ``ywalls``."""
+    periodic unless ``ywalls``.  With ``ywalls``, ``yf`` (ny + 1 increasing
+    face coordinates spanning ``ly``) makes the y spacing non-uniform too."""
 
-    def __init__(self, nx, ny, nz, lx, ly, zf, ywalls=False):
+    def __init__(self, nx, ny, nz, lx, ly, zf, ywalls=False, yf=None):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.ywalls = bool(ywalls)
         self.lx, self.ly = float(lx), float(ly)
@@ -97,6 +105,20 @@ class Grid:
         self.zf = zf
         self.dx = self.lx / self.nx
         self.dy = self.ly / self.ny
+        self.ystretched = yf is not None
+        if self.ystretched:
+            yf = np.asarray(yf, dtype=np.float64)
+            if not self.ywalls:
+                raise ValueError("a stretched y needs walls in y")
+            if yf.shape != (self.ny + 1,) or np.any(np.diff(yf) <= 0):
+                raise ValueError("yf must hold ny + 1 increasing face coordinates")
+            if abs((yf[-1] - yf[0]) - self.ly) > 1e-12 * self.ly:
+                raise ValueError("yf must span ly")
+            self.yf = yf
+            self.dyf = yf[1:] - yf[:-1]                 # width of row j
+            yc = 0.5 * (yf[1:] + yf[:-1])
+            self.dyc = np.zeros(self.ny)                # centre distance across y-face j
+            self.dyc[1:] = yc[1:] - yc[:-1]             # (face 0: the walls)
         self.dzf = zf[1:] - zf[:-1]                     # width of cell k
         self.zc = 0.5 * (zf[1:] + zf[:-1])              # centre of cell k
         self.dzc = np.zeros(self.nz + 1)                # centre distance across z-face k
@@ -109,6 +131,8 @@ class Grid:
 
     def cell_volume(self):
         """Delta V of every cell, broadcastable to the cell shape."""
+        if self.ystretched:
+            return (self.dx * self.dyf)[None, :, None] * self.dzf[:, None, None]
         return (self.dx * self.dy * self.dzf)[:, None, None]
 
 
@@ -125,8 +149,9 @@ def divergence(g, u, v, w):
     if g.ywalls:
         v = np.array(v, dtype=np.float64, copy=True)
         v[:, 0, :] = 0.0
+    dyf = g.dyf[None, :, None] if g.ystretched else g.dy
     return ((np.roll(u, -1, axis=2) - u) / g.dx
-            + (np.roll(v, -1, axis=1) - v) / g.dy
+            + (np.roll(v, -1, axis=1) - v) / dyf
             + (w[1:] - w[:-1]) / g.dzf[:, None, None])
 
 
@@ -134,7 +159,11 @@ def gradient(g, p):
     """Discrete gradient G: cell centres -> faces.  The wall faces carry a
     zero gradient (homogeneous Neumann pressure at no-penetration walls)."""
     gx = (p - np.roll(p, 1, axis=2)) / g.dx
-    gy = (p - np.roll(p, 1, axis=1)) / g.dy
+    if g.ystretched:
+        gy = np.zeros(g.shape)
+        gy[:, 1:] = (p[:, 1:] - p[:, :-1]) / g.dyc[None, 1:, None]
+    else:
+        gy = (p - np.roll(p, 1, axis=1)) / g.dy
     if g.ywalls:
         gy[:, 0, :] = 0.0
     gz = np.zeros((g.nz + 1, g.ny, g.nx))
@@ -158,6 +187,8 @@ def face_density(g, rho):
 def volume_mean(g, f):
     """Volume-weighted mean of a cell field."""
     dv = g.cell_volume()
+    if g.ystretched:
+        return float(np.sum(f * dv) / (np.sum(dv) * g.nx))
     return float(np.sum(f * dv) / (np.sum(dv) * g.nx * g.ny))
 
 
@@ -177,6 +208,31 @@ def _z_coefficients(g):
     return a, c
 
 
+def _y_eigenbasis(g):
+    """Eigenpairs of the y part of L on a stretched y bounded by walls.
+
+    (L_y p)_j = [(p_{j+1} - p_j)/dyc_{j+1} - (p_j - p_{j-1})/dyc_j] / dyf_j,
+    with the wall terms absent, is W^{-1} T with W = diag(dyf) and T
+    symmetric tridiagonal, so its eigenvectors solve T v = lambda W v:
+    scipy's generalized symmetric eigensolver returns them W-orthonormal
+    (V^T W V = I).  Ordered from lambda = 0 (the constant vector, written
+    exactly) to the most negative."""
+    ny = g.ny
+    T = np.zeros((ny, ny))
+    for j in range(1, ny):
+        c = 1.0 / g.dyc[j]
+        T[j, j] -= c
+        T[j - 1, j - 1] -= c
+        T[j, j - 1] = c
+        T[j - 1, j] = c
+    lam, V = sla.eigh(T, np.diag(g.dyf))
+    order = np.argsort(-lam)
+    lam, V = lam[order].copy(), V[:, order].copy()
+    lam[0] = 0.0
+    V[:, 0] = 1.0 / np.sqrt(g.ly)
+    return lam, V
+
+
 def solve_constant(g, f):
     """Constant-coefficient pressure solve by the eigenexpansion method
     (Sec. 3.3.1: homogeneous pressure boundary conditions, solved exactly).
@@ -190,13 +246,18 @@ def solve_constant(g, f):
     With y walls the y step is the eigenbasis of the Neumann second
     difference on cell centres, cos(pi m (j + 1/2) / ny), m = 0 .. ny - 1,
     with eigenvalues -(4 / dy^2) sin^2(pi m / (2 ny)): scipy's DCT-II and its
-    inverse.
+    inverse.  On a stretched y it is the W-orthonormal eigenbasis V of
+    ``_y_eigenbasis``: coefficients V^T W f forward, V c back.
     """
     nx, ny, nz = g.nx, g.ny, g.nz
     fc = f - volume_mean(g, f)
     kx = np.arange(nx // 2 + 1)
     ky = np.arange(ny)
-    if g.ywalls:
+    if g.ystretched:
+        lam_y, V = _y_eigenbasis(g)
+        fh = sfft.rfft(fc, axis=2, workers=WORKERS)
+        fh = np.einsum("mj,kji->kmi", V.T * g.dyf[None, :], fh)
+    elif g.ywalls:
         fh = sfft.rfft(fc, axis=2, workers=WORKERS)
         fh = (sfft.dct(fh.real, type=2, axis=1, workers=WORKERS)
               + 1j * sfft.dct(fh.imag, type=2, axis=1, workers=WORKERS))
@@ -234,7 +295,10 @@ def solve_constant(g, f):
     rhs = np.zeros(nz + 1, dtype=np.complex128)
     rhs[:nz] = fh[:, 0, 0]
     ph[:, 0, 0] = np.linalg.solve(lz, rhs)[:nz]
-    if g.ywalls:
+    if g.ystretched:
+        ph = np.einsum("jm,kmi->kji", V, ph)
+        p = sfft.irfft(ph, n=nx, axis=2, workers=WORKERS)
+    elif g.ywalls:
         ph = (sfft.idct(ph.real, type=2, axis=1, workers=WORKERS)
               + 1j * sfft.idct(ph.imag, type=2, axis=1, workers=WORKERS))
         p = sfft.irfft(ph, n=nx, axis=2, workers=WORKERS)
@@ -414,8 +478,13 @@ def _sparse_operators(g):
         vopen[:, 0, :] = 0.0
     add(cid, np.roll(fid_u, -1, axis=2), 1.0 / g.dx)
     add(cid, fid_u, -1.0 / g.dx)
-    add(cid, np.roll(fid_v, -1, axis=1), np.roll(vopen, -1, axis=1) / g.dy)
-    add(cid, fid_v, -vopen / g.dy)
+    if g.ystretched:
+        dyf = np.broadcast_to(g.dyf[None, :, None], g.shape)
+        add(cid, np.roll(fid_v, -1, axis=1), np.roll(vopen, -1, axis=1) / dyf)
+        add(cid, fid_v, -vopen / dyf)
+    else:
+        add(cid, np.roll(fid_v, -1, axis=1), np.roll(vopen, -1, axis=1) / g.dy)
+        add(cid, fid_v, -vopen / g.dy)
     inv_dzf = np.broadcast_to((1.0 / g.dzf)[:, None, None], g.shape)
     add(cid, fid_w[1:], inv_dzf)
     add(cid, fid_w[:-1], -inv_dzf)
@@ -426,8 +495,14 @@ def _sparse_operators(g):
     # (p_k - p_{k-1})/dzc_k; wall z-faces: no rows (zero gradient).
     add(fid_u, cid, 1.0 / g.dx)
     add(fid_u, np.roll(cid, 1, axis=2), -1.0 / g.dx)
-    add(fid_v, cid, vopen / g.dy)
-    add(fid_v, np.roll(cid, 1, axis=1), -vopen / g.dy)
+    if g.ystretched:
+        # y-face j (j >= 1): (p_j - p_{j-1})/dyc_j; the wall row has no entries
+        dyc = np.broadcast_to(np.where(g.dyc > 0, g.dyc, 1.0)[None, :, None], g.shape)
+        add(fid_v, cid, vopen / dyc)
+        add(fid_v, np.roll(cid, 1, axis=1), -vopen / dyc)
+    else:
+        add(fid_v, cid, vopen / g.dy)
+        add(fid_v, np.roll(cid, 1, axis=1), -vopen / g.dy)
     inv_dzc = np.broadcast_to((1.0 / g.dzc[1:-1])[:, None, None], (nz - 1, ny, nx))
     add(fid_w[1:-1], cid[1:], inv_dzc)
     add(fid_w[1:-1], cid[:-1], -inv_dzc)
@@ -574,6 +649,8 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
     ``p`` is the converged pressure of the forward projection (computed
     here with the same tolerance when not given).
     """
+    if g.ystretched:
+        raise NotImplementedError("adjoint_method3: uniform y only (adjoint_direct takes a stretched y)")
     gw = _zero_walls(gw)
     gv = _zero_ywall_row(g, gv)
     rx, ry, rz = face_density(g, rho)
@@ -663,7 +740,9 @@ def convection(g, u, v, w):
     and at cell edges (cross terms); a velocity is carried to an edge by the
     mean of its two values in x, y or z.  With y walls the wall row of v is
     zero (no-penetration), so every product on a y-wall edge vanishes, and
-    the wall row of C_y is zero."""
+    the wall row of C_y is zero.  Uniform y only."""
+    if g.ystretched:
+        raise NotImplementedError("convection: uniform y only")
     if g.ywalls:
         v = np.array(v, dtype=np.float64, copy=True)
         v[:, 0, :] = 0.0
@@ -698,7 +777,9 @@ def viscous(g, mu, u, v, w):
     shear stresses at edges with the mean mu of the (up to) four cells
     around the edge.  No-slip z walls: the wall velocity is zero, so the
     wall shear uses the half-cell distance to the wall.  With y walls the
-    same holds there (``_viscous_ywalls``)."""
+    same holds there (``_viscous_ywalls``).  Uniform y only."""
+    if g.ystretched:
+        raise NotImplementedError("viscous: uniform y only")
     if g.ywalls:
         return _viscous_ywalls(g, mu, u, v, w)
     D = divergence(g, u, v, w)

@@ -37,6 +37,11 @@ def tanh_zfaces(nz: int, lz: float, beta: float) -> np.ndarray:
     return z
 
 
+def tanh_yfaces(ny: int, ly: float, beta: float) -> np.ndarray:
+    """The same clustering for a y bounded by walls (y faces 0 .. ny)."""
+    return tanh_zfaces(ny, ly, beta)
+
+
 @dataclass
 class Workload:
     name: str
@@ -56,6 +61,7 @@ class Workload:
     S: np.ndarray | None = None
     extra: dict = field(default_factory=dict)
     ywalls: bool = False      # walls at y = 0 and y = ly (v row 0 is the wall face)
+    yf: np.ndarray | None = None  # y face coordinates of a stretched y (walls in y only)
 
     @property
     def shape(self):
@@ -89,12 +95,13 @@ def random_faces(nx, ny, nz, sigma, seed, remove_mean=False, dtype=np.float64, y
     return tuple(out)
 
 
-def spheres_phi(nx, ny, nz, lx, ly, zf, spheres, nsub=4):
+def spheres_phi(nx, ny, nz, lx, ly, zf, spheres, nsub=4, yf=None):
     """Volume fraction of a union of non-overlapping spheres: the fraction of
     the nsub^3 sub-cell centres of each cell inside a sphere (values m/nsub^3).
-    x and y are periodic; z is bounded by the walls.  ``spheres`` is a list of
-    (cx, cy, cz, r).  Cells whose every sub-cell centre is provably inside
-    (or outside) are set to 1 (or 0) without sampling."""
+    x and y are periodic; z is bounded by the walls (and y too when its face
+    coordinates ``yf`` are given: a stretched y between walls).  ``spheres``
+    is a list of (cx, cy, cz, r).  Cells whose every sub-cell centre is
+    provably inside (or outside) are set to 1 (or 0) without sampling."""
     phi = np.zeros((nz, ny, nx))
     dx, dy = lx / nx, ly / ny
     off = (np.arange(nsub) + 0.5) / nsub
@@ -102,24 +109,36 @@ def spheres_phi(nx, ny, nz, lx, ly, zf, spheres, nsub=4):
         k0 = max(int(np.searchsorted(zf, cz - r, side="right")) - 1, 0)
         k1 = min(int(np.searchsorted(zf, cz + r, side="left")), nz)
         i0, i1 = int(math.floor((cx - r) / dx)), int(math.floor((cx + r) / dx)) + 1
-        j0, j1 = int(math.floor((cy - r) / dy)), int(math.floor((cy + r) / dy)) + 1
+        if yf is None:
+            j0, j1 = int(math.floor((cy - r) / dy)), int(math.floor((cy + r) / dy)) + 1
+        else:
+            j0 = max(int(np.searchsorted(yf, cy - r, side="right")) - 1, 0)
+            j1 = min(int(np.searchsorted(yf, cy + r, side="left")), ny)
         ii = np.arange(i0, i1)
         jj = np.arange(j0, j1)
         kk = np.arange(k0, k1)
         dzk = zf[kk + 1] - zf[kk]
         # cell-centre distances and the largest sub-cell-centre offset
         xc = (ii + 0.5) * dx - cx
-        yc = (jj + 0.5) * dy - cy
+        if yf is None:
+            dyj = np.full(len(jj), dy)
+            yc = (jj + 0.5) * dy - cy
+        else:
+            ylo, dyj = yf[jj], yf[jj + 1] - yf[jj]
+            yc = ylo + 0.5 * dyj - cy
         zc = 0.5 * (zf[kk] + zf[kk + 1]) - cz
         dist = np.sqrt(zc[:, None, None] ** 2 + yc[None, :, None] ** 2 + xc[None, None, :] ** 2)
-        reach = (0.5 - 0.5 / nsub) * np.sqrt(dzk[:, None, None] ** 2 + dy * dy + dx * dx)
+        reach = (0.5 - 0.5 / nsub) * np.sqrt(dzk[:, None, None] ** 2 + dyj[None, :, None] ** 2 + dx * dx)
         frac = np.zeros(dist.shape)
         frac[dist + reach <= r] = 1.0
         edge = np.argwhere((dist + reach > r) & (dist - reach <= r))
         if len(edge):
             ke, je, ie = edge[:, 0], edge[:, 1], edge[:, 2]
             sx = (ii[ie][:, None] + off[None, :]) * dx - cx                       # (m, nsub)
-            sy = (jj[je][:, None] + off[None, :]) * dy - cy
+            if yf is None:
+                sy = (jj[je][:, None] + off[None, :]) * dy - cy
+            else:
+                sy = ylo[je][:, None] + off[None, :] * dyj[je][:, None] - cy
             sz = zf[kk[ke]][:, None] + off[None, :] * dzk[ke][:, None] - cz
             inside = (sz[:, :, None, None] ** 2 + sy[:, None, :, None] ** 2
                       + sx[:, None, None, :] ** 2) <= r * r
@@ -260,18 +279,21 @@ def small_bubble_case(n=32, seed=1102, rho_ratio=1000.0, stretched=False, nz=Non
 
 
 def channel_bubble_case(nx=32, ny=None, nz=None, seed=1202, rho_ratio=1000.0, stretched=False,
-                        nbubbles=3, dt=1e-3):
+                        nbubbles=3, dt=1e-3, ybeta=None):
     """Bubbles in a duct: periodic in x, walls in y and z.  The bubbles keep
     a cell's gap from every wall; v* is zero on the y walls (row 0) as w* is
-    on the z walls."""
+    on the z walls.  ``ybeta``: y faces clustered at the walls by
+    ``tanh_yfaces`` with that beta (a stretched y)."""
     ny = ny or nx
     nz = nz or nx
     ly = ny / nx
     zf = tanh_zfaces(nz, 1.0, 1.5) if stretched else uniform_zfaces(nz, 1.0)
+    yf = None if ybeta is None else tanh_yfaces(ny, ly, ybeta)
     rng = np.random.Generator(np.random.PCG64(seed + 10))
     spheres = place_bubbles(nbubbles, 1.0, ly, 1.0, nx, float(np.min(np.diff(zf))),
                             0.08, 0.16, rng, gap_cells=1.0, ywalls=True)
-    phi = spheres_phi(nx, ny, nz, 1.0, ly, zf, spheres)
+    phi = spheres_phi(nx, ny, nz, 1.0, ly, zf, spheres, yf=yf)
     us, vs, ws = random_faces(nx, ny, nz, 0.1, seed, ywalls=True)
-    return Workload(f"{nbubbles} bubbles in a duct {nx}x{ny}x{nz}", nx, ny, nz, 1.0, ly, zf, dt,
-                    us, vs, ws, phi, 1.0, rho_ratio, gas_source(phi), ywalls=True)
+    name = f"{nbubbles} bubbles in a duct {nx}x{ny}x{nz}" + ("" if yf is None else f", tanh({ybeta:g}) y")
+    return Workload(name, nx, ny, nz, 1.0, ly, zf, dt,
+                    us, vs, ws, phi, 1.0, rho_ratio, gas_source(phi), ywalls=True, yf=yf)

@@ -10,12 +10,25 @@ def metrics(nz, zf):
     return dzf, zc
 
 
-def assemble_variable(nx, ny, nz, lx, ly, zf, rho, ywalls=False):
+def y_metrics(ny, ly, yf):
+    """Row widths and centres of y: uniform (yf None) or from the ny + 1 face
+    coordinates yf."""
+    if yf is None:
+        dy = ly / ny
+        return [dy] * ny, [(j + 0.5) * dy for j in range(ny)]
+    dyf = [yf[j + 1] - yf[j] for j in range(ny)]
+    yc = [0.5 * (yf[j + 1] + yf[j]) for j in range(ny)]
+    return dyf, yc
+
+
+def assemble_variable(nx, ny, nz, lx, ly, zf, rho, ywalls=False, yf=None):
     """Matrix of p -> D(beta G p) with beta = 2/(rho_a + rho_b) on each face,
     zero flux through the z walls, periodic x, and y periodic or (ywalls)
-    bounded by walls with zero flux.  rho=None means beta=1."""
+    bounded by walls with zero flux.  rho=None means beta=1.  yf (walls in
+    y only): y face coordinates of a stretched y."""
     dx, dy = lx / nx, ly / ny
     dzf, zc = metrics(nz, zf)
+    dyf, yc = y_metrics(ny, ly, yf)
     n = nx * ny * nz
 
     def idx(i, j, k):
@@ -42,7 +55,10 @@ def assemble_variable(nx, ny, nz, lx, ly, zf, rho, ywalls=False):
                     if ywalls and not 0 <= j + dj < ny:
                         continue  # y wall: no flux
                     nb = (k, (j + dj) % ny, i)
-                    b = beta(cell, nb) / (dy * dy)
+                    if yf is None:
+                        b = beta(cell, nb) / (dy * dy)
+                    else:
+                        b = beta(cell, nb) / (abs(yc[j + dj] - yc[j]) * dyf[j])
                     A[r, idx(i, j + dj, k)] += b
                     A[r, r] -= b
                 for dk in (+1, -1):
@@ -68,16 +84,21 @@ def bordered_solve(A, rhs, weights):
     return sol[:n]
 
 
-def cell_weights(nx, ny, nz, zf):
+def cell_weights(nx, ny, nz, zf, yf=None):
+    """Cell volumes over dx dy (uniform y) or over dx (stretched y, yf)."""
     dzf, _ = metrics(nz, zf)
-    return np.repeat(np.array(dzf), nx * ny)
+    if yf is None:
+        return np.repeat(np.array(dzf), nx * ny)
+    dyf, _ = y_metrics(ny, None, yf)
+    return np.array([dzf[k] * dyf[j] for k in range(nz) for j in range(ny) for _ in range(nx)])
 
 
-def divergence_loops(nx, ny, nz, lx, ly, zf, u, v, w, ywalls=False):
+def divergence_loops(nx, ny, nz, lx, ly, zf, u, v, w, ywalls=False, yf=None):
     """With ywalls, v[k, j, i] is the face below cell j and both wall faces
-    (below cell 0, above cell ny - 1) carry no flux."""
-    dx, dy = lx / nx, ly / ny
+    (below cell 0, above cell ny - 1) carry no flux.  yf: stretched y."""
+    dx = lx / nx
     dzf, _ = metrics(nz, zf)
+    dyf, _ = y_metrics(ny, ly, yf)
     out = np.zeros((nz, ny, nx))
     for k in range(nz):
         for j in range(ny):
@@ -85,7 +106,7 @@ def divergence_loops(nx, ny, nz, lx, ly, zf, u, v, w, ywalls=False):
                 vlo = 0.0 if (ywalls and j == 0) else v[k, j, i]
                 vhi = 0.0 if (ywalls and j == ny - 1) else v[k, (j + 1) % ny, i]
                 out[k, j, i] = ((u[k, j, (i + 1) % nx] - u[k, j, i]) / dx
-                                + (vhi - vlo) / dy
+                                + (vhi - vlo) / dyf[j]
                                 + (w[k + 1, j, i] - w[k, j, i]) / dzf[k])
     return out
 
@@ -127,12 +148,14 @@ def assemble_conduction(nx, ny, nz, lx, ly, zf, kc, ywalls=False):
     return A
 
 
-def gradient_loops(nx, ny, nz, lx, ly, zf, p, ywalls=False):
+def gradient_loops(nx, ny, nz, lx, ly, zf, p, ywalls=False, yf=None):
     """G p on the faces, cell by cell: x faces (i - 1/2), y faces (j - 1/2),
     z faces k = 0 .. nz (the wall faces 0 and nz carry no gradient); with
-    ywalls the wall row j = 0 of the y faces carries none either."""
+    ywalls the wall row j = 0 of the y faces carries none either.  yf:
+    stretched y (walls only)."""
     dx, dy = lx / nx, ly / ny
     _, zc = metrics(nz, zf)
+    _, yc = y_metrics(ny, ly, yf)
     gx = np.zeros((nz, ny, nx))
     gy = np.zeros((nz, ny, nx))
     gz = np.zeros((nz + 1, ny, nx))
@@ -141,7 +164,8 @@ def gradient_loops(nx, ny, nz, lx, ly, zf, p, ywalls=False):
             for i in range(nx):
                 gx[k, j, i] = (p[k, j, i] - p[k, j, (i - 1) % nx]) / dx
                 if not (ywalls and j == 0):
-                    gy[k, j, i] = (p[k, j, i] - p[k, (j - 1) % ny, i]) / dy
+                    dist = dy if yf is None else yc[j] - yc[j - 1]
+                    gy[k, j, i] = (p[k, j, i] - p[k, (j - 1) % ny, i]) / dist
                 if k > 0:
                     gz[k, j, i] = (p[k, j, i] - p[k - 1, j, i]) / (zc[k] - zc[k - 1])
     return gx, gy, gz
