@@ -118,6 +118,19 @@ typedef struct {
                               thermodynamic source (adiabatic y walls) and the predictor
                               (no-slip y walls) take them; the batched and no-allocation
                               entry points take periodic y only */
+    const double* yfaces;  /* host, ny+1 increasing face coordinates spanning ly, or NULL
+                              (uniform y).  Walls in y only (PP_ERR_UNSUPPORTED otherwise),
+                              2 <= ny <= 1024, any parity.  The y step of the eigenexpansion
+                              solve is then the W-orthonormal eigenbasis V of the y part of L
+                              (W^{-1} T, W = diag(dyf), T the symmetric second difference
+                              with centre distances dyc), computed once on the host by Sturm
+                              bisection and inverse iteration: forward V^T W f and back V c
+                              as dense products per z plane (Sec. 3.3.1 needs homogeneous
+                              conditions only).  pressure_solve, pressure_correct (Methods
+                              I, II, III) and pressure_mixture_density take it; the adjoint,
+                              the thermodynamic source and the predictor return
+                              PP_ERR_UNSUPPORTED; PP_ERR_INVALID_ARG for faces that do not
+                              increase or do not span ly (1e-12 relative). */
 } pp_grid;
 
 typedef struct {

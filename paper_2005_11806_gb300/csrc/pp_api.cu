@@ -50,6 +50,13 @@ struct pp_plan_s {
   float* d_cw_f = nullptr;  // [3][nz + 1] FP32 layer factors of the face coefficients
   void *d_twx = nullptr, *d_twy = nullptr;
   void* d_dcty = nullptr;  // walls in y: exp(-i pi m / (2 ny)), m < ny (C2 of the plan's FFT type)
+  // stretched y between walls: row factors (Geo::ym, ym_f) and the transposed
+  // forward (V^T W) and inverse (V) eigenvector matrices in the plan's
+  // transform precision
+  bool ystretch = false;
+  double* d_ym = nullptr;
+  float* d_ym_f = nullptr;
+  void *d_ymt_f = nullptr, *d_ymt_i = nullptr;
   // z solve by the cosine basis (uniform z, FP64 plans; pressure_plan_set_zsolve)
   int zsolve = PP_ZSOLVE_TRIDIAG;
   bool z_uniform = false;
@@ -264,9 +271,11 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr, fl
   const C2<T>* twy = (const C2<T>*)P->d_twy;
   // the split solve (mtab present) keeps its intermediate in the spectrum
   double2* ybuf = (double2*)P->d_spec;
-  const double scale = 1.0 / ((double)P->nx * (double)P->ny);
+  // the dense y step of a stretched y is W-orthonormal: no 1/ny on the way back
+  const double scale = 1.0 / ((double)P->nx * (P->ystretch ? 1.0 : (double)P->ny));
   const C2<T>* dct = (const C2<T>*)P->d_dcty;  // null: periodic y
-  PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream, dct));
+  if (P->ystretch) PP_K(P, K_FFTY_F, launch_ydense<T>(g, (const T*)P->d_ymt_f, spec, P->d_st, P->stream));
+  else PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream, dct));
   if (P->z_tc) {
     PP_K(P, K_TRI, launch_zgemm(g, P->ze, reinterpret_cast<float2*>(spec), P->d_st, P->stream));
   } else if (P->zsolve == PP_ZSOLVE_COSINE) {
@@ -283,7 +292,8 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr, fl
     PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab,
                                      P->use_tri32 ? &P->tri32 : nullptr));
   }
-  PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream, dct));
+  if (P->ystretch) PP_K(P, K_FFTY_I, launch_ydense<T>(g, (const T*)P->d_ymt_i, spec, P->d_st, P->stream));
+  else PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream, dct));
   PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream, delta,
                                        sdelta));
   return PP_OK;
@@ -400,6 +410,10 @@ void free_plan(pp_plan_s* P) {
   if (P->d_twx) cudaFree(P->d_twx);
   if (P->d_twy) cudaFree(P->d_twy);
   if (P->d_dcty) cudaFree(P->d_dcty);
+  if (P->d_ym) cudaFree(P->d_ym);
+  if (P->d_ym_f) cudaFree(P->d_ym_f);
+  if (P->d_ymt_f) cudaFree(P->d_ymt_f);
+  if (P->d_ymt_i) cudaFree(P->d_ymt_i);
   if (P->d_twz) cudaFree(P->d_twz);
   if (P->d_dctz) cudaFree(P->d_dctz);
   if (P->d_lamz) cudaFree(P->d_lamz);
@@ -446,8 +460,16 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       G.bc[2] != PP_BC_WALL)
     return PP_ERR_UNSUPPORTED;
   const bool ywall = (G.bc[1] == PP_BC_WALL);
+  const bool ystretch = G.yfaces != nullptr;
   if ((G.nx & 1) != 0) return PP_ERR_UNSUPPORTED;
-  if (ywall && (G.ny < 2 || (G.ny & 1) != 0)) return PP_ERR_UNSUPPORTED;  // cosine transform by an FFT of even length
+  if (ystretch && (!ywall || G.ny < 2 || G.ny > 1024)) return PP_ERR_UNSUPPORTED;  // dense y step
+  // uniform walls: cosine transform by an FFT of even length
+  if (ywall && !ystretch && (G.ny < 2 || (G.ny & 1) != 0)) return PP_ERR_UNSUPPORTED;
+  if (ystretch) {  // increasing faces spanning ly
+    for (int j = 0; j < G.ny; ++j)
+      if (!(G.yfaces[j + 1] > G.yfaces[j])) return PP_ERR_INVALID_ARG;
+    if (!(std::fabs((G.yfaces[G.ny] - G.yfaces[0]) - G.ly) <= 1e-12 * G.ly)) return PP_ERR_INVALID_ARG;
+  }
   if (G.nx > 2048 || G.ny > 2048) return PP_ERR_UNSUPPORTED;  // one line per block in the FFTs
   if ((long)G.nx * G.ny * (G.nz + 1) > (1L << 31)) return PP_ERR_UNSUPPORTED;
   pp_plan_s* P = new (std::nothrow) pp_plan_s();
@@ -457,7 +479,8 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   P->dx = G.lx / G.nx; P->dy = G.ly / G.ny;
   P->prec = prec;
   P->stream = (cudaStream_t)stream;
-  if (!factor_len(G.nx, &P->fx) || !factor_len(G.ny, &P->fy)) { delete P; return PP_ERR_UNSUPPORTED; }
+  P->ystretch = ystretch;
+  if (!factor_len(G.nx, &P->fx) || (!factor_len(G.ny, &P->fy) && !ystretch)) { delete P; return PP_ERR_UNSUPPORTED; }
   if (cudaGetDevice(&P->device) != cudaSuccess) { delete P; return PP_ERR_CUDA; }
 
   // z metrics (Sec. 3 grid; stretched faces allowed)
@@ -500,6 +523,25 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
     const double s = std::sin(pi * (double)k / (ywall ? 2.0 * (double)G.ny : (double)G.ny));
     lamy[k] = -4.0 / (P->dy * P->dy) * s * s;
   }
+  // stretched y between walls: metrics, row factors and the numerical
+  // eigenbasis of L_y (its eigenvalues replace the cosine ones)
+  std::vector<double> ymet, ymt_f, ymt_i;
+  if (ystretch) {
+    const int ny = G.ny;
+    std::vector<double> yf(G.yfaces, G.yfaces + ny + 1), dyf(ny), yc(ny), inv_dyc(ny + 1, 0.0);
+    for (int j = 0; j < ny; ++j) {
+      dyf[j] = yf[j + 1] - yf[j];
+      yc[j] = 0.5 * (yf[j] + yf[j + 1]);
+    }
+    for (int j = 1; j < ny; ++j) inv_dyc[j] = 1.0 / (yc[j] - yc[j - 1]);
+    if (!build_yeigen_host(ny, dyf.data(), inv_dyc.data(), lamy, ymt_f, ymt_i)) { delete P; return PP_ERR_NUMERIC; }
+    ymet.assign(3 * (size_t)ny, 0.0);
+    for (int j = 0; j < ny; ++j) {
+      ymet[j] = dyf[j] / P->dy;
+      ymet[ny + j] = P->dy * inv_dyc[j];
+      ymet[2 * ny + j] = P->dy / dyf[j];
+    }
+  }
 
   pp_status st = PP_OK;
   const size_t nc = (size_t)G.nx * G.ny * nz;
@@ -519,6 +561,26 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
     free_plan(P);
     return st;
   }
+  if (ystretch) {
+    std::vector<float> ymf(ymet.begin(), ymet.end());
+    const size_t nm = (size_t)G.ny * G.ny;
+    const size_t esz = (prec == PP_FP64) ? sizeof(double) : sizeof(float);
+    if ((st = up(&P->d_ym, ymet)) != PP_OK || (st = dalloc(&P->d_ym_f, ymf.size() * sizeof(float))) != PP_OK ||
+        (st = dalloc(&P->d_ymt_f, nm * esz)) != PP_OK || (st = dalloc(&P->d_ymt_i, nm * esz)) != PP_OK) {
+      free_plan(P);
+      return st;
+    }
+    bool ok = cudaMemcpy(P->d_ym_f, ymf.data(), ymf.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (prec == PP_FP64) {
+      ok = ok && cudaMemcpy(P->d_ymt_f, ymt_f.data(), nm * esz, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(P->d_ymt_i, ymt_i.data(), nm * esz, cudaMemcpyHostToDevice) == cudaSuccess;
+    } else {
+      std::vector<float> f1(ymt_f.begin(), ymt_f.end()), f2(ymt_i.begin(), ymt_i.end());
+      ok = ok && cudaMemcpy(P->d_ymt_f, f1.data(), nm * esz, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(P->d_ymt_i, f2.data(), nm * esz, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) { free_plan(P); return PP_ERR_CUDA; }
+  }
   if (prec == PP_FP64) {
     auto tx = twiddles<double>(G.nx), ty = twiddles<double>(G.ny);
     if ((st = dalloc(&P->d_twx, tx.size() * sizeof(double2))) != PP_OK ||
@@ -528,7 +590,7 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       free_plan(P);
       return PP_ERR_CUDA;
     }
-    if (ywall) {
+    if (ywall && !ystretch) {
       auto tc = dct_twiddles<double>(G.ny);
       if ((st = dalloc(&P->d_dcty, tc.size() * sizeof(double2))) != PP_OK) { free_plan(P); return st; }
       if (cudaMemcpy(P->d_dcty, tc.data(), tc.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -545,7 +607,7 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       free_plan(P);
       return PP_ERR_CUDA;
     }
-    if (ywall) {
+    if (ywall && !ystretch) {
       auto tc = dct_twiddles<float>(G.ny);
       if ((st = dalloc(&P->d_dcty, tc.size() * sizeof(float2))) != PP_OK) { free_plan(P); return st; }
       if (cudaMemcpy(P->d_dcty, tc.data(), tc.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -604,6 +666,8 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   g.inv_dzf = P->d_inv_dzf; g.inv_dzc = P->d_inv_dzc; g.dzf = P->d_dzf;
   g.za = P->d_za; g.zc = P->d_zc; g.lz = lz_sum;
   g.ywall = (G.bc[1] == PP_BC_WALL) ? 1 : 0;
+  g.ym = P->d_ym;
+  g.ym_f = P->d_ym_f;
   if (prec == PP_MIXED_TC) {
     int nzp = 0, zm = 0;
     std::vector<float> mu;
@@ -745,6 +809,7 @@ pp_status pressure_plan_set_method(pp_plan P, int method) {
 pp_status pressure_p0_rate(pp_plan P, const double* phi, const double* kc, const double* T, const double* u,
                            const double* v, const double* w, double p0, double gamma, double* rp) {
   if (check_plan(P) != PP_OK || !phi || !kc || !T || !u || !v || !w || !rp) return PP_ERR_INVALID_ARG;
+  if (P->ystretch) return PP_ERR_UNSUPPORTED;
   if (!(gamma > 0.0) || !std::isfinite(p0)) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P), nw = nwface(P);
   const double *dphi, *dk, *dT, *du, *dv, *dw;
@@ -768,6 +833,7 @@ pp_status pressure_predictor(pp_plan P, const double* u, const double* v, const 
                              double dt_old, const double* const ru_prev[3], double* const u_star[3],
                              double* const ru_out[3]) {
   if (check_plan(P) != PP_OK || !u || !v || !w || !rho || !mu || !gravity || !u_star) return PP_ERR_INVALID_ARG;
+  if (P->ystretch) return PP_ERR_UNSUPPORTED;
   if (!u_star[0] || !u_star[1] || !u_star[2] || !(dt_new > 0.0)) return PP_ERR_INVALID_ARG;
   const double* f[3] = {nullptr, nullptr, nullptr};
   const double* prev[3] = {nullptr, nullptr, nullptr};
@@ -803,6 +869,7 @@ pp_status pressure_dp0dt_extrapolate(double rp_n, double rp_nm1, double dt_new, 
 pp_status pressure_divergence_source(pp_plan P, const double* phi, const double* kc, const double* T, double p0,
                                      double gamma, double dp0dt, double* S) {
   if (check_plan(P) != PP_OK || !phi || !kc || !T || !S) return PP_ERR_INVALID_ARG;
+  if (P->ystretch) return PP_ERR_UNSUPPORTED;
   if (!(gamma > 0.0) || p0 == 0.0 || !std::isfinite(p0) || !std::isfinite(dp0dt)) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P);
   const double *dphi, *dk, *dT;
@@ -922,6 +989,7 @@ pp_status pressure_solve_adjoint(pp_plan P, const double* rho, const double* p, 
                                  pp_info* info) {
   if (check_plan(P) != PP_OK || !rho || !p || !gu || !gv || !gw || !gus || !gvs || !gws || !grho)
     return PP_ERR_INVALID_ARG;
+  if (P->ystretch) return PP_ERR_UNSUPPORTED;
   if (!(dt > 0.0) || !(rtol >= 0.0) || maxit < 0) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P), nw = nwface(P);
   pp_status s;

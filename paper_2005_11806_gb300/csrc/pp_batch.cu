@@ -455,6 +455,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     const pp_grid& G = grids[i];
     if (G.nx < 2 || G.ny < 1 || G.nz < 1 || !(G.lx > 0) || !(G.ly > 0) || !(G.lz > 0)) return PP_ERR_INVALID_ARG;
     if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL) return PP_ERR_UNSUPPORTED;
+    if (G.yfaces != nullptr) return PP_ERR_UNSUPPORTED;
     if ((G.nx & 1) != 0 || G.nx > 2048 || G.ny > 2048) return PP_ERR_UNSUPPORTED;
     FftDesc t;
     if (!factor(G.nx, &t) || !factor(G.ny, &t)) return PP_ERR_UNSUPPORTED;
@@ -564,6 +565,8 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     g.dzf = (const double*)(P + o.dzf); g.za = (const double*)(P + o.za); g.zc = (const double*)(P + o.zc);
     g.inv_dzf_f = (const float*)(P + o.idzff); g.cw_f = (const float*)(P + o.cwf); g.lz = zf[nz] - zf[0];
     g.ywall = 0;
+    g.ym = nullptr;
+    g.ym_f = nullptr;
     d.fc.cx = (double*)(P + o.cx); d.fc.cy = (double*)(P + o.cy); d.fc.cz = (double*)(P + o.cz);
     d.fc.diag = (double*)(P + o.diag); d.fc.rhof = (float*)(P + o.rhof);
     factor(nx, &d.fx);

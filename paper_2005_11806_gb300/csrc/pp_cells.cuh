@@ -34,9 +34,12 @@ __device__ __forceinline__ void cell_prep_faces(const Geo& g, const double* __re
   const size_t plane = (size_t)g.nx * g.ny;
   const double r = rho[c];
   const double w = g.dzf[x.k];
-  fc.cx[c] = 2.0 / (r + rho[x.cim]) * g.inv_dx2 * w;
-  fc.cy[c] = (g.ywall && x.j == 0) ? 0.0 : 2.0 / (r + rho[x.cjm]) * g.inv_dy2 * w;
-  fc.cz[c] = (x.k == 0) ? 0.0 : 2.0 / (r + rho[c - plane]) * g.inv_dzc[x.k];
+  // stretched y: the row of cell j is scaled by dzf_k s_j; the y face below
+  // it carries t_j = dy / dyc_j
+  const double sj = g.ym ? g.ym[x.j] : 1.0, tj = g.ym ? g.ym[g.ny + x.j] : 1.0;
+  fc.cx[c] = 2.0 / (r + rho[x.cim]) * g.inv_dx2 * w * sj;
+  fc.cy[c] = (g.ywall && x.j == 0) ? 0.0 : 2.0 / (r + rho[x.cjm]) * g.inv_dy2 * w * tj;
+  fc.cz[c] = (x.k == 0) ? 0.0 : 2.0 / (r + rho[c - plane]) * g.inv_dzc[x.k] * sj;
   if (x.k == g.nz - 1) fc.cz[c + plane] = 0.0;
   fc.rhof[c] = (float)r;
 }
@@ -50,7 +53,8 @@ __device__ __forceinline__ void cell_prep_diag(const Geo& g, const Faces& fc, si
 }
 
 // d = D u* - (S - meanS) at cell c (wall values of w*, and of v* with walls
-// in y, taken as zero); stores the row-scaled b_s = dzf_k d / dt and
+// in y, taken as zero); stores the row-scaled b_s = dzf_k d / dt (dzf_k s_j
+// d / dt on a stretched y, where the row width is dyf_j = s_j dy) and
 // returns d.
 __device__ __forceinline__ double cell_rhs_b(const Geo& g, const double* __restrict__ us,
                                              const double* __restrict__ vs,
@@ -63,9 +67,10 @@ __device__ __forceinline__ double cell_rhs_b(const Geo& g, const double* __restr
   const double whi = (x.k == g.nz - 1) ? 0.0 : ws[c + plane];
   const double vlo = (g.ywall && x.j == 0) ? 0.0 : vs[c];
   const double vhi = (g.ywall && x.j == g.ny - 1) ? 0.0 : vs[x.cjp];
-  double d = (us[x.cip] - us[c]) / g.dx + (vhi - vlo) / g.dy + (whi - wlo) * g.inv_dzf[x.k];
+  const double sj = g.ym ? g.ym[x.j] : 1.0;
+  double d = (us[x.cip] - us[c]) / g.dx + (vhi - vlo) / (g.dy * sj) + (whi - wlo) * g.inv_dzf[x.k];
   if (S != nullptr) d -= (S[c] - meanS);
-  b[c] = d * g.dzf[x.k] * inv_dt;
+  b[c] = d * g.dzf[x.k] * sj * inv_dt;
   return d;
 }
 
@@ -100,11 +105,14 @@ __device__ __forceinline__ void cell_correct(const Geo& g, const Faces& fc,
   const CellIdx x = cell_index(g, c);
   const size_t plane = (size_t)g.nx * g.ny;
   const double pc = p[c];
-  // dt beta_x / dx = dt dx cx / dzf_k (cx carries dzf_k)
-  const double ax = dt * g.dx * g.inv_dzf[x.k], ay = dt * g.dy * g.inv_dzf[x.k];
+  // dt beta_x / dx = dt dx cx / dzf_k (cx carries dzf_k); on a stretched y
+  // cx and cz also carry s_j, and dt beta_y / dyc_j = dt dy cy / dzf_k
+  // (cy carries dzf_k t_j = dzf_k dy / dyc_j)
+  const double is = g.ym ? g.ym[2 * g.ny + x.j] : 1.0;
+  const double ax = dt * g.dx * g.inv_dzf[x.k] * is, ay = dt * g.dy * g.inv_dzf[x.k];
   u[c] = us[c] - ax * fc.cx[c] * (pc - p[x.cim]);
   v[c] = (g.ywall && x.j == 0) ? 0.0 : vs[c] - ay * fc.cy[c] * (pc - p[x.cjm]);
-  w[c] = (x.k == 0) ? 0.0 : ws[c] - dt * fc.cz[c] * (pc - p[c - plane]);
+  w[c] = (x.k == 0) ? 0.0 : ws[c] - dt * is * fc.cz[c] * (pc - p[c - plane]);
   if (x.k == g.nz - 1) w[c + plane] = 0.0;
 }
 

@@ -60,6 +60,16 @@ struct Geo {
   const float* cw_f;
   double lz;
   int ywall;              // 1: walls at y = 0 and y = ly (v row 0 is the wall face); 0: periodic y
+  // Stretched y between walls (null for a uniform y): [3][ny] row factors
+  // relative to the mean spacing dy = ly / ny,
+  //   ym[j] = s_j = dyf_j / dy, ym[ny + j] = t_j = dy / dyc_j (y-face j below
+  //   row j; t_0 = 0: the walls), ym[2 ny + j] = 1 / s_j,
+  // and their FP32 copy ym_f.  Every cell row is scaled by dzf_k s_j instead
+  // of dzf_k, so with dyf_j = s_j dy and dyc_j = dy / t_j the coefficients
+  // become cx = dzf_k s_j beta / dx^2, cy = dzf_k t_j beta / dy^2 and
+  // cz = s_j beta / dzc (symmetric, as on a uniform y).
+  const double* ym;
+  const float* ym_f;
 };
 
 // Coefficients of D(beta G .) with each cell's row multiplied by its width
@@ -303,6 +313,26 @@ cudaError_t launch_adj_grho(const Geo& g, const double* tx, const double* ty, co
                             double* grho, cudaStream_t s);
 
 int reduce_blocks();  // number of partial sums the reduction kernels write
+
+// y step on a stretched y between walls (Sec. 3.3.1 eigenexpansion with a
+// numerical eigenbasis): every z plane of the spectrum, X[j][kx], becomes
+// M X with M = V^T W (forward, inverse = 0) or V (inverse = 1); mt holds
+// M transposed, mt[j * ny + m] = M[m][j] (pp_kernels_ydense.cu).  ny <= 1024.
+template <typename T>
+cudaError_t launch_ydense(const Geo& g, const T* mt, C2<T>* spec, const DevStatus* st, cudaStream_t s);
+
+// Host: eigenpairs of a symmetric tridiagonal S (diagonal d, off-diagonal e)
+// by Sturm-sequence bisection and inverse iteration with Gram-Schmidt,
+// ascending; Q[k * n + j] = component k of eigenvector j.  False when a pair
+// fails its residual check.
+bool sym_tridiag_eigen(const std::vector<double>& d, const std::vector<double>& e, std::vector<double>& lam,
+                       std::vector<double>& Q);
+// Host: the y eigenbasis of a stretched y between walls: L_y = W^{-1} T with
+// W = diag(dyf), T_{j,j+1} = 1/dyc_{j+1}; eigenvalues lam[m] in descending
+// order (lam[0] = 0, the constant mode, exact) and the transposed matrices
+// of the forward (V^T W) and inverse (V) products.
+bool build_yeigen_host(int ny, const double* dyf, const double* inv_dyc, std::vector<double>& lam,
+                       std::vector<double>& mt_fwd, std::vector<double>& mt_inv);
 
 // Tables of the tensor-core z solve (pp_zgemm.cu).
 struct ZEigen {

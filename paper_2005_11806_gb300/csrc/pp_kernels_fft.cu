@@ -6,7 +6,8 @@
 
 namespace pp {
 
-template <typename T>
+// YS: stretched y between walls (row factors of Geo::ym).
+template <typename T, bool YS>
 __global__ void __launch_bounds__(256, 4) k_resid_fftx(Geo g, Faces fc, FftDesc fx,
                                                     const C2<T>* __restrict__ twx,
                                                     const double* __restrict__ b,
@@ -20,7 +21,7 @@ __global__ void __launch_bounds__(256, 4) k_resid_fftx(Geo g, Faces fc, FftDesc 
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const bool need_exact = (st == nullptr) || st->need_exact;
-  stage_resid_fftx<T>(g, fc, fx, twx, b, rho, p, mode, p_zero, scale_rho, spec, red, rpb, blockIdx.x,
+  stage_resid_fftx<T, YS>(g, fc, fx, twx, b, rho, p, mode, p_zero, scale_rho, spec, red, rpb, blockIdx.x,
                       need_exact, E, delta, smem_raw);
 }
 
@@ -160,12 +161,13 @@ cudaError_t launch_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx, 
   const size_t smem = (sizeof(T) == sizeof(float))
                           ? (nbuf + fft_pad_elems((int)nbuf) + g.nx) * sizeof(float2)
                           : 2 * nbuf * sizeof(C2<T>);
-  cudaError_t e = cudaFuncSetAttribute(k_resid_fftx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = (g.ym != nullptr) ? k_resid_fftx<T, true> : k_resid_fftx<T, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int mode = (red == nullptr) ? 0 : 1;
   (void)inv_dt;
-  k_resid_fftx<T><<<nblk, kThreads, smem, s>>>(g, fc, fx, twx, b, rho, p, mode, p_zero, scale_rho,
-                                          spec, red, rpb, st, E, delta);
+  kern<<<nblk, kThreads, smem, s>>>(g, fc, fx, twx, b, rho, p, mode, p_zero, scale_rho, spec, red, rpb, st, E,
+                                    delta);
   if (nblk_out) *nblk_out = nblk;
   return cudaGetLastError();
 }

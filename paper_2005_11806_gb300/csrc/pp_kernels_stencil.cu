@@ -42,13 +42,16 @@ __global__ void k_prep_diag(Geo g, Faces fc) {
     cell_prep_diag(g, fc, c);
 }
 
-// Fixed-order partial sums of dzf_k * f (grid of kRedBlocks blocks).
+// Fixed-order partial sums of dzf_k * f (dzf_k s_j * f on a stretched y:
+// the cell volume over dx dy) (grid of kRedBlocks blocks).
 __global__ void k_weighted_partial(Geo g, const double* __restrict__ f, double* __restrict__ red) {
   __shared__ double sh[32];
   const size_t plane = (size_t)g.nx * g.ny, n = plane * g.nz;
   double s = 0.0;
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
-    s += g.dzf[c / plane] * f[c];
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const double wy = g.ym ? g.ym[(c / g.nx) % g.ny] : 1.0;
+    s += g.dzf[c / plane] * wy * f[c];
+  }
   s = block_sum<double>(s, sh);
   if (threadIdx.x == 0) red[blockIdx.x] = s;
 }
@@ -215,10 +218,17 @@ __global__ void k_correct_method1(Geo g, Faces fc, const double* __restrict__ us
     const CellIdx x = cell_index(g, c);
     const double idzf = g.inv_dzf[x.k];
     const double dc = (double)delta[c];
-    const double bx = fc.cx[c] * idzf / g.inv_dx2, by = fc.cy[c] * idzf / g.inv_dy2;
+    // stretched y: cx, cz carry s_j and cy carries t_j = dy / dyc_j (t_0 = 0
+    // on the walls, where v is not corrected)
+    const double is = g.ym ? g.ym[2 * g.ny + x.j] : 1.0;
+    const double tj = g.ym ? g.ym[g.ny + x.j] : 1.0;
+    const double bx = fc.cx[c] * idzf * is / g.inv_dx2;
     u[c] += dt * (bx - ir0) * (dc - (double)delta[x.cim]) / g.dx;
-    if (!(g.ywall && x.j == 0)) v[c] += dt * (by - ir0) * (dc - (double)delta[x.cjm]) / g.dy;
-    if (x.k > 0) w[c] += dt * (fc.cz[c] - ir0 * g.inv_dzc[x.k]) * (dc - (double)delta[c - plane]);
+    if (!(g.ywall && x.j == 0)) {
+      const double by = fc.cy[c] * idzf / (g.inv_dy2 * tj);
+      v[c] += dt * (by - ir0) * (dc - (double)delta[x.cjm]) * tj / g.dy;
+    }
+    if (x.k > 0) w[c] += dt * (fc.cz[c] * is - ir0 * g.inv_dzc[x.k]) * (dc - (double)delta[c - plane]);
   }
 }
 

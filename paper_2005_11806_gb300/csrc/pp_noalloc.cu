@@ -150,7 +150,7 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   const pp_grid& G = *grid;
   if (G.nx < 2 || G.ny < 1 || G.nz < 1 || !(G.lx > 0) || !(G.ly > 0) || !(G.lz > 0))
     return PP_ERR_INVALID_ARG;
-  if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL)
+  if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL || G.yfaces != nullptr)
     return PP_ERR_UNSUPPORTED;
   if ((G.nx & 1) != 0) return PP_ERR_UNSUPPORTED;
   // the limits of pressure_plan_create: one transform line per block in the

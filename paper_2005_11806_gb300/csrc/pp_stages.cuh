@@ -128,6 +128,7 @@ __device__ __forceinline__ void load_twiddles_smem(const float2* __restrict__ tw
 // interleaved complex pairs.  Same per-cell arithmetic as the scalar path.
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
+template <bool YS>
 __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc, float* __restrict__ E,
                                                   const float* __restrict__ delta, int scale_rho,
                                                   bool const_scale, float rt_f, long row0, int rpb,
@@ -177,10 +178,21 @@ __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc,
         if (up) rzp = ld4(fc.rhof + c + plane);
         if (dn) rzm = ld4(fc.rhof + c - plane);
         const int nz1 = nz + 1;
-        const float wx = g.cw_f[k];
-        const float wyl = (g.ywall && j == 0) ? 0.f : g.cw_f[nz1 + k];
-        const float wyh = (g.ywall && j + 1 == ny) ? 0.f : g.cw_f[nz1 + k];
-        const float wzp = g.cw_f[2 * nz1 + k + 1], wzm = g.cw_f[2 * nz1 + k];
+        // stretched y: row factor s_j on the x and z faces, t_j and t_{j+1}
+        // on the y faces below and above, 1 / s_j on the cell's value
+        // (a separate instantiation: the uniform one keeps its registers)
+        float wx = g.cw_f[k];
+        float wyl = (g.ywall && j == 0) ? 0.f : g.cw_f[nz1 + k];
+        float wyh = (g.ywall && j + 1 == ny) ? 0.f : g.cw_f[nz1 + k];
+        float wzp = g.cw_f[2 * nz1 + k + 1], wzm = g.cw_f[2 * nz1 + k];
+        if constexpr (YS) {
+          const float sj = g.ym_f[j];
+          wx *= sj;
+          wzp *= sj;
+          wzm *= sj;
+          wyl *= g.ym_f[ny + j];
+          wyh = (j + 1 < ny) ? wyh * g.ym_f[ny + j + 1] : 0.f;
+        }
         const float4 cx = make_float4(wx * face_beta_f(rl, rc.x), wx * face_beta_f(rc.x, rc.y),
                                       wx * face_beta_f(rc.y, rc.z), wx * face_beta_f(rc.z, rc.w));
         const float cxr = wx * face_beta_f(rc.w, rr);
@@ -194,7 +206,8 @@ __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc,
                                        wzm * face_beta_f(rc.z, rzm.z), wzm * face_beta_f(rc.w, rzm.w));
         float4 e = ld4(E + c);
         const float4 rh = scale_rho && !const_scale ? rc : make_float4(rt_f, rt_f, rt_f, rt_f);
-        const float idzf = g.inv_dzf_f[k];
+        float idzf = g.inv_dzf_f[k];
+        if constexpr (YS) idzf *= g.ym_f[2 * ny + j];
         auto cell = [&](float dc, float dxm, float dxp, float cxm, float cxp, float dypv, float cypv,
                         float dymv, float cymv, float dzpv, float czpv, float dzmv, float czmv, float& ev,
                         float rhv) -> float {
@@ -240,7 +253,7 @@ __device__ __forceinline__ void resid_update_vec4(const Geo& g, const Faces& fc,
 // below) into bufA: complex sequence q = (row - row0) / 2 at element offset
 // q * seq_stride (re = even row, im = odd row); s2, s1 accumulate e^2 and
 // |e| of the thread's cells.  Every thread of the block calls it.
-template <typename T>
+template <typename T, bool YS>
 __device__ __forceinline__ void resid_rows(const Geo& g, const Faces& fc, const double* __restrict__ b,
                                            const double* __restrict__ rho, const double* __restrict__ p, int mode,
                                            int p_zero, int scale_rho, long row0, int rpb, bool need_exact,
@@ -261,7 +274,7 @@ __device__ __forceinline__ void resid_rows(const Geo& g, const Faces& fc, const 
   const bool vec = update && sizeof(T) == sizeof(float) && (nx & 3) == 0;
   if (vec) {
     float a2 = 0.f, a1 = 0.f;
-    resid_update_vec4(g, fc, E, delta, scale_rho, const_scale, rt_f, row0, rpb,
+    resid_update_vec4<YS>(g, fc, E, delta, scale_rho, const_scale, rt_f, row0, rpb,
                       reinterpret_cast<float2*>(bufA), seq_stride, a2, a1);
     s2 += (T)a2;
     s1 += (T)a1;
@@ -274,8 +287,14 @@ __device__ __forceinline__ void resid_rows(const Geo& g, const Faces& fc, const 
     const size_t rowoff = (size_t)row * nx;
     const size_t kp = (size_t)k * plane;
     const size_t rowp = kp + (size_t)jp * nx, rowm = kp + (size_t)jm * nx;
-    const float idzf_f = (mode != 0 && sizeof(T) == sizeof(float)) ? g.inv_dzf_f[k] : 0.f;
-    const double idzf = (mode != 0 && sizeof(T) == sizeof(double)) ? g.inv_dzf[k] : 0.0;
+    // stretched y: the row is scaled by dzf_k s_j (Geo::ym)
+    const bool ys = YS && valid;
+    const float idzf_f =
+        (mode != 0 && sizeof(T) == sizeof(float)) ? g.inv_dzf_f[k] * (ys ? g.ym_f[2 * ny + j] : 1.f) : 0.f;
+    const double idzf =
+        (mode != 0 && sizeof(T) == sizeof(double)) ? g.inv_dzf[k] * (ys ? g.ym[2 * ny + j] : 1.0) : 0.0;
+    const float ysj = ys ? g.ym_f[j] : 1.f, ytlo = ys ? g.ym_f[ny + j] : 1.f;
+    const float ythi = ys ? ((j + 1 < ny) ? g.ym_f[ny + j + 1] : 0.f) : 1.f;
     for (int i = i0; i < nx; i += tpr) {
       T r = (T)0;
       if (valid) {
@@ -292,15 +311,17 @@ __device__ __forceinline__ void resid_rows(const Geo& g, const Faces& fc, const 
             const float dc = delta[c];
             const float rcc = fc.rhof[c];
             const int nz1 = nz + 1;
-            const float wx = g.cw_f[k], wy = g.cw_f[nz1 + k];
-            const float wyl = (g.ywall && j == 0) ? 0.f : wy, wyh = (g.ywall && j + 1 == ny) ? 0.f : wy;
+            const float wx = g.cw_f[k] * ysj, wy = g.cw_f[nz1 + k];
+            const float wyl = (g.ywall && j == 0) ? 0.f : wy * ytlo;
+            const float wyh = (g.ywall && j + 1 == ny) ? 0.f : wy * ythi;
             float t = wx * face_beta_f(rcc, fc.rhof[rowoff + ip]) * (delta[rowoff + ip] - dc);
             t = fmaf(wx * face_beta_f(fc.rhof[rowoff + im], rcc), delta[rowoff + im] - dc, t);
             t = fmaf(wyh * face_beta_f(rcc, fc.rhof[rowp + i]), delta[rowp + i] - dc, t);
             t = fmaf(wyl * face_beta_f(rcc, fc.rhof[rowm + i]), delta[rowm + i] - dc, t);
             if (k + 1 < nz)
-              t = fmaf(g.cw_f[2 * nz1 + k + 1] * face_beta_f(rcc, fc.rhof[c + plane]), delta[c + plane] - dc, t);
-            if (k > 0) t = fmaf(g.cw_f[2 * nz1 + k] * face_beta_f(rcc, fc.rhof[c - plane]), delta[c - plane] - dc, t);
+              t = fmaf(g.cw_f[2 * nz1 + k + 1] * ysj * face_beta_f(rcc, fc.rhof[c + plane]), delta[c + plane] - dc, t);
+            if (k > 0)
+              t = fmaf(g.cw_f[2 * nz1 + k] * ysj * face_beta_f(rcc, fc.rhof[c - plane]), delta[c - plane] - dc, t);
             ev = E[c] - t;
             E[c] = ev;
           } else {
@@ -339,7 +360,7 @@ __device__ __forceinline__ void resid_rows(const Geo& g, const Faces& fc, const 
   }
 }
 
-template <typename T>
+template <typename T, bool YS = false>
 __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, const FftDesc& fx,
                                                  const C2<T>* __restrict__ twx,
                                                  const double* __restrict__ b,
@@ -366,7 +387,7 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
   if constexpr (F32) {
     if (fast) load_twiddles_smem(twx, nx, twb);
   }
-  resid_rows<T>(g, fc, b, rho, p, mode, p_zero, scale_rho, row0, rpb, need_exact, E, delta, bufA, nx, s2, s1);
+  resid_rows<T, YS>(g, fc, b, rho, p, mode, p_zero, scale_rho, row0, rpb, need_exact, E, delta, bufA, nx, s2, s1);
   if (mode != 0) {
     // block partial sums of e^2 and |e|: in the arithmetic's own precision
     // (FP32 shuffles on mixed plans: the FP64 pipe is the scarce one)

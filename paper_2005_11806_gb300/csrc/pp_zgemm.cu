@@ -449,28 +449,22 @@ void make_tiles(const std::vector<double>& M, int nzp, std::vector<uint16_t>& ou
 
 }  // namespace
 
-// Builds the eigen tables of L_z on the host; device buffers are allocated
-// by the caller-provided allocator (plan memory).  Returns false when the
-// eigen decomposition failed its own checks.
-bool build_zeigen_host(int nz, const double* dzf, const double* inv_dzc, int* nzp_out, std::vector<float>& mu_out,
-                       int* zero_mode, std::vector<uint16_t>& a1, std::vector<uint16_t>& a2) {
-  const int nzp = ((nz + kTileM - 1) / kTileM) * kTileM;
-  *nzp_out = nzp;
-  // S = W^{-1/2} T W^{-1/2}, T_kk = -(1/dzc_k + 1/dzc_{k+1}), T_{k,k+1} = 1/dzc_{k+1}
-  std::vector<double> d(nz), e(nz > 1 ? nz - 1 : 1, 0.0), e2(nz, 0.0);
-  for (int k = 0; k < nz; ++k) d[k] = -(inv_dzc[k] + inv_dzc[k + 1]) / dzf[k];
-  for (int k = 0; k + 1 < nz; ++k) {
-    e[k] = inv_dzc[k + 1] / std::sqrt(dzf[k] * dzf[k + 1]);
-    e2[k] = e[k] * e[k];
-  }
+// Eigenpairs of the symmetric tridiagonal (d, e), ascending: Sturm-sequence
+// bisection for the eigenvalues, inverse iteration with two Gram-Schmidt
+// passes for the eigenvectors, and a residual check of every pair.
+bool sym_tridiag_eigen(const std::vector<double>& d, const std::vector<double>& e, std::vector<double>& lam,
+                       std::vector<double>& Q) {
+  const int n = (int)d.size();
+  std::vector<double> e2(n, 0.0);
+  for (int k = 0; k + 1 < n; ++k) e2[k] = e[k] * e[k];
   double lo = 0.0, hi = 0.0;  // Gershgorin interval
-  for (int k = 0; k < nz; ++k) {
-    const double r = (k > 0 ? std::fabs(e[k - 1]) : 0.0) + (k + 1 < nz ? std::fabs(e[k]) : 0.0);
+  for (int k = 0; k < n; ++k) {
+    const double r = (k > 0 ? std::fabs(e[k - 1]) : 0.0) + (k + 1 < n ? std::fabs(e[k]) : 0.0);
     lo = std::min(lo, d[k] - r);
     hi = std::max(hi, d[k] + r);
   }
-  std::vector<double> lam(nz);
-  for (int j = 0; j < nz; ++j) {
+  lam.assign(n, 0.0);
+  for (int j = 0; j < n; ++j) {
     double a = lo, b = hi;
     for (int it = 0; it < 200 && b - a > 1e-15 * std::max(1.0, std::max(std::fabs(a), std::fabs(b))); ++it) {
       const double m = 0.5 * (a + b);
@@ -478,11 +472,11 @@ bool build_zeigen_host(int nz, const double* dzf, const double* inv_dzc, int* nz
     }
     lam[j] = 0.5 * (a + b);
   }
-  std::vector<double> Q((size_t)nz * nz);  // Q[k * nz + j] = component k of eigenvector j
+  Q.assign((size_t)n * n, 0.0);
   unsigned long long seed = 0x9E3779B97F4A7C15ull;
-  for (int j = 0; j < nz; ++j) {
-    std::vector<double> v(nz);
-    for (int k = 0; k < nz; ++k) {
+  for (int j = 0; j < n; ++j) {
+    std::vector<double> v(n);
+    for (int k = 0; k < n; ++k) {
       seed = seed * 6364136223846793005ull + 1442695040888963407ull;
       v[k] = (double)(seed >> 11) / 9007199254740992.0 - 0.5;
     }
@@ -492,28 +486,44 @@ bool build_zeigen_host(int nz, const double* dzf, const double* inv_dzc, int* nz
       for (int pass = 0; pass < 2; ++pass)
         for (int i = 0; i < j; ++i) {
           double dot = 0.0;
-          for (int k = 0; k < nz; ++k) dot += Q[(size_t)k * nz + i] * v[k];
-          for (int k = 0; k < nz; ++k) v[k] -= dot * Q[(size_t)k * nz + i];
+          for (int k = 0; k < n; ++k) dot += Q[(size_t)k * n + i] * v[k];
+          for (int k = 0; k < n; ++k) v[k] -= dot * Q[(size_t)k * n + i];
         }
       double nrm = 0.0;
-      for (int k = 0; k < nz; ++k) nrm += v[k] * v[k];
+      for (int k = 0; k < n; ++k) nrm += v[k] * v[k];
       nrm = std::sqrt(nrm);
       if (!(nrm > 0.0)) return false;
-      for (int k = 0; k < nz; ++k) v[k] /= nrm;
+      for (int k = 0; k < n; ++k) v[k] /= nrm;
     }
-    for (int k = 0; k < nz; ++k) Q[(size_t)k * nz + j] = v[k];
+    for (int k = 0; k < n; ++k) Q[(size_t)k * n + j] = v[k];
   }
   // self-check: residual of S q = lambda q for every pair
-  for (int j = 0; j < nz; ++j) {
+  for (int j = 0; j < n; ++j) {
     double res = 0.0;
-    for (int k = 0; k < nz; ++k) {
-      double sq = d[k] * Q[(size_t)k * nz + j];
-      if (k > 0) sq += e[k - 1] * Q[(size_t)(k - 1) * nz + j];
-      if (k + 1 < nz) sq += e[k] * Q[(size_t)(k + 1) * nz + j];
-      res = std::max(res, std::fabs(sq - lam[j] * Q[(size_t)k * nz + j]));
+    for (int k = 0; k < n; ++k) {
+      double sq = d[k] * Q[(size_t)k * n + j];
+      if (k > 0) sq += e[k - 1] * Q[(size_t)(k - 1) * n + j];
+      if (k + 1 < n) sq += e[k] * Q[(size_t)(k + 1) * n + j];
+      res = std::max(res, std::fabs(sq - lam[j] * Q[(size_t)k * n + j]));
     }
     if (res > 1e-8 * std::max(1.0, std::fabs(lo))) return false;
   }
+  return true;
+}
+
+// Builds the eigen tables of L_z on the host; device buffers are allocated
+// by the caller-provided allocator (plan memory).  Returns false when the
+// eigen decomposition failed its own checks.
+bool build_zeigen_host(int nz, const double* dzf, const double* inv_dzc, int* nzp_out, std::vector<float>& mu_out,
+                       int* zero_mode, std::vector<uint16_t>& a1, std::vector<uint16_t>& a2) {
+  const int nzp = ((nz + kTileM - 1) / kTileM) * kTileM;
+  *nzp_out = nzp;
+  // S = W^{-1/2} T W^{-1/2}, T_kk = -(1/dzc_k + 1/dzc_{k+1}), T_{k,k+1} = 1/dzc_{k+1}
+  std::vector<double> d(nz), e(nz > 1 ? nz - 1 : 1, 0.0);
+  for (int k = 0; k < nz; ++k) d[k] = -(inv_dzc[k] + inv_dzc[k + 1]) / dzf[k];
+  for (int k = 0; k + 1 < nz; ++k) e[k] = inv_dzc[k + 1] / std::sqrt(dzf[k] * dzf[k + 1]);
+  std::vector<double> lam, Q;
+  if (!sym_tridiag_eigen(d, e, lam, Q)) return false;
   int zm = 0;
   for (int j = 1; j < nz; ++j)
     if (std::fabs(lam[j]) < std::fabs(lam[zm])) zm = j;
@@ -529,6 +539,48 @@ bool build_zeigen_host(int nz, const double* dzf, const double* inv_dzc, int* nz
     }
   make_tiles(M1, nzp, a1);
   make_tiles(M2, nzp, a2);
+  return true;
+}
+
+// The same decomposition for a stretched y between walls, in the order the
+// spectrum's rows take (mode 0 = the constant, eigenvalue 0, first).  The
+// constant mode is set exactly (q_0 = W^{1/2} 1 / sqrt(ly)) and the others
+// are made orthogonal to it once more.
+bool build_yeigen_host(int ny, const double* dyf, const double* inv_dyc, std::vector<double>& lam,
+                       std::vector<double>& mt_fwd, std::vector<double>& mt_inv) {
+  std::vector<double> d(ny), e(ny > 1 ? ny - 1 : 1, 0.0);
+  for (int j = 0; j < ny; ++j) d[j] = -(inv_dyc[j] + inv_dyc[j + 1]) / dyf[j];
+  for (int j = 0; j + 1 < ny; ++j) e[j] = inv_dyc[j + 1] / std::sqrt(dyf[j] * dyf[j + 1]);
+  std::vector<double> asc, Q;
+  if (!sym_tridiag_eigen(d, e, asc, Q)) return false;
+  double ly = 0.0;
+  for (int j = 0; j < ny; ++j) ly += dyf[j];
+  // mode m of the spectrum = ascending pair ny - 1 - m
+  std::vector<double> q((size_t)ny * ny);  // q[m * ny + j]
+  for (int m = 0; m < ny; ++m)
+    for (int j = 0; j < ny; ++j) q[(size_t)m * ny + j] = Q[(size_t)j * ny + (ny - 1 - m)];
+  for (int j = 0; j < ny; ++j) q[j] = std::sqrt(dyf[j] / ly);
+  for (int m = 1; m < ny; ++m) {
+    double dot = 0.0, nrm = 0.0;
+    for (int j = 0; j < ny; ++j) dot += q[j] * q[(size_t)m * ny + j];
+    for (int j = 0; j < ny; ++j) {
+      q[(size_t)m * ny + j] -= dot * q[j];
+      nrm += q[(size_t)m * ny + j] * q[(size_t)m * ny + j];
+    }
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0.0)) return false;
+    for (int j = 0; j < ny; ++j) q[(size_t)m * ny + j] /= nrm;
+  }
+  lam.assign(ny, 0.0);
+  for (int m = 1; m < ny; ++m) lam[m] = asc[ny - 1 - m];
+  mt_fwd.assign((size_t)ny * ny, 0.0);
+  mt_inv.assign((size_t)ny * ny, 0.0);
+  for (int m = 0; m < ny; ++m)
+    for (int j = 0; j < ny; ++j) {
+      const double v = q[(size_t)m * ny + j];
+      mt_fwd[(size_t)j * ny + m] = v * std::sqrt(dyf[j]);  // (V^T W)[m][j], stored [j][m]
+      mt_inv[(size_t)m * ny + j] = v / std::sqrt(dyf[j]);  // V[j][m], stored [m][j]
+    }
   return true;
 }
 

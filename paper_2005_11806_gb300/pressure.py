@@ -28,7 +28,8 @@ METHODS = {"III": 0, "I": 1, "II": 2}
 class pp_grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
-                ("zfaces", ctypes.POINTER(ctypes.c_double)), ("bc", ctypes.c_int * 3)]
+                ("zfaces", ctypes.POINTER(ctypes.c_double)), ("bc", ctypes.c_int * 3),
+                ("yfaces", ctypes.POINTER(ctypes.c_double))]
 
 
 class pp_info(ctypes.Structure):
@@ -167,19 +168,25 @@ def _sized(plan, *fields):
 
 
 def pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None,
-                         ywalls=False):
+                         ywalls=False, yfaces=None):
     """Create a plan; returns an opaque handle (int).  ``zfaces``: None for a
     uniform z grid, else nz + 1 increasing face coordinates (host array).
-    ``ywalls``: walls at y = 0 and y = ly instead of periodic y."""
+    ``ywalls``: walls at y = 0 and y = ly instead of periodic y.  ``yfaces``
+    (walls in y only): ny + 1 increasing face coordinates of a stretched y."""
     g = pp_grid()
     g.nx, g.ny, g.nz = int(nx), int(ny), int(nz)
     g.lx, g.ly, g.lz = float(lx), float(ly), float(lz)
-    keep = None
+    keep = ykeep = None
     if zfaces is not None:
         keep = np.ascontiguousarray(zfaces, dtype=np.float64)
         if keep.shape != (int(nz) + 1,):
             raise ValueError("zfaces must hold nz + 1 values")
         g.zfaces = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if yfaces is not None:
+        ykeep = np.ascontiguousarray(yfaces, dtype=np.float64)
+        if ykeep.shape != (int(ny) + 1,):
+            raise ValueError("yfaces must hold ny + 1 values")
+        g.yfaces = ykeep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     g.bc[0], g.bc[1], g.bc[2] = PP_BC_PERIODIC, PP_BC_WALL if ywalls else PP_BC_PERIODIC, PP_BC_WALL
     out = ctypes.c_void_p()
     _check(lib().pressure_plan_create(ctypes.byref(g), PRECISIONS[precision], _stream(stream),
@@ -398,10 +405,10 @@ class Plan:
     """Owning wrapper of a plan handle."""
 
     def __init__(self, nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", stream=None,
-                 method="III", ywalls=False, zsolve="tridiag"):
+                 method="III", ywalls=False, zsolve="tridiag", yfaces=None):
         self.shape = (int(nz), int(ny), int(nx))
         self.wshape = (int(nz) + 1, int(ny), int(nx))
-        self.handle = pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces, precision, stream, ywalls)
+        self.handle = pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces, precision, stream, ywalls, yfaces)
         if method != "III":
             pressure_plan_set_method(self.handle, method)
         if zsolve != "tridiag":

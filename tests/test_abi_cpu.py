@@ -3,6 +3,7 @@ exports every function include/pressure_projection.h declares."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -72,6 +73,34 @@ def test_plan_create_rejects_bad_descriptors(dims, lens, prec, bc, code):
     g.bc[0], g.bc[1], g.bc[2] = bc
     out = ctypes.c_void_p()
     got = pressure.lib().pressure_plan_create(ctypes.byref(g), pressure.PRECISIONS[prec], None, ctypes.byref(out))
+    assert got == getattr(pressure, code)
+    assert out.value is None
+
+
+@pytest.mark.parametrize("ny,bc,faces,code", [
+    (8, (0, 0, 1), "tanh", "PP_ERR_UNSUPPORTED"),     # stretched y needs walls in y
+    (1025, (0, 1, 1), "tanh", "PP_ERR_UNSUPPORTED"),  # dense y step: ny <= 1024
+    (8, (0, 1, 1), "flat", "PP_ERR_INVALID_ARG"),     # faces not increasing
+    (8, (0, 1, 1), "short", "PP_ERR_INVALID_ARG"),    # faces do not span ly
+])
+def test_plan_create_rejects_bad_y_faces(ny, bc, faces, code):
+    """The stretched-y descriptor checks also precede any CUDA call."""
+    import ctypes
+    import math
+    pressure = _lib_or_build()
+    yf = np.array([0.5 * (1 + math.tanh(1.5 * (2 * j / ny - 1)) / math.tanh(1.5)) for j in range(ny + 1)])
+    if faces == "flat":
+        yf[3] = yf[2]
+    if faces == "short":
+        yf = yf * 0.9
+    g = pressure.pp_grid()
+    g.nx, g.ny, g.nz = 8, ny, 8
+    g.lx, g.ly, g.lz = 1.0, 1.0, 1.0
+    g.bc[0], g.bc[1], g.bc[2] = bc
+    keep = np.ascontiguousarray(yf)
+    g.yfaces = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out = ctypes.c_void_p()
+    got = pressure.lib().pressure_plan_create(ctypes.byref(g), pressure.PRECISIONS["fp64"], None, ctypes.byref(out))
     assert got == getattr(pressure, code)
     assert out.value is None
 
