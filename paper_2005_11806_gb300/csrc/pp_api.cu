@@ -56,7 +56,11 @@ struct pp_plan_s {
   bool ystretch = false;
   double* d_ym = nullptr;
   float* d_ym_f = nullptr;
-  void *d_ymt_f = nullptr, *d_ymt_i = nullptr;
+  void *d_ymt_f = nullptr, *d_ymt_i = nullptr;  // FP64 plans: the CUDA-core dense step
+  // mixed plans: the tensor-core dense step (BF16 hi/lo tiles of V^T W and
+  // V) runs out of place into d_spec2, where the z solve then works
+  unsigned char *d_ytc_f = nullptr, *d_ytc_i = nullptr;
+  void* d_spec2 = nullptr;
   // z solve by the cosine basis (uniform z, FP64 plans; pressure_plan_set_zsolve)
   int zsolve = PP_ZSOLVE_TRIDIAG;
   bool z_uniform = false;
@@ -99,7 +103,7 @@ struct pp_plan_s {
   double* d_adj[4] = {nullptr};
   double last_mean_S = 0.0;
   Prof prof;
-  bool z_tc = false;           // tensor-core z solve (PP_MIXED_TC)
+  bool z_tc = false;           // tensor-core z expansion (PP_MIXED_TC; uses d_spec2)
   ZEigen ze{};
   float* d_mu = nullptr;
   unsigned char* d_za1 = nullptr;
@@ -269,31 +273,79 @@ pp_status solve_pass(pp_plan_s* P, double* p, int p_zero, T* delta = nullptr, fl
   C2<T>* spec = (C2<T>*)P->d_spec;
   const C2<T>* twx = (const C2<T>*)P->d_twx;
   const C2<T>* twy = (const C2<T>*)P->d_twy;
+  // mixed plans with a stretched y: the tensor-core y step runs out of
+  // place, so the z solve works on the second spectrum buffer
+  const bool ytc = P->ystretch && std::is_same<T, float>::value;
+  C2<T>* zs = ytc ? (C2<T>*)P->d_spec2 : spec;
   // the split solve (mtab present) keeps its intermediate in the spectrum
-  double2* ybuf = (double2*)P->d_spec;
+  double2* ybuf = (double2*)zs;
   // the dense y step of a stretched y is W-orthonormal: no 1/ny on the way back
   const double scale = 1.0 / ((double)P->nx * (P->ystretch ? 1.0 : (double)P->ny));
   const C2<T>* dct = (const C2<T>*)P->d_dcty;  // null: periodic y
-  if (P->ystretch) PP_K(P, K_FFTY_F, launch_ydense<T>(g, (const T*)P->d_ymt_f, spec, P->d_st, P->stream));
-  else PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream, dct));
+  auto ytc_args = [&](const void* x, void* y, const unsigned char* mat) {
+    DenseTcArgs a{};
+    a.x = (const float*)x;
+    a.y = (float*)y;
+    a.mat = mat;
+    a.n = P->ny;
+    a.nt = dense_tc_out_tiles(P->ny);
+    a.nkc = dense_tc_k_chunks(P->ny);
+    a.ncs = 2LL * P->nxh;
+    a.nslab = P->nz;
+    a.slab = 2LL * P->nxh * P->ny;
+    a.ld = 2LL * P->nxh;
+    return a;
+  };
+  if (ytc) PP_K(P, K_FFTY_F, launch_dense_tc(ytc_args(spec, zs, P->d_ytc_f), P->d_st, P->stream));
+  else if (P->ystretch) {
+    if constexpr (std::is_same<T, double>::value)
+      PP_K(P, K_FFTY_F, launch_ydense(g, (const double*)P->d_ymt_f, spec, P->d_st, P->stream));
+  } else PP_K(P, K_FFTY_F, launch_ffty<T>(g, P->fy, twy, spec, 0, P->d_st, P->stream, dct));
   if (P->z_tc) {
-    PP_K(P, K_TRI, launch_zgemm(g, P->ze, reinterpret_cast<float2*>(spec), P->d_st, P->stream));
+    // z expansion on the tensor cores: zs -> the other spectrum buffer with
+    // the eigenvalue divide, then back
+    float* other = (float*)(zs == (C2<T>*)P->d_spec ? P->d_spec2 : P->d_spec);
+    DenseTcArgs a{};
+    a.n = P->nz;
+    a.nt = P->ze.nt;
+    a.nkc = P->ze.nkc;
+    a.ncs = 2LL * P->ny * P->nxh;
+    a.nslab = 1;
+    a.slab = 0;
+    a.ld = a.ncs;
+    a.x = (const float*)zs;
+    a.y = other;
+    a.mat = P->ze.a1;
+    a.mu = P->ze.mu;
+    a.lamx = P->d_lamx;
+    a.lamy = P->d_lamy;
+    a.nxh = P->nxh;
+    a.zero_mode = P->ze.zero_mode;
+    PP_K(P, K_TRI, launch_dense_tc(a, P->d_st, P->stream));
+    a.x = other;
+    a.y = (float*)zs;
+    a.mat = P->ze.a2;
+    a.mu = nullptr;
+    PP_K(P, K_TRI, launch_dense_tc(a, P->d_st, P->stream));
   } else if (P->zsolve == PP_ZSOLVE_COSINE) {
     if constexpr (std::is_same<T, double>::value) {
       const ZDivide zd{P->d_lamx, P->d_lamy, P->d_lamz};
-      PP_K(P, K_ZDCT_F, launch_zdct<double>(g, P->fz, P->d_twz, spec, 0, P->d_st, P->stream, P->d_dctz, zd));
-      PP_K(P, K_ZDCT_I, launch_zdct<double>(g, P->fz, P->d_twz, spec, 1, P->d_st, P->stream, P->d_dctz, zd));
+      PP_K(P, K_ZDCT_F, launch_zdct<double>(g, P->fz, P->d_twz, zs, 0, P->d_st, P->stream, P->d_dctz, zd));
+      PP_K(P, K_ZDCT_I, launch_zdct<double>(g, P->fz, P->d_twz, zs, 1, P->d_st, P->stream, P->d_dctz, zd));
     } else {
       return PP_ERR_UNSUPPORTED;
     }
   } else if (std::is_same<T, float>::value && P->use_z64) {
-    PP_K(P, K_TRI, launch_tridiag_z64(g, P->z64, reinterpret_cast<float2*>(spec), P->d_st, P->stream));
+    PP_K(P, K_TRI, launch_tridiag_z64(g, P->z64, reinterpret_cast<float2*>(zs), P->d_st, P->stream));
   } else {
-    PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, spec, ybuf, P->d_st, P->stream, P->d_mtab,
+    PP_K(P, K_TRI, launch_tridiag<T>(g, P->d_invd, zs, ybuf, P->d_st, P->stream, P->d_mtab,
                                      P->use_tri32 ? &P->tri32 : nullptr));
   }
-  if (P->ystretch) PP_K(P, K_FFTY_I, launch_ydense<T>(g, (const T*)P->d_ymt_i, spec, P->d_st, P->stream));
-  else PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream, dct));
+  if (ytc) PP_K(P, K_FFTY_I, launch_dense_tc(ytc_args(zs, spec, P->d_ytc_i), P->d_st, P->stream));
+  else if (P->ystretch) {
+    if constexpr (std::is_same<T, double>::value)
+      PP_K(P, K_FFTY_I, launch_ydense(g, (const double*)P->d_ymt_i, spec, P->d_st, P->stream));
+  } else PP_K(P, K_FFTY_I, launch_ffty<T>(g, P->fy, twy, spec, 1, P->d_st, P->stream, dct));
   PP_K(P, K_FFTX_I, launch_fftx_inv<T>(g, P->fx, twx, spec, scale, p, p_zero, P->d_st, P->stream, delta,
                                        sdelta));
   return PP_OK;
@@ -414,6 +466,9 @@ void free_plan(pp_plan_s* P) {
   if (P->d_ym_f) cudaFree(P->d_ym_f);
   if (P->d_ymt_f) cudaFree(P->d_ymt_f);
   if (P->d_ymt_i) cudaFree(P->d_ymt_i);
+  if (P->d_ytc_f) cudaFree(P->d_ytc_f);
+  if (P->d_ytc_i) cudaFree(P->d_ytc_i);
+  if (P->d_spec2) cudaFree(P->d_spec2);
   if (P->d_twz) cudaFree(P->d_twz);
   if (P->d_dctz) cudaFree(P->d_dctz);
   if (P->d_lamz) cudaFree(P->d_lamz);
@@ -563,21 +618,38 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   }
   if (ystretch) {
     std::vector<float> ymf(ymet.begin(), ymet.end());
-    const size_t nm = (size_t)G.ny * G.ny;
-    const size_t esz = (prec == PP_FP64) ? sizeof(double) : sizeof(float);
-    if ((st = up(&P->d_ym, ymet)) != PP_OK || (st = dalloc(&P->d_ym_f, ymf.size() * sizeof(float))) != PP_OK ||
-        (st = dalloc(&P->d_ymt_f, nm * esz)) != PP_OK || (st = dalloc(&P->d_ymt_i, nm * esz)) != PP_OK) {
+    const int ny = G.ny;
+    const size_t nm = (size_t)ny * ny;
+    if ((st = up(&P->d_ym, ymet)) != PP_OK || (st = dalloc(&P->d_ym_f, ymf.size() * sizeof(float))) != PP_OK) {
       free_plan(P);
       return st;
     }
     bool ok = cudaMemcpy(P->d_ym_f, ymf.data(), ymf.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
     if (prec == PP_FP64) {
-      ok = ok && cudaMemcpy(P->d_ymt_f, ymt_f.data(), nm * esz, cudaMemcpyHostToDevice) == cudaSuccess &&
-           cudaMemcpy(P->d_ymt_i, ymt_i.data(), nm * esz, cudaMemcpyHostToDevice) == cudaSuccess;
+      if ((st = up((double**)&P->d_ymt_f, ymt_f)) != PP_OK || (st = up((double**)&P->d_ymt_i, ymt_i)) != PP_OK) {
+        free_plan(P);
+        return st;
+      }
     } else {
-      std::vector<float> f1(ymt_f.begin(), ymt_f.end()), f2(ymt_i.begin(), ymt_i.end());
-      ok = ok && cudaMemcpy(P->d_ymt_f, f1.data(), nm * esz, cudaMemcpyHostToDevice) == cudaSuccess &&
-           cudaMemcpy(P->d_ymt_i, f2.data(), nm * esz, cudaMemcpyHostToDevice) == cudaSuccess;
+      // row-major M[m][k] of both products, then their BF16 hi/lo tiles
+      std::vector<double> mf(nm), mi(nm);
+      for (int r = 0; r < ny; ++r)
+        for (int k = 0; k < ny; ++k) {
+          mf[(size_t)r * ny + k] = ymt_f[(size_t)k * ny + r];  // (V^T W)[r][k]
+          mi[(size_t)r * ny + k] = ymt_i[(size_t)k * ny + r];  // V[r][k]
+        }
+      std::vector<uint16_t> tf, ti;
+      dense_tc_tiles(mf, ny, tf);
+      dense_tc_tiles(mi, ny, ti);
+      const size_t nsp2 = (size_t)(G.nx / 2 + 1) * ny * nz;
+      if ((st = dalloc(&P->d_ytc_f, tf.size() * sizeof(uint16_t))) != PP_OK ||
+          (st = dalloc(&P->d_ytc_i, ti.size() * sizeof(uint16_t))) != PP_OK ||
+          (st = dalloc(&P->d_spec2, nsp2 * sizeof(float2))) != PP_OK) {
+        free_plan(P);
+        return st;
+      }
+      ok = ok && cudaMemcpy(P->d_ytc_f, tf.data(), tf.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(P->d_ytc_i, ti.data(), ti.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) == cudaSuccess;
     }
     if (!ok) { free_plan(P); return PP_ERR_CUDA; }
   }
@@ -669,16 +741,21 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   g.ym = P->d_ym;
   g.ym_f = P->d_ym_f;
   if (prec == PP_MIXED_TC) {
-    int nzp = 0, zm = 0;
+    int zm = 0;
+    const int nt = dense_tc_out_tiles(nz);
     std::vector<float> mu;
+    std::vector<double> mf, mi;
     std::vector<uint16_t> a1, a2;
-    if (!build_zeigen_host(nz, dzf.data(), inv_dzc.data(), &nzp, mu, &zm, a1, a2)) {
+    if (!build_zeigen_host(nz, dzf.data(), inv_dzc.data(), nt * 256, mu, &zm, mf, mi)) {
       free_plan(P);
       return PP_ERR_NUMERIC;
     }
+    dense_tc_tiles(mf, nz, a1);
+    dense_tc_tiles(mi, nz, a2);
     if ((st = dalloc(&P->d_mu, mu.size() * sizeof(float))) != PP_OK ||
         (st = dalloc(&P->d_za1, a1.size() * sizeof(uint16_t))) != PP_OK ||
         (st = dalloc(&P->d_za2, a2.size() * sizeof(uint16_t))) != PP_OK ||
+        (!P->d_spec2 && (st = dalloc(&P->d_spec2, nsp * sizeof(float2))) != PP_OK) ||
         cudaMemcpy(P->d_mu, mu.data(), mu.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(P->d_za1, a1.data(), a1.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(P->d_za2, a2.data(), a2.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -686,11 +763,10 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
       return st != PP_OK ? st : PP_ERR_CUDA;
     }
     P->z_tc = true;
-    P->ze.nzp = nzp;
+    P->ze.nt = nt;
+    P->ze.nkc = dense_tc_k_chunks(nz);
     P->ze.mu = P->d_mu;
     P->ze.zero_mode = zm;
-    P->ze.lamx = P->d_lamx;
-    P->ze.lamy = P->d_lamy;
     P->ze.a1 = P->d_za1;
     P->ze.a2 = P->d_za2;
   }

@@ -314,12 +314,13 @@ cudaError_t launch_adj_grho(const Geo& g, const double* tx, const double* ty, co
 
 int reduce_blocks();  // number of partial sums the reduction kernels write
 
-// y step on a stretched y between walls (Sec. 3.3.1 eigenexpansion with a
-// numerical eigenbasis): every z plane of the spectrum, X[j][kx], becomes
-// M X with M = V^T W (forward, inverse = 0) or V (inverse = 1); mt holds
-// M transposed, mt[j * ny + m] = M[m][j] (pp_kernels_ydense.cu).  ny <= 1024.
-template <typename T>
-cudaError_t launch_ydense(const Geo& g, const T* mt, C2<T>* spec, const DevStatus* st, cudaStream_t s);
+// y step of FP64 plans on a stretched y between walls (Sec. 3.3.1
+// eigenexpansion with a numerical eigenbasis): every z plane of the
+// spectrum, X[j][kx], becomes M X in place with M = V^T W (forward) or V
+// (back); mt holds M transposed, mt[j * ny + m] = M[m][j]
+// (pp_kernels_ydense.cu).  ny <= 1024.  Mixed plans take the tensor-core
+// dense transform (launch_dense_tc) instead.
+cudaError_t launch_ydense(const Geo& g, const double* mt, double2* spec, const DevStatus* st, cudaStream_t s);
 
 // Host: eigenpairs of a symmetric tridiagonal S (diagonal d, off-diagonal e)
 // by Sturm-sequence bisection and inverse iteration with Gram-Schmidt,
@@ -334,20 +335,44 @@ bool sym_tridiag_eigen(const std::vector<double>& d, const std::vector<double>& 
 bool build_yeigen_host(int ny, const double* dyf, const double* inv_dyc, std::vector<double>& lam,
                        std::vector<double>& mt_fwd, std::vector<double>& mt_inv);
 
-// Tables of the tensor-core z solve (pp_zgemm.cu).
-struct ZEigen {
-  int nzp;                  // nz padded to a multiple of 128
-  const float* mu;          // [nzp] eigenvalues of L_z (0 on padded modes)
-  int zero_mode;            // index of the zero eigenvalue
-  const double* lamx;       // [nxh]
-  const double* lamy;       // [ny]
-  const unsigned char* a1;  // bf16 hi/lo tiles of V^T W
-  const unsigned char* a2;  // bf16 hi/lo tiles of V
+// Dense transform of strided real lines on the tensor cores, out of place
+// (pp_dense_tc.cu): column g of the real view (slab s = g / ncs, offset
+// c = g % ncs) has entries x_k = x[s * slab + k * ld + c], k < n, and gets
+// y_m = f(m, g) sum_k M[m][k] x_k at y[s * slab + m * ld + c]; f = 1, or
+// with mu set f = 1 / (mu_m + lamx[kx] + lamy[ky]) for the complex entry
+// g / 2 = ky * nxh + kx, 0 for m = zero_mode at g / 2 = 0.  BF16x3 products
+// with FP32 accumulation; M comes as dense_tc_tiles.
+struct DenseTcArgs {
+  const float* x;
+  float* y;
+  const unsigned char* mat;
+  int n, nt, nkc;             // line length; dense_tc_out_tiles(n), dense_tc_k_chunks(n)
+  long long ncs, nslab, slab, ld;
+  const float* mu;            // null: f = 1
+  const double* lamx;
+  const double* lamy;
+  int nxh;
+  int zero_mode;
 };
-cudaError_t launch_zgemm(const Geo& g, const ZEigen& ze, float2* spec, DevStatus* st, cudaStream_t s);
-size_t zgemm_smem_bytes(int nzp);
-// Host: eigen decomposition of L_z and the bf16 hi/lo tiles of V^T W and V.
-bool build_zeigen_host(int nz, const double* dzf, const double* inv_dzc, int* nzp_out, std::vector<float>& mu_out,
-                       int* zero_mode, std::vector<uint16_t>& a1, std::vector<uint16_t>& a2);
+int dense_tc_out_tiles(int n);
+int dense_tc_k_chunks(int n);
+void dense_tc_tiles(const std::vector<double>& M, int n, std::vector<uint16_t>& out);
+cudaError_t launch_dense_tc(const DenseTcArgs& a, DevStatus* st, cudaStream_t s);
+
+// Tables of the tensor-core z expansion (PP_MIXED_TC): two launches of the
+// dense transform, V^T W with the eigenvalue divide into the second
+// spectrum buffer, then V back.
+struct ZEigen {
+  int nt, nkc;              // dense_tc_out_tiles(nz), dense_tc_k_chunks(nz)
+  const float* mu;          // [nt * 256] eigenvalues of L_z (0 on padded modes)
+  int zero_mode;            // index of the zero eigenvalue
+  const unsigned char* a1;  // dense_tc_tiles of V^T W
+  const unsigned char* a2;  // dense_tc_tiles of V
+};
+// Host: eigen decomposition of L_z (pp_eigen_host.cu): eigenvalues (FP32,
+// zero-padded to `pad`), the zero mode, and the row-major matrices V^T W
+// and V.
+bool build_zeigen_host(int nz, const double* dzf, const double* inv_dzc, int pad, std::vector<float>& mu_out,
+                       int* zero_mode, std::vector<double>& m_fwd, std::vector<double>& m_inv);
 
 }  // namespace pp

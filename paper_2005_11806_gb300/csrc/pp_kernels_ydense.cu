@@ -1,7 +1,8 @@
-// y step of the eigenexpansion solve on a stretched y between walls
-// (Sec. 3.3.1): the y part of L is W^{-1} T with W = diag(dyf), and its
-// W-orthonormal eigenvectors V are dense, so the transform is a matrix
-// product per z plane.  The spectrum of plane k is X[j][kx] (complex, kx
+// y step of the eigenexpansion solve of FP64 plans on a stretched y between
+// walls (Sec. 3.3.1): the y part of L is W^{-1} T with W = diag(dyf), and
+// its W-orthonormal eigenvectors V are dense, so the transform is a matrix
+// product per z plane, here on the FP64 pipe (the mixed plans run it on the
+// tensor cores, pp_dense_tc.cu).  The spectrum of plane k is X[j][kx] (complex, kx
 // fastest); the forward step writes (V^T W) X, the inverse step V X, in
 // place.
 //
@@ -84,21 +85,16 @@ static cudaError_t launch_ydense_r(const Geo& g, const T* mt, C2<T>* spec, const
   return cudaGetLastError();
 }
 
-// Columns per block: 4 (FP64) or 8 (FP32) complex values of a row, 64 bytes.
-template <typename T>
-cudaError_t launch_ydense(const Geo& g, const T* mt, C2<T>* spec, const DevStatus* st, cudaStream_t s) {
-  constexpr int TX = sizeof(T) == sizeof(double) ? 4 : 8;
-  const int rows = (g.ny + 255) / 256;
-  switch (rows) {
-    case 1: return launch_ydense_r<T, TX, 1>(g, mt, spec, st, s);
-    case 2: return launch_ydense_r<T, TX, 2>(g, mt, spec, st, s);
-    case 3: return launch_ydense_r<T, TX, 3>(g, mt, spec, st, s);
-    case 4: return launch_ydense_r<T, TX, 4>(g, mt, spec, st, s);
+// Columns per block: 4 complex FP64 values of a row, 64 bytes.
+cudaError_t launch_ydense(const Geo& g, const double* mt, double2* spec, const DevStatus* st, cudaStream_t s) {
+  constexpr int TX = 4;
+  switch ((g.ny + 255) / 256) {
+    case 1: return launch_ydense_r<double, TX, 1>(g, mt, spec, st, s);
+    case 2: return launch_ydense_r<double, TX, 2>(g, mt, spec, st, s);
+    case 3: return launch_ydense_r<double, TX, 3>(g, mt, spec, st, s);
+    case 4: return launch_ydense_r<double, TX, 4>(g, mt, spec, st, s);
     default: return cudaErrorInvalidValue;
   }
 }
-
-template cudaError_t launch_ydense<double>(const Geo&, const double*, double2*, const DevStatus*, cudaStream_t);
-template cudaError_t launch_ydense<float>(const Geo&, const float*, float2*, const DevStatus*, cudaStream_t);
 
 }  // namespace pp

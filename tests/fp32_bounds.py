@@ -38,22 +38,28 @@ def mixed_solve_bound(nx, ny, passes=1, ywalls=False, margin=1.0):
     return margin * passes * per_solve * U32
 
 
+# Relative error of one term of a BF16x3 split product (hi*hi + hi*lo +
+# lo*hi): x = x_hi + x_lo + dx with |x_lo| <= 2^-9 |x| and |dx| <= 2^-9
+# |x_lo|, the same for the matrix entry, so the dropped lo*lo and the two
+# dx terms are each at most 2^-18 of |m x|; FP32 accumulation adds u.
+BF16X3 = 3 * 2.0 ** -18 + U32
+
+
 def mixed_solve_bound_dense_y(nx, ny, dyf, tc=False, nz=None, margin=1.0):
-    """The same bound with the y transforms as dense FP32 products (a
-    stretched y between walls).  Each output of a product is an FMA chain of
-    length ny, so its error is at most ny u sum_j |M_mj x_j| (worst case,
-    no cancellation); normwise || |M| |x| || <= sqrt(ny) ||M|| ||x||, and the
-    forward (V^T W) and inverse (V) matrices of the W-orthonormal basis
-    have norms sqrt(max dyf) and 1 / sqrt(min dyf), so a forward-inverse
-    pair carries sqrt(max dyf / min dyf).  Each of the two y products thus
-    adds ny sqrt(ny max dyf / min dyf) u.  With tc (the tensor-core z
-    expansion) the two z products are BF16x3 (the dropped lo*lo term is
-    2^-16 of a product, times 2^-1 for the rounding of each half): nz
-    sqrt(nz) 2^-17 each, in the same worst-case form."""
+    """The same bound with the y transforms as dense BF16x3 products on the
+    tensor cores (a stretched y between walls).  Each output of a product is
+    a sum of ny terms, so its error is at most ny BF16X3 sum_j |M_mj x_j|
+    (worst case, no cancellation); normwise || |M| |x| || <= sqrt(ny) ||M||
+    ||x||, and the forward (V^T W) and inverse (V) matrices of the
+    W-orthonormal basis have norms sqrt(max dyf) and 1 / sqrt(min dyf), so a
+    forward-inverse pair carries sqrt(max dyf / min dyf).  Each of the two y
+    products thus adds ny sqrt(ny max dyf / min dyf) BF16X3.  With tc (the
+    tensor-core z expansion) the two z products add nz sqrt(nz) BF16X3 each,
+    in the same worst-case form."""
     import math
     ratio = float(max(dyf)) / float(min(dyf))
-    dense = ny * math.sqrt(ny * ratio)
-    per_solve = (1 + 3 * 2 * stockham_passes(nx) + 2 * dense + 2) * U32
+    dense = ny * math.sqrt(ny * ratio) * BF16X3
+    per_solve = (1 + 3 * 2 * stockham_passes(nx) + 2) * U32 + 2 * dense
     if tc:
-        per_solve += 2 * nz * math.sqrt(nz) * 2.0 ** -17
+        per_solve += 2 * nz * math.sqrt(nz) * BF16X3
     return margin * per_solve
