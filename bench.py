@@ -76,6 +76,9 @@ def parse():
                     help="skip timing the passes of a plan with walls in y (cosine y transform)")
     ap.add_argument("--no-zcosine", action="store_true",
                     help="skip timing the cosine z solve against the tridiagonal one (FP64, uniform z)")
+    ap.add_argument("--no-ystretch", action="store_true",
+                    help="skip timing the passes of a plan with a stretched y between walls (dense "
+                         "eigenbasis y step on the tensor cores for mixed plans)")
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the leg that times the hybrid-z mixed plan beside the headline")
     ap.add_argument("--no-sphere256", action="store_true",
@@ -447,6 +450,57 @@ def run_ours(args, rank, world, local_rank):
                          "note": ("the benchmark's fields with walls at y = 0 and y = 2 pi, one projection of "
                                   f"{passes} Method III passes; cosine y transforms (one complex FFT of length ny "
                                   "per column plus the pairwise twiddles), algorithmic bytes = spectrum read + write")}
+        plan = make_plan(args.precision)
+
+    # a stretched y between walls (tanh clustering, beta = 1.5): the same
+    # fields in the duct, a fixed number of passes; the y step is the dense
+    # W-orthonormal eigenbasis, on the tensor cores (BF16x3) for mixed plans
+    if not args.no_ystretch:
+        from paper_2005_11806_gb300 import workloads as wl
+        plan.close()
+        vsy = vs.clone()
+        vsy[:, 0, :] = 0.0
+        yf = wl.tanh_yfaces(w.ny, w.ly, 1.5)
+        plans = pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, lz, zfaces=w.zf, precision=args.precision,
+                        method=args.method, ywalls=True, yfaces=yf)
+        spasses = 80
+
+        def sstep():
+            pp.pressure_mixture_density(plans.handle, phi, w.rho_g, w.rho_l, rho)
+            return pp.pressure_correct(plans.handle, us, vsy, ws, rho, S, w.dt, p, u, v, wo,
+                                       rtol=0.0, maxit=spasses, allow_not_converged=True)
+        for _ in range(3):
+            sstep()
+        torch.cuda.synchronize()
+        pp.pressure_profile_enable(plans.handle, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sinfo = sstep()
+        e1.record()
+        torch.cuda.synchronize()
+        sms = e0.elapsed_time(e1)
+        skern, _ = pp.pressure_profile_read(plans.handle)
+        pp.pressure_profile_enable(plans.handle, False)
+        plans.close()
+        tc = args.precision != "fp64"
+        # BF16x3: three products of 2 ny^2 flop per real column (2 nxh nz of them)
+        flops = (3 if tc else 1) * 2.0 * w.ny * w.ny * 2 * (w.nx // 2 + 1) * w.nz
+        sk = {}
+        for k in ("ffty_fwd", "ffty_inv"):
+            n_, t_ = skern[k]
+            avg = t_ / n_
+            tf = flops / (avg / 1e3) / 1e12
+            sk[k] = {"avg_ms": round(avg, 4), "achieved_tflops": round(tf, 1)}
+            if tc:
+                sk[k]["frac_of_measured_bf16_sustained"] = round(tf / bf16_peak, 4)
+        out["ystretch"] = {"passes": sinfo["iters"], "ms_per_pass": round(sms / max(sinfo["iters"], 1), 4),
+                           "res_after": sinfo["res_final"], "y_transforms": sk,
+                           "kernels_avg_ms": {k: round(t / n, 4) for k, (n, t) in skern.items()},
+                           "note": ("the benchmark's fields in a duct with y faces tanh-clustered at the walls "
+                                    f"(beta 1.5), one projection of {spasses} Method III passes; y step = dense "
+                                    "eigenvector products per z plane, " +
+                                    ("BF16x3 on the tensor cores (k_dense_tc), flops = 3 x 2 ny^2 per real column"
+                                     if tc else "FP64 on the CUDA cores (k_ydense)"))}
         plan = make_plan(args.precision)
 
     # the z solve by the cosine basis against the tridiagonal solve: FP64
