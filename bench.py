@@ -166,7 +166,10 @@ def algorithmic(kernel, w, precision):
         return {"bytes": 2 * cs * nsp, "fp64_flops": 0 if precision != "fp64" else 45 * npts}
     if kernel == "tridiag_z":
         if precision == "mixed_tc":
-            return {"bytes": 2 * cs * nsp, "fp64_flops": 0, "tensor_flops": 3 * 2 * 2 * w.nz * 2 * nsp}
+            # per launch: the z expansion is two launches of the dense
+            # transform (V^T W with the divide, then V), each one BF16x3
+            # product of 2 nz flop per output over the 2 nsp real columns
+            return {"bytes": 2 * cs * nsp, "fp64_flops": 0, "tensor_flops": 3 * 2 * w.nz * 2 * nsp}
         if precision == "fp64":
             # f in, forward values out and back in, x out; multipliers and inverse pivots (FP64)
             return {"bytes": (4 * cs + 16) * nsp, "fp64_flops": 6 * nsp}

@@ -26,6 +26,9 @@
 // Every wait is bounded; a wait that runs out sets DevStatus::pad, the other
 // roles stop at their next wait, and the CTA drains its copies and MMAs
 // before it frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "pp_internal.cuh"
 #include "pp_tc.cuh"
 
@@ -41,27 +44,52 @@ constexpr int kKC = 32;                       // K per chunk
 constexpr uint32_t kSbo = (kKC / 8) * 128;    // 8-row group stride of a chunk
 constexpr int kHalfD = kCols * kKC * 2;       // bytes of one BF16 half of a data chunk (8 KB)
 constexpr int kHalfM = kOut * kKC * 2;        // bytes of one BF16 half of a matrix chunk (16 KB)
-constexpr int kStagesD = 4;
 constexpr int kStagesM = 4;
+constexpr int kBytesF = kCols * kKC * 4;      // FP32 data chunk brought by TMA (16 KB)
 constexpr int kThreadsTC = 320;
-constexpr size_t kSmemTC = (size_t)kStagesM * 2 * kHalfM + (size_t)kStagesD * 2 * kHalfD + 1024;
+
+// Stage counts: with TMA (one slab, 16-byte aligned rows: the z expansion)
+// the copy thread also brings each 32 x 128 FP32 data chunk into a staging
+// ring, and the BF16 ring shrinks to fit 224 KB; without it the convert
+// warps load the columns themselves.
+template <bool TMA> struct Cfg {
+  static constexpr int SD = TMA ? 2 : 4;   // BF16 data stages
+  static constexpr int SF = TMA ? 4 : 0;   // FP32 staging stages
+  static constexpr size_t smem =
+      (size_t)kStagesM * 2 * kHalfM + (size_t)SD * 2 * kHalfD + (size_t)SF * kBytesF + 1024;
+};
 
 struct Bars {
-  uint64_t dfull[kStagesD], dempty[kStagesD], mfull[kStagesM], mempty[kStagesM], tfull[2], tempty[2], drain;
+  uint64_t dfull[4], dempty[4], mfull[kStagesM], mempty[kStagesM], ffull[4], fempty[4], tfull[2], tempty[2],
+      drain;
 };
+
+__device__ __forceinline__ void tma_load_2d(void* dst_smem, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                            uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      :: "r"(smem_u32(dst_smem)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreadsTC, 1) k_dense_tc(DenseTcArgs a, DevStatus* st) {
+template <bool TMA>
+__global__ void __launch_bounds__(kThreadsTC, 1) k_dense_tc(DenseTcArgs a, const __grid_constant__ CUtensorMap tmap,
+                                                          DevStatus* st) {
   if (st != nullptr && st->done) return;
+  constexpr int kStagesD = Cfg<TMA>::SD, kStagesF = Cfg<TMA>::SF;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
   unsigned char* sM = smem;                                   // kStagesM x (hi | lo)
   unsigned char* sD = smem + (size_t)kStagesM * 2 * kHalfM;   // kStagesD x (hi | lo)
+  unsigned char* sF = sD + (size_t)kStagesD * 2 * kHalfD;     // kStagesF x FP32 [32][128]
   __shared__ __align__(8) Bars bars;
   __shared__ uint32_t taddr_s;
   __shared__ volatile int fail_s;
-  __shared__ int consumed_s;
+  __shared__ int consumed_s, consumed_f;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long total_cols = a.ncs * a.nslab;
   const long long ntiles = (total_cols + kCols - 1) / kCols;
@@ -69,11 +97,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_dense_tc(DenseTcArgs a, DevSt
   if (tid == 0) {
     for (int i = 0; i < kStagesD; ++i) { mbar_init(&bars.dfull[i], 128); mbar_init(&bars.dempty[i], 1); }
     for (int i = 0; i < kStagesM; ++i) { mbar_init(&bars.mfull[i], 1); mbar_init(&bars.mempty[i], 1); }
+    for (int i = 0; i < kStagesF; ++i) { mbar_init(&bars.ffull[i], 1); mbar_init(&bars.fempty[i], 128); }
     for (int i = 0; i < 2; ++i) { mbar_init(&bars.tfull[i], 1); mbar_init(&bars.tempty[i], 128); }
     mbar_init(&bars.drain, 1);
     mbar_init_fence();
     fail_s = 0;
     consumed_s = 0;
+    consumed_f = 0;
   }
   if (warp == 1) tmem_alloc(&taddr_s, 2 * kOut);
   tc_fence_before();
@@ -81,15 +111,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_dense_tc(DenseTcArgs a, DevSt
   tc_fence_after();
   const uint32_t tbase = taddr_s;
   auto fail = [&]() { fail_s = 1; };
-  long long issued = 0;  // matrix chunks copied (warp 0, lane 0)
+  long long issued = 0, issued_f = 0;  // chunks copied (warp 0, lane 0)
 
   if (warp == 0) {
-    // ---- matrix producer ------------------------------------------------
+    // ---- matrix producer (and, with TMA, the data chunks) ----------------
     if (lane == 0) {
       long long q = 0;
       for (long long it = blockIdx.x; it < nitems && !fail_s; it += gridDim.x) {
         const int h = (int)(it % a.nt);
         for (int kc = 0; kc < a.nkc && !fail_s; ++kc, ++q) {
+          if constexpr (TMA) {
+            const int f = (int)(q % kStagesF);
+            if (!mbar_wait(&bars.fempty[f], (uint32_t)(((q / kStagesF) & 1) ^ 1))) { fail(); break; }
+            // rows past n and columns past the view read as zeros
+            tma_load_2d(sF + (size_t)f * kBytesF, &tmap, (int)((it / a.nt) * kCols), kc * kKC, &bars.ffull[f],
+                        kBytesF);
+            ++issued_f;
+          }
           const int s = (int)(q % kStagesM);
           if (!mbar_wait(&bars.mempty[s], (uint32_t)(((q / kStagesM) & 1) ^ 1))) { fail(); break; }
           bulk_copy(sM + (size_t)s * 2 * kHalfM, a.mat + ((size_t)h * a.nkc + kc) * 2 * kHalfM, 2 * kHalfM,
@@ -135,6 +173,37 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_dense_tc(DenseTcArgs a, DevSt
       if (!mbar_wait(&bars.drain, 0)) fail();
     }
   } else if (warp < 6) {
+   if constexpr (TMA) {
+    // ---- data converters, TMA-fed: thread = column n of the staged chunk ----
+    const int n = tid - 64;
+    long long q = 0;
+    for (long long it = blockIdx.x; it < nitems && !fail_s; it += gridDim.x) {
+      for (int kc = 0; kc < a.nkc; ++kc, ++q) {
+        const int f = (int)(q % kStagesF);
+        if (!mbar_wait(&bars.ffull[f], (uint32_t)((q / kStagesF) & 1))) { fail(); break; }
+        const float* stg = reinterpret_cast<const float*>(sF + (size_t)f * kBytesF);
+        float v[kKC];
+#pragma unroll
+        for (int e = 0; e < kKC; ++e) v[e] = stg[e * kCols + n];  // a warp reads 128 consecutive bytes
+        mbar_arrive(&bars.fempty[f]);
+        if (tid == 64) consumed_f = (int)(q + 1);
+        const int s = (int)(q % kStagesD);
+        if (!mbar_wait(&bars.dempty[s], (uint32_t)(((q / kStagesD) & 1) ^ 1))) { fail(); break; }
+        unsigned char* dst = sD + (size_t)s * 2 * kHalfD;
+#pragma unroll
+        for (int grp = 0; grp < kKC / 8; ++grp) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) split_pack2(v[grp * 8 + e], v[grp * 8 + e + 1], hi[e >> 1], lo[e >> 1]);
+          const uint32_t o = core_off(n, grp * 8, kSbo);
+          *reinterpret_cast<uint4*>(dst + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(dst + kHalfD + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        fence_async_smem();
+        mbar_arrive(&bars.dfull[s]);
+      }
+    }
+   } else {
     // ---- data converters ---------------------------------------------------
     // Converter warp cw = warp - 2 takes columns 64 (cw & 1) + 2 lane and
     // + 1 (a float2: columns come in pairs within a slab, ncs being even) and
@@ -220,6 +289,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_dense_tc(DenseTcArgs a, DevSt
       PP_CONVERT_STEP(v3, v2)
     }
 #undef PP_CONVERT_STEP
+   }
   } else {
     // ---- epilogue: lane quarter = warp % 4, thread = column ---------------
     const int qd = warp & 3;
@@ -244,19 +314,31 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_dense_tc(DenseTcArgs a, DevSt
       if (!ok) { fail(); break; }
       tc_fence_after();
       for (int c16 = 0; c16 < kOut / 16; ++c16) {
+        const int m0 = h * kOut + c16 * 16;
+        // divide epilogue: 16 eigenvalues as four 16-byte loads (mu is padded
+        // to whole 256-output blocks); the reciprocal is the fast one (2^-22
+        // relative, far inside the 2^-16 of the split products)
+        float fac[16];
+        if (a.mu != nullptr) {
+#pragma unroll
+          for (int e4 = 0; e4 < 4; ++e4) {
+            const float4 m4 = __ldg(reinterpret_cast<const float4*>(a.mu + m0) + e4);
+            fac[4 * e4 + 0] = __fdividef(1.f, m4.x + lam);
+            fac[4 * e4 + 1] = __fdividef(1.f, m4.y + lam);
+            fac[4 * e4 + 2] = __fdividef(1.f, m4.z + lam);
+            fac[4 * e4 + 3] = __fdividef(1.f, m4.w + lam);
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (pinned && m0 + e == a.zero_mode) fac[e] = 0.f;
+        }
         float v[16];
         tmem_ld16(tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * kOut + c16 * 16), v);
-        const int m0 = h * kOut + c16 * 16;
         if (valid) {
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int m = m0 + e;
-            if (m < a.n) {
-              float r = v[e];
-              if (a.mu != nullptr)
-                r = (pinned && m == a.zero_mode) ? 0.f : r * __frcp_rn(a.mu[m] + lam);
-              dst[(long long)m * a.ld] = r;
-            }
+            if (m < a.n) dst[(long long)m * a.ld] = (a.mu != nullptr) ? v[e] * fac[e] : v[e];
           }
         }
       }
@@ -270,6 +352,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_dense_tc(DenseTcArgs a, DevSt
     // copies still in flight land before the CTA's shared memory goes away
     for (long long q = consumed_s; q < issued; ++q)
       mbar_wait(&bars.mfull[q % kStagesM], (uint32_t)((q / kStagesM) & 1));
+    if constexpr (TMA)
+      for (long long q = consumed_f; q < issued_f; ++q)
+        mbar_wait(&bars.ffull[q % kStagesF], (uint32_t)((q / kStagesF) & 1));
     if (st != nullptr) st->pad = 1;
   }
   tc_fence_before();
@@ -307,18 +392,58 @@ void dense_tc_tiles(const std::vector<double>& M, int n, std::vector<uint16_t>& 
     }
 }
 
-cudaError_t launch_dense_tc(const DenseTcArgs& a, DevStatus* st, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC);
+namespace {
+
+// 2D tensor map of the view for the TMA data path: x = the column (FP32,
+// contiguous), y = the line entry k (stride ld), box 128 x 32, zero fill
+// outside.  False when the driver entry point or the encoding fails.
+bool encode_view_map(const DenseTcArgs& a, CUtensorMap* map) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (encode == nullptr) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)a.ncs, (cuuint64_t)a.n};
+  const cuuint64_t strides[1] = {(cuuint64_t)a.ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kCols, (cuuint32_t)kKC};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.x), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool TMA>
+cudaError_t launch_dense_tc_t(const DenseTcArgs& a, const CUtensorMap& map, int grid, DevStatus* st,
+                              cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_dense_tc<TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Cfg<TMA>::smem);
   if (e != cudaSuccess) return e;
+  k_dense_tc<TMA><<<grid, kThreadsTC, Cfg<TMA>::smem, s>>>(a, map, st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_dense_tc(const DenseTcArgs& a, DevStatus* st, cudaStream_t s) {
   int dev = 0, nsm = 0;
+  cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const long long ntiles = (a.ncs * a.nslab + kCols - 1) / kCols;
   const long long nitems = ntiles * a.nt;
   if (nitems <= 0) return cudaSuccess;
   const int grid = (int)(nitems < nsm ? nitems : nsm);
-  k_dense_tc<<<grid, kThreadsTC, kSmemTC, s>>>(a, st);
-  return cudaGetLastError();
+  // TMA data path: one slab, rows 16-byte aligned (the tensor map's stride
+  // rule and the x coordinate rule: tiles start at multiples of 128 floats)
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  const bool tma = a.nslab == 1 && (a.ld * sizeof(float)) % 16 == 0 && ((uintptr_t)a.x % 16) == 0 &&
+                   a.ncs < (1LL << 32) && encode_view_map(a, &map);
+  return tma ? launch_dense_tc_t<true>(a, map, grid, st, s) : launch_dense_tc_t<false>(a, map, grid, st, s);
 }
 
 }  // namespace pp
