@@ -116,8 +116,8 @@ typedef struct {
                               of length ny; pressure_solve, pressure_correct (Methods I, II
                               and III), pressure_solve_adjoint, pressure_mixture_density, the
                               thermodynamic source (adiabatic y walls) and the predictor
-                              (no-slip y walls) take them; the batched and no-allocation
-                              entry points take periodic y only */
+                              (no-slip y walls) take them, and so do the allocation-free
+                              solve and the batched entry points (per grid) */
     const double* yfaces;  /* host, ny+1 increasing face coordinates spanning ly, or NULL
                               (uniform y).  Walls in y only (PP_ERR_UNSUPPORTED otherwise),
                               2 <= ny <= 1024, any parity.  The y step of the eigenexpansion
@@ -278,9 +278,11 @@ pp_status pressure_solve_adjoint(pp_plan plan, const double* rho, const double* 
  * inside the library, held by every GPU that loads the library until the
  * process exits; grids whose spectral array, pivots and tables do not fit
  * return PP_ERR_TOO_LARGE (about 128 x 128 x 64 cells fit).  Grids are
- * periodic in x and y (bc = {PERIODIC, PERIODIC, WALL}); nx even, nx and ny
- * with prime factors in {2, 3, 5} and at most 2048 (else
- * PP_ERR_UNSUPPORTED); zfaces (host, nz + 1 increasing values, or NULL) is
+ * periodic in x, periodic or walled in y (bc = {PERIODIC, PERIODIC, WALL}
+ * or {PERIODIC, WALL, WALL}: the cosine y basis, ny even), walled in z, with
+ * uniform y (yfaces NULL); nx even, nx and ny with prime factors in
+ * {2, 3, 5} and at most 2048 (else PP_ERR_UNSUPPORTED); zfaces (host,
+ * nz + 1 increasing values, or NULL) is
  * read during the call only.  f and p must be device pointers (host
  * pointers return PP_ERR_INVALID_ARG); the caller owns them.  Every table
  * is computed on the device, so the call copies nothing from the host: it
@@ -298,7 +300,8 @@ pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f, double* p
 /* ---- batched projections of independent grids -------------------------
  * Method III projections (Algorithm 1, Sec. 3.3.1) of ngrids independent
  * grids of different sizes, mixed precision only (PP_MIXED_FP32), solved
- * together: each stage of a pass is one grouped launch over the tiles of all
+ * together (each grid periodic in x, periodic or walled in y with uniform
+ * spacing, walled in z): each stage of a pass is one grouped launch over the tiles of all
  * grids, and one call is one CUDA graph launch holding the set-up, a
  * device-side while loop over passes (each grid stops at its own tolerance
  * or maxit; the loop ends when all have stopped) and the correction.

@@ -29,6 +29,7 @@ struct GridDev {
   FftDesc fx, fy;
   const float2* twx;
   const float2* twy;
+  const float2* dcty;  // walls in y: exp(-i pi m / (2 ny)); null: periodic y
   const double* invd;
   const double* mtab;
   TriF32 tri;  // FP32 tables of the well-conditioned z columns
@@ -168,7 +169,8 @@ __global__ void __launch_bounds__(256) kb_ffty(GridDev* G, const int2* __restric
   const GridDev& d = G[w.x];
   if (d.st->done) return;
   const int bz = w.y / d.ntx, bx = w.y - bz * d.ntx;
-  stage_ffty<float, DIR>(d.g, d.fy, d.twy, d.spec, d.tx, bx, bz, smem_raw);
+  if (d.dcty != nullptr) stage_ffty<float, DIR, true>(d.g, d.fy, d.twy, d.spec, d.tx, bx, bz, smem_raw, d.dcty);
+  else stage_ffty<float, DIR>(d.g, d.fy, d.twy, d.spec, d.tx, bx, bz, smem_raw);
 }
 
 __global__ void __launch_bounds__(kTriThreads, 8) kb_tridiag(GridDev* G, const int2* __restrict__ work) {
@@ -454,8 +456,12 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
   for (int i = 0; i < ngrids; ++i) {
     const pp_grid& G = grids[i];
     if (G.nx < 2 || G.ny < 1 || G.nz < 1 || !(G.lx > 0) || !(G.ly > 0) || !(G.lz > 0)) return PP_ERR_INVALID_ARG;
-    if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL) return PP_ERR_UNSUPPORTED;
+    if (G.bc[0] != PP_BC_PERIODIC || (G.bc[1] != PP_BC_PERIODIC && G.bc[1] != PP_BC_WALL) ||
+        G.bc[2] != PP_BC_WALL)
+      return PP_ERR_UNSUPPORTED;
     if (G.yfaces != nullptr) return PP_ERR_UNSUPPORTED;
+    // walls in y: the cosine transform runs as one complex FFT of even length
+    if (G.bc[1] == PP_BC_WALL && (G.ny < 2 || (G.ny & 1) != 0)) return PP_ERR_UNSUPPORTED;
     if ((G.nx & 1) != 0 || G.nx > 2048 || G.ny > 2048) return PP_ERR_UNSUPPORTED;
     FftDesc t;
     if (!factor(G.nx, &t) || !factor(G.ny, &t)) return PP_ERR_UNSUPPORTED;
@@ -479,7 +485,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
   // pool layout: per grid, every buffer and table
   struct Off {
     size_t spec, E, delta, sdelta, b, red, st, cx, cy, cz, diag, rhof, invd, mtab,
-        twx, twy, idzf, idzc, dzf, za, zc, idzff, cwf, lamx, lamy, mtabf, invdf, zcf;
+        twx, twy, dcty, idzf, idzc, dzf, za, zc, idzff, cwf, lamx, lamy, mtabf, invdf, zcf;
   };
   std::vector<Off> off(ngrids);
   Carve cv;
@@ -504,6 +510,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     o.rhof = cv.take(nc * 4);
     o.invd = cv.take(nsp * 8); o.mtab = cv.take(nsp * 8);
     o.twx = cv.take((size_t)G.nx * sizeof(float2)); o.twy = cv.take((size_t)G.ny * sizeof(float2));
+    o.dcty = cv.take((size_t)G.ny * sizeof(float2));
     o.idzf = cv.take((size_t)G.nz * 8); o.idzc = cv.take((size_t)(G.nz + 1) * 8); o.dzf = cv.take((size_t)G.nz * 8);
     o.za = cv.take((size_t)G.nz * 8); o.zc = cv.take((size_t)G.nz * 8); o.idzff = cv.take((size_t)G.nz * 4);
     o.cwf = cv.take(3 * (size_t)(G.nz + 1) * 4);
@@ -544,7 +551,16 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     const double dx = G.lx / nx, dy = G.ly / ny;
     std::vector<double> lamx(nxh), lamy(ny);
     for (int k = 0; k < nxh; ++k) { const double sn = std::sin(pi * k / nx); lamx[k] = -4.0 / (dx * dx) * sn * sn; }
-    for (int k = 0; k < ny; ++k) { const double sn = std::sin(pi * k / ny); lamy[k] = -4.0 / (dy * dy) * sn * sn; }
+    // walls in y: the eigenvalues of the Neumann second difference on the
+    // cosine modes cos(pi k (j + 1/2) / ny)
+    const bool ywall = G.bc[1] == PP_BC_WALL;
+    for (int k = 0; k < ny; ++k) {
+      const double sn = std::sin(pi * k / (ywall ? 2.0 * ny : (double)ny));
+      lamy[k] = -4.0 / (dy * dy) * sn * sn;
+    }
+    std::vector<float2> dcty(ny);
+    for (int m = 0; m < ny; ++m)
+      dcty[m] = make_float2((float)std::cos(pi * m / (2.0 * ny)), (float)(-std::sin(pi * m / (2.0 * ny))));
     const std::vector<float> cwf = layer_factors_f32(nz, dzf, idzc, 1.0 / (dx * dx), 1.0 / (dy * dy));
     std::vector<float2> twx(nx), twy(ny);
     for (int m = 0; m < nx; ++m) twx[m] = make_float2((float)std::cos(two_pi * m / nx), (float)std::sin(two_pi * m / nx));
@@ -555,7 +571,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
         {o.idzc, idzc.data(), idzc.size() * 8}, {o.za, za.data(), za.size() * 8}, {o.zc, zc.data(), zc.size() * 8},
         {o.idzff, idzff.data(), idzff.size() * 4}, {o.lamx, lamx.data(), lamx.size() * 8},
         {o.lamy, lamy.data(), lamy.size() * 8}, {o.zcf, zcf.data(), zcf.size() * 4},
-        {o.cwf, cwf.data(), cwf.size() * 4}};
+        {o.cwf, cwf.data(), cwf.size() * 4}, {o.dcty, dcty.data(), dcty.size() * sizeof(float2)}};
     for (const Up& u : ups)
       if (cudaMemcpy(P + u.off, u.src, u.bytes, cudaMemcpyHostToDevice) != cudaSuccess) { free_batch(B); return PP_ERR_CUDA; }
     Geo& g = d.g;
@@ -564,7 +580,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     g.inv_dzf = (const double*)(P + o.idzf); g.inv_dzc = (const double*)(P + o.idzc);
     g.dzf = (const double*)(P + o.dzf); g.za = (const double*)(P + o.za); g.zc = (const double*)(P + o.zc);
     g.inv_dzf_f = (const float*)(P + o.idzff); g.cw_f = (const float*)(P + o.cwf); g.lz = zf[nz] - zf[0];
-    g.ywall = 0;
+    g.ywall = ywall ? 1 : 0;
     g.ym = nullptr;
     g.ym_f = nullptr;
     d.fc.cx = (double*)(P + o.cx); d.fc.cy = (double*)(P + o.cy); d.fc.cz = (double*)(P + o.cz);
@@ -572,6 +588,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     factor(nx, &d.fx);
     factor(ny, &d.fy);
     d.twx = (const float2*)(P + o.twx); d.twy = (const float2*)(P + o.twy);
+    d.dcty = ywall ? (const float2*)(P + o.dcty) : nullptr;
     d.invd = (const double*)(P + o.invd); d.mtab = (const double*)(P + o.mtab);
     d.spec = (float2*)(P + o.spec); d.E = (float*)(P + o.E); d.delta = (float*)(P + o.delta);
     d.sdelta = (float*)(P + o.sdelta);

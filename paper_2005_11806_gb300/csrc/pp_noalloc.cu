@@ -84,10 +84,14 @@ __global__ void k_na_uniform_faces(double lz, int nz, double* __restrict__ zf) {
 // wavenumbers -(4/h^2) sin^2(pi k / n) of the periodic second difference,
 // and the z metrics of the faces zf (cell widths, centre distances, the
 // sub- and super-diagonal of L_z), each entry computed from zf directly.
+// With walls in y (ywall) the y eigenvalues are those of the Neumann second
+// difference, -(4/dy^2) sin^2(pi m / (2 ny)), and dcty receives the cosine
+// transform's twiddles exp(-i pi m / (2 ny)).
 __global__ void k_na_tables(int nx, int ny, int nz, double dx, double dy, const double* __restrict__ zf,
                             double2* __restrict__ twx, double2* __restrict__ twy, double* __restrict__ dzf,
                             double* __restrict__ idzf, double* __restrict__ idzc, double* __restrict__ za,
-                            double* __restrict__ zc, double* __restrict__ lamx, double* __restrict__ lamy) {
+                            double* __restrict__ zc, double* __restrict__ lamx, double* __restrict__ lamy,
+                            int ywall, double2* __restrict__ dcty) {
   const int nxh = nx / 2 + 1;
   int nmax = nx > ny ? nx : ny;
   if (nz + 1 > nmax) nmax = nz + 1;
@@ -105,8 +109,12 @@ __global__ void k_na_tables(int nx, int ny, int nz, double dx, double dy, const 
     if (m < ny) {
       sincospi(2.0 * (double)m / (double)ny, &sn, &cs);
       twy[m] = make_double2(cs, sn);
-      const double s = sinpi((double)m / (double)ny);
+      const double s = sinpi((double)m / (ywall ? 2.0 * (double)ny : (double)ny));
       lamy[m] = -4.0 / (dy * dy) * s * s;
+      if (ywall) {
+        sincospi((double)m / (2.0 * (double)ny), &sn, &cs);
+        dcty[m] = make_double2(cs, -sn);
+      }
     }
     if (m < nxh) {
       const double s = sinpi((double)m / (double)nx);
@@ -150,9 +158,13 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   const pp_grid& G = *grid;
   if (G.nx < 2 || G.ny < 1 || G.nz < 1 || !(G.lx > 0) || !(G.ly > 0) || !(G.lz > 0))
     return PP_ERR_INVALID_ARG;
-  if (G.bc[0] != PP_BC_PERIODIC || G.bc[1] != PP_BC_PERIODIC || G.bc[2] != PP_BC_WALL || G.yfaces != nullptr)
+  if (G.bc[0] != PP_BC_PERIODIC || (G.bc[1] != PP_BC_PERIODIC && G.bc[1] != PP_BC_WALL) ||
+      G.bc[2] != PP_BC_WALL || G.yfaces != nullptr)
     return PP_ERR_UNSUPPORTED;
+  const int ywall = (G.bc[1] == PP_BC_WALL) ? 1 : 0;
   if ((G.nx & 1) != 0) return PP_ERR_UNSUPPORTED;
+  // walls in y: the cosine transform runs as one complex FFT of even length
+  if (ywall && (G.ny < 2 || (G.ny & 1) != 0)) return PP_ERR_UNSUPPORTED;
   // the limits of pressure_plan_create: one transform line per block in the
   // FFT kernels, 32-bit cell offsets
   if (G.nx > 2048 || G.ny > 2048) return PP_ERR_UNSUPPORTED;
@@ -177,6 +189,7 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   const size_t o_zc = c.take((size_t)nz * sizeof(double));
   const size_t o_lamx = c.take((size_t)nxh * sizeof(double));
   const size_t o_lamy = c.take((size_t)ny * sizeof(double));
+  const size_t o_dcty = c.take(ywall ? (size_t)ny * sizeof(double2) : 0);
   const size_t o_red = c.take((size_t)reduce_blocks() * sizeof(double));
   const size_t o_st = c.take(sizeof(DevStatus));
   const size_t o_zf = c.take((size_t)(nz + 1) * sizeof(double));
@@ -215,7 +228,7 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
     k_na_tables<<<nb, 256, 0, s>>>(nx, ny, nz, dx, dy, dzfaces, (double2*)(S + o_twx), (double2*)(S + o_twy),
                                    (double*)(S + o_dzf), (double*)(S + o_idzf), (double*)(S + o_idzc),
                                    (double*)(S + o_za), (double*)(S + o_zc), (double*)(S + o_lamx),
-                                   (double*)(S + o_lamy));
+                                   (double*)(S + o_lamy), ywall, (double2*)(S + o_dcty));
   }
   if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
 
@@ -230,8 +243,9 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   g.za = (const double*)(S + o_za);
   g.zc = (const double*)(S + o_zc);
   g.lz = zn - z0;
-  g.ywall = 0;
+  g.ywall = ywall;
   double2* spec = (double2*)(S + o_spec);
+  const double2* dct = ywall ? (const double2*)(S + o_dcty) : nullptr;
   double* invd = (double*)(S + o_invd);
   const double2* dtwx = (const double2*)(S + o_twx);
   const double2* dtwy = (const double2*)(S + o_twy);
@@ -244,9 +258,9 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   if (launch_init_status(st, s) != cudaSuccess ||
       launch_setup_pivots(g, (const double*)(S + o_lamx), (const double*)(S + o_lamy), invd, s) != cudaSuccess ||
       launch_resid_fftx<double>(g, none, fx, dtwx, f, 1.0, nullptr, nullptr, 1, 0, spec, nullptr, nullptr, st, s) != cudaSuccess ||
-      launch_ffty<double>(g, fy, dtwy, spec, 0, st, s) != cudaSuccess ||
+      launch_ffty<double>(g, fy, dtwy, spec, 0, st, s, dct) != cudaSuccess ||
       launch_tridiag<double>(g, invd, spec, spec, st, s) != cudaSuccess ||
-      launch_ffty<double>(g, fy, dtwy, spec, 1, st, s) != cudaSuccess ||
+      launch_ffty<double>(g, fy, dtwy, spec, 1, st, s, dct) != cudaSuccess ||
       launch_fftx_inv<double>(g, fx, dtwx, spec, scale, p, 1, st, s) != cudaSuccess ||
       launch_remove_mean(g, p, red, st, s) != cudaSuccess)
     return PP_ERR_CUDA;

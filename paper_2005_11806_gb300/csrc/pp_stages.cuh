@@ -423,11 +423,29 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
   }
 }
 
-// Complex transform along y of one z-plane tile of tx consecutive kx.
-template <typename T, int DIR>
+// Row order of the cosine transform through a complex FFT (Makhoul): the
+// sequence v_r = x_{2r} (r < n/2), v_r = x_{2(n-1-r)+1} (r >= n/2), n even.
+__device__ __forceinline__ int dct_row(int r, int n) { return (r < (n >> 1)) ? 2 * r : 2 * (n - 1 - r) + 1; }
+
+template <typename T> __device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {  // a * conj(b)
+  C2<T> r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.y * b.x - a.x * b.y;
+  return r;
+}
+
+// Complex transform along y of one z-plane tile of tx consecutive kx.  DCT:
+// the cosine transform of walls in y (dct = exp(-i pi m / (2 ny))), in the
+// steps of the persistent kernel below: the forward pass loads the rows in
+// the order dct_row and finishes with X_r = (w_r Z_r + conj(w_r)
+// Z_{ny-r}) / 2, the inverse pass pairs (Y_m, Y_{ny-m}) before its FFT and
+// stores the rows back in the order dct_row.
+template <typename T, int DIR, bool DCT = false>
 __device__ __forceinline__ void stage_ffty(const Geo& g, const FftDesc& fy, const C2<T>* __restrict__ twy,
                                            C2<T>* __restrict__ spec, int tx, int bx, int bz,
-                                           unsigned char* smem_raw) {
+                                           unsigned char* smem_raw, const C2<T>* __restrict__ dct = nullptr) {
+  constexpr bool REORDER_IN = DCT && DIR < 0;
+  constexpr bool REORDER_OUT = DCT && DIR > 0;
   const int ny = g.ny, nxh = g.nxh;
   C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* bufB = bufA + (size_t)ny * tx;
@@ -441,20 +459,49 @@ __device__ __forceinline__ void stage_ffty(const Geo& g, const FftDesc& fy, cons
     if (fast) load_twiddles_smem(twy, ny, twb);
   }
   for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
-    const int y = t >> lg_tx, x = t & (tx - 1);
+    const int r = t >> lg_tx, x = t & (tx - 1);
+    const int y = REORDER_IN ? dct_row(r, ny) : r;
     C2<T> v; v.x = (T)0; v.y = (T)0;
     if (kx0 + x < nxh) v = spec[base + (size_t)y * nxh + kx0 + x];
     bufA[t] = v;
   }
   __syncthreads();
+  if constexpr (REORDER_OUT) {
+    // V_m and V_{ny-m} from the pair (Y_m, Y_{ny-m}), in place; V_0 = Y_0
+    const int half = ny >> 1;
+    for (int t = threadIdx.x; t < half * tx; t += blockDim.x) {
+      const int m = 1 + (t >> lg_tx), x = t & (tx - 1);
+      const C2<T> w = dct[m];
+      const C2<T> a = bufA[m * tx + x], b = bufA[(ny - m) * tx + x];
+      C2<T> d, e;  // a - i b, a + i b
+      d.x = a.x + b.y; d.y = a.y - b.x;
+      e.x = a.x - b.y; e.y = a.y + b.x;
+      bufA[m * tx + x] = cmulc<T>(d, w);
+      if (m != ny - m) bufA[(ny - m) * tx + x] = cmul<T>(e, w);
+    }
+    __syncthreads();
+  }
   const C2<T>* res = nullptr;
   if constexpr (F32) {
     if (fast) res = smem_f2() + fft_dispatch_smem<DIR, true>(0, ny * tx, twb, fy, tx, tx, 1, threadIdx.x, blockDim.x);
   }
   if (!fast) res = fft_dispatch<T, DIR, true>(bufA, bufB, fy, tx, tx, 1, twy, threadIdx.x, blockDim.x);
   for (int t = threadIdx.x; t < ny * tx; t += blockDim.x) {
-    const int y = t >> lg_tx, x = t & (tx - 1);
-    if (kx0 + x < nxh) spec[base + (size_t)y * nxh + kx0 + x] = res[t];
+    const int r = t >> lg_tx, x = t & (tx - 1);
+    if (kx0 + x >= nxh) continue;
+    if constexpr (REORDER_IN) {
+      // X_r = (w_r Z_r + conj(w_r) Z_{ny-r}) / 2
+      const C2<T> w = dct[r];
+      const C2<T> a = cmul<T>(res[t], w);
+      const C2<T> b = cmulc<T>(res[(r == 0 ? 0 : ny - r) * tx + x], w);
+      C2<T> o;
+      o.x = (T)0.5 * (a.x + b.x);
+      o.y = (T)0.5 * (a.y + b.y);
+      spec[base + (size_t)r * nxh + kx0 + x] = o;
+    } else {
+      const int y = REORDER_OUT ? dct_row(r, ny) : r;
+      spec[base + (size_t)y * nxh + kx0 + x] = res[t];
+    }
   }
 }
 
@@ -468,10 +515,6 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Row order of the cosine transform through a complex FFT (Makhoul): the
-// sequence v_r = x_{2r} (r < n/2), v_r = x_{2(n-1-r)+1} (r >= n/2), n even.
-__device__ __forceinline__ int dct_row(int r, int n) { return (r < (n >> 1)) ? 2 * r : 2 * (n - 1 - r) + 1; }
 
 // Lines of the spectrum [nz][ny][nxh] that a persistent transform walks.
 // AXIS = 0: along y (length ny, element stride nxh), one tile per (z plane,
@@ -515,12 +558,6 @@ __device__ __forceinline__ void ffty_issue_tile(const Geo& g, const C2<T>* __res
   cp_async_commit();
 }
 
-template <typename T> __device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {  // a * conj(b)
-  C2<T> r;
-  r.x = a.x * b.x + a.y * b.y;
-  r.y = a.y * b.x - a.x * b.y;
-  return r;
-}
 
 // Persistent y transform.  DCT = false: complex DFT along y (periodic y).
 // DCT = true (walls in y): the eigenbasis of the Neumann second difference

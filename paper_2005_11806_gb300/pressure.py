@@ -195,7 +195,7 @@ def pressure_plan_create(nx, ny, nz, lx, ly, lz, zfaces=None, precision="fp64", 
     return out.value
 
 
-def _grid(nx, ny, nz, lx, ly, lz, zfaces):
+def _grid(nx, ny, nz, lx, ly, lz, zfaces, ywalls=False):
     g = pp_grid()
     g.nx, g.ny, g.nz = int(nx), int(ny), int(nz)
     g.lx, g.ly, g.lz = float(lx), float(ly), float(lz)
@@ -205,14 +205,15 @@ def _grid(nx, ny, nz, lx, ly, lz, zfaces):
         if keep.shape != (int(nz) + 1,):
             raise ValueError("zfaces must hold nz + 1 values")
         g.zfaces = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    g.bc[0], g.bc[1], g.bc[2] = PP_BC_PERIODIC, PP_BC_PERIODIC, PP_BC_WALL
+    g.bc[0], g.bc[1], g.bc[2] = PP_BC_PERIODIC, PP_BC_WALL if ywalls else PP_BC_PERIODIC, PP_BC_WALL
     return g, keep
 
 
-def pressure_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, zfaces=None, stream=None):
+def pressure_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, zfaces=None, stream=None, ywalls=False):
     """FP64 constant-coefficient solve that allocates no device memory (see
-    the header).  f, p: CUDA float64 tensors.  Returns after enqueueing."""
-    g, keep = _grid(nx, ny, nz, lx, ly, lz, zfaces)
+    the header).  f, p: CUDA float64 tensors.  ``ywalls``: walls at y = 0 and
+    y = ly.  Returns after enqueueing."""
+    g, keep = _grid(nx, ny, nz, lx, ly, lz, zfaces, ywalls)
     n = int(nx) * int(ny) * int(nz)
     for x in (f, p):
         got = x.size if isinstance(x, np.ndarray) else getattr(x, "numel", lambda: None)()
@@ -346,7 +347,8 @@ def pressure_profile_read(plan):
 class Batch:
     """Batched projections of independent grids (packed field buffers).
 
-    ``grids``: list of dicts with nx, ny, nz, lx, ly, lz and optional zfaces.
+    ``grids``: list of dicts with nx, ny, nz, lx, ly, lz and optional zfaces
+    and ywalls (walls at y = 0 and y = ly).
     """
 
     def __init__(self, grids, precision="mixed", stream=None):
@@ -354,7 +356,8 @@ class Batch:
         arr = (pp_grid * self.n)()
         self._keep = []
         for k, gd in enumerate(grids):
-            g, keep = _grid(gd["nx"], gd["ny"], gd["nz"], gd["lx"], gd["ly"], gd["lz"], gd.get("zfaces"))
+            g, keep = _grid(gd["nx"], gd["ny"], gd["nz"], gd["lx"], gd["ly"], gd["lz"], gd.get("zfaces"),
+                            bool(gd.get("ywalls", False)))
             arr[k] = g
             self._keep.append(keep)
         out = ctypes.c_void_p()

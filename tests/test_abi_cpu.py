@@ -121,7 +121,8 @@ def test_host_only_entry_points():
     ((2, 4096, 1), (0, 0, 1), "PP_ERR_UNSUPPORTED"),   # one y line per FFT block: ny <= 2048
     ((7, 4, 3), (0, 0, 1), "PP_ERR_UNSUPPORTED"),      # odd nx
     ((14, 4, 3), (0, 0, 1), "PP_ERR_UNSUPPORTED"),     # prime factor 7
-    ((8, 8, 8), (0, 1, 1), "PP_ERR_UNSUPPORTED"),      # walls in y: periodic y only
+    ((8, 7, 8), (0, 1, 1), "PP_ERR_UNSUPPORTED"),      # walls in y need an even ny
+    ((8, 8, 8), (1, 1, 1), "PP_ERR_UNSUPPORTED"),      # walls in x
     ((0, 8, 8), (0, 0, 1), "PP_ERR_INVALID_ARG"),      # empty grid
 ])
 def test_noalloc_rejects_bad_descriptors_before_any_cuda_call(dims, bc, code):
@@ -137,3 +138,27 @@ def test_noalloc_rejects_bad_descriptors_before_any_cuda_call(dims, bc, code):
     got = pressure.lib().pressure_solve_noalloc(ctypes.byref(g), ctypes.cast(buf, ctypes.c_void_p),
                                                 ctypes.cast(buf, ctypes.c_void_p), None)
     assert got == getattr(pressure, code)
+
+
+@pytest.mark.parametrize("dims,bc,yfaces,code", [
+    ((8, 7, 8), (0, 1, 1), False, "PP_ERR_UNSUPPORTED"),   # walls in y need an even ny
+    ((8, 8, 8), (1, 0, 1), False, "PP_ERR_UNSUPPORTED"),   # walls in x
+    ((8, 8, 8), (0, 1, 1), True, "PP_ERR_UNSUPPORTED"),    # a stretched y is single-plan only
+    ((8, 0, 8), (0, 0, 1), False, "PP_ERR_INVALID_ARG"),   # empty grid
+])
+def test_batch_rejects_bad_descriptors_before_any_cuda_call(dims, bc, yfaces, code):
+    """pressure_batch_create checks every grid before it allocates."""
+    import ctypes
+    pressure = _lib_or_build()
+    g = pressure.pp_grid()
+    g.nx, g.ny, g.nz = dims
+    g.lx, g.ly, g.lz = 1.0, 1.0, 1.0
+    g.bc[0], g.bc[1], g.bc[2] = bc
+    keep = np.linspace(0.0, 1.0, dims[1] + 1)
+    if yfaces:
+        g.yfaces = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    arr = (pressure.pp_grid * 1)(g)
+    out = ctypes.c_void_p()
+    got = pressure.lib().pressure_batch_create(arr, 1, pressure.PRECISIONS["mixed"], None, ctypes.byref(out))
+    assert got == getattr(pressure, code)
+    assert out.value is None

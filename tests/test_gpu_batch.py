@@ -53,7 +53,8 @@ def _unpack(batch, cases, p, u, v, w):
 
 
 def _run_batch(pp, cases, rtol, maxit):
-    grids = [dict(nx=w.nx, ny=w.ny, nz=w.nz, lx=w.lx, ly=w.ly, lz=float(w.zf[-1]), zfaces=w.zf) for w, _ in cases]
+    grids = [dict(nx=w.nx, ny=w.ny, nz=w.nz, lx=w.lx, ly=w.ly, lz=float(w.zf[-1]), zfaces=w.zf, ywalls=w.ywalls)
+             for w, _ in cases]
     batch = pp.Batch(grids)
     us, vs, ws, rho, S = _pack(batch, cases)
     p, u, v = (torch.empty(batch.ncell, dtype=torch.float64, device="cuda") for _ in range(3))
@@ -96,6 +97,52 @@ def test_batch_converged_vs_oracle(pp):
         assert infos[k]["status"] == 0 and infos[k]["res_final"] <= 1e-10
         g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf)
         p0, u0, v0, w0, _ = orc.method3(g, w.us, w.vs, w.ws, rho, w.S, w.dt, rtol=1e-13, maxit=3000)
+        Sc = w.S - orc.volume_mean(g, w.S)
+        d0 = orc.divergence(g, w.us, w.vs, w.ws) - Sc
+        _, u, v, ww = res[k]
+        assert np.linalg.norm(orc.divergence(g, u, v, ww) - Sc) <= 1.0001e-10 * np.linalg.norm(d0)
+        for a, b in ((u, u0), (v, v0), (ww, w0)):
+            assert _rel(a, b) < 1e-9
+
+
+def _mixed_wall_cases(ratio):
+    """Periodic and walled-y grids in one batch (ducts: walls in y and z)."""
+    out = _cases(ratio)[:2]
+    for nx, ny, nz, stretched, seed in ((24, 20, 18, True, 1), (32, 30, 16, False, 2), (16, 12, 20, True, 3)):
+        w = wl.channel_bubble_case(nx, ny, nz, seed=1300 + seed, rho_ratio=ratio, stretched=stretched)
+        out.append((w, orc.mixture_density(w.phi, w.rho_g, w.rho_l)))
+    return out
+
+
+def test_batch_walls_in_y_match_single_grid_plans(pp):
+    """A batch that mixes periodic and walled-y grids (the cosine y basis for
+    the latter): fixed pass count, each member equals its single-grid plan."""
+    cases = _mixed_wall_cases(1000.0)
+    infos, res = _run_batch(pp, cases, 0.0, 25)
+    for k, (w, rho) in enumerate(cases):
+        assert infos[k]["iters"] == 25
+        plan = pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, float(w.zf[-1]), zfaces=w.zf, precision="mixed",
+                       ywalls=w.ywalls)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+        p = torch.empty(w.shape, dtype=torch.float64, device="cuda")
+        u, v = torch.empty_like(p), torch.empty_like(p)
+        ww = torch.empty((w.nz + 1, w.ny, w.nx), dtype=torch.float64, device="cuda")
+        pp.pressure_correct(plan.handle, dev(w.us), dev(w.vs), dev(w.ws), dev(rho), dev(w.S), w.dt, p, u, v, ww,
+                            rtol=0.0, maxit=25, allow_not_converged=True)
+        for got, ref in zip(res[k], (p, u, v, ww)):
+            assert _rel(got, ref.cpu().numpy()) < 1e-12, k
+        if w.ywalls:
+            assert np.all(res[k][2][:, 0, :] == 0.0)
+        plan.close()
+
+
+def test_batch_walls_in_y_converged_vs_oracle(pp):
+    cases = _mixed_wall_cases(10.0)
+    infos, res = _run_batch(pp, cases, 1e-10, 3000)
+    for k, (w, rho) in enumerate(cases):
+        assert infos[k]["status"] == 0 and infos[k]["res_final"] <= 1e-10
+        g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf, ywalls=w.ywalls)
+        p0, u0, v0, w0, _ = orc.method3(g, w.us, w.vs, w.ws, rho, w.S, w.dt, rtol=1e-13, maxit=4000)
         Sc = w.S - orc.volume_mean(g, w.S)
         d0 = orc.divergence(g, w.us, w.vs, w.ws) - Sc
         _, u, v, ww = res[k]

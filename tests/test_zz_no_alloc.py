@@ -30,8 +30,8 @@ def pp():
     return pressure
 
 
-def _plan_solve(pp, dims, lengths, zf, f):
-    plan = pp.Plan(*dims, *lengths, zfaces=zf, precision="fp64")
+def _plan_solve(pp, dims, lengths, zf, f, ywalls=False):
+    plan = pp.Plan(*dims, *lengths, zfaces=zf, precision="fp64", ywalls=ywalls)
     p = torch.empty_like(f)
     pp.pressure_solve(plan.handle, f, p)
     torch.cuda.synchronize()
@@ -55,6 +55,30 @@ def test_noalloc_matches_plan_solve_twice(pp):
         err = float(torch.linalg.vector_norm(p - ref) / torch.linalg.vector_norm(ref))
         assert err < FP64_TOL, (dims, err)
         g = orc.Grid(nx, ny, nz, lengths[0], lengths[1], zf)
+        po = orc.solve_constant(g, f.cpu().numpy())
+        err_o = float(np.linalg.norm(p.cpu().numpy() - po) / np.linalg.norm(po))
+        assert err_o < FP64_TOL, (dims, err_o)
+
+
+def test_noalloc_walls_in_y(pp):
+    """Walls in y (the cosine y basis): the same solve as an FP64 plan with
+    walls in y and as the oracle, including a grid with radix-3 and radix-5
+    y lengths; a periodic call after it still matches (the tables are
+    rebuilt every call)."""
+    cases = [((32, 24, 16), (1.0, 0.8, 1.0), 1.5, 5, True),
+             ((20, 30, 9), (1.0, 1.3, 0.7), None, 6, True),
+             ((16, 12, 10), (1.0, 0.9, 1.1), None, 7, False)]
+    for dims, lengths, stretch, seed, ywalls in cases:
+        nx, ny, nz = dims
+        zf = wl.uniform_zfaces(nz, lengths[2]) if stretch is None else wl.tanh_zfaces(nz, lengths[2], stretch)
+        f = torch.from_numpy(np.random.default_rng(seed).standard_normal((nz, ny, nx))).cuda()
+        p = torch.full_like(f, float("nan"))
+        pp.pressure_solve_noalloc(nx, ny, nz, *lengths, f, p, zfaces=zf, ywalls=ywalls)
+        torch.cuda.synchronize()
+        ref = _plan_solve(pp, dims, lengths, zf, f, ywalls)
+        err = float(torch.linalg.vector_norm(p - ref) / torch.linalg.vector_norm(ref))
+        assert err < FP64_TOL, (dims, err)
+        g = orc.Grid(nx, ny, nz, lengths[0], lengths[1], zf, ywalls=ywalls)
         po = orc.solve_constant(g, f.cpu().numpy())
         err_o = float(np.linalg.norm(p.cpu().numpy() - po) / np.linalg.norm(po))
         assert err_o < FP64_TOL, (dims, err_o)
