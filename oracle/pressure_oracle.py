@@ -640,7 +640,8 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
     """The same gradients for any grid size, with Algorithm 1 as the solver.
 
     With W_c = diag(dzf) on cells and W_f = diag(dzf of the layer) on x/y
-    faces, diag(dzc) on z faces, the discrete operators satisfy
+    faces, diag(dzc) on z faces (on a stretched y: W_c = diag(dzf dyf), and
+    dzf dyf, dzf dyc, dzc dyf on x, y, z faces), the discrete operators satisfy
     D^T = -W_f G W_c^{-1} and G^T = -W_c D W_f^{-1}; hence
     A^T = W_c A W_c^{-1}, and lambda = W_c mu with
         A mu = -D(B W_f^{-1} g),
@@ -649,8 +650,6 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
     ``p`` is the converged pressure of the forward projection (computed
     here with the same tolerance when not given).
     """
-    if g.ystretched:
-        raise NotImplementedError("adjoint_method3: uniform y only (adjoint_direct takes a stretched y)")
     gw = _zero_walls(gw)
     gv = _zero_ywall_row(g, gv)
     rx, ry, rz = face_density(g, rho)
@@ -658,12 +657,22 @@ def adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=100
     wz = np.ones(g.nz + 1)
     wz[1:-1] = g.dzc[1:-1]
     wz = wz[:, None, None]
-    ya, yb, yc = gu / (rx * wlay), gv / (ry * wlay), gw / (rz * wz)
+    if g.ystretched:
+        # W_c = diag(dzf dyf) and the face weights of D^T = -W_f G W_c^{-1}
+        # on a stretched y: dzf dyf on x faces, dzf dyc on y faces (the wall
+        # row carries no unknown), dzc dyf on z faces
+        dyc = np.where(g.dyc > 0, g.dyc, 1.0)[None, :, None]
+        wx = wlay * g.dyf[None, :, None]
+        wy = wlay * dyc
+        wz = wz * g.dyf[None, :, None]
+    else:
+        wx = wy = wlay
+    ya, yb, yc = gu / (rx * wx), gv / (ry * wy), gw / (rz * wz)
     zero = np.zeros(g.shape)
     mu, _, _, _, info_adj = method3(g, -dt * ya, -dt * yb, -dt * yc, rho, zero, dt,
                                     rtol=rtol, maxit=maxit)
     gx, gy, gz = gradient(g, mu)
-    gus, gvs, gws = gu + wlay * gx, gv + wlay * gy, gw + wz * gz
+    gus, gvs, gws = gu + wx * gx, gv + wy * gy, gw + wz * gz
     gws = _zero_walls(gws)
     gvs = _zero_ywall_row(g, gvs)
     info_fwd = None

@@ -1065,7 +1065,6 @@ pp_status pressure_solve_adjoint(pp_plan P, const double* rho, const double* p, 
                                  pp_info* info) {
   if (check_plan(P) != PP_OK || !rho || !p || !gu || !gv || !gw || !gus || !gvs || !gws || !grho)
     return PP_ERR_INVALID_ARG;
-  if (P->ystretch) return PP_ERR_UNSUPPORTED;
   if (!(dt > 0.0) || !(rtol >= 0.0) || maxit < 0) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P), nw = nwface(P);
   pp_status s;

@@ -491,10 +491,13 @@ __global__ void k_adj_rhs(Geo g, const double* __restrict__ rho, const double* _
     const size_t cjm = c - (size_t)j * nx + (size_t)(j == 0 ? ny - 1 : j - 1) * nx;
     const double r = rho[c];
     const double idzf = g.inv_dzf[k];
-    yu[c] = -dt * (2.0 / (r + rho[cim])) * gu[c] * idzf;
+    // stretched y (face weights dzf s_j on x faces, dzf / t_j on y faces,
+    // dzc s_j on z faces; s_j = dyf_j / dy, t_j = dy / dyc_j)
+    const double is = g.ym ? g.ym[2 * ny + j] : 1.0, tj = g.ym ? g.ym[ny + j] : 1.0;
+    yu[c] = -dt * (2.0 / (r + rho[cim])) * gu[c] * idzf * is;
     // with walls in y the wall row of v is not an unknown: no gradient enters there
-    yv[c] = (g.ywall && j == 0) ? 0.0 : -dt * (2.0 / (r + rho[cjm])) * gv[c] * idzf;
-    yw[c] = (k == 0) ? 0.0 : -dt * (2.0 / (r + rho[c - plane])) * gw[c] * g.inv_dzc[k];
+    yv[c] = (g.ywall && j == 0) ? 0.0 : -dt * (2.0 / (r + rho[cjm])) * gv[c] * idzf * tj;
+    yw[c] = (k == 0) ? 0.0 : -dt * (2.0 / (r + rho[c - plane])) * gw[c] * g.inv_dzc[k] * is;
     if (k == nz - 1) yw[c + plane] = 0.0;
   }
 }
@@ -516,19 +519,22 @@ __global__ void k_adj_finish(Geo g, const double* __restrict__ rho, const double
     const size_t cjm = c - (size_t)j * nx + (size_t)(j == 0 ? ny - 1 : j - 1) * nx;
     const double dzf = g.dzf[k];
     const double r = rho[c];
-    const double a = gu[c] + dzf * (mu[c] - mu[cim]) * idx;
+    // stretched y: x-face weight dzf s_j, y-face weight dzf / t_j against
+    // G_y = t_j / dy (the two cancel), z-face weight dzc s_j
+    const double sj = g.ym ? g.ym[j] : 1.0, tj = g.ym ? g.ym[ny + j] : 1.0;
+    const double a = gu[c] + dzf * sj * (mu[c] - mu[cim]) * idx;
     const bool vwall = g.ywall && j == 0;  // wall row of v: zero gradient, no density dependence
     const double bb = vwall ? 0.0 : gv[c] + dzf * (mu[c] - mu[cjm]) * idy;
     gus[c] = a;
     gvs[c] = bb;
     const double bx = 2.0 / (r + rho[cim]), by = 2.0 / (r + rho[cjm]);
     tx[c] = -0.5 * bx * bx * (-dt * (p[c] - p[cim]) * idx * a);
-    ty[c] = vwall ? 0.0 : -0.5 * by * by * (-dt * (p[c] - p[cjm]) * idy * bb);
+    ty[c] = vwall ? 0.0 : -0.5 * by * by * (-dt * (p[c] - p[cjm]) * idy * tj * bb);
     if (k == 0) {
       gws[c] = 0.0;
       tz[c] = 0.0;
     } else {
-      const double cc = gw[c] + (mu[c] - mu[c - plane]);
+      const double cc = gw[c] + sj * (mu[c] - mu[c - plane]);
       gws[c] = cc;
       const double bz = 2.0 / (r + rho[c - plane]);
       tz[c] = -0.5 * bz * bz * (-dt * (p[c] - p[c - plane]) * g.inv_dzc[k] * cc);

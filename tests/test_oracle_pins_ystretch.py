@@ -169,6 +169,23 @@ def test_adjoint_direct_dot_product():
     assert np.all(av[:, 0, :] == 0.0)
 
 
+@pytest.mark.parametrize("ybeta,zbeta", [(1.5, None), (2.0, 1.5)])
+def test_adjoint_method3_equals_the_literal_transpose(ybeta, zbeta):
+    """The Algorithm-1 form of the adjoint (W-weighted transposes, the
+    gradient of mu through the projection loop) on a stretched y equals the
+    implicit differentiation of the definition with literal sparse
+    transposes, for u* and for rho; the y-wall row of the gradient is 0."""
+    g, us, vs, ws, rho, S = _case(6, 8, 5, ybeta, zbeta, ratio=100.0)
+    dt = 1e-3
+    rng = np.random.default_rng(21)
+    gu, gv, gw = rng.standard_normal(g.shape), rng.standard_normal(g.shape), rng.standard_normal(ws.shape)
+    ref = orc.adjoint_direct(g, us, vs, ws, rho, S, dt, gu, gv, gw)
+    got = orc.adjoint_method3(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=3000)
+    for a, b in zip(got[:4], ref):
+        assert _rel(a, b) < 1e-9
+    assert np.all(got[1][:, 0, :] == 0.0)
+
+
 def test_uniform_only_terms_refuse_a_stretched_y():
     g, us, vs, ws, rho, S = _case(4, 6, 4, 1.5)
     with pytest.raises(NotImplementedError):
@@ -227,3 +244,31 @@ def test_planted_uniform_volumes_are_caught(monkeypatch):
         test_cell_volumes_and_mean()
     with pytest.raises(AssertionError):
         test_constant_solve_vs_dense_lu((6, 8, 5), 1.5, None)
+
+
+def test_planted_uniform_adjoint_weights_are_caught(monkeypatch):
+    """The adjoint's face weights without the y metrics (dzf on every x/y
+    face, as on a uniform y)."""
+    def planted(g, us, vs, ws, rho, S, dt, gu, gv, gw, rtol=1e-13, maxit=1000, p=None):
+        gw = orc._zero_walls(gw)
+        gv = orc._zero_ywall_row(g, gv)
+        rx, ry, rz = orc.face_density(g, rho)
+        wlay = g.dzf[:, None, None]
+        wz = np.ones(g.nz + 1)
+        wz[1:-1] = g.dzc[1:-1]
+        wz = wz[:, None, None]
+        zero = np.zeros(g.shape)
+        mu = orc.method3(g, -dt * gu / (rx * wlay), -dt * gv / (ry * wlay), -dt * gw / (rz * wz), rho, zero, dt,
+                         rtol=rtol, maxit=maxit)[0]
+        gx, gy, gz = orc.gradient(g, mu)
+        gus = gu + wlay * gx
+        gvs = orc._zero_ywall_row(g, gv + wlay * gy)
+        gws = orc._zero_walls(gw + wz * gz)
+        pp = orc.method3(g, us, vs, ws, rho, S, dt, rtol=rtol, maxit=maxit)[0]
+        px, py, pz = orc.gradient(g, pp)
+        gbeta = orc._face_vector(-dt * px * gus, -dt * py * gvs, -dt * pz * gws)
+        beta = 1.0 / orc._face_vector(rx, ry, rz)
+        return gus, gvs, gws, orc._beta_to_rho(g, beta, gbeta), {}
+    monkeypatch.setattr(orc, "adjoint_method3", planted)
+    with pytest.raises(AssertionError):
+        test_adjoint_method3_equals_the_literal_transpose(1.5, None)
