@@ -127,10 +127,10 @@ typedef struct {
                               bisection and inverse iteration: forward V^T W f and back V c
                               as dense products per z plane (Sec. 3.3.1 needs homogeneous
                               conditions only).  pressure_solve, pressure_correct (Methods
-                              I, II, III), pressure_solve_adjoint and
-                              pressure_mixture_density take it; the thermodynamic source and
-                              the predictor return PP_ERR_UNSUPPORTED; PP_ERR_INVALID_ARG for
-                              faces that do not
+                              I, II, III), pressure_solve_adjoint, pressure_mixture_density
+                              and the thermodynamic source (pressure_p0_rate,
+                              pressure_divergence_source) take it; the predictor returns
+                              PP_ERR_UNSUPPORTED; PP_ERR_INVALID_ARG for faces that do not
                               increase or do not span ly (1e-12 relative). */
 } pp_grid;
 

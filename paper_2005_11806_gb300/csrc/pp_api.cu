@@ -885,7 +885,6 @@ pp_status pressure_plan_set_method(pp_plan P, int method) {
 pp_status pressure_p0_rate(pp_plan P, const double* phi, const double* kc, const double* T, const double* u,
                            const double* v, const double* w, double p0, double gamma, double* rp) {
   if (check_plan(P) != PP_OK || !phi || !kc || !T || !u || !v || !w || !rp) return PP_ERR_INVALID_ARG;
-  if (P->ystretch) return PP_ERR_UNSUPPORTED;
   if (!(gamma > 0.0) || !std::isfinite(p0)) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P), nw = nwface(P);
   const double *dphi, *dk, *dT, *du, *dv, *dw;
@@ -945,7 +944,6 @@ pp_status pressure_dp0dt_extrapolate(double rp_n, double rp_nm1, double dt_new, 
 pp_status pressure_divergence_source(pp_plan P, const double* phi, const double* kc, const double* T, double p0,
                                      double gamma, double dp0dt, double* S) {
   if (check_plan(P) != PP_OK || !phi || !kc || !T || !S) return PP_ERR_INVALID_ARG;
-  if (P->ystretch) return PP_ERR_UNSUPPORTED;
   if (!(gamma > 0.0) || p0 == 0.0 || !std::isfinite(p0) || !std::isfinite(dp0dt)) return PP_ERR_INVALID_ARG;
   const size_t nc = ncell(P);
   const double *dphi, *dk, *dT;

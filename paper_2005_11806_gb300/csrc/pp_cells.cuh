@@ -85,8 +85,13 @@ __device__ __forceinline__ double cell_conduction(const Geo& g, const double* __
   double sx = 0.5 * (k0 + kc[x.cip]) * (T[x.cip] - t0) + 0.5 * (k0 + kc[x.cim]) * (T[x.cim] - t0);
   // with walls in y no heat crosses the faces below row 0 and above row ny - 1
   const bool yhi = !(g.ywall && x.j + 1 == g.ny), ylo = !(g.ywall && x.j == 0);
-  double sy = (yhi ? 0.5 * (k0 + kc[x.cjp]) * (T[x.cjp] - t0) : 0.0) +
-              (ylo ? 0.5 * (k0 + kc[x.cjm]) * (T[x.cjm] - t0) : 0.0);
+  // stretched y: the face below row j is dyc_j = dy / t_j from the centre
+  // below, and the row is dyf_j = s_j dy wide
+  const double thi = (g.ym && yhi) ? g.ym[g.ny + x.j + 1] : 1.0, tlo = g.ym ? g.ym[g.ny + x.j] : 1.0;
+  const double isj = g.ym ? g.ym[2 * g.ny + x.j] : 1.0;
+  double sy = (yhi ? 0.5 * (k0 + kc[x.cjp]) * (T[x.cjp] - t0) * thi : 0.0) +
+              (ylo ? 0.5 * (k0 + kc[x.cjm]) * (T[x.cjm] - t0) * tlo : 0.0);
+  sy *= isj;
   double sz = 0.0;
   if (x.k + 1 < g.nz) sz += 0.5 * (k0 + kc[c + plane]) * (T[c + plane] - t0) * g.inv_dzc[x.k + 1];
   if (x.k > 0) sz += 0.5 * (k0 + kc[c - plane]) * (T[c - plane] - t0) * g.inv_dzc[x.k];

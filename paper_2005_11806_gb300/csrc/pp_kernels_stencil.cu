@@ -247,13 +247,14 @@ __global__ void k_thermo_partial(Geo g, const double* __restrict__ phi, const do
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
     const CellIdx x = cell_index(g, c);
     const double f = phi[c];
-    const double dv = dxdy * g.dzf[x.k];
+    const double sj = g.ym ? g.ym[x.j] : 1.0;  // stretched y: dyf_j = s_j dy
+    const double dv = dxdy * g.dzf[x.k] * sj;
     const double wlo = (x.k == 0) ? 0.0 : w[c];
     const double whi = (x.k == g.nz - 1) ? 0.0 : w[c + plane];
     // the wall row of v (walls in y) carries no flux, like the wall planes of w
     const double vlo = (g.ywall && x.j == 0) ? 0.0 : v[c];
     const double vhi = (g.ywall && x.j == g.ny - 1) ? 0.0 : v[x.cjp];
-    const double div = (u[x.cip] - u[c]) / g.dx + (vhi - vlo) / g.dy + (whi - wlo) * g.inv_dzf[x.k];
+    const double div = (u[x.cip] - u[c]) / g.dx + (vhi - vlo) / (g.dy * sj) + (whi - wlo) * g.inv_dzf[x.k];
     a += f * cell_conduction(g, kc, T, c) * dv;
     b += f * div * dv;
     vg += f * dv;

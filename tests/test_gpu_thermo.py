@@ -91,6 +91,26 @@ def test_p0_rate_and_source_with_walls_in_y(pp, dims):
     assert _rel(host(S), orc.divergence_source(g, w.phi, kc, T, p0, gamma, 0.3 * rp)) < TOL
 
 
+@pytest.mark.parametrize("dims,ybeta", [((24, 16, 18), 1.5), ((20, 21, 12), 2.0)])
+def test_p0_rate_and_source_on_a_stretched_y(pp, dims, ybeta):
+    """A duct with tanh-clustered y faces: the conduction takes the row
+    widths and centre distances, the volume sums the row widths (the
+    oracle's D, G and cell volumes on the same faces)."""
+    nx, ny, nz = dims
+    w = wl.channel_bubble_case(nx, ny, nz, seed=1206, rho_ratio=1000.0, stretched=True, ybeta=ybeta)
+    g = orc.Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.zf, ywalls=True, yf=w.yf)
+    T, kc = _fields(w, 1107)
+    plan = pp.Plan(w.nx, w.ny, w.nz, w.lx, w.ly, float(w.zf[-1] - w.zf[0]), zfaces=w.zf, ywalls=True,
+                   yfaces=w.yf)
+    gamma, p0 = 1.4, 1.1
+    rp = pp.pressure_p0_rate(plan.handle, dev(w.phi), dev(kc), dev(T), dev(w.us), dev(w.vs), dev(w.ws), p0, gamma)
+    rp0 = orc.p0_rate(g, w.phi, kc, T, w.us, w.vs, w.ws, p0, gamma)
+    assert abs(rp - rp0) <= TOL * max(abs(rp0), 1e-300) * 10
+    S = torch.empty(w.shape, dtype=torch.float64, device="cuda")
+    pp.pressure_divergence_source(plan.handle, dev(w.phi), dev(kc), dev(T), p0, gamma, 0.2 * rp, S)
+    assert _rel(host(S), orc.divergence_source(g, w.phi, kc, T, p0, gamma, 0.2 * rp)) < TOL
+
+
 def test_source_feeds_the_projection(pp):
     """S from Eq. 34 is the divergence the projection then imposes:
     D u^{n+1} = S_c to 1e-12 (oracle divergence)."""

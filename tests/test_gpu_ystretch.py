@@ -255,15 +255,13 @@ def test_adjoint_converged_vs_literal_transpose(pp):
 
 
 def test_uniform_y_only_calls_refuse_a_stretched_y(pp):
-    """The thermodynamic source and the predictor are built for a uniform y:
-    they return PP_ERR_UNSUPPORTED before touching a field."""
+    """The predictor is built for a uniform y: it returns PP_ERR_UNSUPPORTED
+    before touching a field."""
     g = _sgrid(16, 12, 8, 1.5)
     plan = _plan(pp, g)
     c = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
     fw = torch.zeros((g.nz + 1, g.ny, g.nx), dtype=torch.float64, device="cuda")
+    ustar = (c.clone(), c.clone(), fw.clone())
     with pytest.raises(pp.PressureError) as e:
-        pp.pressure_divergence_source(plan.handle, c, c, c, 1.0, 1.4, 0.0, c.clone())
-    assert e.value.code == pp.PP_ERR_UNSUPPORTED
-    with pytest.raises(pp.PressureError) as e:
-        pp.pressure_p0_rate(plan.handle, c, c, c, c, c, fw, 1.0, 1.4)
+        pp.pressure_predictor(plan.handle, c, c, fw, c + 1.0, c + 1e-3, (0.0, 0.0, -9.81), 1e-3, ustar)
     assert e.value.code == pp.PP_ERR_UNSUPPORTED
