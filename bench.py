@@ -202,9 +202,10 @@ def algorithmic(kernel, w, precision):
 # is for the PP_MIXED_Z64 kernel
 # (profiles/pass_kernels_mixed_z64_bubbles512x512x128.md).
 # None: not captured for the kernel as it stands.
-RESID_DRAM_B_PER_CELL = {"update": 18.85, "exact": 64.22}
+RESID_DRAM_B_PER_CELL = None  # to be captured for the paired-row update
 DRAM_B_PER_CELL = {
-    "resid_fftx": 0.975 * RESID_DRAM_B_PER_CELL["update"] + 0.025 * RESID_DRAM_B_PER_CELL["exact"],
+    "resid_fftx": None if RESID_DRAM_B_PER_CELL is None else
+    0.975 * RESID_DRAM_B_PER_CELL["update"] + 0.025 * RESID_DRAM_B_PER_CELL["exact"],
     "tridiag_z": 17.23,
 }
 
