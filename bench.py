@@ -197,11 +197,11 @@ def algorithmic(kernel, w, precision):
 # at 512^3, so the bytes scale with the cells processed (the captures and
 # their commands are summarised under profiles/).  The residual kernel's
 # figure is weighted over the 40-pass exact/update cycle: 18.75 B on an
-# update pass, 64.25 B on an exact pass (both from one capture of the kernel
+# update pass, 64.15 B on an exact pass (both from one capture of the kernel
 # as it stands, the paired-row update: profiles/launches_bubbles512_mixed_z64.md).
 # The z solve's is for the PP_MIXED_Z64 kernel
 # (profiles/pass_kernels_mixed_z64_bubbles512x512x128.md).
-RESID_DRAM_B_PER_CELL = {"update": 18.75, "exact": 64.25}
+RESID_DRAM_B_PER_CELL = {"update": 18.75, "exact": 64.15}
 DRAM_B_PER_CELL = {
     "resid_fftx": 0.975 * RESID_DRAM_B_PER_CELL["update"] + 0.025 * RESID_DRAM_B_PER_CELL["exact"],
     "tridiag_z": 17.23,

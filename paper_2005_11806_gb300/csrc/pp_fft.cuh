@@ -349,4 +349,31 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return r;  // valid in thread 0
 }
 
+// Two block sums at once, each added in the same order as block_sum (the
+// same results), through one pair of barriers.  sh: at least 64 entries.
+template <typename T>
+__device__ __forceinline__ void block_sum2(T& a, T& b, T* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    sh[w] = a;
+    sh[32 + w] = b;
+  }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  a = (threadIdx.x < nw) ? sh[threadIdx.x] : (T)0;
+  b = (threadIdx.x < nw) ? sh[32 + threadIdx.x] : (T)0;
+  if (w == 0) {
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+  }
+  // valid in thread 0
+}
+
 }  // namespace pp

@@ -53,13 +53,16 @@ __device__ __forceinline__ void r512_twiddle8(float2* v, const float2* __restric
 // The transform of the thread's line (see above); every thread of the block
 // calls it.  v holds x[64 a + j] on entry and is free once its values are in
 // s1: `after_s1` runs right then (e.g. to load the next line into v) and
-// before the first barrier.  The result X[j + 64 h] is left in u.  The call
-// holds two barriers; s1 is last read before the second, s2 last read after
-// it, so a following call (whose first barrier comes after its s1 writes and
-// before its s2 writes) needs no barrier in between.
-template <int DIR, int TX, class F>
+// before the first barrier; `after_b1` runs right after the first barrier
+// (every thread of the block has then finished what it did before the call).
+// The result X[j + 64 h] is left in u.  The call holds two barriers; s1 is
+// last read before the second, s2 last read after it, so a following call
+// (whose first barrier comes after its s1 writes and before its s2 writes)
+// needs no barrier in between.
+template <int DIR, int TX, class F, class G>
 __device__ __forceinline__ void r512_transform(float2 (&v)[8], float2 (&u)[8], float2* s1, float2* s2,
-                                               const float2* __restrict__ tw, int x, int j, F&& after_s1) {
+                                               const float2* __restrict__ tw, int x, int j, F&& after_s1,
+                                               G&& after_b1) {
   using L = R512<TX>;
   Dft<float, DIR, 8>::run(v);
   r512_twiddle8<DIR>(v, tw, 64, j);
@@ -67,6 +70,7 @@ __device__ __forceinline__ void r512_transform(float2 (&v)[8], float2 (&u)[8], f
   for (int c = 0; c < 8; ++c) s1[(c * 64 + j) * TX + x] = v[c];
   after_s1();
   __syncthreads();
+  after_b1();
   {
     const int c = j >> 3, f = j & 7;
 #pragma unroll
@@ -83,6 +87,12 @@ __device__ __forceinline__ void r512_transform(float2 (&v)[8], float2 (&u)[8], f
     for (int f = 0; f < 8; ++f) u[f] = s2[c * L::CS2 + (gg * 8 + f) * TX + x];
     Dft<float, DIR, 8>::run(u);
   }
+}
+
+template <int DIR, int TX, class F>
+__device__ __forceinline__ void r512_transform(float2 (&v)[8], float2 (&u)[8], float2* s1, float2* s2,
+                                               const float2* __restrict__ tw, int x, int j, F&& after_s1) {
+  r512_transform<DIR, TX>(v, u, s1, s2, tw, x, j, after_s1, []() {});
 }
 
 }  // namespace pp

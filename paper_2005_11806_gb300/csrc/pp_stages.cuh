@@ -503,7 +503,7 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
                                                  bool need_exact, float* __restrict__ E,
                                                  const float* __restrict__ delta,
                                                  unsigned char* smem_raw) {
-  __shared__ double shred[32];
+  __shared__ double shred[64];
   const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
   const int nseq = rpb >> 1;
   C2<T>* bufA = reinterpret_cast<C2<T>*>(smem_raw);
@@ -523,11 +523,10 @@ __device__ __forceinline__ void stage_resid_fftx(const Geo& g, const Faces& fc, 
   if (mode != 0) {
     // block partial sums of e^2 and |e|: in the arithmetic's own precision
     // (FP32 shuffles on mixed plans: the FP64 pipe is the scarce one)
-    const T a2 = block_sum<T>(s2, reinterpret_cast<T*>(shred));
-    const T a1 = block_sum<T>(s1, reinterpret_cast<T*>(shred));
+    block_sum2<T>(s2, s1, reinterpret_cast<T*>(shred));
     if (threadIdx.x == 0) {
-      red[2 * (size_t)blk] = (double)a2;
-      red[2 * (size_t)blk + 1] = (double)a1;
+      red[2 * (size_t)blk] = (double)s2;
+      red[2 * (size_t)blk + 1] = (double)s1;
     }
   }
   __syncthreads();
