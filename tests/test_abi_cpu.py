@@ -54,7 +54,11 @@ def _lib_or_build():
 @pytest.mark.parametrize("dims,lens,prec,bc,code", [
     ((0, 8, 8), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),      # empty grid
     ((8, 8, 0), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),
+    ((8, 0, 8), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),
+    ((-2, 8, 8), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),     # negative size
     ((8, 8, 8), (1, -1, 1), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),     # negative length
+    ((8, 8, 8), (0, 1, 1), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),      # zero length
+    ((8, 8, 8), (1, 1, 0), "fp64", (0, 0, 1), "PP_ERR_INVALID_ARG"),
     ((7, 8, 8), (1, 1, 1), "fp64", (0, 0, 1), "PP_ERR_UNSUPPORTED"),      # odd nx (two real rows per complex FFT)
     ((8, 7, 8), (1, 1, 1), "fp64", (0, 1, 1), "PP_ERR_UNSUPPORTED"),      # odd ny with walls in y
     ((8, 8, 8), (1, 1, 1), "fp64", (1, 0, 1), "PP_ERR_UNSUPPORTED"),      # walls in x
