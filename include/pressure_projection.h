@@ -107,7 +107,10 @@ typedef struct {
     int nx, ny, nz;        /* cells; nx, ny have prime factors in {2,3,5}; nx even;
                               ny even with walls in y */
     double lx, ly, lz;     /* domain lengths */
-    const double* zfaces;  /* host, nz+1 increasing face coordinates, or NULL (uniform) */
+    const double* zfaces;  /* host, nz+1 finite, strictly increasing face coordinates, or
+                              NULL (uniform); read during the call only.  Any other
+                              values: PP_ERR_INVALID_ARG from every entry point that takes
+                              a grid, before any CUDA call */
     int bc[3];             /* {PP_BC_PERIODIC, PP_BC_PERIODIC, PP_BC_WALL}, or walls in y:
                               {PP_BC_PERIODIC, PP_BC_WALL, PP_BC_WALL}.  With walls in y the
                               y transform is the cosine eigenbasis of the Neumann second
@@ -130,8 +133,8 @@ typedef struct {
                               I, II, III), pressure_solve_adjoint, pressure_mixture_density
                               and the thermodynamic source (pressure_p0_rate,
                               pressure_divergence_source) take it; the predictor returns
-                              PP_ERR_UNSUPPORTED; PP_ERR_INVALID_ARG for faces that do not
-                              increase or do not span ly (1e-12 relative). */
+                              PP_ERR_UNSUPPORTED; PP_ERR_INVALID_ARG for faces that are not
+                              finite, do not increase or do not span ly (1e-12 relative). */
 } pp_grid;
 
 typedef struct {

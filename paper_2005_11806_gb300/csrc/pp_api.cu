@@ -520,11 +520,11 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   if (ystretch && (!ywall || G.ny < 2 || G.ny > 1024)) return PP_ERR_UNSUPPORTED;  // dense y step
   // uniform walls: cosine transform by an FFT of even length
   if (ywall && !ystretch && (G.ny < 2 || (G.ny & 1) != 0)) return PP_ERR_UNSUPPORTED;
-  if (ystretch) {  // increasing faces spanning ly
-    for (int j = 0; j < G.ny; ++j)
-      if (!(G.yfaces[j + 1] > G.yfaces[j])) return PP_ERR_INVALID_ARG;
+  if (ystretch) {  // finite, increasing faces spanning ly
+    if (!faces_ok(G.yfaces, G.ny)) return PP_ERR_INVALID_ARG;
     if (!(std::fabs((G.yfaces[G.ny] - G.yfaces[0]) - G.ly) <= 1e-12 * G.ly)) return PP_ERR_INVALID_ARG;
   }
+  if (G.zfaces && !faces_ok(G.zfaces, G.nz)) return PP_ERR_INVALID_ARG;
   if (G.nx > 2048 || G.ny > 2048) return PP_ERR_UNSUPPORTED;  // one line per block in the FFTs
   if ((long)G.nx * G.ny * (G.nz + 1) > (1L << 31)) return PP_ERR_UNSUPPORTED;
   pp_plan_s* P = new (std::nothrow) pp_plan_s();
@@ -541,10 +541,8 @@ pp_status pressure_plan_create(const pp_grid* grid, pp_precision prec, void* str
   // z metrics (Sec. 3 grid; stretched faces allowed)
   const int nz = G.nz;
   std::vector<double> zf(nz + 1);
-  if (G.zfaces) {
+  if (G.zfaces) {  // checked above
     for (int k = 0; k <= nz; ++k) zf[k] = G.zfaces[k];
-    for (int k = 0; k < nz; ++k)
-      if (!(zf[k + 1] > zf[k])) { delete P; return PP_ERR_INVALID_ARG; }
   } else {
     for (int k = 0; k <= nz; ++k) zf[k] = G.lz * (double)k / (double)nz;
   }

@@ -463,8 +463,10 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     // walls in y: the cosine transform runs as one complex FFT of even length
     if (G.bc[1] == PP_BC_WALL && (G.ny < 2 || (G.ny & 1) != 0)) return PP_ERR_UNSUPPORTED;
     if ((G.nx & 1) != 0 || G.nx > 2048 || G.ny > 2048) return PP_ERR_UNSUPPORTED;
+    if ((long long)G.nx * G.ny * (G.nz + 1) > (1LL << 31)) return PP_ERR_UNSUPPORTED;  // 32-bit cell offsets
     FftDesc t;
     if (!factor(G.nx, &t) || !factor(G.ny, &t)) return PP_ERR_UNSUPPORTED;
+    if (G.zfaces && !faces_ok(G.zfaces, G.nz)) return PP_ERR_INVALID_ARG;
   }
   pp_batch_s* B = new (std::nothrow) pp_batch_s();
   if (!B) return PP_ERR_OOM;
@@ -532,9 +534,7 @@ pp_status pressure_batch_create(const pp_grid* grids, int ngrids, pp_precision p
     GridDev& d = B->h_dev[i];
     const int nx = G.nx, ny = G.ny, nz = G.nz, nxh = nx / 2 + 1;
     std::vector<double> zf(nz + 1);
-    for (int k = 0; k <= nz; ++k) zf[k] = G.zfaces ? G.zfaces[k] : G.lz * (double)k / (double)nz;
-    for (int k = 0; k < nz; ++k)
-      if (!(zf[k + 1] > zf[k])) { free_batch(B); return PP_ERR_INVALID_ARG; }
+    for (int k = 0; k <= nz; ++k) zf[k] = G.zfaces ? G.zfaces[k] : G.lz * (double)k / (double)nz;  // checked above
     std::vector<double> dzf(nz), idzf(nz), zcen(nz), idzc(nz + 1, 0.0), za(nz, 0.0), zc(nz, 0.0);
     std::vector<float> idzff(nz), zcf(nz);
     for (int k = 0; k < nz; ++k) {

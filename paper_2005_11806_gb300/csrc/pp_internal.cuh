@@ -110,6 +110,16 @@ __device__ __forceinline__ double widen_f32(float f) {
 // density, as the FP64 coefficients): 2 / (a + b), fast FP32 division.
 __device__ __forceinline__ float face_beta_f(float a, float b) { return __fdividef(2.f, a + b); }
 
+// Host: whether the n + 1 face coordinates f[0..n] are finite and strictly
+// increasing (the grid descriptor's zfaces / yfaces).
+inline bool faces_ok(const double* f, int n) {
+  for (int k = 0; k <= n; ++k)
+    if (!std::isfinite(f[k])) return false;
+  for (int k = 0; k < n; ++k)
+    if (!(f[k + 1] > f[k])) return false;
+  return true;
+}
+
 // Host: the [3][nz + 1] FP32 layer factors of Geo::cw_f.
 inline std::vector<float> layer_factors_f32(int nz, const std::vector<double>& dzf,
                                             const std::vector<double>& inv_dzc, double inv_dx2, double inv_dy2) {

@@ -171,6 +171,7 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   if ((long long)G.nx * G.ny * (G.nz + 1) > (1LL << 31)) return PP_ERR_UNSUPPORTED;
   FftDesc fx, fy;
   if (!factor(G.nx, &fx) || !factor(G.ny, &fy)) return PP_ERR_UNSUPPORTED;
+  if (G.zfaces && !faces_ok(G.zfaces, G.nz)) return PP_ERR_INVALID_ARG;
   if (!is_device(f) || !is_device(p)) return PP_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream_ptr;
   const int nx = G.nx, ny = G.ny, nz = G.nz, nxh = nx / 2 + 1;
@@ -199,14 +200,10 @@ extern "C" pp_status pressure_solve_noalloc(const pp_grid* grid, const double* f
   if (scratch_address(&base) != cudaSuccess) return PP_ERR_CUDA;
   unsigned char* S = (unsigned char*)base;
 
-  // Face coordinates: checked here, sent by value (no host buffer is read
-  // after the call returns); every table is then computed on the device.
+  // Face coordinates (checked above) are sent by value (no host buffer is
+  // read after the call returns); every table is then computed on the device.
   const double z0 = G.zfaces ? G.zfaces[0] : 0.0;
   const double zn = G.zfaces ? G.zfaces[nz] : G.lz;
-  if (G.zfaces) {
-    for (int k = 0; k < nz; ++k)
-      if (!(G.zfaces[k + 1] > G.zfaces[k])) return PP_ERR_INVALID_ARG;
-  }
   const double dx = G.lx / nx, dy = G.ly / ny;
   double* dzfaces = (double*)(S + o_zf);
   if (G.zfaces) {

@@ -166,3 +166,41 @@ def test_batch_rejects_bad_descriptors_before_any_cuda_call(dims, bc, yfaces, co
     got = pressure.lib().pressure_batch_create(arr, 1, pressure.PRECISIONS["mixed"], None, ctypes.byref(out))
     assert got == getattr(pressure, code)
     assert out.value is None
+
+
+@pytest.mark.parametrize("faces", ["flat", "reversed", "nan", "inf"])
+@pytest.mark.parametrize("entry", ["plan", "batch", "noalloc"])
+def test_bad_z_faces_rejected_before_any_cuda_call(entry, faces):
+    """z faces that are not finite and strictly increasing (the Sec. 3 grid
+    needs positive cell widths dzf) are refused by every entry point that
+    takes a grid, before it touches the device."""
+    import ctypes
+    pressure = _lib_or_build()
+    zf = np.linspace(0.0, 1.0, 9)
+    if faces == "flat":
+        zf[3] = zf[2]
+    elif faces == "reversed":
+        zf = zf[::-1].copy()
+    elif faces == "nan":
+        zf[4] = np.nan
+    else:
+        zf[0] = -np.inf
+    keep = np.ascontiguousarray(zf)
+    g = pressure.pp_grid()
+    g.nx, g.ny, g.nz = 8, 8, 8
+    g.lx, g.ly, g.lz = 1.0, 1.0, 1.0
+    g.bc[0], g.bc[1], g.bc[2] = 0, 0, 1
+    g.zfaces = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out = ctypes.c_void_p()
+    L = pressure.lib()
+    if entry == "plan":
+        got = L.pressure_plan_create(ctypes.byref(g), pressure.PRECISIONS["fp64"], None, ctypes.byref(out))
+    elif entry == "batch":
+        arr = (pressure.pp_grid * 1)(g)
+        got = L.pressure_batch_create(arr, 1, pressure.PRECISIONS["mixed"], None, ctypes.byref(out))
+    else:
+        buf = (ctypes.c_double * 8)()
+        got = L.pressure_solve_noalloc(ctypes.byref(g), ctypes.cast(buf, ctypes.c_void_p),
+                                       ctypes.cast(buf, ctypes.c_void_p), None)
+    assert got == pressure.PP_ERR_INVALID_ARG
+    assert out.value is None
